@@ -1,0 +1,222 @@
+/*
+ * gavis.h -- C ABI of the GB300 (sm_103a) GAVIS hot path.
+ *
+ * GAVIS (arxiv 2605.30342) scores candidate camera views of a 3D Gaussian
+ * Splatting scene by the entropy of an uncertainty-aware rendering in which
+ * every Gaussian carries an anisotropic visibility field, stored as spherical
+ * harmonic (SH) coefficients gamma.  This library implements the two
+ * data-parallel halves of that method:
+ *
+ *   gavis_vf_build     visibility-field construction (Alg. "Anisotropic
+ *                      Visibility Field Construction", eq:vis_gamma), using
+ *                      Alg. "Single-view Particle Visibility" per training view;
+ *   gavis_score_views  visibility-field query (Alg. "Query Anisotropic
+ *                      Visibility Field", eq:vis_bound) fused into an
+ *                      uncertainty-aware tile rasterizer (Alg. "3DGS Uncertainty
+ *                      Quantification with Visibility Field", eq:alpha_comp,
+ *                      eq:huber), the per-view score (eq:id without the
+ *                      correlation correction) and the next-best-view argmax
+ *                      (eq:i_gain).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Pointers.  Arguments documented as "device" are CUDA device pointers on the
+ *   context's device; "host" are ordinary host pointers.  The caller owns every
+ *   buffer it passes in; the library never frees or retains them after the
+ *   call returns.  The context owns a grow-only device workspace bounded by the
+ *   budget given at creation.
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Work is enqueued asynchronously on it; outputs are valid once the
+ *   stream has reached the end of the call's work.  A call may synchronise the
+ *   stream internally (to size the sort buffers); this is documented per call.
+ * Threads.  A context is used by one host thread at a time.
+ * Errors.  Every function returns GAVIS_OK (0) or a negative status; the text
+ *   of the last error is kept in the context (gavis_last_error).  Nothing
+ *   aborts the process.  On error no output is guaranteed to be written.
+ * Layout.  Gaussians are structure-of-arrays, index g in [0, n):
+ *   means[3n] (x,y,z), scales[3n] (activated, > 0), rots[4n] (quaternion
+ *   w,x,y,z; normalised inside), opac[n] (in [0,1]), sh[n][(Lc+1)^2][3]
+ *   colour coefficients (coefficient-major, then channel), vf coeffs
+ *   [n][(L+1)^2].  SH index j = l*l + l + m, real basis as defined in the
+ *   paper's derivation of the vMF coefficients.
+ * Cameras.  Pinhole, world->camera rotation R (row-major) and translation t,
+ *   camera looks along +z with x right and y down; the centre of pixel (i,j)
+ *   is at (i + 0.5, j + 0.5).  Every camera in one call has the same W x H.
+ */
+#ifndef GAVIS_H
+#define GAVIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define GAVIS_OK            0
+#define GAVIS_ERR_ARG      -1   /* invalid argument (null pointer, bad size, mismatched W x H ...) */
+#define GAVIS_ERR_CUDA     -2   /* a CUDA runtime call or kernel launch failed */
+#define GAVIS_ERR_OOM      -3   /* device allocation failed */
+#define GAVIS_ERR_BUDGET   -4   /* the workspace needed exceeds the context budget */
+#define GAVIS_ERR_TIMEOUT  -5   /* a bounded device wait gave up */
+
+typedef enum { GAVIS_F32 = 0, GAVIS_F16 = 1, GAVIS_BF16 = 2 } gavis_dtype;
+
+/* 96 bytes; tan_half_fov* = W/(2 fx), H/(2 fy) computed once on the host. */
+typedef struct {
+    int32_t W, H;
+    float fx, fy, cx, cy;
+    float tan_half_fovx, tan_half_fovy;
+    float R[9];
+    float t[3];
+    float campos[3];
+    float znear;                 /* Gaussians with camera depth <= znear are culled (0.2) */
+} gavis_camera;
+
+typedef struct {
+    int64_t n;                   /* number of Gaussians, 0 <= n < 2^31 */
+    const float *means;          /* device [3n] */
+    const float *scales;         /* device [3n] */
+    const float *rots;           /* device [4n] */
+    const float *opac;           /* device [n] */
+    const void *sh;              /* device [n][(sh_degree+1)^2][3], dtype sh_dtype; may be NULL for VF build */
+    int32_t sh_degree;           /* 0..3 */
+    int32_t sh_dtype;            /* gavis_dtype */
+} gavis_gaussians;
+
+typedef struct {
+    int64_t n;                   /* must equal the Gaussians' n */
+    void *coeffs;                /* device [n][(degree+1)^2] of dtype (gamma of eq:vis_gamma) */
+    int32_t degree;              /* L, 0..3 */
+    int32_t dtype;               /* gavis_dtype of coeffs */
+    int32_t n_train_views;       /* |P| of eq:vis_bound; 0 means "never seen": V = 0 everywhere */
+    float kappa;                 /* concentration used to build it */
+} gavis_vf;
+
+typedef struct {
+    float kappa;                 /* vMF concentration, paper default 1 */
+    int32_t vf_degree;           /* SH degree L of the field, paper default 2 */
+    float eps_T;                 /* transmittance cutoff, paper default 1e-4 */
+    float q_cut;                 /* footprint: a Gaussian covers a pixel iff d^T Sigma^-1 d <= q_cut (9) */
+    float beta;                  /* opacity reliability, paper default 0.5 */
+    float o0;                    /* prior opacity, paper default 0.15 */
+    float sigma_c2;              /* constant colour variance, Q_c = sigma_c2 I_3 (0.01) */
+    float logdet_Q0;             /* log |Q_0| of the prior colour covariance, Q_0 = I_3 -> 0 */
+    int32_t tile;                /* tile edge in pixels: 8, 16 or 32 (16) */
+    int32_t views_per_batch;     /* views per kernel chain: 0 = as many as the budget allows, 1 = plain */
+} gavis_params;
+
+typedef struct gavis_ctx gavis_ctx;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * workspace; 0 means 60% of the device memory free at creation.  *out is set
+ * to NULL on failure.  Returns GAVIS_ERR_CUDA if the device cannot be used. */
+int gavis_ctx_create(gavis_ctx **out, int device, size_t hbm_budget_bytes);
+
+/* Free the context and its workspace (synchronises the device first). */
+void gavis_ctx_destroy(gavis_ctx *ctx);
+
+/* Text of the last error on this context ("" if none); valid until the next call. */
+const char *gavis_last_error(const gavis_ctx *ctx);
+
+/* Fill *p with the paper's defaults (Alg. UQ inputs and the construction
+ * hyperparameters): kappa 1, L 2, eps_T 1e-4, q_cut 9, beta 0.5, o0 0.15,
+ * sigma_c2 0.01, logdet_Q0 0, tile 16, views_per_batch 0. */
+int gavis_params_default(gavis_params *p);
+
+/* a_l = 4 pi e^{-kappa} i_l(kappa), l = 0..L (the per-degree factor of
+ * eq:vis_gamma; i_l the modified spherical Bessel function of the first kind).
+ * a: host [L+1].  L in 0..3, kappa >= 0. */
+int gavis_vmf_coeffs(int L, double kappa, double *a);
+
+/* Visibility-field construction (Alg. "Anisotropic Visibility Field
+ * Construction").  For every training view p: the per-Gaussian visibility
+ * v_p[g] = (sum of transmittance over the pixels that reach g) / (their count),
+ * 0 if no pixel reaches g (Alg. "Single-view Particle Visibility"); then
+ * gamma_lm[g] += v_p[g] a_l Y_lm(normalize(x_g - x_p)).
+ *   train: host [n_train] cameras (same W x H); n_train >= 0.
+ *   out: caller-filled n, coeffs (device, n x (L+1)^2 of out->dtype), degree,
+ *        dtype; the call sets n_train_views = n_train and kappa = p->kappa.
+ *   accumulate: 0 overwrites coeffs; 1 adds the new views' contributions to
+ *        the coefficients already there and adds n_train to n_train_views
+ *        (eq:vis_gamma is a sum over views).
+ * Accumulates in float32, stores in out->dtype.  Synchronises `stream` once per
+ * batch of views (to size the sort). */
+int gavis_vf_build(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_camera *train, int n_train,
+                   const gavis_params *p, gavis_vf *out, int accumulate, void *stream);
+
+/* Candidate-view scoring.  For every candidate view c: V[g] by the AM-GM bound
+ * of eq:vis_bound from gamma (|P| = vf->n_train_views), colour from the SH
+ * coefficients, then per pixel front-to-back compositing of the plain colour
+ * (eq:orig_vr) and of the uncertainty (Alg. UQ: eq:alpha_comp weights, the
+ * Huber entropy bound eq:huber with Q_c = sigma_c2 I_3 and the prior Q_0).
+ *   cand: host [n_cand] cameras, same W x H.
+ *   rgb:  device [n_cand][3][H][W] float32 (planar) or NULL.
+ *   unc:  device [n_cand][H][W] float32 per-pixel entropy bound, or NULL.
+ *   score: device [n_cand] float32, mean over pixels of unc (eq:id, f_corr = 0).
+ *   best_dev: device int32 argmax of score (lowest index on ties) or NULL.
+ *   best_host: host int32 or NULL; if given the call synchronises `stream`.
+ * Synchronises `stream` once per batch of views (to size the sort). */
+int gavis_score_views(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf,
+                      const gavis_camera *cand, int n_cand, const gavis_params *p,
+                      float *rgb, float *unc, float *score, int32_t *best_dev, int32_t *best_host,
+                      void *stream);
+
+/* Visibility-field query alone (Alg. "Query Anisotropic Visibility Field").
+ * V: device [n_cams][n] float32.  Culling is not applied: every Gaussian gets
+ * a value. */
+int gavis_vf_query(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf,
+                   const gavis_camera *cams, int n_cams, const gavis_params *p, float *V, void *stream);
+
+/* Tile bins of views, for verification.  Keys are
+ * ((view * TW*TH + tile) << 32) | float_bits(camera depth), values Gaussian
+ * indices, sorted by key with ties in ascending index.  keys/vals: device
+ * [cap]; *M_out (host) receives the number of keys (only min(M, cap) are
+ * written); ranges: device [n_cams*TW*TH][2] uint32 [start, end) or NULL.
+ * Synchronises `stream`. */
+int gavis_debug_bins(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_camera *cams, int n_cams,
+                     const gavis_params *p, uint64_t *keys, uint32_t *vals, int64_t cap,
+                     int64_t *M_out, uint32_t *ranges, void *stream);
+
+/* Per-view particle visibility sums (Alg. "Single-view Particle
+ * Visibility"), for verification.  sumT: device [n_cams][n] float32 (sum of
+ * transmittance over the pixels that reach g); cnt: device [n_cams][n] uint32
+ * (number of those pixels). */
+int gavis_debug_visibility(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_camera *cams,
+                           int n_cams, const gavis_params *p, float *sumT, uint32_t *cnt, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Instrumentation (no counterpart in the paper): per-stage device time from  */
+/* CUDA events recorded on the call's stream, kernel launch counts, and the   */
+/* number of (pixel, Gaussian) pairs composited.                             */
+/* ---------------------------------------------------------------------- */
+enum {
+    GAVIS_STAGE_PROJECT = 0,      /* projection, culling, colour, VF query */
+    GAVIS_STAGE_SCAN = 1,         /* exclusive scan of tile counts */
+    GAVIS_STAGE_EMIT = 2,         /* key emission */
+    GAVIS_STAGE_SORT = 3,         /* radix sort */
+    GAVIS_STAGE_RANGES = 4,       /* tile ranges */
+    GAVIS_STAGE_COMPOSITE_UA = 5, /* uncertainty + colour compositing */
+    GAVIS_STAGE_COMPOSITE_VIS = 6,/* particle-visibility compositing */
+    GAVIS_STAGE_REDUCE = 7,       /* per-view score and argmax */
+    GAVIS_STAGE_VF_ACCUM = 8,     /* SH accumulation of the field */
+    GAVIS_STAGE_COUNT = 9
+};
+
+/* on != 0 starts recording stage events on later calls; every call resets
+ * the accumulators.  Recording adds two events per stage and batch. */
+int gavis_prof_enable(gavis_ctx *ctx, int on);
+
+/* Synchronises the device, then returns per stage the summed device time
+ * (ms[GAVIS_STAGE_COUNT], host) and kernel launches (launches[...], host) since
+ * gavis_prof_enable, the total number of kernels this library launched in the
+ * process (*total_launches, host) and the pairs composited
+ * (pairs[0] uncertainty pass, pairs[1] visibility pass, host).  Any output
+ * pointer may be NULL. */
+int gavis_prof_read(gavis_ctx *ctx, double *ms, int64_t *launches, int64_t *total_launches, uint64_t *pairs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GAVIS_H */

@@ -1,0 +1,328 @@
+"""GB300-native GAVIS hot path: Python binding of the C ABI (include/gavis.h).
+
+This module only marshals arguments: torch tensors become device pointers,
+camera objects become `gavis_camera` records, and every step of the method
+runs in the CUDA library `libgavis.so`.  There is no CPU fallback: if the
+library is missing or no GPU is present, calls raise.
+
+    import paper_2605_30342_gb300 as gv
+    ctx = gv.Context()
+    gs = gv.Gaussians(means, scales, rots, opac, sh, sh_degree)      # cuda tensors
+    vf = ctx.vf_build(gs, train_cams, degree=2)                      # eq:vis_gamma
+    out = ctx.score_views(gs, vf, cand_cams)                         # Alg. UQ + argmax
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+__all__ = ["Context", "Gaussians", "VisibilityField", "Params", "GavisError", "load", "library_path",
+           "F32", "F16", "BF16"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libgavis.so")
+_lock = threading.Lock()
+_lib = None
+
+F32, F16, BF16 = 0, 1, 2
+_TORCH_DTYPE = {F32: torch.float32, F16: torch.float16, BF16: torch.bfloat16}
+_DTYPE_CODE = {torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}
+
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_BUDGET, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+
+
+class GavisError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gavis error {code}: {msg}")
+        self.code = code
+
+
+class gavis_camera(C.Structure):
+    _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float),
+                ("cy", C.c_float), ("tan_half_fovx", C.c_float), ("tan_half_fovy", C.c_float),
+                ("R", C.c_float * 9), ("t", C.c_float * 3), ("campos", C.c_float * 3), ("znear", C.c_float)]
+
+
+class gavis_gaussians(C.Structure):
+    _fields_ = [("n", C.c_int64), ("means", C.c_void_p), ("scales", C.c_void_p), ("rots", C.c_void_p),
+                ("opac", C.c_void_p), ("sh", C.c_void_p), ("sh_degree", C.c_int32), ("sh_dtype", C.c_int32)]
+
+
+class gavis_vf(C.Structure):
+    _fields_ = [("n", C.c_int64), ("coeffs", C.c_void_p), ("degree", C.c_int32), ("dtype", C.c_int32),
+                ("n_train_views", C.c_int32), ("kappa", C.c_float)]
+
+
+class gavis_params(C.Structure):
+    _fields_ = [("kappa", C.c_float), ("vf_degree", C.c_int32), ("eps_T", C.c_float), ("q_cut", C.c_float),
+                ("beta", C.c_float), ("o0", C.c_float), ("sigma_c2", C.c_float), ("logdet_Q0", C.c_float),
+                ("tile", C.c_int32), ("views_per_batch", C.c_int32)]
+
+
+EXPORTS = ["gavis_ctx_create", "gavis_ctx_destroy", "gavis_last_error", "gavis_params_default",
+           "gavis_vmf_coeffs", "gavis_vf_build", "gavis_score_views", "gavis_vf_query", "gavis_debug_bins",
+           "gavis_debug_visibility", "gavis_prof_enable", "gavis_prof_read"]
+
+STAGES = ["project", "scan", "emit", "sort", "ranges", "composite_ua", "composite_vis", "reduce", "vf_accum"]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load(path: str | None = None):
+    """Load libgavis.so (built by `__graft_entry__.build()` or
+    `python -m paper_2605_30342_gb300.build`).  Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or _LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libgavis.so not built ({p}); run __graft_entry__.build()")
+        lib = C.CDLL(p)
+        vp, i32, i64 = C.c_void_p, C.c_int, C.c_int64
+        lib.gavis_ctx_create.argtypes = [C.POINTER(vp), i32, C.c_size_t]
+        lib.gavis_ctx_destroy.argtypes = [vp]
+        lib.gavis_ctx_destroy.restype = None
+        lib.gavis_last_error.argtypes = [vp]
+        lib.gavis_last_error.restype = C.c_char_p
+        lib.gavis_params_default.argtypes = [C.POINTER(gavis_params)]
+        lib.gavis_vmf_coeffs.argtypes = [i32, C.c_double, C.POINTER(C.c_double)]
+        lib.gavis_vf_build.argtypes = [vp, C.POINTER(gavis_gaussians), C.POINTER(gavis_camera), i32,
+                                       C.POINTER(gavis_params), C.POINTER(gavis_vf), i32, vp]
+        lib.gavis_score_views.argtypes = [vp, C.POINTER(gavis_gaussians), C.POINTER(gavis_vf),
+                                          C.POINTER(gavis_camera), i32, C.POINTER(gavis_params), vp, vp, vp, vp,
+                                          C.POINTER(C.c_int32), vp]
+        lib.gavis_vf_query.argtypes = [vp, C.POINTER(gavis_gaussians), C.POINTER(gavis_vf), C.POINTER(gavis_camera),
+                                       i32, C.POINTER(gavis_params), vp, vp]
+        lib.gavis_debug_bins.argtypes = [vp, C.POINTER(gavis_gaussians), C.POINTER(gavis_camera), i32,
+                                         C.POINTER(gavis_params), vp, vp, i64, C.POINTER(C.c_int64), vp, vp]
+        lib.gavis_debug_visibility.argtypes = [vp, C.POINTER(gavis_gaussians), C.POINTER(gavis_camera), i32,
+                                               C.POINTER(gavis_params), vp, vp, vp]
+        lib.gavis_prof_enable.argtypes = [vp, i32]
+        lib.gavis_prof_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                        C.POINTER(C.c_uint64)]
+        _lib = lib
+        return lib
+
+
+# ----------------------------------------------------------------------------
+# argument marshalling
+# ----------------------------------------------------------------------------
+
+def Params(**kw) -> gavis_params:
+    """Paper defaults (gavis_params_default) with keyword overrides."""
+    p = gavis_params()
+    load().gavis_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def camera_records(cams) -> C.Array:
+    """Any objects with W, H, fx, fy, cx, cy, tan_half_fovx, tan_half_fovy,
+    R (3x3), t (3), campos (3) and znear attributes."""
+    arr = (gavis_camera * max(len(cams), 1))()
+    for i, c in enumerate(cams):
+        r = arr[i]
+        r.W, r.H = int(c.W), int(c.H)
+        r.fx, r.fy, r.cx, r.cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+        r.tan_half_fovx, r.tan_half_fovy = float(c.tan_half_fovx), float(c.tan_half_fovy)
+        R = [float(x) for row in c.R for x in row]
+        for k in range(9):
+            r.R[k] = R[k]
+        for k in range(3):
+            r.t[k] = float(c.t[k])
+            r.campos[k] = float(c.campos[k])
+        r.znear = float(getattr(c, "znear", 0.2))
+    return arr
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev(t: torch.Tensor, name: str, dtype=None) -> int:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+class Gaussians:
+    """Structure-of-arrays Gaussian scene resident on the device."""
+
+    def __init__(self, means, scales, rots, opac, sh=None, sh_degree=None):
+        self.means, self.scales, self.rots, self.opac, self.sh = means, scales, rots, opac, sh
+        self.n = int(means.shape[0])
+        if sh is not None and sh_degree is None:
+            sh_degree = int(round(sh.shape[1] ** 0.5)) - 1
+        self.sh_degree = int(sh_degree or 0)
+        s = gavis_gaussians()
+        s.n = self.n
+        s.means = _dev(means, "means", torch.float32)
+        s.scales = _dev(scales, "scales", torch.float32)
+        s.rots = _dev(rots, "rots", torch.float32)
+        s.opac = _dev(opac, "opac", torch.float32)
+        s.sh = _dev(sh, "sh") if sh is not None else None
+        s.sh_degree = self.sh_degree
+        s.sh_dtype = _DTYPE_CODE[sh.dtype] if sh is not None else 0
+        self.struct = s
+
+    @classmethod
+    def from_numpy(cls, scene, device="cuda", sh_dtype=torch.float32):
+        t = lambda a, dt=torch.float32: torch.as_tensor(a).to(device=device, dtype=dt).contiguous()
+        return cls(t(scene.means), t(scene.scales), t(scene.rots), t(scene.opac),
+                   t(scene.sh, sh_dtype), scene.sh_degree)
+
+
+class VisibilityField:
+    """gamma [n, (L+1)^2] on the device plus |P| and kappa."""
+
+    def __init__(self, coeffs: torch.Tensor, degree: int, n_train_views: int, kappa: float):
+        self.coeffs, self.degree, self.n_train_views, self.kappa = coeffs, int(degree), int(n_train_views), float(kappa)
+
+    def struct(self) -> gavis_vf:
+        s = gavis_vf()
+        s.n = int(self.coeffs.shape[0])
+        s.coeffs = _dev(self.coeffs, "coeffs")
+        s.degree = self.degree
+        s.dtype = _DTYPE_CODE[self.coeffs.dtype]
+        s.n_train_views = self.n_train_views
+        s.kappa = self.kappa
+        return s
+
+
+class Context:
+    """A device context with a bounded, grow-only workspace."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0):
+        self._lib = load()
+        self._h = C.c_void_p()
+        rc = self._lib.gavis_ctx_create(C.byref(self._h), int(device), C.c_size_t(int(budget_bytes)))
+        if rc != OK:
+            raise GavisError(rc, f"gavis_ctx_create(device={device}) failed")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            self._lib.gavis_ctx_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != OK:
+            raise GavisError(rc, self._lib.gavis_last_error(self._h).decode())
+
+    @staticmethod
+    def vmf_coeffs(L: int, kappa: float):
+        a = (C.c_double * (L + 1))()
+        rc = load().gavis_vmf_coeffs(int(L), float(kappa), a)
+        if rc != OK:
+            raise GavisError(rc, "gavis_vmf_coeffs")
+        return list(a)
+
+    # -------------------------------------------------------------- VF CONST
+    def vf_build(self, gs: Gaussians, train_cams, degree: int = 2, dtype=torch.float32, params=None,
+                 out: VisibilityField | None = None, accumulate: bool = False, stream=None) -> VisibilityField:
+        p = params or Params(vf_degree=degree)
+        if out is None:
+            coeffs = torch.zeros((gs.n, (degree + 1) ** 2), dtype=dtype, device=gs.means.device)
+            out = VisibilityField(coeffs, degree, 0, float(p.kappa))
+        vs = out.struct()
+        cams = camera_records(train_cams)
+        self._check(self._lib.gavis_vf_build(self._h, C.byref(gs.struct), cams, len(train_cams), C.byref(p),
+                                             C.byref(vs), int(bool(accumulate)), _stream_ptr(stream)))
+        out.n_train_views, out.kappa = int(vs.n_train_views), float(vs.kappa)
+        return out
+
+    # -------------------------------------------------------------- scoring
+    def score_views(self, gs: Gaussians, vf: VisibilityField, cand_cams, params=None, want_rgb=True,
+                    want_unc=True, out=None, sync_best=True, stream=None):
+        """Returns dict(score [n], best (int or device tensor), rgb [n,3,H,W], unc [n,H,W])."""
+        p = params or Params(vf_degree=vf.degree)
+        n = len(cand_cams)
+        dev = gs.means.device
+        W, H = (int(cand_cams[0].W), int(cand_cams[0].H)) if n else (0, 0)
+        out = out or {}
+        rgb = out.get("rgb") if "rgb" in out else (torch.empty((n, 3, H, W), device=dev) if want_rgb else None)
+        unc = out.get("unc") if "unc" in out else (torch.empty((n, H, W), device=dev) if want_unc else None)
+        score = out.get("score") if "score" in out else torch.empty(n, device=dev)
+        best_dev = out.get("best_dev") if "best_dev" in out else torch.empty(1, dtype=torch.int32, device=dev)
+        best_host = C.c_int32(-1)
+        vs = vf.struct()
+        cams = camera_records(cand_cams)
+        self._check(self._lib.gavis_score_views(
+            self._h, C.byref(gs.struct), C.byref(vs), cams, n, C.byref(p),
+            C.c_void_p(rgb.data_ptr() if rgb is not None else None),
+            C.c_void_p(unc.data_ptr() if unc is not None else None),
+            C.c_void_p(score.data_ptr()), C.c_void_p(best_dev.data_ptr()),
+            C.byref(best_host) if sync_best else None, _stream_ptr(stream)))
+        return dict(score=score, best=int(best_host.value) if sync_best else best_dev, rgb=rgb, unc=unc,
+                    best_dev=best_dev)
+
+    def vf_query(self, gs: Gaussians, vf: VisibilityField, cams, params=None, stream=None):
+        p = params or Params(vf_degree=vf.degree)
+        V = torch.empty((len(cams), gs.n), device=gs.means.device)
+        vs = vf.struct()
+        self._check(self._lib.gavis_vf_query(self._h, C.byref(gs.struct), C.byref(vs), camera_records(cams),
+                                             len(cams), C.byref(p), C.c_void_p(V.data_ptr()), _stream_ptr(stream)))
+        return V
+
+    # -------------------------------------------------------------- instrumentation
+    def prof_enable(self, on: bool = True):
+        self._check(self._lib.gavis_prof_enable(self._h, int(bool(on))))
+
+    def prof_read(self):
+        """dict(stage -> (ms, launches)), total kernel launches, pairs (ua, vis)."""
+        ms = (C.c_double * len(STAGES))()
+        la = (C.c_int64 * len(STAGES))()
+        tot = C.c_int64(0)
+        pairs = (C.c_uint64 * 2)()
+        self._check(self._lib.gavis_prof_read(self._h, ms, la, C.byref(tot), pairs))
+        return dict(stages={k: (ms[i], int(la[i])) for i, k in enumerate(STAGES)}, total_launches=int(tot.value),
+                    pairs=(int(pairs[0]), int(pairs[1])))
+
+    # -------------------------------------------------------------- verification hooks
+    def debug_bins(self, gs: Gaussians, cams, params=None, cap=None, stream=None):
+        p = params or Params()
+        TW = (int(cams[0].W) + p.tile - 1) // p.tile
+        TH = (int(cams[0].H) + p.tile - 1) // p.tile
+        ranges = torch.zeros((len(cams) * TW * TH, 2), dtype=torch.int32, device=gs.means.device)
+        M = C.c_int64(0)
+        recs = camera_records(cams)
+        self._check(self._lib.gavis_debug_bins(self._h, C.byref(gs.struct), recs, len(cams), C.byref(p), None,
+                                               None, 0, C.byref(M), C.c_void_p(ranges.data_ptr()),
+                                               _stream_ptr(stream)))
+        m = int(M.value)
+        keys = torch.empty(max(m, 1), dtype=torch.int64, device=gs.means.device)
+        vals = torch.empty(max(m, 1), dtype=torch.int32, device=gs.means.device)
+        self._check(self._lib.gavis_debug_bins(self._h, C.byref(gs.struct), recs, len(cams), C.byref(p),
+                                               C.c_void_p(keys.data_ptr()), C.c_void_p(vals.data_ptr()), m,
+                                               C.byref(M), C.c_void_p(ranges.data_ptr()), _stream_ptr(stream)))
+        return keys[:m], vals[:m], ranges
+
+    def debug_visibility(self, gs: Gaussians, cams, params=None, stream=None):
+        p = params or Params()
+        sumT = torch.zeros((len(cams), gs.n), device=gs.means.device)
+        cnt = torch.zeros((len(cams), gs.n), dtype=torch.int32, device=gs.means.device)
+        self._check(self._lib.gavis_debug_visibility(self._h, C.byref(gs.struct), camera_records(cams), len(cams),
+                                                     C.byref(p), C.c_void_p(sumT.data_ptr()),
+                                                     C.c_void_p(cnt.data_ptr()), _stream_ptr(stream)))
+        return sumT, cnt

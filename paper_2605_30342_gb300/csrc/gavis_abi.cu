@@ -1,0 +1,805 @@
+// gavis_abi.cu -- host side of the C ABI declared in include/gavis.h.
+//
+// Every entry point validates its arguments, then runs the kernel chain on the
+// caller's stream in batches of views:
+//
+//   project (+ VF query + colour)  ->  exclusive scan of tile counts  ->
+//   [sync: read the key count]  ->  emit keys  ->  radix sort  ->  ranges  ->
+//   composite (uncertainty + colour, or particle visibility)  ->  reductions
+//
+// The batch size is the number of views whose per-(view, Gaussian) records fit
+// in the context's workspace budget; if a batch's keys do not fit, the batch is
+// halved and re-run.  Nothing here runs the method on the host: the host only
+// sizes buffers, copies camera records and launches kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gavis_internal.cuh"
+
+using namespace gavis;
+
+std::atomic<long long> gavis::g_launches{0};
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace
+
+struct ProfRec {
+    int stage;
+    cudaEvent_t a, b;
+};
+
+struct gavis_ctx {
+    int device = 0;
+    size_t budget = 0;
+    size_t used = 0;
+    std::string err;
+    Buf rec, vis, keys, small, gamma, cams;
+    unsigned long long *h_total = nullptr;   // pinned
+    int32_t *h_best = nullptr;               // pinned
+    // instrumentation
+    bool prof_on = false;
+    std::vector<ProfRec> pending;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[GAVIS_STAGE_COUNT] = {};
+    long long prof_launches[GAVIS_STAGE_COUNT] = {};
+    unsigned long long *d_pairs = nullptr;   // device [2]
+};
+
+namespace {
+
+int fail(gavis_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                          \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess) return fail(ctx, GAVIS_ERR_CUDA, "%s: %s (%s:%d)", #call,                  \
+                                           cudaGetErrorString(e_), __FILE__, __LINE__);                   \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// grow-only device buffer within the context budget
+int ensure(gavis_ctx *ctx, Buf &b, size_t bytes)
+{
+    bytes = align256(bytes ? bytes : 256);
+    if (b.cap >= bytes) return GAVIS_OK;
+    const size_t other = ctx->used - b.cap;
+    if (other + bytes > ctx->budget)
+        return fail(ctx, GAVIS_ERR_BUDGET, "workspace of %zu bytes exceeds the budget (%zu used of %zu)", bytes,
+                    other, ctx->budget);
+    if (b.p) {
+        CK(cudaDeviceSynchronize());
+        CK(cudaFree(b.p));
+        b.p = nullptr;
+        ctx->used -= b.cap;
+        b.cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, GAVIS_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    b.cap = bytes;
+    ctx->used += bytes;
+    return GAVIS_OK;
+}
+
+cudaEvent_t take_event(gavis_ctx *ctx)
+{
+    if (!ctx->pool.empty()) {
+        cudaEvent_t e = ctx->pool.back();
+        ctx->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Records the device time and launch count of one stage (RAII scope).
+struct Stage {
+    gavis_ctx *ctx;
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    long long l0;
+    Stage(gavis_ctx *c, int st, cudaStream_t str) : ctx(c), stage(st), s(str), l0(g_launches.load())
+    {
+        if (ctx->prof_on) {
+            a = take_event(ctx);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~Stage()
+    {
+        if (ctx->prof_on) {
+            ctx->prof_launches[stage] += g_launches.load() - l0;
+            cudaEvent_t b = take_event(ctx);
+            cudaEventRecord(b, s);
+            ctx->pending.push_back({stage, a, b});
+        }
+    }
+};
+
+bool is_pow2_tile(int t) { return t == 8 || t == 16 || t == 32; }
+
+int check_params(gavis_ctx *ctx, const gavis_params *p)
+{
+    if (!p) return fail(ctx, GAVIS_ERR_ARG, "params is NULL");
+    if (!is_pow2_tile(p->tile)) return fail(ctx, GAVIS_ERR_ARG, "tile must be 8, 16 or 32 (got %d)", p->tile);
+    if (!(p->eps_T > 0.0f && p->eps_T < 1.0f)) return fail(ctx, GAVIS_ERR_ARG, "eps_T must be in (0,1)");
+    if (!(p->q_cut > 0.0f)) return fail(ctx, GAVIS_ERR_ARG, "q_cut must be > 0");
+    if (!(p->beta >= 0.0f && p->beta <= 1.0f)) return fail(ctx, GAVIS_ERR_ARG, "beta must be in [0,1]");
+    if (!(p->o0 >= 0.0f && p->o0 <= 1.0f)) return fail(ctx, GAVIS_ERR_ARG, "o0 must be in [0,1]");
+    if (!(p->sigma_c2 > 0.0f)) return fail(ctx, GAVIS_ERR_ARG, "sigma_c2 must be > 0");
+    if (!(p->kappa >= 0.0f)) return fail(ctx, GAVIS_ERR_ARG, "kappa must be >= 0");
+    if (p->views_per_batch < 0) return fail(ctx, GAVIS_ERR_ARG, "views_per_batch must be >= 0");
+    return GAVIS_OK;
+}
+
+int check_gaussians(gavis_ctx *ctx, const gavis_gaussians *gs, bool need_sh)
+{
+    if (!gs) return fail(ctx, GAVIS_ERR_ARG, "gaussians is NULL");
+    if (gs->n < 0 || gs->n >= (int64_t)1 << 31) return fail(ctx, GAVIS_ERR_ARG, "n out of range");
+    if (gs->n > 0 && (!gs->means || !gs->scales || !gs->rots || !gs->opac))
+        return fail(ctx, GAVIS_ERR_ARG, "NULL Gaussian array");
+    if (need_sh) {
+        if (gs->sh_degree < 0 || gs->sh_degree > 3) return fail(ctx, GAVIS_ERR_ARG, "sh_degree must be 0..3");
+        if (gs->sh_dtype < 0 || gs->sh_dtype > 2) return fail(ctx, GAVIS_ERR_ARG, "bad sh_dtype");
+        if (gs->n > 0 && !gs->sh) return fail(ctx, GAVIS_ERR_ARG, "sh is NULL");
+    }
+    if (gs->n > 0 && ((uintptr_t)gs->rots & 15u)) return fail(ctx, GAVIS_ERR_ARG, "rots must be 16-byte aligned");
+    return GAVIS_OK;
+}
+
+int check_cams(gavis_ctx *ctx, const gavis_camera *cams, int n)
+{
+    if (n < 0) return fail(ctx, GAVIS_ERR_ARG, "negative camera count");
+    if (n > 0 && !cams) return fail(ctx, GAVIS_ERR_ARG, "cameras is NULL");
+    for (int i = 0; i < n; ++i) {
+        const gavis_camera &c = cams[i];
+        if (c.W <= 0 || c.H <= 0 || c.W > 16384 || c.H > 16384)
+            return fail(ctx, GAVIS_ERR_ARG, "camera %d: W, H must be in 1..16384", i);
+        if (c.W != cams[0].W || c.H != cams[0].H)
+            return fail(ctx, GAVIS_ERR_ARG, "camera %d: every camera in a call must share W x H", i);
+        if (!(c.fx > 0.0f && c.fy > 0.0f)) return fail(ctx, GAVIS_ERR_ARG, "camera %d: focal lengths must be > 0", i);
+        if (!(c.znear > 0.0f)) return fail(ctx, GAVIS_ERR_ARG, "camera %d: znear must be > 0", i);
+    }
+    return GAVIS_OK;
+}
+
+RasterConsts raster_consts(const gavis_params *p)
+{
+    RasterConsts rc;
+    rc.eps_T = p->eps_T;
+    rc.q_cut = p->q_cut;
+    rc.beta = p->beta;
+    rc.o0 = p->o0;
+    const double l2pie = std::log(2.0 * M_PI) + 1.0;
+    rc.k_c = (float)(0.5 * 3.0 * std::log((double)p->sigma_c2) + 1.5 * l2pie);
+    rc.k_0 = (float)(0.5 * (double)p->logdet_Q0 + 1.5 * l2pie);
+    return rc;
+}
+
+// i_l(kappa) by closed forms and upward recurrence (kappa >= 1) or the power
+// series (kappa < 1).
+void bessel_i(int L, double x, double *out)
+{
+    if (x < 1.0) {
+        for (int l = 0; l <= L; ++l) {
+            double df = 1.0;
+            for (int k = 3; k <= 2 * l + 1; k += 2) df *= (double)k;
+            double term = std::pow(x, l) / df, sum = term;
+            for (int k = 1; k < 60; ++k) {
+                term *= 0.5 * x * x / ((double)k * (double)(2 * l + 2 * k + 1));
+                sum += term;
+            }
+            out[l] = sum;
+        }
+        return;
+    }
+    out[0] = std::sinh(x) / x;
+    if (L >= 1) out[1] = (x * std::cosh(x) - std::sinh(x)) / (x * x);
+    for (int l = 1; l < L; ++l) out[l + 1] = out[l - 1] - (2.0 * l + 1.0) / x * out[l];
+}
+
+struct Geometry {
+    int W, H, TW, TH, TT;
+};
+
+Geometry geometry_of(const gavis_camera *cams, int tile)
+{
+    Geometry g;
+    g.W = cams[0].W;
+    g.H = cams[0].H;
+    g.TW = (g.W + tile - 1) / tile;
+    g.TH = (g.H + tile - 1) / tile;
+    g.TT = g.TW * g.TH;
+    return g;
+}
+
+int bits_for(uint64_t x)
+{
+    int b = 0;
+    while (b < 64 && (x >> b) != 0) ++b;
+    return b;
+}
+
+// per-batch workspace: records + counts/offsets
+struct RecLayout {
+    GeoRec *geo;
+    UaRec *ua;
+    uint2 *rect;
+    uint32_t *counts, *offsets;
+    void *scan_tmp;
+    size_t bytes;
+};
+
+RecLayout rec_layout(void *base, size_t nvn, bool ua)
+{
+    RecLayout L;
+    char *p = reinterpret_cast<char *>(base);
+    size_t off = 0;
+    auto take = [&](size_t b) { char *q = p ? p + off : nullptr; off += align256(b); return q; };
+    L.geo = reinterpret_cast<GeoRec *>(take(nvn * sizeof(GeoRec)));
+    L.ua = ua ? reinterpret_cast<UaRec *>(take(nvn * sizeof(UaRec))) : nullptr;
+    L.rect = reinterpret_cast<uint2 *>(take(nvn * sizeof(uint2)));
+    L.counts = reinterpret_cast<uint32_t *>(take(nvn * sizeof(uint32_t)));
+    L.offsets = reinterpret_cast<uint32_t *>(take(nvn * sizeof(uint32_t)));
+    L.scan_tmp = take(scan_tmp_bytes(nvn) + 64);
+    L.bytes = off;
+    return L;
+}
+
+struct KeyLayout {
+    uint64_t *k0, *k1;
+    uint32_t *v0, *v1;
+    void *tmp;
+    size_t bytes;
+};
+
+KeyLayout key_layout(void *base, size_t M)
+{
+    KeyLayout L;
+    char *p = reinterpret_cast<char *>(base);
+    size_t off = 0;
+    auto take = [&](size_t b) { char *q = p ? p + off : nullptr; off += align256(b); return q; };
+    L.k0 = reinterpret_cast<uint64_t *>(take(M * 8));
+    L.k1 = reinterpret_cast<uint64_t *>(take(M * 8));
+    L.v0 = reinterpret_cast<uint32_t *>(take(M * 4));
+    L.v1 = reinterpret_cast<uint32_t *>(take(M * 4));
+    L.tmp = take(radix_tmp_bytes(M));
+    L.bytes = off;
+    return L;
+}
+
+struct SmallLayout {
+    uint2 *ranges;
+    float *tile_sums;
+    unsigned long long *d_total;
+    int32_t *best;
+    size_t bytes;
+};
+
+SmallLayout small_layout(void *base, size_t nvt)
+{
+    SmallLayout L;
+    char *p = reinterpret_cast<char *>(base);
+    size_t off = 0;
+    auto take = [&](size_t b) { char *q = p ? p + off : nullptr; off += align256(b); return q; };
+    L.ranges = reinterpret_cast<uint2 *>(take(nvt * sizeof(uint2)));
+    L.tile_sums = reinterpret_cast<float *>(take(nvt * sizeof(float)));
+    L.d_total = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long)));
+    L.best = reinterpret_cast<int32_t *>(take(sizeof(int32_t)));
+    L.bytes = off;
+    return L;
+}
+
+enum Mode { MODE_SCORE, MODE_VIS, MODE_BINS };
+
+struct ChainOut {
+    // score mode
+    float *rgb = nullptr, *unc = nullptr, *score = nullptr;
+    // vis mode: per-batch sums land in ctx->vis; callback consumes them
+    // bins mode
+    uint64_t *keys = nullptr;
+    uint32_t *vals = nullptr;
+    int64_t cap = 0;
+    int64_t M = 0;
+    uint32_t *ranges = nullptr;
+};
+
+size_t per_view_bytes(int64_t n, int TT, Mode m)
+{
+    size_t rec = (size_t)n * (sizeof(GeoRec) + (m == MODE_SCORE ? sizeof(UaRec) : 0) + 8 + 4 + 4);
+    size_t vis = m == MODE_VIS ? (size_t)n * 12 : 0;
+    size_t keys = (size_t)n * 2 * 24;   // typical: ~2 tiles per Gaussian per view
+    return rec + vis + keys + (size_t)TT * 12;
+}
+
+int auto_batch(gavis_ctx *ctx, int64_t n, int TT, int n_views, Mode m, int requested)
+{
+    if (requested > 0) return requested < n_views ? requested : n_views;
+    const size_t per = per_view_bytes(n, TT, m);
+    // buffers are reused across batches, so the whole budget is available
+    long long nv = (long long)((ctx->budget * 7 / 10) / (per ? per : 1));
+    if (nv < 1) nv = 1;
+    if (nv > 256) nv = 256;
+    if (nv > n_views) nv = n_views;
+    return (int)nv;
+}
+
+// One batch of views [v0, v0+nv) through project -> ... -> composite.
+// Returns GAVIS_ERR_BUDGET (without side effects on outputs) when the keys of
+// this batch do not fit, so the caller can halve the batch.
+int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_vf *vf, const gavis_camera *d_cams,
+              int nv, int v0, const gavis_params *p, const Geometry &G, ChainOut &out, cudaStream_t s,
+              const gavis_camera *h_cams_all)
+{
+    const int64_t n = gs->n;
+    const size_t nvn = (size_t)nv * (size_t)n;
+    const size_t nvt = (size_t)nv * (size_t)G.TT;
+    int rc;
+
+    RecLayout RL = rec_layout(nullptr, nvn, mode == MODE_SCORE);
+    if ((rc = ensure(ctx, ctx->rec, RL.bytes)) != GAVIS_OK) return rc;
+    RL = rec_layout(ctx->rec.p, nvn, mode == MODE_SCORE);
+    SmallLayout SL = small_layout(nullptr, nvt);
+    if ((rc = ensure(ctx, ctx->small, SL.bytes)) != GAVIS_OK) return rc;
+    SL = small_layout(ctx->small.p, nvt);
+
+    ProjectArgs pa;
+    pa.means = gs->means; pa.scales = gs->scales; pa.rots = gs->rots; pa.opac = gs->opac;
+    pa.sh = gs->sh; pa.sh_degree = gs->sh_degree; pa.sh_dtype = gs->sh_dtype;
+    pa.gamma = (mode == MODE_SCORE && vf) ? vf->coeffs : nullptr;
+    pa.vf_degree = (mode == MODE_SCORE && vf) ? vf->degree : 0;
+    pa.vf_dtype = (mode == MODE_SCORE && vf) ? vf->dtype : 0;
+    pa.n_train = (mode == MODE_SCORE && vf) ? vf->n_train_views : 0;
+    pa.q_cut = p->q_cut; pa.beta = p->beta; pa.o0 = p->o0;
+    pa.tile = p->tile; pa.TW = G.TW; pa.TH = G.TH;
+    pa.cams = d_cams + v0; pa.nv = nv; pa.n = n;
+    pa.geo = RL.geo; pa.ua = RL.ua; pa.rect = RL.rect; pa.counts = RL.counts;
+    {
+        Stage st(ctx, GAVIS_STAGE_PROJECT, s);
+        CK(launch_project(pa, s));
+    }
+    {
+        Stage st(ctx, GAVIS_STAGE_SCAN, s);
+        CK(exclusive_scan_u32(RL.counts, RL.offsets, nvn, RL.scan_tmp, SL.d_total, s));
+    }
+    CK(cudaMemcpyAsync(ctx->h_total, SL.d_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const unsigned long long M = *ctx->h_total;
+    if (M >= (1ull << 32) - 1) return fail(ctx, GAVIS_ERR_BUDGET, "more than 2^32 keys in one batch");
+
+    KeyLayout KL = key_layout(nullptr, (size_t)M);
+    if ((rc = ensure(ctx, ctx->keys, KL.bytes)) != GAVIS_OK) return rc;
+    KL = key_layout(ctx->keys.p, (size_t)M);
+
+    {
+        Stage st(ctx, GAVIS_STAGE_EMIT, s);
+        CK(launch_emit(RL.rect, RL.geo, RL.counts, RL.offsets, nv, n, G.TW, G.TH, KL.k0, KL.v0, s));
+    }
+    const int end_bit = 32 + bits_for((uint64_t)nvt - 1);
+    bool alt = false;
+    {
+        Stage st(ctx, GAVIS_STAGE_SORT, s);
+        CK(radix_sort_pairs(KL.k0, KL.v0, KL.k1, KL.v1, (size_t)M, end_bit, KL.tmp, &alt, s));
+    }
+    uint64_t *keys = alt ? KL.k1 : KL.k0;
+    uint32_t *vals = alt ? KL.v1 : KL.v0;
+    {
+        Stage st(ctx, GAVIS_STAGE_RANGES, s);
+        CK(cudaMemsetAsync(SL.ranges, 0, nvt * sizeof(uint2), s));
+        CK(launch_ranges(keys, (size_t)M, SL.ranges, s));
+    }
+
+    if (mode == MODE_BINS) {
+        const int64_t off = out.M;
+        if (off < out.cap && out.keys) {
+            const int64_t m = (int64_t)M < out.cap - off ? (int64_t)M : out.cap - off;
+            // keys carry the view index within the batch: shift them to the global index
+            CK(cudaMemcpyAsync(out.keys + off, keys, (size_t)m * 8, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(out.vals + off, vals, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
+        }
+        if (out.ranges)
+            CK(cudaMemcpyAsync(out.ranges + 2 * (size_t)v0 * G.TT, SL.ranges, nvt * sizeof(uint2),
+                               cudaMemcpyDeviceToDevice, s));
+        out.M += (int64_t)M;
+        return GAVIS_OK;
+    }
+
+    CompositeArgs ca;
+    memset(&ca, 0, sizeof(ca));
+    ca.ranges = SL.ranges; ca.vals = vals; ca.geo = RL.geo; ca.ua = RL.ua;
+    ca.n = n; ca.nv = nv; ca.v0 = v0; ca.W = G.W; ca.H = G.H; ca.tile = p->tile; ca.TW = G.TW; ca.TH = G.TH;
+    ca.rc = raster_consts(p);
+    ca.tile_sums = SL.tile_sums;
+    if (mode == MODE_SCORE) {
+        ca.rgb = out.rgb; ca.unc = out.unc;
+        ca.pairs = ctx->prof_on ? ctx->d_pairs : nullptr;
+        {
+            Stage st(ctx, GAVIS_STAGE_COMPOSITE_UA, s);
+            CK(launch_composite_ua(ca, s));
+        }
+        Stage st(ctx, GAVIS_STAGE_REDUCE, s);
+        CK(launch_view_reduce(SL.tile_sums, nv, G.TT, 1.0f / ((float)G.W * (float)G.H), out.score + v0, s));
+    } else {
+        if ((rc = ensure(ctx, ctx->vis, nvn * 12)) != GAVIS_OK) return rc;
+        ca.sumT = reinterpret_cast<unsigned long long *>(ctx->vis.p);
+        ca.cnt = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(ctx->vis.p) + nvn * 8);
+        ca.pairs = ctx->prof_on ? ctx->d_pairs + 1 : nullptr;
+        Stage st(ctx, GAVIS_STAGE_COMPOSITE_VIS, s);
+        CK(cudaMemsetAsync(ctx->vis.p, 0, nvn * 12, s));
+        CK(launch_composite_vis(ca, s));
+    }
+    (void)h_cams_all;
+    return GAVIS_OK;
+}
+
+int upload_cams(gavis_ctx *ctx, const gavis_camera *cams, int n, cudaStream_t s)
+{
+    int rc = ensure(ctx, ctx->cams, sizeof(gavis_camera) * (size_t)(n > 0 ? n : 1));
+    if (rc != GAVIS_OK) return rc;
+    if (n > 0)
+        CK(cudaMemcpyAsync(ctx->cams.p, cams, sizeof(gavis_camera) * (size_t)n, cudaMemcpyHostToDevice, s));
+    return GAVIS_OK;
+}
+
+// Runs the chain over all views in batches, halving a batch whose keys do
+// not fit.  `after` is called once per completed batch (VF accumulation).
+template <class After>
+int run_views(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_vf *vf, const gavis_camera *cams,
+              int n_views, const gavis_params *p, ChainOut &out, cudaStream_t s, After after)
+{
+    if (n_views == 0 || gs->n == 0) return GAVIS_OK;
+    const Geometry G = geometry_of(cams, p->tile);
+    int rc = upload_cams(ctx, cams, n_views, s);
+    if (rc != GAVIS_OK) return rc;
+    const gavis_camera *d_cams = reinterpret_cast<const gavis_camera *>(ctx->cams.p);
+    int nv = auto_batch(ctx, gs->n, G.TT, n_views, mode, p->views_per_batch);
+    int v0 = 0;
+    while (v0 < n_views) {
+        int cur = nv < n_views - v0 ? nv : n_views - v0;
+        rc = run_batch(ctx, mode, gs, vf, d_cams, cur, v0, p, G, out, s, cams);
+        if (rc == GAVIS_ERR_BUDGET && cur > 1 && mode != MODE_BINS) {
+            nv = cur / 2;
+            continue;
+        }
+        if (rc != GAVIS_OK) return rc;
+        rc = after(v0, cur);
+        if (rc != GAVIS_OK) return rc;
+        v0 += cur;
+    }
+    return GAVIS_OK;
+}
+
+int check_vf(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf)
+{
+    if (!vf) return fail(ctx, GAVIS_ERR_ARG, "vf is NULL");
+    if (vf->n != gs->n) return fail(ctx, GAVIS_ERR_ARG, "vf->n (%lld) != gaussians n (%lld)", (long long)vf->n,
+                                    (long long)gs->n);
+    if (vf->degree < 0 || vf->degree > 3) return fail(ctx, GAVIS_ERR_ARG, "vf degree must be 0..3");
+    if (vf->dtype < 0 || vf->dtype > 2) return fail(ctx, GAVIS_ERR_ARG, "bad vf dtype");
+    if (vf->n_train_views < 0) return fail(ctx, GAVIS_ERR_ARG, "negative n_train_views");
+    if (vf->n > 0 && !vf->coeffs) return fail(ctx, GAVIS_ERR_ARG, "vf coeffs is NULL");
+    return GAVIS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gavis_ctx_create(gavis_ctx **out, int device, size_t hbm_budget_bytes)
+{
+    if (!out) return GAVIS_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return GAVIS_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return GAVIS_ERR_CUDA;
+    gavis_ctx *ctx = new gavis_ctx();
+    ctx->device = device;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        delete ctx;
+        return GAVIS_ERR_CUDA;
+    }
+    ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : fr / 10 * 6;
+    if (cudaMallocHost(&ctx->h_total, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_best, sizeof(int32_t)) != cudaSuccess) {
+        delete ctx;
+        return GAVIS_ERR_CUDA;
+    }
+    *out = ctx;
+    return GAVIS_OK;
+}
+
+void gavis_ctx_destroy(gavis_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (Buf *b : {&ctx->rec, &ctx->vis, &ctx->keys, &ctx->small, &ctx->gamma, &ctx->cams})
+        if (b->p) cudaFree(b->p);
+    if (ctx->h_total) cudaFreeHost(ctx->h_total);
+    if (ctx->h_best) cudaFreeHost(ctx->h_best);
+    if (ctx->d_pairs) cudaFree(ctx->d_pairs);
+    for (auto &r : ctx->pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+    delete ctx;
+}
+
+int gavis_prof_enable(gavis_ctx *ctx, int on)
+{
+    if (!ctx) return GAVIS_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    if (!ctx->d_pairs) CK(cudaMalloc(&ctx->d_pairs, 2 * sizeof(unsigned long long)));
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemset(ctx->d_pairs, 0, 2 * sizeof(unsigned long long)));
+    for (auto &r : ctx->pending) {
+        ctx->pool.push_back(r.a);
+        ctx->pool.push_back(r.b);
+    }
+    ctx->pending.clear();
+    for (int k = 0; k < GAVIS_STAGE_COUNT; ++k) {
+        ctx->prof_ms[k] = 0.0;
+        ctx->prof_launches[k] = 0;
+    }
+    ctx->prof_on = on != 0;
+    return GAVIS_OK;
+}
+
+int gavis_prof_read(gavis_ctx *ctx, double *ms, int64_t *launches, int64_t *total_launches, uint64_t *pairs)
+{
+    if (!ctx) return GAVIS_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    CK(cudaDeviceSynchronize());
+    for (auto &r : ctx->pending) {
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, r.a, r.b));
+        ctx->prof_ms[r.stage] += (double)t;
+        ctx->pool.push_back(r.a);
+        ctx->pool.push_back(r.b);
+    }
+    ctx->pending.clear();
+    for (int k = 0; k < GAVIS_STAGE_COUNT; ++k) {
+        if (ms) ms[k] = ctx->prof_ms[k];
+        if (launches) launches[k] = ctx->prof_launches[k];
+    }
+    if (total_launches) *total_launches = g_launches.load();
+    if (pairs) {
+        unsigned long long h[2] = {0, 0};
+        if (ctx->d_pairs) CK(cudaMemcpy(h, ctx->d_pairs, sizeof(h), cudaMemcpyDeviceToHost));
+        pairs[0] = h[0];
+        pairs[1] = h[1];
+    }
+    return GAVIS_OK;
+}
+
+const char *gavis_last_error(const gavis_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int gavis_params_default(gavis_params *p)
+{
+    if (!p) return GAVIS_ERR_ARG;
+    p->kappa = 1.0f;
+    p->vf_degree = 2;
+    p->eps_T = 1e-4f;
+    p->q_cut = 9.0f;
+    p->beta = 0.5f;
+    p->o0 = 0.15f;
+    p->sigma_c2 = 0.01f;
+    p->logdet_Q0 = 0.0f;
+    p->tile = 16;
+    p->views_per_batch = 0;
+    return GAVIS_OK;
+}
+
+int gavis_vmf_coeffs(int L, double kappa, double *a)
+{
+    if (!a || L < 0 || L > 3 || !(kappa >= 0.0)) return GAVIS_ERR_ARG;
+    double i[4] = {0, 0, 0, 0};
+    if (kappa == 0.0) {
+        i[0] = 1.0;
+    } else {
+        bessel_i(L, kappa, i);
+    }
+    const double zeta = std::exp(-kappa);
+    for (int l = 0; l <= L; ++l) a[l] = 4.0 * M_PI * zeta * i[l];
+    return GAVIS_OK;
+}
+
+int gavis_vf_build(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_camera *train, int n_train,
+                   const gavis_params *p, gavis_vf *out, int accumulate, void *stream)
+{
+    if (!ctx) return GAVIS_ERR_ARG;
+    int rc;
+    if ((rc = check_params(ctx, p)) || (rc = check_gaussians(ctx, gs, false)) || (rc = check_cams(ctx, train, n_train)))
+        return rc;
+    if (!out) return fail(ctx, GAVIS_ERR_ARG, "out is NULL");
+    if (out->n != gs->n) return fail(ctx, GAVIS_ERR_ARG, "out->n != gaussians n");
+    if (out->degree < 0 || out->degree > 3) return fail(ctx, GAVIS_ERR_ARG, "out degree must be 0..3");
+    if (out->dtype < 0 || out->dtype > 2) return fail(ctx, GAVIS_ERR_ARG, "bad out dtype");
+    if (out->n > 0 && !out->coeffs) return fail(ctx, GAVIS_ERR_ARG, "out coeffs is NULL");
+    if (accumulate && out->n_train_views < 0) return fail(ctx, GAVIS_ERR_ARG, "negative n_train_views");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int L = out->degree;
+    const size_t K = (size_t)(L + 1) * (L + 1);
+    const size_t count = (size_t)gs->n * K;
+    if ((rc = ensure(ctx, ctx->gamma, count * sizeof(float))) != GAVIS_OK) return rc;
+    float *g32 = reinterpret_cast<float *>(ctx->gamma.p);
+    if (accumulate) CK(launch_vf_load(out->coeffs, out->dtype, count, g32, s));
+    else CK(cudaMemsetAsync(g32, 0, count * sizeof(float), s));
+    double ad[4] = {0, 0, 0, 0};
+    gavis_vmf_coeffs(L, (double)p->kappa, ad);
+    ChainOut co;
+    auto after = [&](int v0, int nv) -> int {
+        AccumArgs aa;
+        aa.means = gs->means;
+        aa.cams = reinterpret_cast<const gavis_camera *>(ctx->cams.p) + v0;
+        aa.nv = nv;
+        aa.n = gs->n;
+        const size_t nvn = (size_t)nv * (size_t)gs->n;
+        aa.sumT = reinterpret_cast<const unsigned long long *>(ctx->vis.p);
+        aa.cnt = reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(ctx->vis.p) + nvn * 8);
+        for (int l = 0; l < 4; ++l) aa.a_l[l] = (float)ad[l];
+        aa.L = L;
+        aa.gamma32 = g32;
+        Stage st(ctx, GAVIS_STAGE_VF_ACCUM, s);
+        CK(launch_vf_accumulate(aa, s));
+        return GAVIS_OK;
+    };
+    rc = run_views(ctx, MODE_VIS, gs, nullptr, train, n_train, p, co, s, after);
+    if (rc != GAVIS_OK) return rc;
+    CK(launch_vf_store(g32, count, out->coeffs, out->dtype, accumulate, s));
+    out->n_train_views = accumulate ? out->n_train_views + n_train : n_train;
+    out->kappa = p->kappa;
+    return GAVIS_OK;
+}
+
+int gavis_score_views(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf, const gavis_camera *cand,
+                      int n_cand, const gavis_params *p, float *rgb, float *unc, float *score, int32_t *best_dev,
+                      int32_t *best_host, void *stream)
+{
+    if (!ctx) return GAVIS_ERR_ARG;
+    int rc;
+    if ((rc = check_params(ctx, p)) || (rc = check_gaussians(ctx, gs, true)) || (rc = check_vf(ctx, gs, vf)) ||
+        (rc = check_cams(ctx, cand, n_cand)))
+        return rc;
+    if (n_cand > 0 && !score) return fail(ctx, GAVIS_ERR_ARG, "score is NULL");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    ChainOut co;
+    co.rgb = rgb;
+    co.unc = unc;
+    co.score = score;
+    if (gs->n == 0 && n_cand > 0) {
+        // empty scene: every pixel has an empty list, H = 0 and rgb = 0
+        const size_t plane = (size_t)cand[0].W * cand[0].H;
+        if (rgb) CK(cudaMemsetAsync(rgb, 0, (size_t)n_cand * 3 * plane * sizeof(float), s));
+        if (unc) CK(cudaMemsetAsync(unc, 0, (size_t)n_cand * plane * sizeof(float), s));
+        CK(cudaMemsetAsync(score, 0, (size_t)n_cand * sizeof(float), s));
+    } else {
+        rc = run_views(ctx, MODE_SCORE, gs, vf, cand, n_cand, p, co, s, [](int, int) { return GAVIS_OK; });
+        if (rc != GAVIS_OK) return rc;
+    }
+    if (best_dev || best_host) {
+        SmallLayout SL = small_layout(nullptr, 1);
+        if ((rc = ensure(ctx, ctx->small, SL.bytes)) != GAVIS_OK) return rc;
+        SL = small_layout(ctx->small.p, 1);
+        int32_t *dbest = best_dev ? best_dev : SL.best;
+        Stage st(ctx, GAVIS_STAGE_REDUCE, s);
+        if (n_cand > 0) CK(launch_argmax(score, n_cand, dbest, s));
+        else CK(cudaMemsetAsync(dbest, 0xff, sizeof(int32_t), s));
+        if (best_host) {
+            CK(cudaMemcpyAsync(ctx->h_best, dbest, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            *best_host = *ctx->h_best;
+        }
+    }
+    return GAVIS_OK;
+}
+
+int gavis_vf_query(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf, const gavis_camera *cams,
+                   int n_cams, const gavis_params *p, float *V, void *stream)
+{
+    if (!ctx) return GAVIS_ERR_ARG;
+    int rc;
+    if ((rc = check_params(ctx, p)) || (rc = check_gaussians(ctx, gs, false)) || (rc = check_vf(ctx, gs, vf)) ||
+        (rc = check_cams(ctx, cams, n_cams)))
+        return rc;
+    if (n_cams > 0 && gs->n > 0 && !V) return fail(ctx, GAVIS_ERR_ARG, "V is NULL");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if ((rc = upload_cams(ctx, cams, n_cams, s)) != GAVIS_OK) return rc;
+    QueryArgs qa;
+    qa.means = gs->means;
+    qa.gamma = vf->coeffs;
+    qa.vf_degree = vf->degree;
+    qa.vf_dtype = vf->dtype;
+    qa.n_train = vf->n_train_views;
+    qa.cams = reinterpret_cast<const gavis_camera *>(ctx->cams.p);
+    qa.nv = n_cams;
+    qa.n = gs->n;
+    qa.V = V;
+    CK(launch_query(qa, s));
+    return GAVIS_OK;
+}
+
+int gavis_debug_bins(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_camera *cams, int n_cams,
+                     const gavis_params *p, uint64_t *keys, uint32_t *vals, int64_t cap, int64_t *M_out,
+                     uint32_t *ranges, void *stream)
+{
+    if (!ctx) return GAVIS_ERR_ARG;
+    int rc;
+    if ((rc = check_params(ctx, p)) || (rc = check_gaussians(ctx, gs, false)) || (rc = check_cams(ctx, cams, n_cams)))
+        return rc;
+    if (!M_out) return fail(ctx, GAVIS_ERR_ARG, "M_out is NULL");
+    if (cap > 0 && (!keys || !vals)) return fail(ctx, GAVIS_ERR_ARG, "keys/vals NULL with cap > 0");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    gavis_params q = *p;
+    q.views_per_batch = n_cams;   // one batch: keys carry the view index within the call
+    ChainOut co;
+    co.keys = keys;
+    co.vals = vals;
+    co.cap = cap;
+    co.ranges = ranges;
+    if (ranges && n_cams > 0 && gs->n == 0) {
+        const Geometry G = geometry_of(cams, p->tile);
+        CK(cudaMemsetAsync(ranges, 0, (size_t)n_cams * G.TT * 8, s));
+    }
+    rc = run_views(ctx, MODE_BINS, gs, nullptr, cams, n_cams, &q, co, s, [](int, int) { return GAVIS_OK; });
+    if (rc != GAVIS_OK) return rc;
+    CK(cudaStreamSynchronize(s));
+    *M_out = co.M;
+    return GAVIS_OK;
+}
+
+int gavis_debug_visibility(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_camera *cams, int n_cams,
+                           const gavis_params *p, float *sumT, uint32_t *cnt, void *stream)
+{
+    if (!ctx) return GAVIS_ERR_ARG;
+    int rc;
+    if ((rc = check_params(ctx, p)) || (rc = check_gaussians(ctx, gs, false)) || (rc = check_cams(ctx, cams, n_cams)))
+        return rc;
+    if (n_cams > 0 && gs->n > 0 && (!sumT || !cnt)) return fail(ctx, GAVIS_ERR_ARG, "sumT/cnt is NULL");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    ChainOut co;
+    auto after = [&](int v0, int nv) -> int {
+        const size_t nvn = (size_t)nv * (size_t)gs->n;
+        const unsigned long long *sT = reinterpret_cast<const unsigned long long *>(ctx->vis.p);
+        const uint32_t *c = reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(ctx->vis.p) + nvn * 8);
+        CK(launch_vis_export(sT, c, nvn, sumT + (size_t)v0 * gs->n, cnt + (size_t)v0 * gs->n, s));
+        return GAVIS_OK;
+    };
+    return run_views(ctx, MODE_VIS, gs, nullptr, cams, n_cams, p, co, s, after);
+}
+
+}  // extern "C"

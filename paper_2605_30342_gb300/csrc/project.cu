@@ -1,0 +1,293 @@
+// project.cu -- per (view, Gaussian) projection, culling, colour and
+// visibility-field query.
+//
+// One thread per Gaussian; the thread loads the Gaussian's parameters once
+// (centre, scale, rotation, opacity, colour SH, visibility-field SH) and loops
+// over every view of the batch, whose cameras sit in shared memory.  The
+// Gaussian record is therefore read from HBM once per batch rather than once
+// per view.
+//
+// Image-space geometry is evaluated with explicit round-to-nearest intrinsics
+// (no contraction) in a fixed operation order, so that depth keys, conics and
+// tile rectangles are reproducible bit for bit by any IEEE-754 float32
+// implementation of the same sequence: 3DGS EWA projection (Sigma2D = J W
+// Sigma3D W^T J^T + 0.3 I, Jacobian with the 1.3 tan(fov/2) clamp), conic =
+// Sigma2D^-1, a footprint of q = d^T conic d <= q_cut, and the tile rectangle
+// of the footprint's bounding box inflated by 2^-10 (relative and absolute).
+//
+// The visibility field is queried here (Alg. "Query Anisotropic Visibility
+// Field"): V~ = sum_j gamma_j Y_j(d), d = normalize(x_g - x_cam), clamped to
+// [0, |P|], then V = 1 - (1 - V~/|P|)^|P| (eq:vis_bound), evaluated as
+// -expm1(|P| log1p(-V~/|P|)).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "gavis_internal.cuh"
+#include "sh_basis.cuh"
+
+namespace gavis {
+namespace {
+
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fd(float a, float b) { return __fdiv_rn(a, b); }
+
+__device__ __forceinline__ float ld_coef(const void *p, size_t i, int dtype)
+{
+    if (dtype == GAVIS_F16) return __half2float(reinterpret_cast<const __half *>(p)[i]);
+    if (dtype == GAVIS_BF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(p)[i]);
+    return reinterpret_cast<const float *>(p)[i];
+}
+
+struct Sigma3 {
+    float s00, s01, s02, s11, s12, s22;
+};
+
+// Sigma3D = (R S)(R S)^T from a quaternion (w,x,y,z) and scales.
+__device__ __forceinline__ Sigma3 sigma3d(const float *sc, float qw, float qx, float qy, float qz)
+{
+    float qn = __fsqrt_rn(fa(fa(fa(fm(qw, qw), fm(qx, qx)), fm(qy, qy)), fm(qz, qz)));
+    qw = fd(qw, qn); qx = fd(qx, qn); qy = fd(qy, qn); qz = fd(qz, qn);
+    float xx = fm(qx, qx), yy = fm(qy, qy), zz = fm(qz, qz);
+    float xy = fm(qx, qy), xz = fm(qx, qz), yz = fm(qy, qz);
+    float wx = fm(qw, qx), wy = fm(qw, qy), wz = fm(qw, qz);
+    float G[9];
+    G[0] = fs(1.0f, fm(2.0f, fa(yy, zz))); G[1] = fm(2.0f, fs(xy, wz));        G[2] = fm(2.0f, fa(xz, wy));
+    G[3] = fm(2.0f, fa(xy, wz));        G[4] = fs(1.0f, fm(2.0f, fa(xx, zz))); G[5] = fm(2.0f, fs(yz, wx));
+    G[6] = fm(2.0f, fs(xz, wy));        G[7] = fm(2.0f, fa(yz, wx));        G[8] = fs(1.0f, fm(2.0f, fa(xx, yy)));
+    float M[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = fm(G[3 * i + j], sc[j]);
+    Sigma3 S;
+    S.s00 = fa(fa(fm(M[0], M[0]), fm(M[1], M[1])), fm(M[2], M[2]));
+    S.s01 = fa(fa(fm(M[0], M[3]), fm(M[1], M[4])), fm(M[2], M[5]));
+    S.s02 = fa(fa(fm(M[0], M[6]), fm(M[1], M[7])), fm(M[2], M[8]));
+    S.s11 = fa(fa(fm(M[3], M[3]), fm(M[4], M[4])), fm(M[5], M[5]));
+    S.s12 = fa(fa(fm(M[3], M[6]), fm(M[4], M[7])), fm(M[5], M[8]));
+    S.s22 = fa(fa(fm(M[6], M[6]), fm(M[7], M[7])), fm(M[8], M[8]));
+    return S;
+}
+
+struct Proj {
+    float z, u, v, A, B, C;
+    int x0, x1, y0, y1;
+    int status;   // 0 culled, 1 has tiles, 2 valid but off-screen
+};
+
+__device__ __forceinline__ Proj project_one(const gavis_camera &cam, float x, float y, float z, const Sigma3 &S,
+                                            float q_cut, float rb, int TW, int TH)
+{
+    Proj o;
+    o.status = 0;
+    o.x0 = o.x1 = o.y0 = o.y1 = 0;
+    o.u = o.v = o.A = o.B = o.C = 0.0f;
+    const float *R = cam.R, *t = cam.t;
+    float tx = fa(fa(fa(fm(R[0], x), fm(R[1], y)), fm(R[2], z)), t[0]);
+    float ty = fa(fa(fa(fm(R[3], x), fm(R[4], y)), fm(R[5], z)), t[1]);
+    float tz = fa(fa(fa(fm(R[6], x), fm(R[7], y)), fm(R[8], z)), t[2]);
+    o.z = tz;
+    if (!(tz > cam.znear)) return o;
+    float limx = fm(1.3f, cam.tan_half_fovx), limy = fm(1.3f, cam.tan_half_fovy);
+    float txz = fd(tx, tz), tyz = fd(ty, tz);
+    float ctx = fm(fminf(limx, fmaxf(-limx, txz)), tz);
+    float cty = fm(fminf(limy, fmaxf(-limy, tyz)), tz);
+    float tz2 = fm(tz, tz);
+    float J00 = fd(cam.fx, tz), J02 = -fd(fm(cam.fx, ctx), tz2);
+    float J11 = fd(cam.fy, tz), J12 = -fd(fm(cam.fy, cty), tz2);
+    float T00 = fa(fm(J00, R[0]), fm(J02, R[6])), T01 = fa(fm(J00, R[1]), fm(J02, R[7]));
+    float T02 = fa(fm(J00, R[2]), fm(J02, R[8]));
+    float T10 = fa(fm(J11, R[3]), fm(J12, R[6])), T11 = fa(fm(J11, R[4]), fm(J12, R[7]));
+    float T12 = fa(fm(J11, R[5]), fm(J12, R[8]));
+    float U00 = fa(fa(fm(T00, S.s00), fm(T01, S.s01)), fm(T02, S.s02));
+    float U01 = fa(fa(fm(T00, S.s01), fm(T01, S.s11)), fm(T02, S.s12));
+    float U02 = fa(fa(fm(T00, S.s02), fm(T01, S.s12)), fm(T02, S.s22));
+    float U10 = fa(fa(fm(T10, S.s00), fm(T11, S.s01)), fm(T12, S.s02));
+    float U11 = fa(fa(fm(T10, S.s01), fm(T11, S.s11)), fm(T12, S.s12));
+    float U12 = fa(fa(fm(T10, S.s02), fm(T11, S.s12)), fm(T12, S.s22));
+    float a = fa(fa(fa(fm(U00, T00), fm(U01, T01)), fm(U02, T02)), 0.3f);
+    float b = fa(fa(fm(U00, T10), fm(U01, T11)), fm(U02, T12));
+    float c = fa(fa(fa(fm(U10, T10), fm(U11, T11)), fm(U12, T12)), 0.3f);
+    float det = fs(fm(a, c), fm(b, b));
+    if (!(det > 0.0f)) return o;
+    o.A = fd(c, det);
+    o.B = fd(-b, det);
+    o.C = fd(a, det);
+    o.u = fa(fm(cam.fx, txz), cam.cx);
+    o.v = fa(fm(cam.fy, tyz), cam.cy);
+    float ex = fa(fm(__fsqrt_rn(fm(q_cut, a)), 1.0009765625f), 0.0009765625f);
+    float ey = fa(fm(__fsqrt_rn(fm(q_cut, c)), 1.0009765625f), 0.0009765625f);
+    float x0 = floorf(fm(fs(fs(o.u, ex), 0.5f), rb)), x1 = floorf(fm(fs(fa(o.u, ex), 0.5f), rb));
+    float y0 = floorf(fm(fs(fs(o.v, ey), 0.5f), rb)), y1 = floorf(fm(fs(fa(o.v, ey), 0.5f), rb));
+    x0 = fmaxf(x0, 0.0f); y0 = fmaxf(y0, 0.0f);
+    x1 = fminf(x1, (float)(TW - 1)); y1 = fminf(y1, (float)(TH - 1));
+    if (!(x0 <= x1) || !(y0 <= y1)) { o.status = 2; return o; }
+    o.x0 = (int)x0; o.x1 = (int)x1; o.y0 = (int)y0; o.y1 = (int)y1;
+    o.status = 1;
+    return o;
+}
+
+template <int LC, int LV, bool UA>
+__global__ void __launch_bounds__(128) k_project(ProjectArgs a)
+{
+    extern __shared__ gavis_camera s_cams[];
+    for (int i = threadIdx.x; i < a.nv; i += blockDim.x) s_cams[i] = a.cams[i];
+    __syncthreads();
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.n) return;
+    const float mx = a.means[3 * g], my = a.means[3 * g + 1], mz = a.means[3 * g + 2];
+    const float sc[3] = {a.scales[3 * g], a.scales[3 * g + 1], a.scales[3 * g + 2]};
+    const float4 q = reinterpret_cast<const float4 *>(a.rots)[g];
+    const float op = a.opac[g];
+    const Sigma3 S = sigma3d(sc, q.x, q.y, q.z, q.w);
+    const float rb = 1.0f / (float)a.tile;
+
+    constexpr int KC = (LC + 1) * (LC + 1);
+    constexpr int KV = (LV + 1) * (LV + 1);
+    constexpr int KM = KC > KV ? KC : KV;
+    constexpr int LM = LC > LV ? LC : LV;
+    float th[UA ? KC * 3 : 1];
+    float gm[UA ? KV : 1];
+    if (UA) {
+#pragma unroll
+        for (int j = 0; j < KC * 3; ++j) th[j] = ld_coef(a.sh, (size_t)g * KC * 3 + j, a.sh_dtype);
+#pragma unroll
+        for (int j = 0; j < KV; ++j) gm[j] = a.gamma ? ld_coef(a.gamma, (size_t)g * KV + j, a.vf_dtype) : 0.0f;
+    }
+    const float P = (float)a.n_train;
+
+    for (int v = 0; v < a.nv; ++v) {
+        const gavis_camera &cam = s_cams[v];
+        const Proj p = project_one(cam, mx, my, mz, S, a.q_cut, rb, a.TW, a.TH);
+        const size_t r = (size_t)v * (size_t)a.n + (size_t)g;
+        if (p.status != 1) {
+            a.counts[r] = 0u;
+            continue;
+        }
+        a.counts[r] = (uint32_t)((p.x1 - p.x0 + 1) * (p.y1 - p.y0 + 1));
+        a.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.x1 << 16), (uint32_t)p.y0 | ((uint32_t)p.y1 << 16));
+        GeoRec gr;
+        gr.a = make_float4(p.u, p.v, p.A, fa(p.B, p.B));
+        gr.b = make_float4(p.C, op, p.z, 0.0f);
+        a.geo[r] = gr;
+        if (UA) {
+            float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
+            float rn = rsqrtf(dx * dx + dy * dy + dz * dz);
+            float Y[KM];
+            sh_basis<LM>(dx * rn, dy * rn, dz * rn, Y);
+            float col[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int j = 0; j < KC; ++j) {
+                col[0] = fmaf(th[3 * j], Y[j], col[0]);
+                col[1] = fmaf(th[3 * j + 1], Y[j], col[1]);
+                col[2] = fmaf(th[3 * j + 2], Y[j], col[2]);
+            }
+            float V = 0.0f;
+            if (a.n_train > 0) {
+                float vt = 0.0f;
+#pragma unroll
+                for (int j = 0; j < KV; ++j) vt = fmaf(gm[j], Y[j], vt);
+                vt = fminf(fmaxf(vt, 0.0f), P);
+                V = -expm1f(P * log1pf(-vt / P));
+                V = fminf(fmaxf(V, 0.0f), 1.0f);
+            }
+            const float nv1 = 1.0f - V;
+            UaRec ur;
+            ur.a = make_float4(V + a.beta * nv1, a.o0 * (1.0f - a.beta) * nv1, V, col[0]);
+            ur.b = make_float4(col[1], col[2], 0.0f, 0.0f);
+            a.ua[r] = ur;
+        }
+    }
+}
+
+template <int LV>
+__global__ void __launch_bounds__(128) k_query(QueryArgs a)
+{
+    extern __shared__ gavis_camera s_cams[];
+    for (int i = threadIdx.x; i < a.nv; i += blockDim.x) s_cams[i] = a.cams[i];
+    __syncthreads();
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.n) return;
+    constexpr int KV = (LV + 1) * (LV + 1);
+    float gm[KV];
+#pragma unroll
+    for (int j = 0; j < KV; ++j) gm[j] = a.gamma ? ld_coef(a.gamma, (size_t)g * KV + j, a.vf_dtype) : 0.0f;
+    const float mx = a.means[3 * g], my = a.means[3 * g + 1], mz = a.means[3 * g + 2];
+    const float P = (float)a.n_train;
+    for (int v = 0; v < a.nv; ++v) {
+        const gavis_camera &cam = s_cams[v];
+        float V = 0.0f;
+        if (a.n_train > 0) {
+            float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
+            float rn = rsqrtf(dx * dx + dy * dy + dz * dz);
+            float Y[KV];
+            sh_basis<LV>(dx * rn, dy * rn, dz * rn, Y);
+            float vt = 0.0f;
+#pragma unroll
+            for (int j = 0; j < KV; ++j) vt = fmaf(gm[j], Y[j], vt);
+            vt = fminf(fmaxf(vt, 0.0f), P);
+            V = fminf(fmaxf(-expm1f(P * log1pf(-vt / P)), 0.0f), 1.0f);
+        }
+        a.V[(size_t)v * a.n + g] = V;
+    }
+}
+
+template <int LC, int LV>
+cudaError_t launch_ua(const ProjectArgs &a, cudaStream_t s, int blocks, size_t smem)
+{
+    k_project<LC, LV, true><<<blocks, 128, smem, s>>>(a); count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s)
+{
+    if (a.n == 0 || a.nv == 0) return cudaSuccess;
+    const int blocks = (int)((a.n + 127) / 128);
+    const size_t smem = sizeof(gavis_camera) * (size_t)a.nv;
+    if (smem > 48 * 1024) {
+        // opt in to larger dynamic shared memory for big batches
+        cudaFuncSetAttribute(k_project<0, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    if (!a.ua) {
+        k_project<0, 0, false><<<blocks, 128, smem, s>>>(a); count_launch();
+        return cudaGetLastError();
+    }
+#define GAVIS_UA_CASE(LC, LV)                                                                            \
+    if (a.sh_degree == LC && a.vf_degree == LV) {                                                        \
+        if (smem > 48 * 1024)                                                                            \
+            cudaFuncSetAttribute(k_project<LC, LV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                 (int)smem);                                                             \
+        return launch_ua<LC, LV>(a, s, blocks, smem);                                                    \
+    }
+    GAVIS_UA_CASE(0, 0) GAVIS_UA_CASE(0, 1) GAVIS_UA_CASE(0, 2) GAVIS_UA_CASE(0, 3)
+    GAVIS_UA_CASE(1, 0) GAVIS_UA_CASE(1, 1) GAVIS_UA_CASE(1, 2) GAVIS_UA_CASE(1, 3)
+    GAVIS_UA_CASE(2, 0) GAVIS_UA_CASE(2, 1) GAVIS_UA_CASE(2, 2) GAVIS_UA_CASE(2, 3)
+    GAVIS_UA_CASE(3, 0) GAVIS_UA_CASE(3, 1) GAVIS_UA_CASE(3, 2) GAVIS_UA_CASE(3, 3)
+#undef GAVIS_UA_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_query(const QueryArgs &a, cudaStream_t s)
+{
+    if (a.n == 0 || a.nv == 0) return cudaSuccess;
+    const int blocks = (int)((a.n + 127) / 128);
+    const size_t smem = sizeof(gavis_camera) * (size_t)a.nv;
+    switch (a.vf_degree) {
+    case 0: if (smem > 48 * 1024) cudaFuncSetAttribute(k_query<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_query<0><<<blocks, 128, smem, s>>>(a); count_launch(); break;
+    case 1: if (smem > 48 * 1024) cudaFuncSetAttribute(k_query<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_query<1><<<blocks, 128, smem, s>>>(a); count_launch(); break;
+    case 2: if (smem > 48 * 1024) cudaFuncSetAttribute(k_query<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_query<2><<<blocks, 128, smem, s>>>(a); count_launch(); break;
+    case 3: if (smem > 48 * 1024) cudaFuncSetAttribute(k_query<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_query<3><<<blocks, 128, smem, s>>>(a); count_launch(); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gavis

@@ -1,0 +1,461 @@
+// raster.cu -- tile binning, per-tile front-to-back compositing and the
+// reductions of the GAVIS hot path.
+//
+//   k_emit            one key per (view, Gaussian, tile of its rectangle)
+//   k_ranges          [start, end) of every (view, tile) in the sorted keys
+//   k_composite_ua    Alg. "3DGS Uncertainty Quantification with Visibility
+//                     Field" + plain colour (eq:orig_vr), one thread per pixel
+//   k_composite_vis   Alg. "Single-view Particle Visibility", one thread per
+//                     pixel, per-Gaussian sums reduced across the tile
+//   k_view_reduce     per-view mean of the per-pixel entropy (eq:id)
+//   k_argmax          next-best view (eq:i_gain)
+//   k_vf_accumulate   gamma_lm += v a_l Y_lm(d_p) (eq:vis_gamma)
+//
+// Compositing stages the tile's list in shared memory in batches of one entry
+// per thread (gathered from the per-view records by Gaussian index) and loops
+// over the batch per pixel.  The footprint value q of a (pixel, Gaussian) pair
+// uses explicit round-to-nearest operations in a fixed order, so the overlap
+// decision q <= q_cut is reproducible bit for bit.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "gavis_internal.cuh"
+#include "sh_basis.cuh"
+
+namespace gavis {
+namespace {
+
+__device__ __forceinline__ float footprint_q(float px, float py, float u, float v, float A, float B2, float C)
+{
+    const float dx = __fsub_rn(px, u), dy = __fsub_rn(py, v);
+    const float qa = __fmul_rn(A, dx);
+    const float qb = __fmaf_rn(B2, dy, qa);
+    const float qc = __fmul_rn(C, dy);
+    const float qd = __fmul_rn(qc, dy);
+    return __fmaf_rn(qb, dx, qd);
+}
+
+__global__ void k_emit(const uint2 *rect, const GeoRec *geo, const uint32_t *counts, const uint32_t *offsets,
+                       int nv, int64_t n, int TW, int TH, uint64_t *keys, uint32_t *vals)
+{
+    const size_t total = (size_t)nv * (size_t)n;
+    const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= total) return;
+    if (counts[r] == 0u) return;
+    const uint32_t v = (uint32_t)(r / (size_t)n);
+    const uint32_t g = (uint32_t)(r - (size_t)v * (size_t)n);
+    const uint2 rc = rect[r];
+    const uint32_t x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu, y1 = rc.y >> 16;
+    const uint32_t zb = __float_as_uint(geo[r].b.z);
+    uint32_t off = offsets[r];
+    const uint64_t vbase = (uint64_t)v * (uint64_t)(TW * TH);
+    for (uint32_t ty = y0; ty <= y1; ++ty)
+        for (uint32_t tx = x0; tx <= x1; ++tx) {
+            keys[off] = ((vbase + (uint64_t)(ty * (uint32_t)TW + tx)) << 32) | (uint64_t)zb;
+            vals[off] = g;
+            ++off;
+        }
+}
+
+__global__ void k_ranges(const uint64_t *keys, size_t M, uint2 *ranges)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const uint32_t t = (uint32_t)(keys[i] >> 32);
+    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = (uint32_t)i;
+    if (i == M - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = (uint32_t)(i + 1);
+}
+
+template <int TILE>
+__global__ void __launch_bounds__(TILE *TILE) k_composite_ua(CompositeArgs a)
+{
+    constexpr int NT = TILE * TILE;
+    __shared__ float4 s_g0[NT];   // u, v, A, 2B
+    __shared__ float2 s_g1[NT];   // C, opacity
+    __shared__ float4 s_u0[NT];   // a1, a0, V, r
+    __shared__ float2 s_u1[NT];   // g, b
+    __shared__ float s_red[NT / 32];
+    __shared__ uint32_t s_pairs[NT / 32];
+
+    const int tiles = a.TW * a.TH;
+    const int vb = blockIdx.x / tiles;
+    const int t = blockIdx.x - vb * tiles;
+    const int tx = t % a.TW, ty = t / a.TW;
+    const int tid = threadIdx.x;
+    const int i = tx * TILE + (tid % TILE), j = ty * TILE + (tid / TILE);
+    const bool inside = i < a.W && j < a.H;
+    const float px = (float)i + 0.5f, py = (float)j + 0.5f;
+    const uint2 rg = a.ranges[blockIdx.x];
+    const size_t vrow = (size_t)vb * (size_t)a.n;
+    const RasterConsts rc = a.rc;
+
+    float T = 1.0f, Tc = 1.0f, Hs = 0.0f, w0 = 0.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
+    bool ua_on = inside, rgb_on = inside;
+    uint32_t npairs = 0;
+
+    for (uint32_t base = rg.x; base < rg.y; base += NT) {
+        if (__syncthreads_count(ua_on || rgb_on) == 0) break;
+        const uint32_t e = base + tid;
+        if (e < rg.y) {
+            const size_t r = vrow + a.vals[e];
+            const GeoRec gr = a.geo[r];
+            const UaRec ur = a.ua[r];
+            s_g0[tid] = gr.a;
+            s_g1[tid] = make_float2(gr.b.x, gr.b.y);
+            s_u0[tid] = ur.a;
+            s_u1[tid] = make_float2(ur.b.x, ur.b.y);
+        }
+        __syncthreads();
+        const int cnt = (int)min((uint32_t)NT, rg.y - base);
+        for (int k = 0; k < cnt && (ua_on || rgb_on); ++k) {
+            const float4 g0 = s_g0[k];
+            const float2 g1 = s_g1[k];
+            const float q = footprint_q(px, py, g0.x, g0.y, g0.z, g0.w, g1.x);
+            if (!(q <= rc.q_cut)) continue;
+            ++npairs;
+            const float alpha = g1.y * __expf(-0.5f * q);
+            if (rgb_on) {
+                const float4 u0 = s_u0[k];
+                const float2 u1 = s_u1[k];
+                const float w = alpha * Tc;
+                cr = fmaf(w, u0.w, cr);
+                cg = fmaf(w, u1.x, cg);
+                cb = fmaf(w, u1.y, cb);
+                Tc = Tc * (1.0f - alpha);
+                if (Tc < rc.eps_T) rgb_on = false;
+            }
+            if (ua_on) {
+                const float4 u0 = s_u0[k];
+                const float as = fmaf(alpha, u0.x, u0.y);   // eq:alpha_comp
+                const float w = as * T;
+                const float wv = w * u0.z;                   // weight of the visible component
+                if (wv > 1e-30f) Hs = fmaf(wv, rc.k_c - __logf(wv), Hs);
+                w0 = fmaf(w, 1.0f - u0.z, w0);                // weight of the prior component
+                T = T * (1.0f - as);
+                if (T < rc.eps_T) ua_on = false;
+            }
+        }
+    }
+    float h = 0.0f;
+    if (inside) {
+        if (w0 > 1e-30f) Hs = fmaf(w0, rc.k_0 - __logf(w0), Hs);   // invisible component of eq:huber
+        const size_t vg = (size_t)(a.v0 + vb);
+        const size_t pix = (size_t)j * a.W + i;
+        const size_t plane = (size_t)a.W * a.H;
+        if (a.unc) a.unc[vg * plane + pix] = Hs;
+        if (a.rgb) {
+            a.rgb[(vg * 3 + 0) * plane + pix] = cr;
+            a.rgb[(vg * 3 + 1) * plane + pix] = cg;
+            a.rgb[(vg * 3 + 2) * plane + pix] = cb;
+        }
+        h = Hs;
+    }
+    // tile partial sum of the per-pixel entropy (fixed order: deterministic)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_down_sync(0xffffffffu, h, o);
+    const uint32_t wp = __reduce_add_sync(0xffffffffu, npairs);
+    if ((tid & 31) == 0) {
+        s_red[tid >> 5] = h;
+        s_pairs[tid >> 5] = wp;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float s = 0.0f;
+        unsigned long long np = 0;
+        for (int w = 0; w < NT / 32; ++w) {
+            s += s_red[w];
+            np += s_pairs[w];
+        }
+        a.tile_sums[blockIdx.x] = s;
+        if (a.pairs && np) atomicAdd(a.pairs, np);
+    }
+}
+
+template <int TILE>
+__global__ void __launch_bounds__(TILE *TILE) k_composite_vis(CompositeArgs a)
+{
+    constexpr int NT = TILE * TILE;
+    __shared__ float4 s_g0[NT];
+    __shared__ float2 s_g1[NT];
+    __shared__ unsigned long long s_sum[NT];
+    __shared__ uint32_t s_cnt[NT];
+    __shared__ uint32_t s_idx[NT];
+
+    const int tiles = a.TW * a.TH;
+    const int vb = blockIdx.x / tiles;
+    const int t = blockIdx.x - vb * tiles;
+    const int tx = t % a.TW, ty = t / a.TW;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int i = tx * TILE + (tid % TILE), j = ty * TILE + (tid / TILE);
+    const bool inside = i < a.W && j < a.H;
+    const float px = (float)i + 0.5f, py = (float)j + 0.5f;
+    const uint2 rg = a.ranges[blockIdx.x];
+    const size_t vrow = (size_t)vb * (size_t)a.n;
+    const float eps = a.rc.eps_T, qcut = a.rc.q_cut;
+
+    float T = 1.0f;
+    bool on = inside;
+    uint32_t wpairs = 0;
+    s_sum[tid] = 0ull;
+    s_cnt[tid] = 0u;
+
+    for (uint32_t base = rg.x; base < rg.y; base += NT) {
+        if (__syncthreads_count(on) == 0) break;
+        const uint32_t e = base + tid;
+        if (e < rg.y) {
+            const uint32_t g = a.vals[e];
+            const GeoRec gr = a.geo[vrow + g];
+            s_g0[tid] = gr.a;
+            s_g1[tid] = make_float2(gr.b.x, gr.b.y);
+            s_idx[tid] = g;
+        }
+        __syncthreads();
+        const int cnt = (int)min((uint32_t)NT, rg.y - base);
+        for (int k = 0; k < cnt; ++k) {
+            if (!__any_sync(0xffffffffu, on)) break;   // warp-uniform
+            const float4 g0 = s_g0[k];
+            const float2 g1 = s_g1[k];
+            const float q = footprint_q(px, py, g0.x, g0.y, g0.z, g0.w, g1.x);
+            const bool hit = on && (q <= qcut);
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (m) {
+                wpairs += (uint32_t)__popc(m);
+                const uint32_t tq = hit ? __float2uint_rn(T * kTScale) : 0u;
+                const uint32_t s = __reduce_add_sync(0xffffffffu, tq);
+                if (lane == 0) {
+                    atomicAdd(&s_sum[k], (unsigned long long)s);
+                    atomicAdd(&s_cnt[k], (uint32_t)__popc(m));
+                }
+            }
+            if (hit) {
+                const float alpha = g1.y * __expf(-0.5f * q);
+                T = T * (1.0f - alpha);
+                if (T < eps) on = false;
+            }
+        }
+        __syncthreads();
+        if (tid < cnt && s_cnt[tid] > 0u) {
+            const size_t r = vrow + s_idx[tid];
+            atomicAdd(&a.sumT[r], s_sum[tid]);
+            atomicAdd(&a.cnt[r], s_cnt[tid]);
+        }
+        s_sum[tid] = 0ull;
+        s_cnt[tid] = 0u;
+    }
+    if (a.pairs && lane == 0 && wpairs) atomicAdd(a.pairs, (unsigned long long)wpairs);
+}
+
+__global__ void k_view_reduce(const float *tile_sums, int tiles, float inv_pixels, float *score)
+{
+    __shared__ float s[256];
+    const float *ts = tile_sums + (size_t)blockIdx.x * tiles;
+    float acc = 0.0f;
+    for (int k = threadIdx.x; k < tiles; k += 256) acc += ts[k];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) score[blockIdx.x] = s[0] * inv_pixels;
+}
+
+__global__ void k_argmax(const float *score, int n, int32_t *best)
+{
+    __shared__ float sv[1024];
+    __shared__ int si[1024];
+    float bv = -INFINITY;
+    int bi = 0x7fffffff;
+    for (int k = threadIdx.x; k < n; k += 1024) {
+        float x = score[k];
+        if (x > bv || (x == bv && k < bi)) { bv = x; bi = k; }
+    }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            float x = sv[threadIdx.x + o];
+            int xi = si[threadIdx.x + o];
+            if (x > sv[threadIdx.x] || (x == sv[threadIdx.x] && xi < si[threadIdx.x])) {
+                sv[threadIdx.x] = x;
+                si[threadIdx.x] = xi;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *best = si[0] == 0x7fffffff ? -1 : si[0];
+}
+
+template <int L>
+__global__ void __launch_bounds__(128) k_vf_accumulate(AccumArgs a)
+{
+    extern __shared__ gavis_camera s_cams[];
+    for (int k = threadIdx.x; k < a.nv; k += blockDim.x) s_cams[k] = a.cams[k];
+    __syncthreads();
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.n) return;
+    constexpr int K = (L + 1) * (L + 1);
+    float acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = a.gamma32[(size_t)g * K + k];
+    const float mx = a.means[3 * g], my = a.means[3 * g + 1], mz = a.means[3 * g + 2];
+    for (int v = 0; v < a.nv; ++v) {
+        const size_t r = (size_t)v * (size_t)a.n + (size_t)g;
+        const uint32_t c = a.cnt[r];
+        if (c == 0u) continue;   // Phi = 0: no pixel of this view reaches g
+        const float vis = (float)a.sumT[r] * (1.0f / kTScale) / (float)c;
+        const gavis_camera &cam = s_cams[v];
+        const float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
+        const float rn = rsqrtf(dx * dx + dy * dy + dz * dz);
+        float Y[K];
+        sh_basis<L>(dx * rn, dy * rn, dz * rn, Y);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int l = k >= 9 ? 3 : (k >= 4 ? 2 : (k >= 1 ? 1 : 0));
+            acc[k] = fmaf(vis * a.a_l[l], Y[k], acc[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) a.gamma32[(size_t)g * K + k] = acc[k];
+}
+
+__global__ void k_vf_store(const float *src, size_t count, void *out, int dtype, int accumulate)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float x = src[i];
+    if (dtype == GAVIS_F16) {
+        __half *o = reinterpret_cast<__half *>(out);
+        o[i] = __float2half_rn(x);
+    } else if (dtype == GAVIS_BF16) {
+        __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(out);
+        o[i] = __float2bfloat16_rn(x);
+    } else {
+        reinterpret_cast<float *>(out)[i] = x;
+    }
+    (void)accumulate;
+}
+
+__global__ void k_vf_load(const void *in, int dtype, size_t count, float *dst)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float x;
+    if (dtype == GAVIS_F16) x = __half2float(reinterpret_cast<const __half *>(in)[i]);
+    else if (dtype == GAVIS_BF16) x = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(in)[i]);
+    else x = reinterpret_cast<const float *>(in)[i];
+    dst[i] = x;
+}
+
+__global__ void k_vis_export(const unsigned long long *sumT, const uint32_t *cnt, size_t count, float *sumT_f,
+                             uint32_t *cnt_out)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    if (sumT_f) sumT_f[i] = (float)((double)sumT[i] * (1.0 / 16777216.0));
+    if (cnt_out) cnt_out[i] = cnt[i];
+}
+
+inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_emit(const uint2 *rect, const GeoRec *geo, const uint32_t *counts, const uint32_t *offsets,
+                        int nv, int64_t n, int TW, int TH, uint64_t *keys, uint32_t *vals, cudaStream_t s)
+{
+    const size_t total = (size_t)nv * (size_t)n;
+    if (total == 0) return cudaSuccess;
+    k_emit<<<nblk(total, 256), 256, 0, s>>>(rect, geo, counts, offsets, nv, n, TW, TH, keys, vals); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ranges(const uint64_t *keys, size_t M, uint2 *ranges, cudaStream_t s)
+{
+    if (M == 0) return cudaSuccess;
+    k_ranges<<<nblk(M, 256), 256, 0, s>>>(keys, M, ranges); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_composite_ua(const CompositeArgs &a, cudaStream_t s)
+{
+    const unsigned blocks = (unsigned)(a.nv * a.TW * a.TH);
+    if (blocks == 0) return cudaSuccess;
+    switch (a.tile) {
+    case 8: k_composite_ua<8><<<blocks, 64, 0, s>>>(a); count_launch(); break;
+    case 16: k_composite_ua<16><<<blocks, 256, 0, s>>>(a); count_launch(); break;
+    case 32: k_composite_ua<32><<<blocks, 1024, 0, s>>>(a); count_launch(); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_composite_vis(const CompositeArgs &a, cudaStream_t s)
+{
+    const unsigned blocks = (unsigned)(a.nv * a.TW * a.TH);
+    if (blocks == 0) return cudaSuccess;
+    switch (a.tile) {
+    case 8: k_composite_vis<8><<<blocks, 64, 0, s>>>(a); count_launch(); break;
+    case 16: k_composite_vis<16><<<blocks, 256, 0, s>>>(a); count_launch(); break;
+    case 32: k_composite_vis<32><<<blocks, 1024, 0, s>>>(a); count_launch(); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_view_reduce(const float *tile_sums, int nv, int tiles_per_view, float inv_pixels, float *score,
+                               cudaStream_t s)
+{
+    if (nv == 0) return cudaSuccess;
+    k_view_reduce<<<nv, 256, 0, s>>>(tile_sums, tiles_per_view, inv_pixels, score); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_argmax(const float *score, int n, int32_t *best, cudaStream_t s)
+{
+    k_argmax<<<1, 1024, 0, s>>>(score, n, best); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vf_accumulate(const AccumArgs &a, cudaStream_t s)
+{
+    if (a.n == 0 || a.nv == 0) return cudaSuccess;
+    const unsigned blocks = nblk((size_t)a.n, 128);
+    const size_t smem = sizeof(gavis_camera) * (size_t)a.nv;
+    switch (a.L) {
+#define GAVIS_ACC_CASE(L)                                                                                   \
+    case L:                                                                                                 \
+        if (smem > 48 * 1024)                                                                               \
+            cudaFuncSetAttribute(k_vf_accumulate<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        k_vf_accumulate<L><<<blocks, 128, smem, s>>>(a); count_launch();                                                    \
+        break;
+        GAVIS_ACC_CASE(0) GAVIS_ACC_CASE(1) GAVIS_ACC_CASE(2) GAVIS_ACC_CASE(3)
+#undef GAVIS_ACC_CASE
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vf_store(const float *gamma32, size_t count, void *out, int dtype, int accumulate, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    k_vf_store<<<nblk(count, 256), 256, 0, s>>>(gamma32, count, out, dtype, accumulate); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vf_load(const void *in, int dtype, size_t count, float *gamma32, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    k_vf_load<<<nblk(count, 256), 256, 0, s>>>(in, dtype, count, gamma32); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vis_export(const unsigned long long *sumT, const uint32_t *cnt, size_t count, float *sumT_f,
+                              uint32_t *cnt_out, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    k_vis_export<<<nblk(count, 256), 256, 0, s>>>(sumT, cnt, count, sumT_f, cnt_out); count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace gavis

@@ -1,0 +1,253 @@
+// sort.cu -- device-wide exclusive scan and stable LSD radix sort of
+// (uint64 key, uint32 value) pairs.
+//
+// Radix sort: 8-bit digits, one pass per digit over [0, end_bit).  Each pass
+// is (1) a per-block digit histogram over a tile of 4096 keys, (2) an
+// exclusive scan of the histograms in digit-major order, which gives every
+// (digit, block) its output offset, and (3) a stable scatter: items are
+// ranked within a warp with __match_any_sync, warps are ordered by a shared
+// prefix, rounds of 256 items in input order, so equal digits keep their
+// input order.  Starting from index-ascending input this yields the canonical
+// (key, index) order.
+#include "gavis_internal.cuh"
+
+namespace gavis {
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 8;
+constexpr int kScanChunk = kScanThreads * kScanItems;   // 8192 elements per block
+
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long *s_warp)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) s_warp[warp] = v;
+    __syncthreads();
+    unsigned long long t = 0;
+    if (warp == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    return t;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *in, size_t n,
+                                                              unsigned long long *partials)
+{
+    __shared__ unsigned long long s_warp[32];
+    const size_t base = (size_t)blockIdx.x * kScanChunk;
+    unsigned long long v = 0;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        size_t i = base + (size_t)r * kScanThreads + threadIdx.x;
+        if (i < n) v += in[i];
+    }
+    v = block_sum_u64(v, s_warp);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+}
+
+// single block: exclusive scan of nb partials, total -> partials[nb] and *d_total
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(unsigned long long *partials, int nb,
+                                                                unsigned long long *d_total)
+{
+    __shared__ unsigned long long s[kScanThreads];
+    __shared__ unsigned long long s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += kScanThreads) {
+        int i = base + threadIdx.x;
+        unsigned long long x = i < nb ? partials[i] : 0ull;
+        s[threadIdx.x] = x;
+        __syncthreads();
+        for (int o = 1; o < kScanThreads; o <<= 1) {
+            unsigned long long y = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0ull;
+            __syncthreads();
+            s[threadIdx.x] += y;
+            __syncthreads();
+        }
+        unsigned long long carry = s_carry;
+        if (i < nb) partials[i] = carry + s[threadIdx.x] - x;
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1) s_carry = carry + s[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[nb] = s_carry;
+        if (d_total) *d_total = s_carry;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *in, uint32_t *out, size_t n,
+                                                             const unsigned long long *partials)
+{
+    __shared__ uint32_t s_warp[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t base = (size_t)blockIdx.x * kScanChunk + (size_t)threadIdx.x * kScanItems;
+    uint32_t x[kScanItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        size_t i = base + r;
+        x[r] = i < n ? in[i] : 0u;
+        sum += x[r];
+    }
+    // exclusive scan of per-thread sums across the block
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;   // inclusive over warps
+    }
+    __syncthreads();
+    uint32_t run = (uint32_t)partials[blockIdx.x] + (warp ? s_warp[warp - 1] : 0u) + inc - sum;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        size_t i = base + r;
+        if (i < n) out[i] = run;
+        run += x[r];
+    }
+}
+
+constexpr int kRsThreads = 256;
+constexpr int kRsRounds = 16;
+constexpr int kRsTile = kRsThreads * kRsRounds;   // 4096 keys per block
+constexpr int kRsWarps = kRsThreads / 32;
+
+__global__ void __launch_bounds__(kRsThreads) k_radix_hist(const uint64_t *keys, size_t n, int shift,
+                                                           uint32_t *hist, int nblocks)
+{
+    __shared__ uint32_t s_h[256];
+    s_h[threadIdx.x] = 0;
+    __syncthreads();
+    const size_t base = (size_t)blockIdx.x * kRsTile;
+    const int lane = threadIdx.x & 31;
+#pragma unroll 4
+    for (int r = 0; r < kRsRounds; ++r) {
+        size_t i = base + (size_t)r * kRsThreads + threadIdx.x;
+        int d = i < n ? (int)((keys[i] >> shift) & 255u) : 256;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (d < 256 && lane == __ffs(peers) - 1) atomicAdd(&s_h[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = s_h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const uint64_t *kin, const uint32_t *vin,
+                                                              uint64_t *kout, uint32_t *vout, size_t n, int shift,
+                                                              const uint32_t *offs, int nblocks)
+{
+    __shared__ uint32_t s_goff[256];
+    __shared__ uint32_t s_run[256];
+    __shared__ uint32_t s_wc[kRsWarps][257];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    s_goff[tid] = offs[(size_t)tid * nblocks + blockIdx.x];
+    s_run[tid] = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    const size_t base = (size_t)blockIdx.x * kRsTile;
+    for (int r = 0; r < kRsRounds; ++r) {
+        const size_t i = base + (size_t)r * kRsThreads + tid;
+        const bool valid = i < n;
+        const uint64_t k = valid ? kin[i] : 0ull;
+        const uint32_t val = valid ? vin[i] : 0u;
+        const int d = valid ? (int)((k >> shift) & 255u) : 256;
+        for (int x = tid; x < kRsWarps * 257; x += kRsThreads) (&s_wc[0][0])[x] = 0u;
+        __syncthreads();
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = (uint32_t)__popc(peers & lt);
+        if (lane == __ffs(peers) - 1) s_wc[warp][d] = (uint32_t)__popc(peers);
+        __syncthreads();
+        {
+            uint32_t run = s_run[tid];
+#pragma unroll
+            for (int w = 0; w < kRsWarps; ++w) {
+                uint32_t c = s_wc[w][tid];
+                s_wc[w][tid] = run;
+                run += c;
+            }
+            s_run[tid] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = s_goff[d] + s_wc[warp][d] + rank;
+            kout[pos] = k;
+            vout[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+size_t scan_tmp_bytes(size_t n)
+{
+    size_t nb = (n + kScanChunk - 1) / kScanChunk;
+    return (nb + 1) * sizeof(unsigned long long);
+}
+
+cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, void *tmp,
+                               unsigned long long *d_total, cudaStream_t s)
+{
+    const size_t nb = (n + kScanChunk - 1) / kScanChunk;
+    unsigned long long *partials = reinterpret_cast<unsigned long long *>(tmp);
+    if (n == 0) {
+        if (d_total) return cudaMemsetAsync(d_total, 0, sizeof(unsigned long long), s);
+        return cudaSuccess;
+    }
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partials); count_launch();
+    k_scan_partials<<<1, kScanThreads, 0, s>>>(partials, (int)nb, d_total); count_launch();
+    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partials); count_launch();
+    return cudaGetLastError();
+}
+
+size_t radix_tmp_bytes(size_t n)
+{
+    size_t nblocks = (n + kRsTile - 1) / kRsTile;
+    size_t h = 256 * nblocks;
+    size_t a = (h * sizeof(uint32_t) + 255) & ~(size_t)255;
+    return 2 * a + scan_tmp_bytes(h) + 256;
+}
+
+cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, size_t n,
+                             int end_bit, void *tmp, bool *result_in_alt, cudaStream_t s)
+{
+    *result_in_alt = false;
+    if (n <= 1) return cudaSuccess;
+    const int nblocks = (int)((n + kRsTile - 1) / kRsTile);
+    const size_t h = 256 * (size_t)nblocks;
+    const size_t a = (h * sizeof(uint32_t) + 255) & ~(size_t)255;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(tmp);
+    uint32_t *offs = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(tmp) + a);
+    void *stmp = reinterpret_cast<char *>(tmp) + 2 * a;
+    uint64_t *kin = keys, *kout = keys_alt;
+    uint32_t *vin = vals, *vout = vals_alt;
+    bool alt = false;
+    for (int shift = 0; shift < end_bit; shift += 8) {
+        k_radix_hist<<<nblocks, kRsThreads, 0, s>>>(kin, n, shift, hist, nblocks); count_launch();
+        cudaError_t e = exclusive_scan_u32(hist, offs, h, stmp, nullptr, s);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<<<nblocks, kRsThreads, 0, s>>>(kin, vin, kout, vout, n, shift, offs, nblocks); count_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        uint64_t *tk = kin; kin = kout; kout = tk;
+        uint32_t *tv = vin; vin = vout; vout = tv;
+        alt = !alt;
+    }
+    *result_in_alt = alt;
+    return cudaSuccess;
+}
+
+}  // namespace gavis

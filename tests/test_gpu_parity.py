@@ -1,0 +1,277 @@
+"""Parity of the CUDA library with the CPU oracle (element by element).
+
+Tile bins and sort keys must match bit for bit; per-pixel uncertainty, colour,
+visibility-field coefficients (as gamma/|P|), queried visibilities and view
+scores within 1e-4 absolute; the selected view must match whenever the
+oracle's top-2 gap exceeds 2e-4.  Pixels whose transmittance test lands within
+0.1% of eps_T in the float64 oracle are counted and left out of the value
+gate: float32 rounding may legitimately flip them.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenegen as sg
+from _util import GAP, TOL, compare_views, sorted_gap
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gv():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2605_30342_gb300 as pkg
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def ctx(gv):
+    c = gv.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_scene(gv, sc, sh_dtype=torch.float32):
+    return gv.Gaussians.from_numpy(sc, sh_dtype=sh_dtype)
+
+
+CASES = {
+    "tiny": dict(k=1),                                                           # 2k Gaussians, 128x128
+    "tiny_ragged": dict(k=1, n=900, n_train=3, n_cand=5, train_wh=(100, 75), cand_wh=(100, 75)),
+    "room_small": dict(k=2, n=20000, n_train=4, n_cand=4, train_wh=(160, 120), cand_wh=(200, 136)),
+}
+
+
+def case(name):
+    kw = dict(CASES[name])
+    return sg.config(kw.pop("k"), **kw)
+
+
+# --------------------------------------------------------------------------- bins / keys
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("tile", [16, 8])
+def test_bins_bit_exact(ctx, gv, name, tile):
+    c = case(name)
+    sc, cams = c["scene"], c["cand"]
+    gs = gpu_scene(gv, sc)
+    keys, vals, ranges = ctx.debug_bins(gs, cams, gv.Params(tile=tile))
+    rk, rv = oracle.bins(cams, sc, tile=tile)
+    gk = keys.cpu().numpy().view(np.uint64)
+    gvals = vals.cpu().numpy().view(np.uint32)
+    assert len(gk) == len(rk) > 0
+    assert np.array_equal(gk, rk)
+    assert np.array_equal(gvals, rv)
+    TT = ((cams[0].W + tile - 1) // tile) * ((cams[0].H + tile - 1) // tile)
+    rr = oracle.ranges(rk, len(cams) * TT)
+    assert np.array_equal(ranges.cpu().numpy().view(np.uint32), rr)
+
+
+# --------------------------------------------------------------------------- VF query
+
+@pytest.mark.parametrize("L,P,dtype", [(2, 8, torch.float32), (3, 100, torch.float32), (3, 200, torch.float16),
+                                       (1, 1, torch.float32), (0, 0, torch.float32)])
+def test_vf_query_parity(ctx, gv, L, P, dtype):
+    c = case("tiny")
+    sc = c["scene"]
+    rng = np.random.default_rng(L * 7 + P)
+    K = (L + 1) ** 2
+    gamma = rng.normal(0, 1, (sc.n, K)) * (P / 3.0 + 0.1)
+    gamma[:, 0] = np.abs(gamma[:, 0]) * 3.0
+    gamma[:50] = 0.0
+    g_dev = torch.as_tensor(gamma).to("cuda", dtype)
+    vf = gv.VisibilityField(g_dev.contiguous(), L, P, 1.0)
+    gs = gpu_scene(gv, sc)
+    V = ctx.vf_query(gs, vf, c["cand"][:4]).cpu().numpy()
+    gq = g_dev.double().cpu().numpy()
+    for v, cam in enumerate(c["cand"][:4]):
+        Vr, _ = oracle.vf_query(gq, L, P, cam, sc.means)
+        assert np.abs(V[v] - Vr).max() <= TOL
+        assert np.all(V[v][:50] == 0.0)
+
+
+# --------------------------------------------------------------------------- VF CONST
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_single_view_visibility_parity(ctx, gv, name):
+    c = case(name)
+    sc, cams = c["scene"], c["train"][:3]
+    gs = gpu_scene(gv, sc)
+    sumT, cnt = ctx.debug_visibility(gs, cams)
+    sumT, cnt = sumT.cpu().numpy(), cnt.cpu().numpy()
+    for v, cam in enumerate(cams):
+        rs, rc, amb, _ = oracle.visibility_view(cam, sc)
+        ok = ~amb
+        assert np.array_equal(cnt[v][ok], rc[ok])                    # pixel counts are integers: exact
+        vis_g = np.where(cnt[v] > 0, sumT[v] / np.maximum(cnt[v], 1), 0.0)
+        vis_r = np.where(rc > 0, rs / np.maximum(rc, 1), 0.0)
+        assert np.abs(vis_g[ok] - vis_r[ok]).max() <= TOL
+        assert (cnt[v] > 0).sum() > 10
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+def test_vf_build_parity(ctx, gv, name, dtype):
+    c = case(name)
+    sc, train = c["scene"], c["train"]
+    gs = gpu_scene(gv, sc)
+    L = c["vf_degree"]
+    vf = ctx.vf_build(gs, train, degree=L, dtype=dtype)
+    assert vf.n_train_views == len(train)
+    g = vf.coeffs.double().cpu().numpy()
+    ref, amb, _ = oracle.vf_build(train, sc, L)
+    ok = ~amb
+    P = len(train)
+    # float16 storage rounds |gamma| <= ~1.6 P to 2^-11 relative: state it and gate on it
+    tol = TOL if dtype == torch.float32 else TOL + 2.0 ** -11 * np.abs(ref[ok]).max() / P
+    err = np.abs(g[ok] - ref[ok]).max() / P
+    assert err <= tol, (err, tol)
+    assert ok.mean() > 0.8   # at least 80% of Gaussians are clear of the eps_T rounding margin
+
+
+def test_vf_build_batched_equals_plain(ctx, gv):
+    c = case("room_small")
+    gs = gpu_scene(gv, c["scene"])
+    a = ctx.vf_build(gs, c["train"], degree=3, params=gv.Params(views_per_batch=1, vf_degree=3)).coeffs
+    b = ctx.vf_build(gs, c["train"], degree=3, params=gv.Params(views_per_batch=0, vf_degree=3)).coeffs
+    assert torch.equal(a, b)   # integer visibility sums: batching changes nothing
+
+
+def test_vf_accumulate_is_additive(ctx, gv):
+    """eq:vis_gamma is a sum over views: building on P1 then adding P2 equals
+    building on P1 u P2."""
+    c = case("tiny")
+    gs = gpu_scene(gv, c["scene"])
+    full = ctx.vf_build(gs, c["train"], degree=2)
+    part = ctx.vf_build(gs, c["train"][:5], degree=2)
+    part = ctx.vf_build(gs, c["train"][5:], degree=2, out=part, accumulate=True)
+    assert part.n_train_views == full.n_train_views == len(c["train"])
+    assert torch.allclose(part.coeffs, full.coeffs, atol=1e-5)
+
+
+# --------------------------------------------------------------------------- scoring
+
+def oracle_gamma(c):
+    g, _, _ = oracle.vf_build(c["train"], c["scene"], c["vf_degree"])
+    return g.astype(np.float32)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("tile", [16, 8, 32])
+def test_score_views_parity(ctx, gv, name, tile):
+    c = case(name)
+    sc, cand = c["scene"], c["cand"]
+    L = c["vf_degree"]
+    g32 = oracle_gamma(c)
+    vf = gv.VisibilityField(torch.as_tensor(g32).cuda(), L, len(c["train"]), 1.0)
+    gs = gpu_scene(gv, sc)
+    out = ctx.score_views(gs, vf, cand, params=gv.Params(tile=tile, vf_degree=L))
+    unc, rgb, score = out["unc"].cpu().numpy(), out["rgb"].cpu().numpy(), out["score"].cpu().numpy()
+    ref = oracle.score_views(sc, g32.astype(np.float64), L, len(c["train"]), cand)
+    err, n_amb = compare_views(unc, rgb, ref)
+    npix = len(cand) * cand[0].W * cand[0].H
+    assert err <= TOL, err
+    assert n_amb <= 0.01 * npix
+    # view scores: the ambiguous pixels' actual differences are allowed for
+    amb_slack = np.array([np.abs(unc[v] - ref["unc"][v])[ref["amb"][v]].sum() / unc[v].size for v in range(len(cand))])
+    assert np.all(np.abs(score - ref["score"]) <= TOL + amb_slack)
+    if sorted_gap(ref["score"]) > GAP:
+        assert out["best"] == ref["best"]
+
+
+def test_score_batched_equals_plain(ctx, gv):
+    c = case("room_small")
+    g32 = oracle_gamma(c)
+    vf = gv.VisibilityField(torch.as_tensor(g32).cuda(), 3, len(c["train"]), 1.0)
+    gs = gpu_scene(gv, c["scene"])
+    a = ctx.score_views(gs, vf, c["cand"], params=gv.Params(views_per_batch=1, vf_degree=3))
+    b = ctx.score_views(gs, vf, c["cand"], params=gv.Params(views_per_batch=0, vf_degree=3))
+    for k in ("unc", "rgb", "score"):
+        assert torch.equal(a[k], b[k]), k
+    assert a["best"] == b["best"]
+
+
+def test_end_to_end_tiny(ctx, gv):
+    """VF CONST on the GPU feeding scoring on the GPU, against the oracle run
+    end to end on the same inputs."""
+    c = case("tiny")
+    sc = c["scene"]
+    gs = gpu_scene(gv, sc)
+    vf = ctx.vf_build(gs, c["train"], degree=2)
+    out = ctx.score_views(gs, vf, c["cand"])
+    g, amb_g, _ = oracle.vf_build(c["train"], sc, 2)
+    ref = oracle.score_views(sc, g, 2, len(c["train"]), c["cand"])
+    # Gaussians whose field is ambiguous shift V slightly: compare the scores
+    assert np.abs(out["score"].cpu().numpy() - ref["score"]).max() <= 1e-3
+    if sorted_gap(ref["score"]) > GAP:
+        assert out["best"] == ref["best"]
+
+
+# --------------------------------------------------------------------------- edge cases
+
+def test_empty_scene(ctx, gv):
+    c = case("tiny")
+    sc = c["scene"].subset(np.arange(0))
+    gs = gpu_scene(gv, sc)
+    vf = ctx.vf_build(gs, c["train"], degree=2)
+    out = ctx.score_views(gs, vf, c["cand"][:3])
+    assert torch.all(out["unc"] == 0) and torch.all(out["rgb"] == 0) and torch.all(out["score"] == 0)
+    assert out["best"] == 0
+
+
+def test_no_candidates_and_no_training_views(ctx, gv):
+    c = case("tiny")
+    gs = gpu_scene(gv, c["scene"])
+    vf = ctx.vf_build(gs, [], degree=2)
+    assert vf.n_train_views == 0 and torch.all(vf.coeffs == 0)
+    out = ctx.score_views(gs, vf, [])
+    assert out["best"] == -1
+    # |P| = 0: V = 0 everywhere, every Gaussian carries the prior (P8)
+    out = ctx.score_views(gs, vf, c["cand"][:2])
+    ref = oracle.score_views(c["scene"], np.zeros((c["scene"].n, 9)), 2, 0, c["cand"][:2])
+    err, _ = compare_views(out["unc"].cpu().numpy(), out["rgb"].cpu().numpy(), ref)
+    assert err <= TOL
+
+
+def test_all_culled_view(ctx, gv):
+    c = case("tiny")
+    gs = gpu_scene(gv, c["scene"])
+    away = sg.look_at_camera((0, 0, 3.0), (0, 0, 6.0), 64, 64)   # looks away from the cloud
+    vf = ctx.vf_build(gs, [away], degree=2)
+    assert torch.all(vf.coeffs == 0)
+    out = ctx.score_views(gs, vf, [away])
+    assert torch.all(out["unc"] == 0) and out["score"].item() == 0.0
+
+
+def test_fp16_colour_and_field(ctx, gv):
+    """Half-precision storage of colour and visibility coefficients, float32
+    compositing: parity with the oracle run on the same rounded inputs, and the
+    storage error against the float32 inputs stated."""
+    c = case("room_small")
+    sc = c["scene"]
+    g32 = oracle_gamma(c)
+    g16 = torch.as_tensor(g32).half()
+    sh16 = torch.as_tensor(sc.sh).half()
+    vf = gv.VisibilityField(g16.cuda(), 3, len(c["train"]), 1.0)
+    gs = gpu_scene(gv, sc, sh_dtype=torch.float16)
+    out = ctx.score_views(gs, vf, c["cand"])
+    ref = oracle.score_views(sc, g16.double().numpy(), 3, len(c["train"]), c["cand"], sh=sh16.double().numpy())
+    err, _ = compare_views(out["unc"].cpu().numpy(), out["rgb"].cpu().numpy(), ref)
+    assert err <= TOL
+    ref32 = oracle.score_views(sc, g32.astype(np.float64), 3, len(c["train"]), c["cand"])
+    storage_err = np.abs(out["score"].cpu().numpy() - ref32["score"]).max()
+    assert storage_err < 5e-3   # half-precision storage effect on the view score
+
+
+def test_invalid_arguments_raise(ctx, gv):
+    c = case("tiny")
+    gs = gpu_scene(gv, c["scene"])
+    cams = [c["cand"][0], sg.fibonacci_cameras(2, 3.0, 64, 64)[1]]
+    vf = ctx.vf_build(gs, c["train"][:1], degree=2)
+    with pytest.raises(gv.GavisError) as e:
+        ctx.score_views(gs, vf, cams)      # mixed resolutions
+    assert e.value.code == gv.ERR_ARG
+    with pytest.raises(gv.GavisError):
+        ctx.score_views(gs, vf, c["cand"][:1], params=gv.Params(tile=12))
