@@ -186,6 +186,35 @@ int gavis_debug_bins(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_came
 int gavis_debug_visibility(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_camera *cams,
                            int n_cams, const gavis_params *p, float *sumT, uint32_t *cnt, void *stream);
 
+/* Allocation-free scoring of ONE candidate view (no counterpart in the paper:
+ * an interface addition for callers that cannot allocate device memory).
+ * Who needs it: applications whose memory manager has already reserved the
+ * GPU's memory for its own pool, so that a raw cudaMalloc would fail or
+ * fragment that pool, and real-time loops that cannot accept the device-wide
+ * synchronisation cudaMalloc/cudaFree may imply.  The call computes exactly
+ * what gavis_score_views computes for a single camera (same kernels), but all
+ * scratch memory lives in a fixed 16 MiB array inside the library's device
+ * image; it allocates nothing (no cudaMalloc, no pinned host memory, no
+ * library allocator) and needs no context.
+ *   gs, vf: as for gavis_score_views.  cam: host, one camera.
+ *   rgb: device [3][H][W] or NULL; unc: device [H][W] or NULL; score: device [1].
+ *   err: optional host buffer of err_len bytes for the error text.
+ * Limits: n <= 32768 Gaussians, at most 4096 tiles (e.g. 1024 x 1024 pixels at
+ *   tile 16), at most 2^19 tile keys; beyond them the call returns
+ *   GAVIS_ERR_ARG (sizes) or GAVIS_ERR_BUDGET (keys) with a message and
+ *   launches nothing further.
+ * Set-up: the first call on each device looks up the array's device address
+ *   (with that device current); make that first call before any stream
+ *   capture.  The array is held by every GPU that loads this library until the
+ *   process exits.
+ * Sharing: every call on a device uses the same array, which keeps the last
+ *   call's contents; calls whose GPU work overlaps (other streams or threads)
+ *   race on it and must be serialised by the caller.
+ * Synchronises `stream` once (to read the number of tile keys). */
+int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_vf *vf, const gavis_camera *cam,
+                             const gavis_params *p, float *rgb, float *unc, float *score, char *err,
+                             size_t err_len, void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* Instrumentation (no counterpart in the paper): per-stage device time from  */
 /* CUDA events recorded on the call's stream, kernel launch counts, and the   */
