@@ -383,6 +383,7 @@ def run_gavis(args):
             "latency_ms": {"p50": percentile(step_ms, 50), "p99": percentile(step_ms, 99), "what": "one step"},
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in st.items()},
             "pairs_per_step": {"uncertainty": pairs_ua // args.steps, "visibility": pairs_vis // args.steps},
+            "tile_keys_per_step": prof["keys"] // args.steps,
             "best_view": best,
         }
         print(json.dumps(line), flush=True)

@@ -156,7 +156,7 @@ def sh_real(L: int, d) -> np.ndarray:
 def project(cam, scene, q_cut=9.0, tile=16):
     rec = cam_record(cam)
     n = scene.n
-    out = np.zeros((n, 10), np.float32)
+    out = np.zeros((n, 12), np.float32)
     st = np.zeros(n, np.int32)
     lib().oracle_project(n, _p(rec), _p(_f32(scene.means)), _p(_f32(scene.scales)),
                          _p(_f32(scene.rots)), float(q_cut), int(tile), _p(out), _p(st))

@@ -163,6 +163,7 @@ void oracle_vmf_coeffs(int L, double kappa, double *a) { vmf_coeffs(L, kappa, a)
 
 typedef struct {
     float z, u, v, A, B, C, a, c; /* depth, centre, conic, Sigma2D diagonal */
+    float ex, ey;                 /* inflated footprint half-extents */
     int x0, x1, y0, y1;           /* tile rectangle (inclusive) */
     int status;                   /* 0 culled, 1 tiles, 2 valid but no tiles */
 } oproj;
@@ -240,6 +241,8 @@ static void project_fp32(const float *cam, const float *mean, const float *scale
     /* tile rectangle from inflated footprint half-extents */
     float ex = sqrtf(qcut * a) * 1.0009765625f + 0.0009765625f;
     float ey = sqrtf(qcut * c) * 1.0009765625f + 0.0009765625f;
+    o->ex = ex;
+    o->ey = ey;
     float rb = 1.0f / (float)tile;  /* tile is a power of two: exact */
     float x0 = floorf(((o->u - ex) - 0.5f) * rb), x1 = floorf(((o->u + ex) - 0.5f) * rb);
     float y0 = floorf(((o->v - ey) - 0.5f) * rb), y1 = floorf(((o->v + ey) - 0.5f) * rb);
@@ -271,8 +274,8 @@ static uint32_t fbits(float f)
     return u;
 }
 
-/* Geometry of every Gaussian in one view.  out: n x 10 floats
- * (z, u, v, A, B, C, x0, x1, y0, y1), status: n ints. */
+/* Geometry of every Gaussian in one view.  out: n x 12 floats
+ * (z, u, v, A, B, C, x0, x1, y0, y1, ex, ey), status: n ints. */
 void oracle_project(int64_t n, const float *cam, const float *means, const float *scales,
                     const float *rots, double qcut, int tile, float *out, int32_t *status)
 {
@@ -280,9 +283,10 @@ void oracle_project(int64_t n, const float *cam, const float *means, const float
     for (int64_t g = 0; g < n; ++g) {
         oproj p;
         project_fp32(cam, means + 3 * g, scales + 3 * g, rots + 4 * g, (float)qcut, tile, &p);
-        float *o = out + 10 * g;
+        float *o = out + 12 * g;
         o[0] = p.z; o[1] = p.u; o[2] = p.v; o[3] = p.A; o[4] = p.B; o[5] = p.C;
         o[6] = (float)p.x0; o[7] = (float)p.x1; o[8] = (float)p.y0; o[9] = (float)p.y1;
+        o[10] = p.ex; o[11] = p.ey;
         status[g] = p.status;
     }
 }

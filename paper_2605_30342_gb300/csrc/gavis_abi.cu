@@ -53,6 +53,7 @@ struct gavis_ctx {
     double prof_ms[GAVIS_STAGE_COUNT] = {};
     long long prof_launches[GAVIS_STAGE_COUNT] = {};
     unsigned long long *d_pairs = nullptr;   // device [2]
+    unsigned long long prof_keys = 0;        // tile keys sorted since gavis_prof_enable
 };
 
 namespace {
@@ -390,6 +391,7 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     CK(cudaStreamSynchronize(s));
     const unsigned long long M = *ctx->h_total;
     if (M >= (1ull << 32) - 1) return fail(ctx, GAVIS_ERR_BUDGET, "more than 2^32 keys in one batch");
+    if (ctx->prof_on) ctx->prof_keys += M;
 
     KeyLayout KL = key_layout(nullptr, (size_t)M);
     if ((rc = ensure(ctx, ctx->keys, KL.bytes)) != GAVIS_OK) return rc;
@@ -570,6 +572,7 @@ int gavis_prof_enable(gavis_ctx *ctx, int on)
         ctx->prof_ms[k] = 0.0;
         ctx->prof_launches[k] = 0;
     }
+    ctx->prof_keys = 0;
     ctx->prof_on = on != 0;
     return GAVIS_OK;
 }
@@ -597,6 +600,7 @@ int gavis_prof_read(gavis_ctx *ctx, double *ms, int64_t *launches, int64_t *tota
         if (ctx->d_pairs) CK(cudaMemcpy(h, ctx->d_pairs, sizeof(h), cudaMemcpyDeviceToHost));
         pairs[0] = h[0];
         pairs[1] = h[1];
+        pairs[2] = ctx->prof_keys;
     }
     return GAVIS_OK;
 }

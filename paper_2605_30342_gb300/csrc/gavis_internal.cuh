@@ -1,8 +1,9 @@
 // gavis_internal.cuh -- shared declarations of the CUDA translation units.
 //
 // Record layouts (HBM, one entry per (view-in-batch, Gaussian), index v*N + g):
-//   GeoRec  32 B  a = (u, v, A, 2B)  b = (C, opacity, depth z, 0)
-//           image-space centre and conic of the projected Gaussian.
+//   GeoRec  32 B  a = (u, v, A, 2B)  b = (C, opacity, depth z, ext)
+//           image-space centre and conic of the projected Gaussian; ext packs
+//           the footprint half-extents (ex, ey) as two halves rounded up.
 //   UaRec   32 B  a = (a1, a0, V, r)  b = (g, b, 0, 0)
 //           alpha* = a1 * alpha + a0 (eq:alpha_comp, a1 = V + beta(1-V),
 //           a0 = o0(1-beta)(1-V)), the queried visibility V (eq:vis_bound) and

@@ -72,7 +72,7 @@ __device__ __forceinline__ Sigma3 sigma3d(const float *sc, float qw, float qx, f
 }
 
 struct Proj {
-    float z, u, v, A, B, C;
+    float z, u, v, A, B, C, ex, ey;
     int x0, x1, y0, y1;
     int status;   // 0 culled, 1 has tiles, 2 valid but off-screen
 };
@@ -83,7 +83,7 @@ __device__ __forceinline__ Proj project_one(const gavis_camera &cam, float x, fl
     Proj o;
     o.status = 0;
     o.x0 = o.x1 = o.y0 = o.y1 = 0;
-    o.u = o.v = o.A = o.B = o.C = 0.0f;
+    o.u = o.v = o.A = o.B = o.C = o.ex = o.ey = 0.0f;
     const float *R = cam.R, *t = cam.t;
     float tx = fa(fa(fa(fm(R[0], x), fm(R[1], y)), fm(R[2], z)), t[0]);
     float ty = fa(fa(fa(fm(R[3], x), fm(R[4], y)), fm(R[5], z)), t[1]);
@@ -119,6 +119,8 @@ __device__ __forceinline__ Proj project_one(const gavis_camera &cam, float x, fl
     o.v = fa(fm(cam.fy, tyz), cam.cy);
     float ex = fa(fm(__fsqrt_rn(fm(q_cut, a)), 1.0009765625f), 0.0009765625f);
     float ey = fa(fm(__fsqrt_rn(fm(q_cut, c)), 1.0009765625f), 0.0009765625f);
+    o.ex = ex;
+    o.ey = ey;
     float x0 = floorf(fm(fs(fs(o.u, ex), 0.5f), rb)), x1 = floorf(fm(fs(fa(o.u, ex), 0.5f), rb));
     float y0 = floorf(fm(fs(fs(o.v, ey), 0.5f), rb)), y1 = floorf(fm(fs(fa(o.v, ey), 0.5f), rb));
     x0 = fmaxf(x0, 0.0f); y0 = fmaxf(y0, 0.0f);
@@ -170,7 +172,10 @@ __global__ void __launch_bounds__(128) k_project(ProjectArgs a)
         a.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.x1 << 16), (uint32_t)p.y0 | ((uint32_t)p.y1 << 16));
         GeoRec gr;
         gr.a = make_float4(p.u, p.v, p.A, fa(p.B, p.B));
-        gr.b = make_float4(p.C, op, p.z, 0.0f);
+        // footprint half-extents, rounded up to half precision (conservative)
+        const uint32_t ext = (uint32_t)__half_as_ushort(__float2half_ru(p.ex)) |
+                             ((uint32_t)__half_as_ushort(__float2half_ru(p.ey)) << 16);
+        gr.b = make_float4(p.C, op, p.z, __uint_as_float(ext));
         a.geo[r] = gr;
         if (UA) {
             float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];

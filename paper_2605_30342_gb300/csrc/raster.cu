@@ -13,7 +13,9 @@
 //
 // Compositing stages the tile's list in shared memory in batches of one entry
 // per thread (gathered from the per-view records by Gaussian index) and loops
-// over the batch per pixel.  The footprint value q of a (pixel, Gaussian) pair
+// over the batch per pixel.  Each warp covers an 8 x 4 pixel block and skips,
+// as a whole, the entries whose footprint box (half-extents rounded up) misses
+// the block's pixel centres; those entries have q > q_cut at all its pixels.  The footprint value q of a (pixel, Gaussian) pair
 // uses explicit round-to-nearest operations in a fixed order, so the overlap
 // decision q <= q_cut is reproducible bit for bit.
 #include <cuda_bf16.h>
@@ -24,6 +26,20 @@
 
 namespace gavis {
 namespace {
+
+// footprint box (x0, x1, y0, y1) from the packed half-extents
+__device__ __forceinline__ float4 footprint_box(float u, float v, float ext_bits)
+{
+    const uint32_t e = __float_as_uint(ext_bits);
+    const float ex = __half2float(__ushort_as_half((unsigned short)(e & 0xffffu)));
+    const float ey = __half2float(__ushort_as_half((unsigned short)(e >> 16)));
+    return make_float4(u - ex, u + ex, v - ey, v + ey);
+}
+
+__device__ __forceinline__ bool box_misses(const float4 b, float bx0, float bx1, float by0, float by1)
+{
+    return b.y < bx0 || b.x > bx1 || b.w < by0 || b.z > by1;
+}
 
 __device__ __forceinline__ float footprint_q(float px, float py, float u, float v, float A, float B2, float C)
 {
@@ -70,10 +86,12 @@ template <int TILE>
 __global__ void __launch_bounds__(TILE *TILE) k_composite_ua(CompositeArgs a)
 {
     constexpr int NT = TILE * TILE;
-    __shared__ float4 s_g0[NT];   // u, v, A, 2B
-    __shared__ float2 s_g1[NT];   // C, opacity
-    __shared__ float4 s_u0[NT];   // a1, a0, V, r
-    __shared__ float2 s_u1[NT];   // g, b
+    constexpr int NB = NT < 256 ? NT : 256;   // entries staged per batch
+    __shared__ float4 s_g0[NB];   // u, v, A, 2B
+    __shared__ float2 s_g1[NB];   // C, opacity
+    __shared__ float4 s_u0[NB];   // a1, a0, V, r
+    __shared__ float2 s_u1[NB];   // g, b
+    __shared__ float4 s_box[NB];  // footprint box
     __shared__ float s_red[NT / 32];
     __shared__ uint32_t s_pairs[NT / 32];
 
@@ -81,8 +99,11 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite_ua(CompositeArgs a)
     const int vb = blockIdx.x / tiles;
     const int t = blockIdx.x - vb * tiles;
     const int tx = t % a.TW, ty = t / a.TW;
-    const int tid = threadIdx.x;
-    const int i = tx * TILE + (tid % TILE), j = ty * TILE + (tid / TILE);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wx = (warp % (TILE / 8)) * 8, wy = (warp / (TILE / 8)) * 4;
+    const int i = tx * TILE + wx + (lane & 7), j = ty * TILE + wy + (lane >> 3);
+    const float bx0 = (float)(tx * TILE + wx) + 0.5f, bx1 = bx0 + 7.0f;
+    const float by0 = (float)(ty * TILE + wy) + 0.5f, by1 = by0 + 3.0f;
     const bool inside = i < a.W && j < a.H;
     const float px = (float)i + 0.5f, py = (float)j + 0.5f;
     const uint2 rg = a.ranges[blockIdx.x];
@@ -93,10 +114,10 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite_ua(CompositeArgs a)
     bool ua_on = inside, rgb_on = inside;
     uint32_t npairs = 0;
 
-    for (uint32_t base = rg.x; base < rg.y; base += NT) {
+    for (uint32_t base = rg.x; base < rg.y; base += NB) {
         if (__syncthreads_count(ua_on || rgb_on) == 0) break;
         const uint32_t e = base + tid;
-        if (e < rg.y) {
+        if (tid < NB && e < rg.y) {
             const size_t r = vrow + a.vals[e];
             const GeoRec gr = a.geo[r];
             const UaRec ur = a.ua[r];
@@ -104,10 +125,12 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite_ua(CompositeArgs a)
             s_g1[tid] = make_float2(gr.b.x, gr.b.y);
             s_u0[tid] = ur.a;
             s_u1[tid] = make_float2(ur.b.x, ur.b.y);
+            s_box[tid] = footprint_box(gr.a.x, gr.a.y, gr.b.w);
         }
         __syncthreads();
-        const int cnt = (int)min((uint32_t)NT, rg.y - base);
+        const int cnt = (int)min((uint32_t)NB, rg.y - base);
         for (int k = 0; k < cnt && (ua_on || rgb_on); ++k) {
+            if (box_misses(s_box[k], bx0, bx1, by0, by1)) continue;   // uniform across the warp
             const float4 g0 = s_g0[k];
             const float2 g1 = s_g1[k];
             const float q = footprint_q(px, py, g0.x, g0.y, g0.z, g0.w, g1.x);
@@ -175,18 +198,23 @@ template <int TILE>
 __global__ void __launch_bounds__(TILE *TILE) k_composite_vis(CompositeArgs a)
 {
     constexpr int NT = TILE * TILE;
-    __shared__ float4 s_g0[NT];
-    __shared__ float2 s_g1[NT];
-    __shared__ unsigned long long s_sum[NT];
-    __shared__ uint32_t s_cnt[NT];
-    __shared__ uint32_t s_idx[NT];
+    constexpr int NB = NT < 256 ? NT : 256;   // entries staged per batch
+    __shared__ float4 s_g0[NB];
+    __shared__ float2 s_g1[NB];
+    __shared__ unsigned long long s_sum[NB];
+    __shared__ uint32_t s_cnt[NB];
+    __shared__ uint32_t s_idx[NB];
+    __shared__ float4 s_box[NB];
 
     const int tiles = a.TW * a.TH;
     const int vb = blockIdx.x / tiles;
     const int t = blockIdx.x - vb * tiles;
     const int tx = t % a.TW, ty = t / a.TW;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int i = tx * TILE + (tid % TILE), j = ty * TILE + (tid / TILE);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wx = (warp % (TILE / 8)) * 8, wy = (warp / (TILE / 8)) * 4;
+    const int i = tx * TILE + wx + (lane & 7), j = ty * TILE + wy + (lane >> 3);
+    const float bx0 = (float)(tx * TILE + wx) + 0.5f, bx1 = bx0 + 7.0f;
+    const float by0 = (float)(ty * TILE + wy) + 0.5f, by1 = by0 + 3.0f;
     const bool inside = i < a.W && j < a.H;
     const float px = (float)i + 0.5f, py = (float)j + 0.5f;
     const uint2 rg = a.ranges[blockIdx.x];
@@ -196,23 +224,27 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite_vis(CompositeArgs a)
     float T = 1.0f;
     bool on = inside;
     uint32_t wpairs = 0;
-    s_sum[tid] = 0ull;
-    s_cnt[tid] = 0u;
+    if (tid < NB) {
+        s_sum[tid] = 0ull;
+        s_cnt[tid] = 0u;
+    }
 
-    for (uint32_t base = rg.x; base < rg.y; base += NT) {
+    for (uint32_t base = rg.x; base < rg.y; base += NB) {
         if (__syncthreads_count(on) == 0) break;
         const uint32_t e = base + tid;
-        if (e < rg.y) {
+        if (tid < NB && e < rg.y) {
             const uint32_t g = a.vals[e];
             const GeoRec gr = a.geo[vrow + g];
             s_g0[tid] = gr.a;
             s_g1[tid] = make_float2(gr.b.x, gr.b.y);
             s_idx[tid] = g;
+            s_box[tid] = footprint_box(gr.a.x, gr.a.y, gr.b.w);
         }
         __syncthreads();
-        const int cnt = (int)min((uint32_t)NT, rg.y - base);
+        const int cnt = (int)min((uint32_t)NB, rg.y - base);
         for (int k = 0; k < cnt; ++k) {
             if (!__any_sync(0xffffffffu, on)) break;   // warp-uniform
+            if (box_misses(s_box[k], bx0, bx1, by0, by1)) continue;   // uniform across the warp
             const float4 g0 = s_g0[k];
             const float2 g1 = s_g1[k];
             const float q = footprint_q(px, py, g0.x, g0.y, g0.z, g0.w, g1.x);
@@ -239,8 +271,10 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite_vis(CompositeArgs a)
             atomicAdd(&a.sumT[r], s_sum[tid]);
             atomicAdd(&a.cnt[r], s_cnt[tid]);
         }
-        s_sum[tid] = 0ull;
-        s_cnt[tid] = 0u;
+        if (tid < NB) {
+            s_sum[tid] = 0ull;
+            s_cnt[tid] = 0u;
+        }
     }
     if (a.pairs && lane == 0 && wpairs) atomicAdd(a.pairs, (unsigned long long)wpairs);
 }

@@ -146,47 +146,100 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const uint64_t *keys,
     hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = s_h[threadIdx.x];
 }
 
+// Stable scatter of one 4096-item tile.  Warp w owns the contiguous items
+// [512 w, 512 (w+1)) and ranks them in input order against warp-private digit
+// counters (match_any within each 32-item round); the warps' counters are then
+// turned into block-local digit offsets, items are placed in shared memory in
+// sorted order, and written out so that consecutive threads write consecutive
+// addresses of each digit run.
+constexpr size_t kRsSmem = (size_t)kRsTile * 12 + (size_t)(kRsWarps + 3) * 256 * 4;
+
 __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const uint64_t *kin, const uint32_t *vin,
                                                               uint64_t *kout, uint32_t *vout, size_t n, int shift,
-                                                              const uint32_t *offs, int nblocks)
+                                                              const uint32_t *hist, const uint32_t *offs,
+                                                              int nblocks)
 {
-    __shared__ uint32_t s_goff[256];
-    __shared__ uint32_t s_run[256];
-    __shared__ uint32_t s_wc[kRsWarps][257];
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *s_key = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *s_val = reinterpret_cast<uint32_t *>(smem + (size_t)kRsTile * 8);
+    uint32_t *s_wc = reinterpret_cast<uint32_t *>(smem + (size_t)kRsTile * 12);   // [warps][256]
+    uint32_t *s_goff = s_wc + kRsWarps * 256;
+    uint32_t *s_lstart = s_goff + 256;
+    uint32_t *s_tmp = s_lstart + 256;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    s_goff[tid] = offs[(size_t)tid * nblocks + blockIdx.x];
-    s_run[tid] = 0;
     const unsigned lt = (1u << lane) - 1u;
     const size_t base = (size_t)blockIdx.x * kRsTile;
-    for (int r = 0; r < kRsRounds; ++r) {
-        const size_t i = base + (size_t)r * kRsThreads + tid;
-        const bool valid = i < n;
-        const uint64_t k = valid ? kin[i] : 0ull;
-        const uint32_t val = valid ? vin[i] : 0u;
-        const int d = valid ? (int)((k >> shift) & 255u) : 256;
-        for (int x = tid; x < kRsWarps * 257; x += kRsThreads) (&s_wc[0][0])[x] = 0u;
-        __syncthreads();
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rank = (uint32_t)__popc(peers & lt);
-        if (lane == __ffs(peers) - 1) s_wc[warp][d] = (uint32_t)__popc(peers);
-        __syncthreads();
-        {
-            uint32_t run = s_run[tid];
+
+    // this block's digit counts -> block-local digit starts (exclusive scan)
+    const uint32_t mycnt = hist[(size_t)tid * nblocks + blockIdx.x];
+    s_goff[tid] = offs[(size_t)tid * nblocks + blockIdx.x];
+    for (int w = 0; w < kRsWarps; ++w) s_wc[w * 256 + tid] = 0u;
+    {
+        uint32_t x = mycnt;
 #pragma unroll
-            for (int w = 0; w < kRsWarps; ++w) {
-                uint32_t c = s_wc[w][tid];
-                s_wc[w][tid] = run;
-                run += c;
-            }
-            s_run[tid] = run;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
+        if (lane == 31) s_tmp[warp] = x;
         __syncthreads();
-        if (valid) {
-            const uint32_t pos = s_goff[d] + s_wc[warp][d] + rank;
-            kout[pos] = k;
-            vout[pos] = val;
+        uint32_t wpre = 0;
+        for (int w = 0; w < warp; ++w) wpre += s_tmp[w];
+        s_lstart[tid] = wpre + x - mycnt;
+    }
+
+    // phase A: warp-private stable ranks
+    constexpr int R = kRsTile / kRsThreads;   // 16 rounds of 32 items per warp
+    uint64_t k[R];
+    uint32_t v[R], rk[R];
+    int d[R];
+    uint32_t *wc = s_wc + warp * 256;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const size_t i = base + (size_t)warp * (32 * R) + (size_t)r * 32 + lane;
+        const bool valid = i < n;
+        k[r] = valid ? kin[i] : 0ull;
+        v[r] = valid ? vin[i] : 0u;
+        d[r] = valid ? (int)((k[r] >> shift) & 255u) : 256;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
+        const uint32_t prior = d[r] < 256 ? wc[d[r]] : 0u;
+        rk[r] = prior + (uint32_t)__popc(peers & lt);
+        __syncwarp();
+        if (d[r] < 256 && lane == __ffs(peers) - 1) wc[d[r]] = prior + (uint32_t)__popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: offsets of the warps' runs inside the block's digit run
+    {
+        uint32_t run = s_lstart[tid];
+        for (int w = 0; w < kRsWarps; ++w) {
+            const uint32_t c = s_wc[w * 256 + tid];
+            s_wc[w * 256 + tid] = run;
+            run += c;
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    // phase B: place in shared memory in sorted order
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (d[r] < 256) {
+            const uint32_t lp = wc[d[r]] + rk[r];
+            s_key[lp] = k[r];
+            s_val[lp] = v[r];
+        }
+    }
+    __syncthreads();
+    // phase C: coalesced write-out
+    const int cnt = (int)min((size_t)kRsTile, n - base);
+    for (int i = tid; i < cnt; i += kRsThreads) {
+        const uint64_t kk = s_key[i];
+        const int dd = (int)((kk >> shift) & 255u);
+        const uint32_t pos = s_goff[dd] + ((uint32_t)i - s_lstart[dd]);
+        kout[pos] = kk;
+        vout[pos] = s_val[i];
     }
 }
 
@@ -232,6 +285,8 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
     uint32_t *hist = reinterpret_cast<uint32_t *>(tmp);
     uint32_t *offs = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(tmp) + a);
     void *stmp = reinterpret_cast<char *>(tmp) + 2 * a;
+    // per device, idempotent
+    cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRsSmem);
     uint64_t *kin = keys, *kout = keys_alt;
     uint32_t *vin = vals, *vout = vals_alt;
     bool alt = false;
@@ -239,7 +294,7 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
         k_radix_hist<<<nblocks, kRsThreads, 0, s>>>(kin, n, shift, hist, nblocks); count_launch();
         cudaError_t e = exclusive_scan_u32(hist, offs, h, stmp, nullptr, s);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<nblocks, kRsThreads, 0, s>>>(kin, vin, kout, vout, n, shift, offs, nblocks); count_launch();
+        k_radix_scatter<<<nblocks, kRsThreads, kRsSmem, s>>>(kin, vin, kout, vout, n, shift, hist, offs, nblocks); count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         uint64_t *tk = kin; kin = kout; kout = tk;

@@ -248,6 +248,12 @@ def test_tile_rect_is_conservative(k):
         tx, ty = (pix % cam.W) // 16, (pix // cam.W) // 16
         assert np.all(st[g] == 1)
         assert np.all((out[g, 6] <= tx) & (tx <= out[g, 7]) & (out[g, 8] <= ty) & (ty <= out[g, 9]))
+        # at pixel granularity too: the pixel centre lies in the footprint box
+        # [u - ex, u + ex] x [v - ey, v + ey] (what lets a warp skip an entry)
+        px = (pix % cam.W).astype(np.float32) + np.float32(0.5)
+        py = (pix // cam.W).astype(np.float32) + np.float32(0.5)
+        assert np.all((out[g, 1] - out[g, 10] <= px) & (px <= out[g, 1] + out[g, 10]))
+        assert np.all((out[g, 2] - out[g, 11] <= py) & (py <= out[g, 2] + out[g, 11]))
 
 
 # --------------------------------------------------------------------------- compositing
