@@ -307,6 +307,28 @@ def run_gavis(args):
     ms_per_step = total_ms / args.steps
     value = world * n_cand / (ms_per_step / 1e3)
 
+    # ---------------- per-call work counts (one untimed instrumented pass) ----------------
+    ctx.prof_enable(True)
+    ctx.vf_build(gs, train, degree=L, params=prm, out=vf)
+    vis_vf = ctx.prof_read()["visible"]
+    ctx.prof_enable(True)
+    ctx.score_views(gs, vf, cand, params=prm, out=outs, sync_best=False)
+    vis_sc = ctx.prof_read()["visible"]
+    ctx.prof_enable(False)
+    b = torch.tensor([], dtype=cdt).element_size()
+    K, Kc = (L + 1) ** 2, (sc.sh_degree + 1) ** 2
+    # per-view byte model: centres of every Gaussian for culling, the rest of
+    # the record for visible ones, outputs (visibility sums, or rgb + unc)
+    bytes_vf = len(train) * sc.n * 12 + vis_vf * (32 + 8) + sc.n * K * b
+    bytes_sc = n_cand * sc.n * 12 + vis_sc * (32 + Kc * 3 * b + K * b) + n_cand * W * H * 16
+    model_bytes = bytes_vf + bytes_sc
+    hbm = {"model_bytes_per_step": int(model_bytes), "achieved_gbs": model_bytes / (ms_per_step / 1e3) / 1e9,
+           "peak_gbs": peaks()[0].get("hbm_gbs"),
+           "frac": model_bytes / (ms_per_step / 1e3) / 1e9 / peaks()[0].get("hbm_gbs", 6800.0),
+           "visible_records": {"vf_build": int(vis_vf), "score": int(vis_sc)},
+           "note": "per-view algorithmic bytes (Gaussian data counted once per view; the batched chain "
+                   "reads it once per batch), divided by the device time of the step"}
+
     # ---------------- end to end through host buffers ----------------
     e2e_steps = max(1, args.e2e_steps)
     h2d = sum(v.numel() * v.element_size() for v in host.values()) + gv.camera_records(train)._length_ * 96 \
@@ -384,6 +406,7 @@ def run_gavis(args):
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in st.items()},
             "pairs_per_step": {"uncertainty": pairs_ua // args.steps, "visibility": pairs_vis // args.steps},
             "tile_keys_per_step": prof["keys"] // args.steps,
+            "hbm": hbm,
             "best_view": best,
         }
         print(json.dumps(line), flush=True)

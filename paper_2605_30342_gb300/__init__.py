@@ -294,10 +294,10 @@ class Context:
         ms = (C.c_double * len(STAGES))()
         la = (C.c_int64 * len(STAGES))()
         tot = C.c_int64(0)
-        pairs = (C.c_uint64 * 3)()
+        pairs = (C.c_uint64 * 4)()
         self._check(self._lib.gavis_prof_read(self._h, ms, la, C.byref(tot), pairs))
         return dict(stages={k: (ms[i], int(la[i])) for i, k in enumerate(STAGES)}, total_launches=int(tot.value),
-                    pairs=(int(pairs[0]), int(pairs[1])), keys=int(pairs[2]))
+                    pairs=(int(pairs[0]), int(pairs[1])), keys=int(pairs[2]), visible=int(pairs[3]))
 
     # -------------------------------------------------------------- verification hooks
     def debug_bins(self, gs: Gaussians, cams, params=None, cap=None, stream=None):

@@ -44,7 +44,7 @@ struct gavis_ctx {
     size_t used = 0;
     std::string err;
     Buf rec, vis, keys, small, gamma, cams;
-    unsigned long long *h_total = nullptr;   // pinned
+    BatchInfo *h_info = nullptr;             // pinned
     int32_t *h_best = nullptr;               // pinned
     // instrumentation
     bool prof_on = false;
@@ -54,6 +54,7 @@ struct gavis_ctx {
     long long prof_launches[GAVIS_STAGE_COUNT] = {};
     unsigned long long *d_pairs = nullptr;   // device [2]
     unsigned long long prof_keys = 0;        // tile keys sorted since gavis_prof_enable
+    unsigned long long prof_visible = 0;     // visible (view, Gaussian) records since then
 };
 
 namespace {
@@ -296,7 +297,7 @@ KeyLayout key_layout(void *base, size_t M)
 struct SmallLayout {
     uint2 *ranges;
     float *tile_sums;
-    unsigned long long *d_total;
+    BatchInfo *info;
     int32_t *best;
     size_t bytes;
 };
@@ -309,7 +310,7 @@ SmallLayout small_layout(void *base, size_t nvt)
     auto take = [&](size_t b) { char *q = p ? p + off : nullptr; off += align256(b); return q; };
     L.ranges = reinterpret_cast<uint2 *>(take(nvt * sizeof(uint2)));
     L.tile_sums = reinterpret_cast<float *>(take(nvt * sizeof(float)));
-    L.d_total = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long)));
+    L.info = reinterpret_cast<BatchInfo *>(take(sizeof(BatchInfo)));
     L.best = reinterpret_cast<int32_t *>(take(sizeof(int32_t)));
     L.bytes = off;
     return L;
@@ -379,19 +380,29 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     pa.tile = p->tile; pa.TW = G.TW; pa.TH = G.TH;
     pa.cams = d_cams + v0; pa.nv = nv; pa.n = n;
     pa.geo = RL.geo; pa.ua = RL.ua; pa.rect = RL.rect; pa.counts = RL.counts;
+    pa.zrange = SL.info->zrange;
+    pa.visible = &SL.info->visible;
     {
         Stage st(ctx, GAVIS_STAGE_PROJECT, s);
+        CK(cudaMemsetAsync(SL.info, 0xff, sizeof(BatchInfo), s));            // zmin = all ones
+        CK(cudaMemsetAsync(&SL.info->zrange[1], 0, sizeof(uint32_t), s));    // zmax = 0
+        CK(cudaMemsetAsync(&SL.info->visible, 0, sizeof(unsigned long long), s));
         CK(launch_project(pa, s));
     }
     {
         Stage st(ctx, GAVIS_STAGE_SCAN, s);
-        CK(exclusive_scan_u32(RL.counts, RL.offsets, nvn, RL.scan_tmp, SL.d_total, s));
+        CK(exclusive_scan_u32(RL.counts, RL.offsets, nvn, RL.scan_tmp, &SL.info->total, s));
     }
-    CK(cudaMemcpyAsync(ctx->h_total, SL.d_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_info, SL.info, sizeof(BatchInfo), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    const unsigned long long M = *ctx->h_total;
+    const unsigned long long M = ctx->h_info->total;
+    const uint32_t zmin = ctx->h_info->zrange[0];
+    const int zb = M ? depth_bits(zmin, ctx->h_info->zrange[1]) : 0;
     if (M >= (1ull << 32) - 1) return fail(ctx, GAVIS_ERR_BUDGET, "more than 2^32 keys in one batch");
-    if (ctx->prof_on) ctx->prof_keys += M;
+    if (ctx->prof_on) {
+        ctx->prof_keys += M;
+        ctx->prof_visible += ctx->h_info->visible;
+    }
 
     KeyLayout KL = key_layout(nullptr, (size_t)M);
     if ((rc = ensure(ctx, ctx->keys, KL.bytes)) != GAVIS_OK) return rc;
@@ -399,9 +410,9 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
 
     {
         Stage st(ctx, GAVIS_STAGE_EMIT, s);
-        CK(launch_emit(RL.rect, RL.geo, RL.counts, RL.offsets, nv, n, G.TW, G.TH, KL.k0, KL.v0, s));
+        CK(launch_emit(RL.rect, RL.geo, RL.counts, RL.offsets, nv, n, G.TW, G.TH, zb, zmin, KL.k0, KL.v0, s));
     }
-    const int end_bit = 32 + bits_for((uint64_t)nvt - 1);
+    const int end_bit = zb + bits_for((uint64_t)nvt - 1);
     bool alt = false;
     {
         Stage st(ctx, GAVIS_STAGE_SORT, s);
@@ -412,15 +423,15 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     {
         Stage st(ctx, GAVIS_STAGE_RANGES, s);
         CK(cudaMemsetAsync(SL.ranges, 0, nvt * sizeof(uint2), s));
-        CK(launch_ranges(keys, (size_t)M, SL.ranges, s));
+        CK(launch_ranges(keys, (size_t)M, zb, SL.ranges, s));
     }
 
     if (mode == MODE_BINS) {
         const int64_t off = out.M;
         if (off < out.cap && out.keys) {
             const int64_t m = (int64_t)M < out.cap - off ? (int64_t)M : out.cap - off;
-            // keys carry the view index within the batch: shift them to the global index
-            CK(cudaMemcpyAsync(out.keys + off, keys, (size_t)m * 8, cudaMemcpyDeviceToDevice, s));
+            // canonical keys; one batch, so the view index is the call's
+            CK(launch_keys_export(keys, (size_t)m, zb, zmin, out.keys + off, s));
             CK(cudaMemcpyAsync(out.vals + off, vals, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
         }
         if (out.ranges)
@@ -529,7 +540,7 @@ int gavis_ctx_create(gavis_ctx **out, int device, size_t hbm_budget_bytes)
         return GAVIS_ERR_CUDA;
     }
     ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : fr / 10 * 6;
-    if (cudaMallocHost(&ctx->h_total, sizeof(unsigned long long)) != cudaSuccess ||
+    if (cudaMallocHost(&ctx->h_info, sizeof(BatchInfo)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_best, sizeof(int32_t)) != cudaSuccess) {
         delete ctx;
         return GAVIS_ERR_CUDA;
@@ -545,7 +556,7 @@ void gavis_ctx_destroy(gavis_ctx *ctx)
     cudaDeviceSynchronize();
     for (Buf *b : {&ctx->rec, &ctx->vis, &ctx->keys, &ctx->small, &ctx->gamma, &ctx->cams})
         if (b->p) cudaFree(b->p);
-    if (ctx->h_total) cudaFreeHost(ctx->h_total);
+    if (ctx->h_info) cudaFreeHost(ctx->h_info);
     if (ctx->h_best) cudaFreeHost(ctx->h_best);
     if (ctx->d_pairs) cudaFree(ctx->d_pairs);
     for (auto &r : ctx->pending) {
@@ -573,6 +584,7 @@ int gavis_prof_enable(gavis_ctx *ctx, int on)
         ctx->prof_launches[k] = 0;
     }
     ctx->prof_keys = 0;
+    ctx->prof_visible = 0;
     ctx->prof_on = on != 0;
     return GAVIS_OK;
 }
@@ -601,6 +613,7 @@ int gavis_prof_read(gavis_ctx *ctx, double *ms, int64_t *launches, int64_t *tota
         pairs[0] = h[0];
         pairs[1] = h[1];
         pairs[2] = ctx->prof_keys;
+        pairs[3] = ctx->prof_visible;
     }
     return GAVIS_OK;
 }

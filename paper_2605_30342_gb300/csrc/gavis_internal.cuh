@@ -10,7 +10,12 @@
 //           the SH colour (eq:rgb_sh).
 //   rect    8 B   (x0 | x1 << 16, y0 | y1 << 16) inclusive tile rectangle.
 //   counts  4 B   tiles touched (0 = culled).
-// Keys: ((view * TW*TH + tile) << 32) | float_bits(depth); values: g.
+// Keys: ((view * TW*TH + tile) << zb) | (float_bits(depth) - zmin); values: g.
+// zmin/zmax are the smallest/largest depth bit patterns of the batch (depths
+// are positive, so their bit patterns order like the depths) and zb the bits
+// of zmax - zmin: the canonical key ((view * TW*TH + tile) << 32) |
+// float_bits(depth) orders exactly like this compacted one, which needs fewer
+// radix passes.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -59,6 +64,8 @@ struct ProjectArgs {
     UaRec *ua;              // NULL for the visibility pass
     uint2 *rect;
     uint32_t *counts;
+    uint32_t *zrange;       // [2] min and max depth bits of visible records (atomic)
+    unsigned long long *visible;   // count of visible records (atomic), or NULL
 };
 cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s);
 
@@ -87,9 +94,26 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
                              size_t n, int end_bit, void *tmp, bool *result_in_alt, cudaStream_t s);
 
 // ---------------------------------------------------------------- raster.cu
+struct BatchInfo {                // device, read back once per batch
+    unsigned long long total;     // number of keys
+    uint32_t zrange[2];           // min, max depth bits of visible records
+    unsigned long long visible;   // (view, Gaussian) records with tiles
+};
+// key compaction of a batch: bits of the depth part
+inline int depth_bits(uint32_t zmin, uint32_t zmax)
+{
+    int b = 0;
+    const uint32_t d = zmax > zmin ? zmax - zmin : 0u;
+    while (b < 32 && (d >> b) != 0u) ++b;
+    return b;
+}
 cudaError_t launch_emit(const uint2 *rect, const GeoRec *geo, const uint32_t *counts, const uint32_t *offsets,
-                        int nv, int64_t n, int TW, int TH, uint64_t *keys, uint32_t *vals, cudaStream_t s);
-cudaError_t launch_ranges(const uint64_t *keys, size_t M, uint2 *ranges, cudaStream_t s);
+                        int nv, int64_t n, int TW, int TH, int zb, uint32_t zmin, uint64_t *keys, uint32_t *vals,
+                        cudaStream_t s);
+cudaError_t launch_ranges(const uint64_t *keys, size_t M, int zb, uint2 *ranges, cudaStream_t s);
+// canonical keys ((tile << 32) | depth bits) from compacted ones
+cudaError_t launch_keys_export(const uint64_t *keys, size_t M, int zb, uint32_t zmin, uint64_t *out,
+                               cudaStream_t s);
 
 struct CompositeArgs {
     const uint2 *ranges;

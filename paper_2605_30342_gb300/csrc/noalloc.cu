@@ -131,7 +131,7 @@ extern "C" int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_v
     const size_t n = (size_t)gs->n;
     Carver c{ds.ptr};
     gavis_camera *d_cam = reinterpret_cast<gavis_camera *>(c.take(sizeof(gavis_camera)));
-    unsigned long long *d_total = reinterpret_cast<unsigned long long *>(c.take(sizeof(unsigned long long)));
+    BatchInfo *d_info = reinterpret_cast<BatchInfo *>(c.take(sizeof(BatchInfo)));
     GeoRec *geo = reinterpret_cast<GeoRec *>(c.take(n * sizeof(GeoRec)));
     UaRec *ua = reinterpret_cast<UaRec *>(c.take(n * sizeof(UaRec)));
     uint2 *rect = reinterpret_cast<uint2 *>(c.take(n * sizeof(uint2)));
@@ -153,11 +153,19 @@ extern "C" int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_v
     pa.tile = p->tile; pa.TW = TW; pa.TH = TH;
     pa.cams = d_cam; pa.nv = 1; pa.n = gs->n;
     pa.geo = geo; pa.ua = ua; pa.rect = rect; pa.counts = counts;
+    pa.zrange = d_info->zrange;
+    pa.visible = nullptr;
+    // what must start at a fixed value: the depth range (min = all ones, max = 0)
+    NA_CK(cudaMemsetAsync(d_info, 0xff, sizeof(BatchInfo), s));
+    NA_CK(cudaMemsetAsync(&d_info->zrange[1], 0, sizeof(uint32_t), s));
     NA_CK(launch_project(pa, s));
-    NA_CK(exclusive_scan_u32(counts, offsets, n, scan_tmp, d_total, s));
-    unsigned long long M = 0;   // pageable host variable: no pinned allocation
-    NA_CK(cudaMemcpyAsync(&M, d_total, sizeof(M), cudaMemcpyDeviceToHost, s));
+    NA_CK(exclusive_scan_u32(counts, offsets, n, scan_tmp, &d_info->total, s));
+    BatchInfo info;   // pageable host variable: no pinned allocation
+    NA_CK(cudaMemcpyAsync(&info, d_info, sizeof(info), cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));
+    const unsigned long long M = info.total;
+    const uint32_t zmin = info.zrange[0];
+    const int zb = M ? depth_bits(zmin, info.zrange[1]) : 0;
     if (M > kMaxKeys)
         return report(err, err_len, GAVIS_ERR_BUDGET, "%llu tile keys exceed the no-allocation maximum of %zu", M,
                       kMaxKeys);
@@ -170,15 +178,15 @@ extern "C" int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_v
         return report(err, err_len, GAVIS_ERR_BUDGET, "tile keys do not fit the %zu-byte scratch array",
                       kNoAllocScratchBytes);
 
-    NA_CK(launch_emit(rect, geo, counts, offsets, 1, gs->n, TW, TH, k0, v0, s));
+    NA_CK(launch_emit(rect, geo, counts, offsets, 1, gs->n, TW, TH, zb, zmin, k0, v0, s));
     int bits = 0;
     while (bits < 32 && ((uint64_t)(TT - 1) >> bits) != 0) ++bits;
     bool alt = false;
-    NA_CK(radix_sort_pairs(k0, v0, k1, v1, (size_t)M, 32 + bits, rtmp, &alt, s));
+    NA_CK(radix_sort_pairs(k0, v0, k1, v1, (size_t)M, zb + bits, rtmp, &alt, s));
     const uint64_t *keys = alt ? k1 : k0;
     const uint32_t *vals = alt ? v1 : v0;
     NA_CK(cudaMemsetAsync(ranges, 0, (size_t)TT * sizeof(uint2), s));   // tiles without keys stay empty
-    NA_CK(launch_ranges(keys, (size_t)M, ranges, s));
+    NA_CK(launch_ranges(keys, (size_t)M, zb, ranges, s));
 
     CompositeArgs ca;
     memset(&ca, 0, sizeof(ca));

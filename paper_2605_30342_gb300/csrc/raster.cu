@@ -52,7 +52,7 @@ __device__ __forceinline__ float footprint_q(float px, float py, float u, float 
 }
 
 __global__ void k_emit(const uint2 *rect, const GeoRec *geo, const uint32_t *counts, const uint32_t *offsets,
-                       int nv, int64_t n, int TW, int TH, uint64_t *keys, uint32_t *vals)
+                       int nv, int64_t n, int TW, int TH, int zb, uint32_t zmin, uint64_t *keys, uint32_t *vals)
 {
     const size_t total = (size_t)nv * (size_t)n;
     const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -62,143 +62,201 @@ __global__ void k_emit(const uint2 *rect, const GeoRec *geo, const uint32_t *cou
     const uint32_t g = (uint32_t)(r - (size_t)v * (size_t)n);
     const uint2 rc = rect[r];
     const uint32_t x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu, y1 = rc.y >> 16;
-    const uint32_t zb = __float_as_uint(geo[r].b.z);
+    const uint32_t zl = __float_as_uint(geo[r].b.z) - zmin;
     uint32_t off = offsets[r];
     const uint64_t vbase = (uint64_t)v * (uint64_t)(TW * TH);
     for (uint32_t ty = y0; ty <= y1; ++ty)
         for (uint32_t tx = x0; tx <= x1; ++tx) {
-            keys[off] = ((vbase + (uint64_t)(ty * (uint32_t)TW + tx)) << 32) | (uint64_t)zb;
+            keys[off] = ((vbase + (uint64_t)(ty * (uint32_t)TW + tx)) << zb) | (uint64_t)zl;
             vals[off] = g;
             ++off;
         }
 }
 
-__global__ void k_ranges(const uint64_t *keys, size_t M, uint2 *ranges)
+__global__ void k_ranges(const uint64_t *keys, size_t M, int zb, uint2 *ranges)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
-    const uint32_t t = (uint32_t)(keys[i] >> 32);
-    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = (uint32_t)i;
-    if (i == M - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = (uint32_t)(i + 1);
+    const uint32_t t = (uint32_t)(keys[i] >> zb);
+    if (i == 0 || (uint32_t)(keys[i - 1] >> zb) != t) ranges[t].x = (uint32_t)i;
+    if (i == M - 1 || (uint32_t)(keys[i + 1] >> zb) != t) ranges[t].y = (uint32_t)(i + 1);
 }
 
-template <int TILE>
-__global__ void __launch_bounds__(TILE *TILE) k_composite_ua(CompositeArgs a)
+__global__ void k_keys_export(const uint64_t *keys, size_t M, int zb, uint32_t zmin, uint64_t *out)
 {
-    constexpr int NT = TILE * TILE;
-    constexpr int NB = NT < 256 ? NT : 256;   // entries staged per batch
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const uint64_t k = keys[i];
+    const uint64_t low = zb ? (k & ((1ull << zb) - 1ull)) : 0ull;
+    out[i] = ((k >> zb) << 32) | (uint64_t)((uint32_t)low + zmin);
+}
+
+// 2^x and log2(x) on the special-function unit (PTX ex2/lg2, approximate;
+// exp(x) = 2^(x log2 e) and ln(x) = ln2 log2(x))
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+constexpr float kNegHalfLog2e = -0.72134752044448170368f;   // -log2(e) / 2
+constexpr float kLn2 = 0.69314718055994530942f;
+
+// Uncertainty + colour compositing.  Each thread owns two pixels of an 8 x 8
+// block per warp, (x, y) and (x, y + 4).  Per pixel and overlapping entry:
+// alpha = o 2^(-q log2(e)/2); colour w = alpha Tc, Tc -= w; uncertainty
+// alpha* = a1 alpha + a0 (eq:alpha_comp), w = alpha* T, wv = w V, T -= w.
+// The entropy bound (eq:huber) is assembled once per pixel from
+// sum(wv), sum(wv log2 wv) and the prior mass w0 = (1 - T) - sum(wv).
+template <int TILE>
+__global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a)
+{
+    constexpr int NT = TILE * TILE / 2;
+    constexpr int NB = 256;   // entries staged per batch
+    constexpr int NW = NT / 32;
     __shared__ float4 s_g0[NB];   // u, v, A, 2B
     __shared__ float2 s_g1[NB];   // C, opacity
     __shared__ float4 s_u0[NB];   // a1, a0, V, r
     __shared__ float2 s_u1[NB];   // g, b
     __shared__ float4 s_box[NB];  // footprint box
-    __shared__ float s_red[NT / 32];
-    __shared__ uint32_t s_pairs[NT / 32];
+    __shared__ float s_red[NW];
+    __shared__ uint32_t s_pairs[NW];
 
     const int tiles = a.TW * a.TH;
     const int vb = blockIdx.x / tiles;
     const int t = blockIdx.x - vb * tiles;
     const int tx = t % a.TW, ty = t / a.TW;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wx = (warp % (TILE / 8)) * 8, wy = (warp / (TILE / 8)) * 4;
-    const int i = tx * TILE + wx + (lane & 7), j = ty * TILE + wy + (lane >> 3);
+    const int wx = (warp % (TILE / 8)) * 8, wy = (warp / (TILE / 8)) * 8;
+    const int i = tx * TILE + wx + (lane & 7);
+    const int j0 = ty * TILE + wy + (lane >> 3);
     const float bx0 = (float)(tx * TILE + wx) + 0.5f, bx1 = bx0 + 7.0f;
-    const float by0 = (float)(ty * TILE + wy) + 0.5f, by1 = by0 + 3.0f;
-    const bool inside = i < a.W && j < a.H;
-    const float px = (float)i + 0.5f, py = (float)j + 0.5f;
+    const float by0 = (float)(ty * TILE + wy) + 0.5f, by1 = by0 + 7.0f;
+    const float px = (float)i + 0.5f;
     const uint2 rg = a.ranges[blockIdx.x];
     const size_t vrow = (size_t)vb * (size_t)a.n;
     const RasterConsts rc = a.rc;
 
-    float T = 1.0f, Tc = 1.0f, Hs = 0.0f, w0 = 0.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
-    bool ua_on = inside, rgb_on = inside;
+    float T[2], Tc[2], sl[2], swv[2], cr[2], cg[2], cb[2], py[2];
+    bool ua_on[2], rgb_on[2], inside[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int j = j0 + 4 * p;
+        inside[p] = i < a.W && j < a.H;
+        py[p] = (float)j + 0.5f;
+        T[p] = 1.0f; Tc[p] = 1.0f; sl[p] = 0.0f; swv[p] = 0.0f; cr[p] = 0.0f; cg[p] = 0.0f; cb[p] = 0.0f;
+        ua_on[p] = inside[p];
+        rgb_on[p] = inside[p];
+    }
     uint32_t npairs = 0;
 
     for (uint32_t base = rg.x; base < rg.y; base += NB) {
-        if (__syncthreads_count(ua_on || rgb_on) == 0) break;
-        const uint32_t e = base + tid;
-        if (tid < NB && e < rg.y) {
-            const size_t r = vrow + a.vals[e];
-            const GeoRec gr = a.geo[r];
-            const UaRec ur = a.ua[r];
-            s_g0[tid] = gr.a;
-            s_g1[tid] = make_float2(gr.b.x, gr.b.y);
-            s_u0[tid] = ur.a;
-            s_u1[tid] = make_float2(ur.b.x, ur.b.y);
-            s_box[tid] = footprint_box(gr.a.x, gr.a.y, gr.b.w);
+        const bool any = ua_on[0] || rgb_on[0] || ua_on[1] || rgb_on[1];
+        if (__syncthreads_count(any) == 0) break;
+        for (int k = tid; k < NB; k += NT) {
+            const uint32_t e = base + k;
+            if (e < rg.y) {
+                const size_t r = vrow + a.vals[e];
+                const GeoRec gr = a.geo[r];
+                const UaRec ur = a.ua[r];
+                s_g0[k] = gr.a;
+                s_g1[k] = make_float2(gr.b.x, gr.b.y);
+                s_u0[k] = ur.a;
+                s_u1[k] = make_float2(ur.b.x, ur.b.y);
+                s_box[k] = footprint_box(gr.a.x, gr.a.y, gr.b.w);
+            }
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)NB, rg.y - base);
-        for (int k = 0; k < cnt && (ua_on || rgb_on); ++k) {
+        for (int k = 0; k < cnt && (ua_on[0] || rgb_on[0] || ua_on[1] || rgb_on[1]); ++k) {
             if (box_misses(s_box[k], bx0, bx1, by0, by1)) continue;   // uniform across the warp
             const float4 g0 = s_g0[k];
             const float2 g1 = s_g1[k];
-            const float q = footprint_q(px, py, g0.x, g0.y, g0.z, g0.w, g1.x);
-            if (!(q <= rc.q_cut)) continue;
-            ++npairs;
-            const float alpha = g1.y * __expf(-0.5f * q);
-            if (rgb_on) {
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                if (!(ua_on[p] || rgb_on[p])) continue;
+                const float q = footprint_q(px, py[p], g0.x, g0.y, g0.z, g0.w, g1.x);
+                if (!(q <= rc.q_cut)) continue;
+                ++npairs;
+                const float alpha = g1.y * ex2_approx(q * kNegHalfLog2e);
                 const float4 u0 = s_u0[k];
-                const float2 u1 = s_u1[k];
-                const float w = alpha * Tc;
-                cr = fmaf(w, u0.w, cr);
-                cg = fmaf(w, u1.x, cg);
-                cb = fmaf(w, u1.y, cb);
-                Tc = Tc * (1.0f - alpha);
-                if (Tc < rc.eps_T) rgb_on = false;
-            }
-            if (ua_on) {
-                const float4 u0 = s_u0[k];
-                const float as = fmaf(alpha, u0.x, u0.y);   // eq:alpha_comp
-                const float w = as * T;
-                const float wv = w * u0.z;                   // weight of the visible component
-                if (wv > 1e-30f) Hs = fmaf(wv, rc.k_c - __logf(wv), Hs);
-                w0 = fmaf(w, 1.0f - u0.z, w0);                // weight of the prior component
-                T = T * (1.0f - as);
-                if (T < rc.eps_T) ua_on = false;
+                if (rgb_on[p]) {
+                    const float2 u1 = s_u1[k];
+                    const float w = alpha * Tc[p];
+                    cr[p] = fmaf(w, u0.w, cr[p]);
+                    cg[p] = fmaf(w, u1.x, cg[p]);
+                    cb[p] = fmaf(w, u1.y, cb[p]);
+                    Tc[p] -= w;
+                    rgb_on[p] = Tc[p] >= rc.eps_T;
+                }
+                if (ua_on[p]) {
+                    const float as = fmaf(alpha, u0.x, u0.y);   // eq:alpha_comp
+                    const float w = as * T[p];
+                    const float wv = w * u0.z;                   // weight of the visible component
+                    sl[p] = fmaf(wv, lg2_approx(fmaxf(wv, 1e-30f)), sl[p]);
+                    swv[p] += wv;
+                    T[p] -= w;
+                    ua_on[p] = T[p] >= rc.eps_T;
+                }
             }
         }
     }
     float h = 0.0f;
-    if (inside) {
-        if (w0 > 1e-30f) Hs = fmaf(w0, rc.k_0 - __logf(w0), Hs);   // invisible component of eq:huber
-        const size_t vg = (size_t)(a.v0 + vb);
-        const size_t pix = (size_t)j * a.W + i;
-        const size_t plane = (size_t)a.W * a.H;
+    const size_t vg = (size_t)(a.v0 + vb);
+    const size_t plane = (size_t)a.W * a.H;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        if (!inside[p]) continue;
+        // eq:huber: visible components sum wv (k_c - ln wv); prior w0 (k_0 - ln w0)
+        const float w0 = fmaxf((1.0f - T[p]) - swv[p], 0.0f);
+        float Hs = fmaf(rc.k_c, swv[p], -kLn2 * sl[p]);
+        if (w0 > 1e-30f) Hs = fmaf(w0, rc.k_0 - kLn2 * lg2_approx(w0), Hs);
+        const size_t pix = (size_t)(j0 + 4 * p) * a.W + i;
         if (a.unc) a.unc[vg * plane + pix] = Hs;
         if (a.rgb) {
-            a.rgb[(vg * 3 + 0) * plane + pix] = cr;
-            a.rgb[(vg * 3 + 1) * plane + pix] = cg;
-            a.rgb[(vg * 3 + 2) * plane + pix] = cb;
+            a.rgb[(vg * 3 + 0) * plane + pix] = cr[p];
+            a.rgb[(vg * 3 + 1) * plane + pix] = cg[p];
+            a.rgb[(vg * 3 + 2) * plane + pix] = cb[p];
         }
-        h = Hs;
+        h += Hs;
     }
     // tile partial sum of the per-pixel entropy (fixed order: deterministic)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) h += __shfl_down_sync(0xffffffffu, h, o);
     const uint32_t wp = __reduce_add_sync(0xffffffffu, npairs);
-    if ((tid & 31) == 0) {
-        s_red[tid >> 5] = h;
-        s_pairs[tid >> 5] = wp;
+    if (lane == 0) {
+        s_red[warp] = h;
+        s_pairs[warp] = wp;
     }
     __syncthreads();
     if (tid == 0) {
-        float s = 0.0f;
+        float sum = 0.0f;
         unsigned long long np = 0;
-        for (int w = 0; w < NT / 32; ++w) {
-            s += s_red[w];
+        for (int w = 0; w < NW; ++w) {
+            sum += s_red[w];
             np += s_pairs[w];
         }
-        a.tile_sums[blockIdx.x] = s;
+        a.tile_sums[blockIdx.x] = sum;
         if (a.pairs && np) atomicAdd(a.pairs, np);
     }
 }
 
+// Single-view particle visibility.  Each thread owns two pixels of an 8 x 8
+// block per warp.  Per overlapping entry a pixel contributes its current T
+// (fixed point, 2^-24) and a count of one to the Gaussian's sums; the warp
+// adds its 64 pixels with one redux, the block in shared memory, and one
+// global atomic per (tile, Gaussian) follows each batch.
 template <int TILE>
-__global__ void __launch_bounds__(TILE *TILE) k_composite_vis(CompositeArgs a)
+__global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs a)
 {
-    constexpr int NT = TILE * TILE;
-    constexpr int NB = NT < 256 ? NT : 256;   // entries staged per batch
+    constexpr int NT = TILE * TILE / 2;
+    constexpr int NB = 256;
     __shared__ float4 s_g0[NB];
     __shared__ float2 s_g1[NB];
     __shared__ unsigned long long s_sum[NB];
@@ -211,69 +269,76 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite_vis(CompositeArgs a)
     const int t = blockIdx.x - vb * tiles;
     const int tx = t % a.TW, ty = t / a.TW;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wx = (warp % (TILE / 8)) * 8, wy = (warp / (TILE / 8)) * 4;
-    const int i = tx * TILE + wx + (lane & 7), j = ty * TILE + wy + (lane >> 3);
+    const int wx = (warp % (TILE / 8)) * 8, wy = (warp / (TILE / 8)) * 8;
+    const int i = tx * TILE + wx + (lane & 7);
+    const int j0 = ty * TILE + wy + (lane >> 3);
     const float bx0 = (float)(tx * TILE + wx) + 0.5f, bx1 = bx0 + 7.0f;
-    const float by0 = (float)(ty * TILE + wy) + 0.5f, by1 = by0 + 3.0f;
-    const bool inside = i < a.W && j < a.H;
-    const float px = (float)i + 0.5f, py = (float)j + 0.5f;
+    const float by0 = (float)(ty * TILE + wy) + 0.5f, by1 = by0 + 7.0f;
+    const float px = (float)i + 0.5f, py0 = (float)j0 + 0.5f, py1 = py0 + 4.0f;
     const uint2 rg = a.ranges[blockIdx.x];
     const size_t vrow = (size_t)vb * (size_t)a.n;
     const float eps = a.rc.eps_T, qcut = a.rc.q_cut;
 
-    float T = 1.0f;
-    bool on = inside;
+    float T0 = 1.0f, T1 = 1.0f;
+    bool on0 = i < a.W && j0 < a.H, on1 = i < a.W && j0 + 4 < a.H;
     uint32_t wpairs = 0;
-    if (tid < NB) {
-        s_sum[tid] = 0ull;
-        s_cnt[tid] = 0u;
+    for (int k = tid; k < NB; k += NT) {
+        s_sum[k] = 0ull;
+        s_cnt[k] = 0u;
     }
 
     for (uint32_t base = rg.x; base < rg.y; base += NB) {
-        if (__syncthreads_count(on) == 0) break;
-        const uint32_t e = base + tid;
-        if (tid < NB && e < rg.y) {
-            const uint32_t g = a.vals[e];
-            const GeoRec gr = a.geo[vrow + g];
-            s_g0[tid] = gr.a;
-            s_g1[tid] = make_float2(gr.b.x, gr.b.y);
-            s_idx[tid] = g;
-            s_box[tid] = footprint_box(gr.a.x, gr.a.y, gr.b.w);
+        if (__syncthreads_count(on0 || on1) == 0) break;
+        for (int k = tid; k < NB; k += NT) {
+            const uint32_t e = base + k;
+            if (e < rg.y) {
+                const uint32_t g = a.vals[e];
+                const GeoRec gr = a.geo[vrow + g];
+                s_g0[k] = gr.a;
+                s_g1[k] = make_float2(gr.b.x, gr.b.y);
+                s_idx[k] = g;
+                s_box[k] = footprint_box(gr.a.x, gr.a.y, gr.b.w);
+            }
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)NB, rg.y - base);
         for (int k = 0; k < cnt; ++k) {
-            if (!__any_sync(0xffffffffu, on)) break;   // warp-uniform
+            if (!__any_sync(0xffffffffu, on0 || on1)) break;          // warp-uniform
             if (box_misses(s_box[k], bx0, bx1, by0, by1)) continue;   // uniform across the warp
             const float4 g0 = s_g0[k];
             const float2 g1 = s_g1[k];
-            const float q = footprint_q(px, py, g0.x, g0.y, g0.z, g0.w, g1.x);
-            const bool hit = on && (q <= qcut);
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (m) {
-                wpairs += (uint32_t)__popc(m);
-                const uint32_t tq = hit ? __float2uint_rn(T * kTScale) : 0u;
-                const uint32_t s = __reduce_add_sync(0xffffffffu, tq);
+            const float q0 = footprint_q(px, py0, g0.x, g0.y, g0.z, g0.w, g1.x);
+            const float q1 = footprint_q(px, py1, g0.x, g0.y, g0.z, g0.w, g1.x);
+            const bool h0 = on0 && (q0 <= qcut), h1 = on1 && (q1 <= qcut);
+            const unsigned m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
+            if (m0 | m1) {
+                const uint32_t tq = (h0 ? __float2uint_rn(T0 * kTScale) : 0u) + (h1 ? __float2uint_rn(T1 * kTScale) : 0u);
+                const uint32_t sum = __reduce_add_sync(0xffffffffu, tq);
+                const uint32_t c = (uint32_t)(__popc(m0) + __popc(m1));
+                wpairs += c;
                 if (lane == 0) {
-                    atomicAdd(&s_sum[k], (unsigned long long)s);
-                    atomicAdd(&s_cnt[k], (uint32_t)__popc(m));
+                    atomicAdd(&s_sum[k], (unsigned long long)sum);
+                    atomicAdd(&s_cnt[k], c);
                 }
             }
-            if (hit) {
-                const float alpha = g1.y * __expf(-0.5f * q);
-                T = T * (1.0f - alpha);
-                if (T < eps) on = false;
+            if (h0) {
+                T0 = fmaf(-T0, g1.y * ex2_approx(q0 * kNegHalfLog2e), T0);
+                on0 = T0 >= eps;
+            }
+            if (h1) {
+                T1 = fmaf(-T1, g1.y * ex2_approx(q1 * kNegHalfLog2e), T1);
+                on1 = T1 >= eps;
             }
         }
         __syncthreads();
-        if (tid < cnt && s_cnt[tid] > 0u) {
-            const size_t r = vrow + s_idx[tid];
-            atomicAdd(&a.sumT[r], s_sum[tid]);
-            atomicAdd(&a.cnt[r], s_cnt[tid]);
-        }
-        if (tid < NB) {
-            s_sum[tid] = 0ull;
-            s_cnt[tid] = 0u;
+        for (int k = tid; k < cnt; k += NT) {
+            if (s_cnt[k] > 0u) {
+                const size_t r = vrow + s_idx[k];
+                atomicAdd(&a.sumT[r], s_sum[k]);
+                atomicAdd(&a.cnt[r], s_cnt[k]);
+                s_sum[k] = 0ull;
+                s_cnt[k] = 0u;
+            }
         }
     }
     if (a.pairs && lane == 0 && wpairs) atomicAdd(a.pairs, (unsigned long long)wpairs);
@@ -396,18 +461,26 @@ inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 }  // namespace
 
 cudaError_t launch_emit(const uint2 *rect, const GeoRec *geo, const uint32_t *counts, const uint32_t *offsets,
-                        int nv, int64_t n, int TW, int TH, uint64_t *keys, uint32_t *vals, cudaStream_t s)
+                        int nv, int64_t n, int TW, int TH, int zb, uint32_t zmin, uint64_t *keys, uint32_t *vals,
+                        cudaStream_t s)
 {
     const size_t total = (size_t)nv * (size_t)n;
     if (total == 0) return cudaSuccess;
-    k_emit<<<nblk(total, 256), 256, 0, s>>>(rect, geo, counts, offsets, nv, n, TW, TH, keys, vals); count_launch();
+    k_emit<<<nblk(total, 256), 256, 0, s>>>(rect, geo, counts, offsets, nv, n, TW, TH, zb, zmin, keys, vals); count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_ranges(const uint64_t *keys, size_t M, uint2 *ranges, cudaStream_t s)
+cudaError_t launch_ranges(const uint64_t *keys, size_t M, int zb, uint2 *ranges, cudaStream_t s)
 {
     if (M == 0) return cudaSuccess;
-    k_ranges<<<nblk(M, 256), 256, 0, s>>>(keys, M, ranges); count_launch();
+    k_ranges<<<nblk(M, 256), 256, 0, s>>>(keys, M, zb, ranges); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keys_export(const uint64_t *keys, size_t M, int zb, uint32_t zmin, uint64_t *out, cudaStream_t s)
+{
+    if (M == 0) return cudaSuccess;
+    k_keys_export<<<nblk(M, 256), 256, 0, s>>>(keys, M, zb, zmin, out); count_launch();
     return cudaGetLastError();
 }
 
@@ -416,9 +489,9 @@ cudaError_t launch_composite_ua(const CompositeArgs &a, cudaStream_t s)
     const unsigned blocks = (unsigned)(a.nv * a.TW * a.TH);
     if (blocks == 0) return cudaSuccess;
     switch (a.tile) {
-    case 8: k_composite_ua<8><<<blocks, 64, 0, s>>>(a); count_launch(); break;
-    case 16: k_composite_ua<16><<<blocks, 256, 0, s>>>(a); count_launch(); break;
-    case 32: k_composite_ua<32><<<blocks, 1024, 0, s>>>(a); count_launch(); break;
+    case 8: k_composite_ua<8><<<blocks, 32, 0, s>>>(a); count_launch(); break;
+    case 16: k_composite_ua<16><<<blocks, 128, 0, s>>>(a); count_launch(); break;
+    case 32: k_composite_ua<32><<<blocks, 512, 0, s>>>(a); count_launch(); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -429,9 +502,9 @@ cudaError_t launch_composite_vis(const CompositeArgs &a, cudaStream_t s)
     const unsigned blocks = (unsigned)(a.nv * a.TW * a.TH);
     if (blocks == 0) return cudaSuccess;
     switch (a.tile) {
-    case 8: k_composite_vis<8><<<blocks, 64, 0, s>>>(a); count_launch(); break;
-    case 16: k_composite_vis<16><<<blocks, 256, 0, s>>>(a); count_launch(); break;
-    case 32: k_composite_vis<32><<<blocks, 1024, 0, s>>>(a); count_launch(); break;
+    case 8: k_composite_vis<8><<<blocks, 32, 0, s>>>(a); count_launch(); break;
+    case 16: k_composite_vis<16><<<blocks, 128, 0, s>>>(a); count_launch(); break;
+    case 32: k_composite_vis<32><<<blocks, 512, 0, s>>>(a); count_launch(); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
