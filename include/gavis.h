@@ -163,6 +163,25 @@ int gavis_score_views(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
                       float *rgb, float *unc, float *score, int32_t *best_dev, int32_t *best_host,
                       void *stream);
 
+/* Visibility-field density control (Alg. "Visibility Field Density Control").
+ * Virtual particles at the caller-drawn centres virt_means (device [3 n_virt],
+ * uniform in the scene volume; their number is floor(rho * volume)) get an
+ * identity rotation, the isotropic scale s with (4/3) pi s^3 rho = 1 + eta and
+ * zero opacity.  Alg. "Single-view Particle Visibility" runs on the union of
+ * the scene and the virtual particles for every training view (virtual
+ * particles are transparent), and each virtual particle's multi-view
+ * visibility is 1 - prod_p (1 - v_p).  Particles with visibility <= eps_v lie
+ * in under-explored space and are kept; the others (free space) are pruned.
+ * Kept particles enter uncertainty scoring with gamma = 0, i.e. V = 0.
+ *   vis_out: device [n_virt] float32 or NULL; keep: device [n_virt] uint8 (0/1);
+ *   kept_means: device [3 n_virt] or NULL, receives the kept centres in input
+ *   order; n_keep: host or NULL (synchronises `stream`); scale_out: host or NULL.
+ * Paper defaults: rho 100, eta 0.5, eps_v 0.95. */
+int gavis_vf_density_control(gavis_ctx *ctx, const gavis_gaussians *gs, const float *virt_means, int64_t n_virt,
+                             const gavis_camera *train, int n_train, const gavis_params *p, float rho, float eta,
+                             float eps_v, float *vis_out, uint8_t *keep, float *kept_means, int64_t *n_keep,
+                             float *scale_out, void *stream);
+
 /* Visibility-field query alone (Alg. "Query Anisotropic Visibility Field").
  * V: device [n_cams][n] float32.  Culling is not applied: every Gaussian gets
  * a value. */
@@ -214,6 +233,50 @@ int gavis_debug_visibility(gavis_ctx *ctx, const gavis_gaussians *gs, const gavi
 int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_vf *vf, const gavis_camera *cam,
                              const gavis_params *p, float *rgb, float *unc, float *score, char *err,
                              size_t err_len, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Serving (no counterpart in the paper): continuous batching of scoring     */
+/* requests over resident scenes.                                             */
+/* ---------------------------------------------------------------------- */
+typedef struct gavis_server gavis_server;
+
+/* Start a server on `device` with n_workers worker threads (1..16), each with
+ * its own CUDA stream and workspace (hbm_budget_bytes / n_workers; 0 = 60% of
+ * free memory in total), batching at most max_views_per_batch views (1..1024).
+ * Requests are admitted in arrival order while the sum of the admitted
+ * requests' workspace estimates fits hbm_budget_bytes. */
+int gavis_server_create(gavis_server **out, int device, size_t hbm_budget_bytes, int n_workers,
+                        int max_views_per_batch);
+
+/* Stop the workers (after the batches in flight) and free the server. */
+void gavis_server_destroy(gavis_server *s);
+
+const char *gavis_server_last_error(const gavis_server *s);
+
+/* Register a resident scene; gs and vf point to caller-owned device memory
+ * that must stay valid until the server is destroyed.  *scene_id receives
+ * its index. */
+int gavis_server_add_scene(gavis_server *s, const gavis_gaussians *gs, const gavis_vf *vf, int *scene_id);
+
+/* Queue a scoring request: the host cameras are copied (one W x H per
+ * request); score (device [n_cams]) and unc (device [n_cams][H][W] or NULL)
+ * must stay valid until gavis_server_wait returns for it.  The views of a
+ * request may be scored across several batches and share batches with other
+ * requests on the same scene, resolution and parameters; every view gets the
+ * result gavis_score_views gives it. */
+int gavis_server_submit(gavis_server *s, int scene_id, const gavis_camera *cams, int n_cams, const gavis_params *p,
+                        float *score, float *unc, int64_t *request_id);
+
+/* Wait up to timeout_ms for a request; on completion returns its status and
+ * sets *best (argmax of its scores, lowest index on ties) and *latency_ms
+ * (submit to completion), and forgets the request.  Returns GAVIS_ERR_TIMEOUT
+ * (request kept) if it is not finished in time. */
+int gavis_server_wait(gavis_server *s, int64_t request_id, int timeout_ms, int32_t *best, double *latency_ms);
+
+/* Counters: views scored, batches run, the most requests one batch served,
+ * the peak of the admitted workspace estimates and the budget. */
+int gavis_server_stats(gavis_server *s, int64_t *views_scored, int64_t *batches, int64_t *max_requests_in_batch,
+                       size_t *peak_reserved_bytes, size_t *budget_bytes);
 
 /* ---------------------------------------------------------------------- */
 /* Instrumentation (no counterpart in the paper): per-stage device time from  */

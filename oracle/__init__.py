@@ -86,6 +86,8 @@ def _declare(L):
     L.oracle_visibility_view.restype = i64
     L.oracle_vf_build.argtypes = [i32, vp, i64, vp, vp, vp, vp, i32, vp, vp, vp, vp]
     L.oracle_render_view.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]
+    L.oracle_density_control.argtypes = [i32, vp, i64, vp, vp, vp, vp, i64, vp, dbl, dbl, dbl, vp, vp, vp, vp]
+    L.oracle_density_control.restype = i64
 
 
 # ----------------------------------------------------------------------------
@@ -253,6 +255,26 @@ def vf_build(cams, scene, L, prm=None, want_vis=False):
                           _p(_f32(scene.rots)), _p(_f32(scene.opac)), int(L), _p(prm), _p(gamma),
                           _p(vis) if want_vis else None, _p(amb))
     return gamma, amb.astype(bool), vis
+
+
+def virtual_scale(rho, eta):
+    """s with (4/3) pi s^3 rho = 1 + eta (Alg. Visibility Field Density Control)."""
+    return (3.0 * (1.0 + eta) / (4.0 * np.pi * rho)) ** (1.0 / 3.0)
+
+
+def density_control(cams, scene, vmeans, rho=100.0, eta=0.5, eps_v=0.95, prm=None):
+    """Multi-view visibility of the virtual particles (float64), keep mask
+    (visibility <= eps_v) and the rounding-ambiguity mask."""
+    prm = params() if prm is None else prm
+    vm = _f32(vmeans).reshape(-1, 3)
+    nv = vm.shape[0]
+    vis = np.zeros(nv)
+    keep = np.zeros(nv, np.uint8)
+    amb = np.zeros(nv, np.uint8)
+    lib().oracle_density_control(len(cams), _p(cam_records(cams)), scene.n, _p(_f32(scene.means)),
+                                 _p(_f32(scene.scales)), _p(_f32(scene.rots)), _p(_f32(scene.opac)), nv, _p(vm),
+                                 float(rho), float(eta), float(eps_v), _p(prm), _p(vis), _p(keep), _p(amb))
+    return vis, keep.astype(bool), amb.astype(bool)
 
 
 def render_view(cam, scene, V, prm=None, sh=None):

@@ -35,6 +35,8 @@
  *                        by, in canonical order (stable, ties by index).
  *   oracle_composite     one pixel's compositing over a given list (pins).
  *   oracle_visibility_view  Alg. "Single-view Particle Visibility" alone.
+ *   oracle_density_control  Alg. "Visibility Field Density Control": virtual
+ *                        particles, product visibility over views, pruning.
  *
  * Readings of the paper used here (the paper is silent or loose on these):
  *   - the footprint exponent is -q/2 with q = d^T Sigma2D^{-1} d (3DGS), and a
@@ -748,4 +750,65 @@ void oracle_render_view(const float *cam, int64_t n, const float *means, const f
     free_lists(&Lst);
     free(col);
     free(P);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg. Visibility Field Density Control                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Virtual particles: centres x_j (caller-drawn, uniform in the scene),
+ * identity rotation, isotropic scale s with (4/3) pi s^3 rho = 1 + eta,
+ * opacity 0.  Their multi-view visibility 1 - prod_p (1 - v_p[j]) is
+ * computed with Alg. Single-view Particle Visibility on the union of the
+ * scene and the virtual particles; a particle is kept (under-explored) iff
+ * that visibility is <= eps_v.
+ *   vis_out: n_virt (float64); keep: n_virt (0/1); amb (optional): n_virt,
+ *   set when a rounding-sensitive transmittance test touched the particle.
+ * Returns the number kept. */
+int64_t oracle_density_control(int nview, const float *cams, int64_t n, const float *means, const float *scales,
+                               const float *rots, const float *opac, int64_t n_virt, const float *vmeans,
+                               double rho, double eta, double eps_v, const double *prm, double *vis_out,
+                               uint8_t *keep, uint8_t *amb)
+{
+    const int64_t na = n + n_virt;
+    const double s = cbrt(3.0 * (1.0 + eta) / (4.0 * M_PI * rho));
+    float *am = (float *)malloc(sizeof(float) * 3 * (size_t)(na > 0 ? na : 1));
+    float *as = (float *)malloc(sizeof(float) * 3 * (size_t)(na > 0 ? na : 1));
+    float *ar = (float *)malloc(sizeof(float) * 4 * (size_t)(na > 0 ? na : 1));
+    float *ao = (float *)malloc(sizeof(float) * (size_t)(na > 0 ? na : 1));
+    memcpy(am, means, sizeof(float) * 3 * (size_t)n);
+    memcpy(as, scales, sizeof(float) * 3 * (size_t)n);
+    memcpy(ar, rots, sizeof(float) * 4 * (size_t)n);
+    memcpy(ao, opac, sizeof(float) * (size_t)n);
+    for (int64_t j = 0; j < n_virt; ++j) {
+        for (int k = 0; k < 3; ++k) {
+            am[3 * (n + j) + k] = vmeans[3 * j + k];
+            as[3 * (n + j) + k] = (float)s;
+        }
+        ar[4 * (n + j)] = 1.0f;
+        ar[4 * (n + j) + 1] = ar[4 * (n + j) + 2] = ar[4 * (n + j) + 3] = 0.0f;
+        ao[n + j] = 0.0f;
+    }
+    double *prod = (double *)malloc(sizeof(double) * (size_t)(n_virt > 0 ? n_virt : 1));
+    for (int64_t j = 0; j < n_virt; ++j) prod[j] = 1.0;
+    double *sumT = (double *)malloc(sizeof(double) * (size_t)(na > 0 ? na : 1));
+    int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(na > 0 ? na : 1));
+    uint8_t *ab = (uint8_t *)calloc((size_t)(na > 0 ? na : 1), 1);
+    for (int p = 0; p < nview; ++p) {
+        oracle_visibility_view(cams + (size_t)C_LEN * p, na, am, as, ar, ao, prm, sumT, cnt, ab);
+        for (int64_t j = 0; j < n_virt; ++j) {
+            double v = cnt[n + j] > 0 ? sumT[n + j] / (double)cnt[n + j] : 0.0;
+            prod[j] *= 1.0 - v;
+        }
+    }
+    int64_t kept = 0;
+    for (int64_t j = 0; j < n_virt; ++j) {
+        double vt = 1.0 - prod[j];
+        if (vis_out) vis_out[j] = vt;
+        keep[j] = (uint8_t)(vt <= eps_v);
+        kept += keep[j];
+        if (amb) amb[j] = ab[n + j];
+    }
+    free(am); free(as); free(ar); free(ao); free(prod); free(sumT); free(cnt); free(ab);
+    return kept;
 }

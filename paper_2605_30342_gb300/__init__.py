@@ -19,7 +19,7 @@ import threading
 
 import torch
 
-__all__ = ["Context", "Gaussians", "VisibilityField", "Params", "GavisError", "load", "library_path",
+__all__ = ["Context", "Gaussians", "VisibilityField", "Params", "GavisError", "Server", "load", "library_path",
            "F32", "F16", "BF16"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -64,7 +64,9 @@ class gavis_params(C.Structure):
 
 EXPORTS = ["gavis_ctx_create", "gavis_ctx_destroy", "gavis_last_error", "gavis_params_default",
            "gavis_vmf_coeffs", "gavis_vf_build", "gavis_score_views", "gavis_vf_query", "gavis_debug_bins",
-           "gavis_debug_visibility", "gavis_prof_enable", "gavis_prof_read"]
+           "gavis_debug_visibility", "gavis_prof_enable", "gavis_prof_read", "gavis_vf_density_control",
+           "gavis_server_create", "gavis_server_destroy", "gavis_server_last_error", "gavis_server_add_scene",
+           "gavis_server_submit", "gavis_server_wait", "gavis_server_stats"]
 
 STAGES = ["project", "scan", "emit", "sort", "ranges", "composite_ua", "composite_vis", "reduce", "vf_accum"]
 
@@ -103,6 +105,20 @@ def load(path: str | None = None):
                                          C.POINTER(gavis_params), vp, vp, i64, C.POINTER(C.c_int64), vp, vp]
         lib.gavis_debug_visibility.argtypes = [vp, C.POINTER(gavis_gaussians), C.POINTER(gavis_camera), i32,
                                                C.POINTER(gavis_params), vp, vp, vp]
+        lib.gavis_vf_density_control.argtypes = [vp, C.POINTER(gavis_gaussians), vp, i64, C.POINTER(gavis_camera), i32,
+                                                 C.POINTER(gavis_params), C.c_float, C.c_float, C.c_float, vp, vp, vp,
+                                                 C.POINTER(C.c_int64), C.POINTER(C.c_float), vp]
+        lib.gavis_server_create.argtypes = [C.POINTER(vp), i32, C.c_size_t, i32, i32]
+        lib.gavis_server_destroy.argtypes = [vp]
+        lib.gavis_server_destroy.restype = None
+        lib.gavis_server_last_error.argtypes = [vp]
+        lib.gavis_server_last_error.restype = C.c_char_p
+        lib.gavis_server_add_scene.argtypes = [vp, C.POINTER(gavis_gaussians), C.POINTER(gavis_vf), C.POINTER(C.c_int)]
+        lib.gavis_server_submit.argtypes = [vp, i32, C.POINTER(gavis_camera), i32, C.POINTER(gavis_params), vp, vp,
+                                            C.POINTER(C.c_int64)]
+        lib.gavis_server_wait.argtypes = [vp, i64, i32, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+        lib.gavis_server_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                           C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
         lib.gavis_prof_enable.argtypes = [vp, i32]
         lib.gavis_prof_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                         C.POINTER(C.c_uint64)]
@@ -285,6 +301,43 @@ class Context:
                                              len(cams), C.byref(p), C.c_void_p(V.data_ptr()), _stream_ptr(stream)))
         return V
 
+    # -------------------------------------------------------------- density control
+    def density_control(self, gs: Gaussians, virt_means: torch.Tensor, train_cams, rho: float = 100.0,
+                        eta: float = 0.5, eps_v: float = 0.95, params=None, stream=None):
+        """Alg. "Visibility Field Density Control": returns dict(vis [n_virt],
+        keep [n_virt] bool, kept_means [n_keep, 3], n_keep, scale)."""
+        p = params or Params()
+        vm = virt_means.contiguous()
+        nv = int(vm.shape[0])
+        vis = torch.empty(nv, device=gs.means.device)
+        keep = torch.empty(nv, dtype=torch.uint8, device=gs.means.device)
+        kept = torch.empty((max(nv, 1), 3), device=gs.means.device)
+        nk, scale = C.c_int64(0), C.c_float(0.0)
+        self._check(self._lib.gavis_vf_density_control(
+            self._h, C.byref(gs.struct), C.c_void_p(_dev(vm, "virt_means", torch.float32) if nv else None), nv,
+            camera_records(train_cams), len(train_cams), C.byref(p), float(rho), float(eta), float(eps_v),
+            C.c_void_p(vis.data_ptr() if nv else None), C.c_void_p(keep.data_ptr() if nv else None),
+            C.c_void_p(kept.data_ptr()), C.byref(nk), C.byref(scale), _stream_ptr(stream)))
+        n_keep = int(nk.value)
+        return dict(vis=vis, keep=keep.bool(), kept_means=kept[:n_keep], n_keep=n_keep, scale=float(scale.value))
+
+    @staticmethod
+    def augment(gs: Gaussians, vf: VisibilityField, kept_means: torch.Tensor, scale: float):
+        """The scene used for uncertainty scoring after density control: the
+        trained Gaussians plus the kept virtual particles (identity rotation,
+        isotropic `scale`, zero opacity, zero colour, gamma = 0 so V = 0)."""
+        k = int(kept_means.shape[0])
+        dev = gs.means.device
+        means = torch.cat([gs.means, kept_means.to(dev, torch.float32)])
+        scales = torch.cat([gs.scales, torch.full((k, 3), float(scale), device=dev)])
+        rots = torch.cat([gs.rots, torch.tensor([1.0, 0.0, 0.0, 0.0], device=dev).repeat(k, 1)])
+        opac = torch.cat([gs.opac, torch.zeros(k, device=dev)])
+        sh = torch.cat([gs.sh, torch.zeros((k,) + tuple(gs.sh.shape[1:]), dtype=gs.sh.dtype, device=dev)])
+        coeffs = torch.cat([vf.coeffs, torch.zeros((k, vf.coeffs.shape[1]), dtype=vf.coeffs.dtype, device=dev)])
+        return (Gaussians(means.contiguous(), scales.contiguous(), rots.contiguous(), opac.contiguous(),
+                          sh.contiguous(), gs.sh_degree),
+                VisibilityField(coeffs.contiguous(), vf.degree, vf.n_train_views, vf.kappa))
+
     # -------------------------------------------------------------- instrumentation
     def prof_enable(self, on: bool = True):
         self._check(self._lib.gavis_prof_enable(self._h, int(bool(on))))
@@ -326,3 +379,72 @@ class Context:
                                                      C.byref(p), C.c_void_p(sumT.data_ptr()),
                                                      C.c_void_p(cnt.data_ptr()), _stream_ptr(stream)))
         return sumT, cnt
+
+
+class Server:
+    """Continuous-batching scoring server over resident scenes (C ABI
+    gavis_server_*).  Scenes and their fields must outlive the server; this
+    wrapper keeps references to them and to each request's output tensors."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0, n_workers: int = 2, max_views_per_batch: int = 64):
+        self._lib = load()
+        self._h = C.c_void_p()
+        rc = self._lib.gavis_server_create(C.byref(self._h), int(device), C.c_size_t(int(budget_bytes)),
+                                           int(n_workers), int(max_views_per_batch))
+        if rc != OK:
+            raise GavisError(rc, "gavis_server_create failed")
+        self.device = device
+        self._keep = {}
+        self._scenes = []
+
+    def _check(self, rc):
+        if rc != OK:
+            raise GavisError(rc, self._lib.gavis_server_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            self._lib.gavis_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_scene(self, gs: Gaussians, vf: VisibilityField) -> int:
+        vs = vf.struct()
+        sid = C.c_int(-1)
+        self._check(self._lib.gavis_server_add_scene(self._h, C.byref(gs.struct), C.byref(vs), C.byref(sid)))
+        self._scenes.append((gs, vf, vs))
+        return int(sid.value)
+
+    def submit(self, scene_id: int, cams, params=None, want_unc: bool = False) -> int:
+        p = params or Params()
+        dev = torch.device("cuda", self.device)
+        score = torch.empty(len(cams), device=dev)
+        unc = torch.empty((len(cams), int(cams[0].H), int(cams[0].W)), device=dev) if want_unc else None
+        rid = C.c_int64(0)
+        self._check(self._lib.gavis_server_submit(self._h, int(scene_id), camera_records(cams), len(cams), C.byref(p),
+                                                  C.c_void_p(score.data_ptr()),
+                                                  C.c_void_p(unc.data_ptr() if unc is not None else None),
+                                                  C.byref(rid)))
+        self._keep[int(rid.value)] = (score, unc)
+        return int(rid.value)
+
+    def wait(self, request_id: int, timeout_ms: int = 600000):
+        """dict(score, unc, best, latency_ms); raises GavisError (code
+        ERR_TIMEOUT) if the request is not finished in time."""
+        best, lat = C.c_int32(-1), C.c_double(0.0)
+        self._check(self._lib.gavis_server_wait(self._h, int(request_id), int(timeout_ms), C.byref(best),
+                                                C.byref(lat)))
+        score, unc = self._keep.pop(int(request_id))
+        return dict(score=score, unc=unc, best=int(best.value), latency_ms=float(lat.value))
+
+    def stats(self):
+        v, b, m = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+        pk, bud = C.c_size_t(0), C.c_size_t(0)
+        self._check(self._lib.gavis_server_stats(self._h, C.byref(v), C.byref(b), C.byref(m), C.byref(pk),
+                                                 C.byref(bud)))
+        return dict(views_scored=int(v.value), batches=int(b.value), max_requests_in_batch=int(m.value),
+                    peak_reserved_bytes=int(pk.value), budget_bytes=int(bud.value))

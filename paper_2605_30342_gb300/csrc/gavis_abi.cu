@@ -43,7 +43,7 @@ struct gavis_ctx {
     size_t budget = 0;
     size_t used = 0;
     std::string err;
-    Buf rec, vis, keys, small, gamma, cams;
+    Buf rec, vis, keys, small, gamma, cams, aug;
     BatchInfo *h_info = nullptr;             // pinned
     int32_t *h_best = nullptr;               // pinned
     // instrumentation
@@ -554,7 +554,7 @@ void gavis_ctx_destroy(gavis_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    for (Buf *b : {&ctx->rec, &ctx->vis, &ctx->keys, &ctx->small, &ctx->gamma, &ctx->cams})
+    for (Buf *b : {&ctx->rec, &ctx->vis, &ctx->keys, &ctx->small, &ctx->gamma, &ctx->cams, &ctx->aug})
         if (b->p) cudaFree(b->p);
     if (ctx->h_info) cudaFreeHost(ctx->h_info);
     if (ctx->h_best) cudaFreeHost(ctx->h_best);
@@ -795,6 +795,76 @@ int gavis_debug_bins(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_came
     if (rc != GAVIS_OK) return rc;
     CK(cudaStreamSynchronize(s));
     *M_out = co.M;
+    return GAVIS_OK;
+}
+
+int gavis_vf_density_control(gavis_ctx *ctx, const gavis_gaussians *gs, const float *virt_means, int64_t n_virt,
+                             const gavis_camera *train, int n_train, const gavis_params *p, float rho, float eta,
+                             float eps_v, float *vis_out, uint8_t *keep, float *kept_means, int64_t *n_keep,
+                             float *scale_out, void *stream)
+{
+    if (!ctx) return GAVIS_ERR_ARG;
+    int rc;
+    if ((rc = check_params(ctx, p)) || (rc = check_gaussians(ctx, gs, false)) || (rc = check_cams(ctx, train, n_train)))
+        return rc;
+    if (n_virt < 0 || gs->n + n_virt >= ((int64_t)1 << 31)) return fail(ctx, GAVIS_ERR_ARG, "n_virt out of range");
+    if (n_virt > 0 && (!virt_means || !keep)) return fail(ctx, GAVIS_ERR_ARG, "virt_means/keep is NULL");
+    if (!(rho > 0.0f) || !(eta > -1.0f)) return fail(ctx, GAVIS_ERR_ARG, "rho must be > 0 and eta > -1");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const double sd = std::cbrt(3.0 * (1.0 + (double)eta) / (4.0 * M_PI * (double)rho));
+    if (scale_out) *scale_out = (float)sd;
+    if (n_virt == 0) {
+        if (n_keep) *n_keep = 0;
+        return GAVIS_OK;
+    }
+    // the union of the scene and the virtual particles, plus the per-particle
+    // product, keep flags and their scan
+    const int64_t na = gs->n + n_virt;
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off += align256(b); return o; };
+    const size_t o_m = take((size_t)na * 12), o_s = take((size_t)na * 12), o_r = take((size_t)na * 16),
+                 o_o = take((size_t)na * 4), o_p = take((size_t)n_virt * 4), o_k = take((size_t)n_virt * 4),
+                 o_q = take((size_t)n_virt * 4), o_t = take(scan_tmp_bytes((size_t)n_virt) + 64),
+                 o_n = take(sizeof(unsigned long long));
+    if ((rc = ensure(ctx, ctx->aug, off)) != GAVIS_OK) return rc;
+    char *base = reinterpret_cast<char *>(ctx->aug.p);
+    float *am = reinterpret_cast<float *>(base + o_m), *as = reinterpret_cast<float *>(base + o_s);
+    float *ar = reinterpret_cast<float *>(base + o_r), *ao = reinterpret_cast<float *>(base + o_o);
+    float *prod = reinterpret_cast<float *>(base + o_p);
+    uint32_t *keep32 = reinterpret_cast<uint32_t *>(base + o_k), *pos = reinterpret_cast<uint32_t *>(base + o_q);
+    void *stmp = base + o_t;
+    unsigned long long *d_nk = reinterpret_cast<unsigned long long *>(base + o_n);
+    const size_t n = (size_t)gs->n;
+    if (n) {
+        CK(cudaMemcpyAsync(am, gs->means, n * 12, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(as, gs->scales, n * 12, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ar, gs->rots, n * 16, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ao, gs->opac, n * 4, cudaMemcpyDeviceToDevice, s));
+    }
+    CK(launch_virtual_fill(virt_means, n_virt, (float)sd, am + 3 * n, as + 3 * n, ar + 4 * n, ao + n, s));
+    CK(launch_fill_f32(prod, (size_t)n_virt, 1.0f, s));
+    gavis_gaussians all = *gs;
+    all.n = na;
+    all.means = am; all.scales = as; all.rots = ar; all.opac = ao;
+    ChainOut co;
+    auto after = [&](int, int nv) -> int {
+        const size_t nvn = (size_t)nv * (size_t)na;
+        const unsigned long long *sT = reinterpret_cast<const unsigned long long *>(ctx->vis.p);
+        const uint32_t *c = reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(ctx->vis.p) + nvn * 8);
+        CK(launch_vf_product(sT, c, nv, na, gs->n, n_virt, prod, s));
+        return GAVIS_OK;
+    };
+    rc = run_views(ctx, MODE_VIS, &all, nullptr, train, n_train, p, co, s, after);
+    if (rc != GAVIS_OK) return rc;
+    CK(launch_density_finalize(prod, n_virt, eps_v, vis_out, keep, keep32, s));
+    CK(exclusive_scan_u32(keep32, pos, (size_t)n_virt, stmp, d_nk, s));
+    if (kept_means) CK(launch_compact_kept(virt_means, keep32, pos, n_virt, kept_means, s));
+    if (n_keep) {
+        CK(cudaMemcpyAsync(ctx->h_info, d_nk, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        *n_keep = (int64_t)ctx->h_info->total;
+    }
     return GAVIS_OK;
 }
 

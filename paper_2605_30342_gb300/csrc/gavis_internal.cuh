@@ -153,6 +153,16 @@ cudaError_t launch_vf_accumulate(const AccumArgs &a, cudaStream_t s);
 cudaError_t launch_vf_store(const float *gamma32, size_t count, void *out, int dtype, int accumulate,
                             cudaStream_t s);
 cudaError_t launch_vf_load(const void *in, int dtype, size_t count, float *gamma32, cudaStream_t s);
+// density control
+cudaError_t launch_virtual_fill(const float *vmeans, int64_t n_virt, float scale, float *means, float *scales,
+                                float *rots, float *opac, cudaStream_t s);
+cudaError_t launch_fill_f32(float *x, size_t count, float value, cudaStream_t s);
+cudaError_t launch_vf_product(const unsigned long long *sumT, const uint32_t *cnt, int nv, int64_t n_all,
+                              int64_t first, int64_t n_virt, float *prod, cudaStream_t s);
+cudaError_t launch_density_finalize(const float *prod, int64_t n_virt, float eps_v, float *vis, uint8_t *keep,
+                                    uint32_t *keep_u32, cudaStream_t s);
+cudaError_t launch_compact_kept(const float *vmeans, const uint32_t *keep_u32, const uint32_t *pos, int64_t n_virt,
+                                float *kept_means, cudaStream_t s);
 cudaError_t launch_vis_export(const unsigned long long *sumT, const uint32_t *cnt, size_t count, float *sumT_f,
                               uint32_t *cnt_out, cudaStream_t s);
 

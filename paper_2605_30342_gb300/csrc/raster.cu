@@ -41,6 +41,39 @@ __device__ __forceinline__ bool box_misses(const float4 b, float bx0, float bx1,
     return b.y < bx0 || b.x > bx1 || b.w < by0 || b.z > by1;
 }
 
+// Bit w set iff the footprint box touches the pixel centres of warp block w
+// (8 x 8 pixels, TILE/8 blocks per row) of tile (tx, ty).
+template <int TILE>
+__device__ __forceinline__ uint32_t warp_block_mask(const float4 b, int tx, int ty)
+{
+    constexpr int WPR = TILE / 8;
+    uint32_t m = 0u;
+#pragma unroll
+    for (int w = 0; w < WPR * WPR; ++w) {
+        const float x0 = (float)(tx * TILE + (w % WPR) * 8) + 0.5f, y0 = (float)(ty * TILE + (w / WPR) * 8) + 0.5f;
+        if (!box_misses(b, x0, x0 + 7.0f, y0, y0 + 7.0f)) m |= 1u << w;
+    }
+    return m;
+}
+
+// The warp's entries of a staged batch (bit `warp` of s_wm), compacted in
+// order into list; returns their number (warp-uniform).
+template <int NB>
+__device__ __forceinline__ int build_warp_list(const uint32_t *s_wm, int warp, int lane, uint16_t *list)
+{
+    int n = 0;
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int c = 0; c < NB; c += 32) {
+        const bool mine = (s_wm[c + lane] >> warp) & 1u;
+        const unsigned b = __ballot_sync(0xffffffffu, mine);
+        if (mine) list[n + __popc(b & lt)] = (uint16_t)(c + lane);
+        n += __popc(b);
+    }
+    __syncwarp();
+    return n;
+}
+
 __device__ __forceinline__ float footprint_q(float px, float py, float u, float v, float A, float B2, float C)
 {
     const float dx = __fsub_rn(px, u), dy = __fsub_rn(py, v);
@@ -124,7 +157,8 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
     __shared__ float2 s_g1[NB];   // C, opacity
     __shared__ float4 s_u0[NB];   // a1, a0, V, r
     __shared__ float2 s_u1[NB];   // g, b
-    __shared__ float4 s_box[NB];  // footprint box
+    __shared__ uint32_t s_wm[NB];         // which warp blocks each entry's footprint box touches
+    __shared__ uint16_t s_list[NW][NB];   // per warp: its entries of the batch, in order
     __shared__ float s_red[NW];
     __shared__ uint32_t s_pairs[NW];
 
@@ -161,6 +195,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
         if (__syncthreads_count(any) == 0) break;
         for (int k = tid; k < NB; k += NT) {
             const uint32_t e = base + k;
+            uint32_t wm = 0u;
             if (e < rg.y) {
                 const size_t r = vrow + a.vals[e];
                 const GeoRec gr = a.geo[r];
@@ -169,13 +204,14 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
                 s_g1[k] = make_float2(gr.b.x, gr.b.y);
                 s_u0[k] = ur.a;
                 s_u1[k] = make_float2(ur.b.x, ur.b.y);
-                s_box[k] = footprint_box(gr.a.x, gr.a.y, gr.b.w);
+                wm = warp_block_mask<TILE>(footprint_box(gr.a.x, gr.a.y, gr.b.w), tx, ty);
             }
+            s_wm[k] = wm;
         }
         __syncthreads();
-        const int cnt = (int)min((uint32_t)NB, rg.y - base);
-        for (int k = 0; k < cnt && (ua_on[0] || rgb_on[0] || ua_on[1] || rgb_on[1]); ++k) {
-            if (box_misses(s_box[k], bx0, bx1, by0, by1)) continue;   // uniform across the warp
+        const int nk = build_warp_list<NB>(s_wm, warp, lane, s_list[warp]);
+        for (int idx = 0; idx < nk && (ua_on[0] || rgb_on[0] || ua_on[1] || rgb_on[1]); ++idx) {
+            const int k = s_list[warp][idx];
             const float4 g0 = s_g0[k];
             const float2 g1 = s_g1[k];
 #pragma unroll
@@ -262,7 +298,8 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
     __shared__ unsigned long long s_sum[NB];
     __shared__ uint32_t s_cnt[NB];
     __shared__ uint32_t s_idx[NB];
-    __shared__ float4 s_box[NB];
+    __shared__ uint32_t s_wm[NB];
+    __shared__ uint16_t s_list[NT / 32][NB];
 
     const int tiles = a.TW * a.TH;
     const int vb = blockIdx.x / tiles;
@@ -291,20 +328,23 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
         if (__syncthreads_count(on0 || on1) == 0) break;
         for (int k = tid; k < NB; k += NT) {
             const uint32_t e = base + k;
+            uint32_t wm = 0u;
             if (e < rg.y) {
                 const uint32_t g = a.vals[e];
                 const GeoRec gr = a.geo[vrow + g];
                 s_g0[k] = gr.a;
                 s_g1[k] = make_float2(gr.b.x, gr.b.y);
                 s_idx[k] = g;
-                s_box[k] = footprint_box(gr.a.x, gr.a.y, gr.b.w);
+                wm = warp_block_mask<TILE>(footprint_box(gr.a.x, gr.a.y, gr.b.w), tx, ty);
             }
+            s_wm[k] = wm;
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)NB, rg.y - base);
-        for (int k = 0; k < cnt; ++k) {
+        const int nk = build_warp_list<NB>(s_wm, warp, lane, s_list[warp]);
+        for (int idx = 0; idx < nk; ++idx) {
             if (!__any_sync(0xffffffffu, on0 || on1)) break;          // warp-uniform
-            if (box_misses(s_box[k], bx0, bx1, by0, by1)) continue;   // uniform across the warp
+            const int k = s_list[warp][idx];
             const float4 g0 = s_g0[k];
             const float2 g1 = s_g1[k];
             const float q0 = footprint_q(px, py0, g0.x, g0.y, g0.z, g0.w, g1.x);
@@ -456,6 +496,63 @@ __global__ void k_vis_export(const unsigned long long *sumT, const uint32_t *cnt
     if (cnt_out) cnt_out[i] = cnt[i];
 }
 
+// ------------------------------------------------------------------ density control
+// virtual particles: identity rotation, isotropic scale, zero opacity
+__global__ void k_virtual_fill(const float *vmeans, int64_t n_virt, float scale, float *means, float *scales,
+                               float *rots, float *opac)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_virt) return;
+    for (int k = 0; k < 3; ++k) {
+        means[3 * j + k] = vmeans[3 * j + k];
+        scales[3 * j + k] = scale;
+    }
+    reinterpret_cast<float4 *>(rots)[j] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+    opac[j] = 0.0f;
+}
+
+__global__ void k_fill_f32(float *x, size_t count, float value)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) x[i] = value;
+}
+
+// prod[j] *= 1 - v_p[first + j] for every view p of the batch
+__global__ void k_vf_product(const unsigned long long *sumT, const uint32_t *cnt, int nv, int64_t n_all, int64_t first,
+                             int64_t n_virt, float *prod)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_virt) return;
+    float pr = prod[j];
+    for (int v = 0; v < nv; ++v) {
+        const size_t r = (size_t)v * (size_t)n_all + (size_t)(first + j);
+        const uint32_t c = cnt[r];
+        if (c) pr *= 1.0f - (float)sumT[r] * (1.0f / kTScale) / (float)c;
+    }
+    prod[j] = pr;
+}
+
+__global__ void k_density_finalize(const float *prod, int64_t n_virt, float eps_v, float *vis, uint8_t *keep,
+                                   uint32_t *keep_u32)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_virt) return;
+    const float v = 1.0f - prod[j];
+    const bool k = v <= eps_v;   // low visibility: under-explored, kept
+    if (vis) vis[j] = v;
+    keep[j] = (uint8_t)k;
+    keep_u32[j] = (uint32_t)k;
+}
+
+__global__ void k_compact_kept(const float *vmeans, const uint32_t *keep_u32, const uint32_t *pos, int64_t n_virt,
+                               float *kept_means)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_virt || !keep_u32[j]) return;
+    const uint32_t q = pos[j];
+    for (int k = 0; k < 3; ++k) kept_means[3 * (size_t)q + k] = vmeans[3 * j + k];
+}
+
 inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -554,6 +651,45 @@ cudaError_t launch_vf_load(const void *in, int dtype, size_t count, float *gamma
 {
     if (count == 0) return cudaSuccess;
     k_vf_load<<<nblk(count, 256), 256, 0, s>>>(in, dtype, count, gamma32); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_virtual_fill(const float *vmeans, int64_t n_virt, float scale, float *means, float *scales,
+                                float *rots, float *opac, cudaStream_t s)
+{
+    if (n_virt == 0) return cudaSuccess;
+    k_virtual_fill<<<nblk((size_t)n_virt, 256), 256, 0, s>>>(vmeans, n_virt, scale, means, scales, rots, opac); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_f32(float *x, size_t count, float value, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    k_fill_f32<<<nblk(count, 256), 256, 0, s>>>(x, count, value); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vf_product(const unsigned long long *sumT, const uint32_t *cnt, int nv, int64_t n_all, int64_t first,
+                              int64_t n_virt, float *prod, cudaStream_t s)
+{
+    if (n_virt == 0 || nv == 0) return cudaSuccess;
+    k_vf_product<<<nblk((size_t)n_virt, 256), 256, 0, s>>>(sumT, cnt, nv, n_all, first, n_virt, prod); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_density_finalize(const float *prod, int64_t n_virt, float eps_v, float *vis, uint8_t *keep,
+                                    uint32_t *keep_u32, cudaStream_t s)
+{
+    if (n_virt == 0) return cudaSuccess;
+    k_density_finalize<<<nblk((size_t)n_virt, 256), 256, 0, s>>>(prod, n_virt, eps_v, vis, keep, keep_u32); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_kept(const float *vmeans, const uint32_t *keep_u32, const uint32_t *pos, int64_t n_virt,
+                                float *kept_means, cudaStream_t s)
+{
+    if (n_virt == 0) return cudaSuccess;
+    k_compact_kept<<<nblk((size_t)n_virt, 256), 256, 0, s>>>(vmeans, keep_u32, pos, n_virt, kept_means); count_launch();
     return cudaGetLastError();
 }
 

@@ -275,3 +275,54 @@ def test_invalid_arguments_raise(ctx, gv):
     assert e.value.code == gv.ERR_ARG
     with pytest.raises(gv.GavisError):
         ctx.score_views(gs, vf, c["cand"][:1], params=gv.Params(tile=12))
+
+
+# --------------------------------------------------------------------------- density control
+
+@pytest.mark.parametrize("name", ["tiny", "room_small"])
+def test_density_control_parity(ctx, gv, name):
+    """Alg. Visibility Field Density Control against the oracle: multi-view
+    visibility of the virtual particles within 1e-4, same kept set except
+    particles whose visibility lies within 1e-4 of eps_v or that a
+    rounding-sensitive transmittance test touched."""
+    c = case(name)
+    sc = c["scene"]
+    lo, hi = sc.bbox_min.astype(np.float64), sc.bbox_max.astype(np.float64)
+    rho = 2000.0 / float(np.prod(hi - lo))                    # ~2000 virtual particles
+    nvirt = int(np.floor(rho * np.prod(hi - lo)))
+    vm = np.random.default_rng(11).uniform(lo, hi, (nvirt, 3)).astype(np.float32)
+    gs = gpu_scene(gv, sc)
+    out = ctx.density_control(gs, torch.as_tensor(vm).cuda(), c["train"], rho=rho, eta=0.5, eps_v=0.95)
+    vis_r, keep_r, amb = oracle.density_control(c["train"], sc, vm, rho=rho, eta=0.5, eps_v=0.95)
+    vis_g = out["vis"].cpu().numpy()
+    ok = ~amb
+    assert np.abs(vis_g[ok] - vis_r[ok]).max() <= TOL
+    clear = ok & (np.abs(vis_r - 0.95) > TOL)
+    assert np.array_equal(out["keep"].cpu().numpy()[clear], keep_r[clear])
+    assert out["n_keep"] == int(out["keep"].sum().item())
+    np.testing.assert_array_equal(out["kept_means"].cpu().numpy(), vm[out["keep"].cpu().numpy()])
+    assert out["scale"] == pytest.approx(oracle.virtual_scale(rho, 0.5), rel=1e-6)
+    assert 0 < out["n_keep"] < nvirt
+
+
+def test_density_control_feeds_scoring(ctx, gv):
+    """Kept virtual particles join scoring with V = 0: the augmented scene's
+    scores match the oracle run on the same augmented scene."""
+    c = case("tiny")
+    sc = c["scene"]
+    vm = np.random.default_rng(12).uniform(-1.5, 1.5, (500, 3)).astype(np.float32)
+    gs = gpu_scene(gv, sc)
+    vf = ctx.vf_build(gs, c["train"][:3], degree=2)
+    dc = ctx.density_control(gs, torch.as_tensor(vm).cuda(), c["train"][:3], rho=100.0)
+    gs2, vf2 = gv.Context.augment(gs, vf, dc["kept_means"], dc["scale"])
+    out = ctx.score_views(gs2, vf2, c["cand"][:4])
+    k = dc["n_keep"]
+    aug = sg.Scene(np.concatenate([sc.means, dc["kept_means"].cpu().numpy()]),
+                   np.concatenate([sc.scales, np.full((k, 3), dc["scale"], np.float32)]),
+                   np.concatenate([sc.rots, np.tile(np.array([[1, 0, 0, 0]], np.float32), (k, 1))]),
+                   np.concatenate([sc.opac, np.zeros(k, np.float32)]),
+                   np.concatenate([sc.sh, np.zeros((k,) + sc.sh.shape[1:], np.float32)]), sc.sh_degree)
+    ref = oracle.score_views(aug, vf2.coeffs.double().cpu().numpy(), 2, 3, c["cand"][:4])
+    err, _ = compare_views(out["unc"].cpu().numpy(), out["rgb"].cpu().numpy(), ref)
+    assert err <= TOL
+    assert k > 0

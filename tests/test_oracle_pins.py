@@ -466,3 +466,52 @@ def test_score_is_mean_entropy_and_argmax():
     for v in range(4):
         assert out["score"][v] == pytest.approx(out["unc"][v].mean(), abs=1e-15)
     assert out["best"] == int(np.argmax(out["score"]))
+
+
+# --------------------------------------------------------------------------- density control
+
+def test_virtual_particle_scale():
+    """(4/3) pi s^3 rho = 1 + eta; the defaults rho = 100, eta = 0.5."""
+    for rho, eta in ((100.0, 0.5), (10.0, 0.5), (1000.0, 0.2)):
+        s = oracle.virtual_scale(rho, eta)
+        assert 4.0 / 3.0 * math.pi * s ** 3 * rho == pytest.approx(1.0 + eta, rel=1e-12)
+
+
+def wall_scene(o):
+    """Three large thin Gaussians at z = 1, 1.1, 1.2 covering the view."""
+    return sg.Scene(np.array([[0, 0, 1.0], [0, 0, 1.1], [0, 0, 1.2]], np.float32),
+                    np.array([[20.0, 20.0, 0.01]] * 3, np.float32), np.array([[1, 0, 0, 0]] * 3, np.float32),
+                    np.array([o] * 3, np.float32), np.zeros((3, 1, 3), np.float32), 0)
+
+
+def test_density_control_free_occluded_and_unseen():
+    """A virtual particle in front of the camera with nothing before it is seen
+    (visibility 1): free space, pruned.  Behind opaque walls, or outside the
+    field of view, it is never reached (visibility 0): kept.  Virtual
+    particles are transparent, so two on one ray are both seen."""
+    cam = axis_camera(32, 32, 30.0, 15.5, 15.5)
+    vm = np.array([[0, 0, 0.6], [0, 0, 0.8], [0, 0, 3.0], [5.0, 0, 1.0]], np.float32)
+    vis, keep, amb = oracle.density_control([cam], wall_scene(0.9999), vm)
+    np.testing.assert_allclose(vis, [1.0, 1.0, 0.0, 0.0], atol=1e-12)
+    assert keep.tolist() == [False, False, True, True]
+    # transparent walls: the far particle is seen too
+    vis, keep, _ = oracle.density_control([cam], wall_scene(0.0), vm)
+    np.testing.assert_allclose(vis[:3], [1.0, 1.0, 1.0], atol=1e-12)
+    assert keep.tolist() == [False, False, False, True]
+
+
+def test_density_control_product_over_views():
+    """1 - prod_p (1 - v_p): one view that sees the particle fully is enough;
+    the threshold eps_v decides with <=."""
+    cam_a = axis_camera(32, 32, 30.0, 15.5, 15.5)
+    cam_b = sg.Camera(W=32, H=32, fx=30.0, fy=30.0, cx=15.5, cy=15.5, tan_half_fovx=32 / 60, tan_half_fovy=32 / 60,
+                      R=np.diag([1.0, -1.0, -1.0]).astype(np.float32), t=np.zeros(3, np.float32),
+                      campos=np.zeros(3, np.float32))   # looks down -z: sees nothing of the particle
+    vm = np.array([[0, 0, 0.6]], np.float32)
+    empty = sg.tiny_scene(1, seed=1).subset(np.arange(0))
+    vis, keep, _ = oracle.density_control([cam_b, cam_a], empty, vm)
+    assert vis[0] == pytest.approx(1.0, abs=1e-12) and not keep[0]
+    vis, keep, _ = oracle.density_control([cam_b], empty, vm)
+    assert vis[0] == 0.0 and keep[0]
+    vis, keep, _ = oracle.density_control([cam_a], empty, vm, eps_v=1.0)
+    assert keep[0]   # visibility 1 <= eps_v = 1
