@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-views", type=int, default=1)
+    ap.add_argument("--serving", action="store_true", help="serving workload: Poisson requests over 4 resident scenes")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean request rate (req/s)")
+    ap.add_argument("--requests", type=int, default=300, help="serving: number of requests")
+    ap.add_argument("--workers", type=int, default=4, help="serving: worker streams")
+    ap.add_argument("--batch-views", type=int, default=128, help="serving: views per batch")
     return ap.parse_args()
 
 
@@ -435,10 +440,79 @@ def traffic_for(kernel):
         return None
 
 
+def run_serving(args):
+    """Serving workload: 4 resident scenes (100k, 500k, 1M, 2M Gaussians, one
+    room each as in the room workload, fields from 50 training views), Poisson
+    arrivals, 8-512 candidate views per request (log-uniform) at one of four
+    resolutions, f16 coefficients, f32 compositing."""
+    import numpy as np
+    import torch
+    import scenegen as sg
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2605_30342_gb300 as gv
+    dev = torch.device("cuda", 0)
+    ctx = gv.Context(0)
+    scenes = []
+    for k, n in enumerate((100_000, 500_000, 1_000_000, 2_000_000)):
+        sc = sg.multi_room_scene(n, 1, 1, seed=k, sh_degree=3)
+        gs = gv.Gaussians.from_numpy(sc, sh_dtype=torch.float16)
+        train = sg.walk_cameras(50, sc, 640, 480, seed=k + 1, x_frac=(0.0, 0.5))
+        vf = ctx.vf_build(gs, train, degree=3, dtype=torch.float16)
+        scenes.append((sc, gs, vf))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(7)
+    res = [(160, 120), (320, 240), (640, 480), (800, 600)]
+    reqs = []
+    t = 0.0
+    for r in range(args.requests):
+        t += rng.exponential(1.0 / args.rate)
+        sid = int(rng.integers(4))
+        nv = int(round(np.exp(rng.uniform(np.log(8), np.log(512)))))
+        W, H = res[int(rng.integers(4))]
+        cams = sg.se2_cameras(nv, scenes[sid][0], W, H, seed=1000 + r)
+        reqs.append((t, sid, cams))
+    srv = gv.Server(0, n_workers=args.workers, max_views_per_batch=args.batch_views)
+    ids = [srv.add_scene(gs, vf) for _, gs, vf in scenes]
+    prm = gv.Params(vf_degree=3)
+    sampler = ClockSampler(0)
+    sampler.start()
+    t0 = time.perf_counter()
+    rids = []
+    for (ta, sid, cams) in reqs:
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        rids.append(srv.submit(ids[sid], cams, params=prm))
+    out = [srv.wait(r) for r in rids]
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    lat = [o["latency_ms"] for o in out]
+    views = sum(len(c) for _, _, c in reqs)
+    st = srv.stats()
+    srv.close()
+    line = {
+        "metric": "serving: views/s and p50/p99 request latency (4 resident scenes 100k-2M Gaussians)",
+        "value": views / wall, "unit": "views/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "serving: Poisson arrivals over 4 resident room scenes (100k, 500k, 1M, 2M)",
+                   "rate_req_s": args.rate, "requests": args.requests, "views": views,
+                   "views_per_request": "log-uniform 8..512", "resolutions": res, "coeff_storage": "f16",
+                   "workers": args.workers, "batch_views": args.batch_views},
+        "latency_ms": {"p50": percentile(lat, 50), "p99": percentile(lat, 99), "max": max(lat)},
+        "offered_views_per_s": views / reqs[-1][0],
+        "wall_s": wall, "server": st, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serving:
+        run_serving(args)
     else:
         run_gavis(args)
 
