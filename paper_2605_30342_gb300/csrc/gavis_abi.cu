@@ -239,12 +239,6 @@ Geometry geometry_of(const gavis_camera *cams, int tile)
     return g;
 }
 
-int bits_for(uint64_t x)
-{
-    int b = 0;
-    while (b < 64 && (x >> b) != 0) ++b;
-    return b;
-}
 
 // per-batch workspace: records + counts/offsets
 struct RecLayout {
@@ -272,24 +266,35 @@ RecLayout rec_layout(void *base, size_t nvn, bool ua)
     return L;
 }
 
+// per-batch workspace of the two-level binning: stage A over the nrec visible
+// records (64-bit keys, record indices, their tile counts and offsets), stage
+// B over the M tile entries (32-bit tile ids, Gaussian indices)
 struct KeyLayout {
-    uint64_t *k0, *k1;
-    uint32_t *v0, *v1;
+    uint64_t *a_k0, *a_k1;
+    uint32_t *a_v0, *a_v1, *a_cnt, *a_off;
+    uint32_t *b_k0, *b_k1, *b_v0, *b_v1;
     void *tmp;
     size_t bytes;
 };
 
-KeyLayout key_layout(void *base, size_t M)
+KeyLayout key_layout(void *base, size_t nrec, size_t M)
 {
     KeyLayout L;
     char *p = reinterpret_cast<char *>(base);
     size_t off = 0;
     auto take = [&](size_t b) { char *q = p ? p + off : nullptr; off += align256(b); return q; };
-    L.k0 = reinterpret_cast<uint64_t *>(take(M * 8));
-    L.k1 = reinterpret_cast<uint64_t *>(take(M * 8));
-    L.v0 = reinterpret_cast<uint32_t *>(take(M * 4));
-    L.v1 = reinterpret_cast<uint32_t *>(take(M * 4));
-    L.tmp = take(radix_tmp_bytes(M));
+    L.a_k0 = reinterpret_cast<uint64_t *>(take(nrec * 8));
+    L.a_k1 = reinterpret_cast<uint64_t *>(take(nrec * 8));
+    L.a_v0 = reinterpret_cast<uint32_t *>(take(nrec * 4));
+    L.a_v1 = reinterpret_cast<uint32_t *>(take(nrec * 4));
+    L.a_cnt = reinterpret_cast<uint32_t *>(take(nrec * 4));
+    L.a_off = reinterpret_cast<uint32_t *>(take(nrec * 4));
+    L.b_k0 = reinterpret_cast<uint32_t *>(take(M * 4));
+    L.b_k1 = reinterpret_cast<uint32_t *>(take(M * 4));
+    L.b_v0 = reinterpret_cast<uint32_t *>(take(M * 4));
+    L.b_v1 = reinterpret_cast<uint32_t *>(take(M * 4));
+    const size_t big = nrec > M ? nrec : M;
+    L.tmp = take(radix_tmp_bytes(big) + scan_tmp_bytes(big) + 64);
     L.bytes = off;
     return L;
 }
@@ -382,48 +387,62 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     pa.geo = RL.geo; pa.ua = RL.ua; pa.rect = RL.rect; pa.counts = RL.counts;
     pa.zrange = SL.info->zrange;
     pa.visible = &SL.info->visible;
+    pa.total = &SL.info->total;
     {
         Stage st(ctx, GAVIS_STAGE_PROJECT, s);
-        CK(cudaMemsetAsync(SL.info, 0xff, sizeof(BatchInfo), s));            // zmin = all ones
-        CK(cudaMemsetAsync(&SL.info->zrange[1], 0, sizeof(uint32_t), s));    // zmax = 0
-        CK(cudaMemsetAsync(&SL.info->visible, 0, sizeof(unsigned long long), s));
+        CK(cudaMemsetAsync(SL.info, 0, sizeof(BatchInfo), s));
+        CK(cudaMemsetAsync(&SL.info->zrange[0], 0xff, sizeof(uint32_t), s));   // zmin = all ones
         CK(launch_project(pa, s));
     }
     {
+        // positions of the visible records, in (view, index) order
         Stage st(ctx, GAVIS_STAGE_SCAN, s);
-        CK(exclusive_scan_u32(RL.counts, RL.offsets, nvn, RL.scan_tmp, &SL.info->total, s));
+        CK(exclusive_scan_u32(RL.counts, RL.offsets, nvn, RL.scan_tmp, nullptr, s, true));
     }
     CK(cudaMemcpyAsync(ctx->h_info, SL.info, sizeof(BatchInfo), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    const unsigned long long M = ctx->h_info->total;
+    const unsigned long long M = ctx->h_info->total, nrec = ctx->h_info->visible;
     const uint32_t zmin = ctx->h_info->zrange[0];
-    const int zb = M ? depth_bits(zmin, ctx->h_info->zrange[1]) : 0;
-    if (M >= (1ull << 32) - 1) return fail(ctx, GAVIS_ERR_BUDGET, "more than 2^32 keys in one batch");
+    const int zb = nrec ? depth_bits(zmin, ctx->h_info->zrange[1]) : 0;
+    if (M >= (1ull << 32) - 1) return fail(ctx, GAVIS_ERR_BUDGET, "more than 2^32 tile entries in one batch");
     if (ctx->prof_on) {
         ctx->prof_keys += M;
-        ctx->prof_visible += ctx->h_info->visible;
+        ctx->prof_visible += nrec;
     }
 
-    KeyLayout KL = key_layout(nullptr, (size_t)M);
+    KeyLayout KL = key_layout(nullptr, (size_t)nrec, (size_t)M);
     if ((rc = ensure(ctx, ctx->keys, KL.bytes)) != GAVIS_OK) return rc;
-    KL = key_layout(ctx->keys.p, (size_t)M);
-
+    KL = key_layout(ctx->keys.p, (size_t)nrec, (size_t)M);
+    bool alt_a = false, alt_b = false;
     {
+        // stage A: records sorted by (view, depth), ties in index order
         Stage st(ctx, GAVIS_STAGE_EMIT, s);
-        CK(launch_emit(RL.rect, RL.geo, RL.counts, RL.offsets, nv, n, G.TW, G.TH, zb, zmin, KL.k0, KL.v0, s));
+        CK(launch_emit_records(RL.counts, RL.offsets, RL.geo, nv, n, zb, zmin, KL.a_k0, KL.a_v0, s));
     }
-    const int end_bit = zb + bits_for((uint64_t)nvt - 1);
-    bool alt = false;
     {
         Stage st(ctx, GAVIS_STAGE_SORT, s);
-        CK(radix_sort_pairs(KL.k0, KL.v0, KL.k1, KL.v1, (size_t)M, end_bit, KL.tmp, &alt, s));
+        CK(radix_sort_pairs<uint64_t>(KL.a_k0, KL.a_v0, KL.a_k1, KL.a_v1, (size_t)nrec, bits_of((uint64_t)nv - 1) + zb,
+                                      KL.tmp, &alt_a, s));
     }
-    uint64_t *keys = alt ? KL.k1 : KL.k0;
-    uint32_t *vals = alt ? KL.v1 : KL.v0;
+    const uint32_t *recs = alt_a ? KL.a_v1 : KL.a_v0;
+    {
+        // stage B: tile entries in stage-A order
+        Stage st(ctx, GAVIS_STAGE_EMIT, s);
+        CK(launch_gather_counts(recs, RL.counts, (size_t)nrec, KL.a_cnt, s));
+        CK(exclusive_scan_u32(KL.a_cnt, KL.a_off, (size_t)nrec, KL.tmp, nullptr, s));
+        CK(launch_emit_tiles(recs, KL.a_off, (size_t)nrec, RL.rect, n, G.TW, G.TH, KL.b_k0, KL.b_v0, s));
+    }
+    {
+        Stage st(ctx, GAVIS_STAGE_SORT, s);
+        CK(radix_sort_pairs<uint32_t>(KL.b_k0, KL.b_v0, KL.b_k1, KL.b_v1, (size_t)M, bits_of((uint64_t)nvt - 1),
+                                      KL.tmp, &alt_b, s));
+    }
+    const uint32_t *keys = alt_b ? KL.b_k1 : KL.b_k0;
+    const uint32_t *vals = alt_b ? KL.b_v1 : KL.b_v0;
     {
         Stage st(ctx, GAVIS_STAGE_RANGES, s);
         CK(cudaMemsetAsync(SL.ranges, 0, nvt * sizeof(uint2), s));
-        CK(launch_ranges(keys, (size_t)M, zb, SL.ranges, s));
+        CK(launch_ranges(keys, (size_t)M, SL.ranges, s));
     }
 
     if (mode == MODE_BINS) {
@@ -431,7 +450,7 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
         if (off < out.cap && out.keys) {
             const int64_t m = (int64_t)M < out.cap - off ? (int64_t)M : out.cap - off;
             // canonical keys; one batch, so the view index is the call's
-            CK(launch_keys_export(keys, (size_t)m, zb, zmin, out.keys + off, s));
+            CK(launch_keys_export(keys, vals, (size_t)m, RL.geo, n, G.TT, out.keys + off, s));
             CK(cudaMemcpyAsync(out.vals + off, vals, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
         }
         if (out.ranges)

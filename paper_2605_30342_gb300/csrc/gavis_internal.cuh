@@ -10,12 +10,10 @@
 //           the SH colour (eq:rgb_sh).
 //   rect    8 B   (x0 | x1 << 16, y0 | y1 << 16) inclusive tile rectangle.
 //   counts  4 B   tiles touched (0 = culled).
-// Keys: ((view * TW*TH + tile) << zb) | (float_bits(depth) - zmin); values: g.
-// zmin/zmax are the smallest/largest depth bit patterns of the batch (depths
-// are positive, so their bit patterns order like the depths) and zb the bits
-// of zmax - zmin: the canonical key ((view * TW*TH + tile) << 32) |
-// float_bits(depth) orders exactly like this compacted one, which needs fewer
-// radix passes.
+// Canonical order of a batch's tile lists: by key ((view * TW*TH + tile) << 32)
+// | float_bits(depth), ties by Gaussian index.  Depths are positive, so their
+// bit patterns order like the depths; zmin/zmax are the smallest/largest of
+// the batch and zb the bits of zmax - zmin (depth keys are stored minus zmin).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -65,7 +63,8 @@ struct ProjectArgs {
     uint2 *rect;
     uint32_t *counts;
     uint32_t *zrange;       // [2] min and max depth bits of visible records (atomic)
-    unsigned long long *visible;   // count of visible records (atomic), or NULL
+    unsigned long long *visible;   // count of visible records (atomic)
+    unsigned long long *total;     // count of tile entries (atomic)
 };
 cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s);
 
@@ -82,38 +81,50 @@ cudaError_t launch_query(const QueryArgs &a, cudaStream_t s);
 
 // ---------------------------------------------------------------- sort.cu
 // exclusive scan of n uint32 into out (may alias in); writes the total (u64)
-// to *d_total (device).  tmp: scan_tmp_bytes(n) bytes.
+// to *d_total (device).  flags = true scans (in[i] != 0) instead of in[i].
+// tmp: scan_tmp_bytes(n) bytes.
 size_t scan_tmp_bytes(size_t n);
 cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, void *tmp,
-                               unsigned long long *d_total, cudaStream_t s);
+                               unsigned long long *d_total, cudaStream_t s, bool flags = false);
 
 // stable LSD radix sort of (keys, vals) on bits [0, end_bit); ping-pong
-// buffers; *result_in_alt tells which buffer holds the result.
+// buffers; *result_in_alt tells which buffer holds the result.  KeyT is
+// uint64_t or uint32_t.
 size_t radix_tmp_bytes(size_t n);
-cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
-                             size_t n, int end_bit, void *tmp, bool *result_in_alt, cudaStream_t s);
+template <typename KeyT>
+cudaError_t radix_sort_pairs(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_t *vals_alt, size_t n, int end_bit,
+                             void *tmp, bool *result_in_alt, cudaStream_t s);
 
 // ---------------------------------------------------------------- raster.cu
 struct BatchInfo {                // device, read back once per batch
-    unsigned long long total;     // number of keys
+    unsigned long long total;     // number of tile entries
     uint32_t zrange[2];           // min, max depth bits of visible records
     unsigned long long visible;   // (view, Gaussian) records with tiles
 };
-// key compaction of a batch: bits of the depth part
-inline int depth_bits(uint32_t zmin, uint32_t zmax)
+// bits needed to represent x
+inline int bits_of(uint64_t x)
 {
     int b = 0;
-    const uint32_t d = zmax > zmin ? zmax - zmin : 0u;
-    while (b < 32 && (d >> b) != 0u) ++b;
+    while (b < 64 && (x >> b) != 0) ++b;
     return b;
 }
-cudaError_t launch_emit(const uint2 *rect, const GeoRec *geo, const uint32_t *counts, const uint32_t *offsets,
-                        int nv, int64_t n, int TW, int TH, int zb, uint32_t zmin, uint64_t *keys, uint32_t *vals,
-                        cudaStream_t s);
-cudaError_t launch_ranges(const uint64_t *keys, size_t M, int zb, uint2 *ranges, cudaStream_t s);
-// canonical keys ((tile << 32) | depth bits) from compacted ones
-cudaError_t launch_keys_export(const uint64_t *keys, size_t M, int zb, uint32_t zmin, uint64_t *out,
-                               cudaStream_t s);
+// bits of the depth part of the record keys of a batch
+inline int depth_bits(uint32_t zmin, uint32_t zmax) { return bits_of(zmax > zmin ? zmax - zmin : 0u); }
+// Two-level binning.  Stage A: one key per visible (view, Gaussian) record,
+// ((view << zb) | (depth bits - zmin)), value the record index, sorted.
+// Stage B: in that order, one entry per tile of the record's rectangle with
+// key view * TW*TH + tile and value g, stably sorted by tile: each tile's list
+// ends up in (depth, index) order.
+cudaError_t launch_emit_records(const uint32_t *counts, const uint32_t *pos, const GeoRec *geo, int nv, int64_t n,
+                                int zb, uint32_t zmin, uint64_t *keyA, uint32_t *valA, cudaStream_t s);
+cudaError_t launch_gather_counts(const uint32_t *valA, const uint32_t *counts, size_t nrec, uint32_t *cnt_sorted,
+                                 cudaStream_t s);
+cudaError_t launch_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect,
+                              int64_t n, int TW, int TH, uint32_t *keyB, uint32_t *valB, cudaStream_t s);
+cudaError_t launch_ranges(const uint32_t *keys, size_t M, uint2 *ranges, cudaStream_t s);
+// canonical keys ((view*tiles + tile) << 32) | depth bits, for verification
+cudaError_t launch_keys_export(const uint32_t *keyB, const uint32_t *valB, size_t M, const GeoRec *geo, int64_t n,
+                               int tiles_per_view, uint64_t *out, cudaStream_t s);
 
 struct CompositeArgs {
     const uint2 *ranges;

@@ -136,12 +136,11 @@ extern "C" int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_v
     UaRec *ua = reinterpret_cast<UaRec *>(c.take(n * sizeof(UaRec)));
     uint2 *rect = reinterpret_cast<uint2 *>(c.take(n * sizeof(uint2)));
     uint32_t *counts = reinterpret_cast<uint32_t *>(c.take(n * sizeof(uint32_t)));
-    uint32_t *offsets = reinterpret_cast<uint32_t *>(c.take(n * sizeof(uint32_t)));
+    uint32_t *pos = reinterpret_cast<uint32_t *>(c.take(n * sizeof(uint32_t)));
     void *scan_tmp = c.take(scan_tmp_bytes(n));
     uint2 *ranges = reinterpret_cast<uint2 *>(c.take((size_t)TT * sizeof(uint2)));
     float *tile_sums = reinterpret_cast<float *>(c.take((size_t)TT * sizeof(float)));
-    const size_t key_region = c.off;
-    if (key_region > kNoAllocScratchBytes)
+    if (c.off > kNoAllocScratchBytes)
         return report(err, err_len, GAVIS_ERR_BUDGET, "scratch layout exceeds %zu bytes", kNoAllocScratchBytes);
 
     NA_CK(cudaMemcpyAsync(d_cam, cam, sizeof(gavis_camera), cudaMemcpyHostToDevice, s));
@@ -154,39 +153,49 @@ extern "C" int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_v
     pa.cams = d_cam; pa.nv = 1; pa.n = gs->n;
     pa.geo = geo; pa.ua = ua; pa.rect = rect; pa.counts = counts;
     pa.zrange = d_info->zrange;
-    pa.visible = nullptr;
-    // what must start at a fixed value: the depth range (min = all ones, max = 0)
-    NA_CK(cudaMemsetAsync(d_info, 0xff, sizeof(BatchInfo), s));
-    NA_CK(cudaMemsetAsync(&d_info->zrange[1], 0, sizeof(uint32_t), s));
+    pa.visible = &d_info->visible;
+    pa.total = &d_info->total;
+    // what must start at fixed values: the counters (0) and the depth minimum (all ones)
+    NA_CK(cudaMemsetAsync(d_info, 0, sizeof(BatchInfo), s));
+    NA_CK(cudaMemsetAsync(&d_info->zrange[0], 0xff, sizeof(uint32_t), s));
     NA_CK(launch_project(pa, s));
-    NA_CK(exclusive_scan_u32(counts, offsets, n, scan_tmp, &d_info->total, s));
+    NA_CK(exclusive_scan_u32(counts, pos, n, scan_tmp, nullptr, s, true));
     BatchInfo info;   // pageable host variable: no pinned allocation
     NA_CK(cudaMemcpyAsync(&info, d_info, sizeof(info), cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));
-    const unsigned long long M = info.total;
+    const unsigned long long M = info.total, nrec = info.visible;
     const uint32_t zmin = info.zrange[0];
-    const int zb = M ? depth_bits(zmin, info.zrange[1]) : 0;
+    const int zb = nrec ? depth_bits(zmin, info.zrange[1]) : 0;
     if (M > kMaxKeys)
-        return report(err, err_len, GAVIS_ERR_BUDGET, "%llu tile keys exceed the no-allocation maximum of %zu", M,
+        return report(err, err_len, GAVIS_ERR_BUDGET, "%llu tile entries exceed the no-allocation maximum of %zu", M,
                       kMaxKeys);
-    uint64_t *k0 = reinterpret_cast<uint64_t *>(c.take(M * 8));
-    uint64_t *k1 = reinterpret_cast<uint64_t *>(c.take(M * 8));
-    uint32_t *v0 = reinterpret_cast<uint32_t *>(c.take(M * 4));
-    uint32_t *v1 = reinterpret_cast<uint32_t *>(c.take(M * 4));
-    void *rtmp = c.take(radix_tmp_bytes(M));
+    uint64_t *a_k0 = reinterpret_cast<uint64_t *>(c.take(nrec * 8));
+    uint64_t *a_k1 = reinterpret_cast<uint64_t *>(c.take(nrec * 8));
+    uint32_t *a_v0 = reinterpret_cast<uint32_t *>(c.take(nrec * 4));
+    uint32_t *a_v1 = reinterpret_cast<uint32_t *>(c.take(nrec * 4));
+    uint32_t *a_cnt = reinterpret_cast<uint32_t *>(c.take(nrec * 4));
+    uint32_t *a_off = reinterpret_cast<uint32_t *>(c.take(nrec * 4));
+    uint32_t *b_k0 = reinterpret_cast<uint32_t *>(c.take(M * 4));
+    uint32_t *b_k1 = reinterpret_cast<uint32_t *>(c.take(M * 4));
+    uint32_t *b_v0 = reinterpret_cast<uint32_t *>(c.take(M * 4));
+    uint32_t *b_v1 = reinterpret_cast<uint32_t *>(c.take(M * 4));
+    const size_t big = nrec > M ? (size_t)nrec : (size_t)M;
+    void *rtmp = c.take(radix_tmp_bytes(big) + scan_tmp_bytes(big) + 64);
     if (c.off > kNoAllocScratchBytes)
-        return report(err, err_len, GAVIS_ERR_BUDGET, "tile keys do not fit the %zu-byte scratch array",
+        return report(err, err_len, GAVIS_ERR_BUDGET, "tile entries do not fit the %zu-byte scratch array",
                       kNoAllocScratchBytes);
-
-    NA_CK(launch_emit(rect, geo, counts, offsets, 1, gs->n, TW, TH, zb, zmin, k0, v0, s));
-    int bits = 0;
-    while (bits < 32 && ((uint64_t)(TT - 1) >> bits) != 0) ++bits;
-    bool alt = false;
-    NA_CK(radix_sort_pairs(k0, v0, k1, v1, (size_t)M, zb + bits, rtmp, &alt, s));
-    const uint64_t *keys = alt ? k1 : k0;
-    const uint32_t *vals = alt ? v1 : v0;
-    NA_CK(cudaMemsetAsync(ranges, 0, (size_t)TT * sizeof(uint2), s));   // tiles without keys stay empty
-    NA_CK(launch_ranges(keys, (size_t)M, zb, ranges, s));
+    bool alt_a = false, alt_b = false;
+    NA_CK(launch_emit_records(counts, pos, geo, 1, gs->n, zb, zmin, a_k0, a_v0, s));
+    NA_CK(radix_sort_pairs<uint64_t>(a_k0, a_v0, a_k1, a_v1, (size_t)nrec, zb, rtmp, &alt_a, s));
+    const uint32_t *recs = alt_a ? a_v1 : a_v0;
+    NA_CK(launch_gather_counts(recs, counts, (size_t)nrec, a_cnt, s));
+    NA_CK(exclusive_scan_u32(a_cnt, a_off, (size_t)nrec, rtmp, nullptr, s));
+    NA_CK(launch_emit_tiles(recs, a_off, (size_t)nrec, rect, gs->n, TW, TH, b_k0, b_v0, s));
+    NA_CK(radix_sort_pairs<uint32_t>(b_k0, b_v0, b_k1, b_v1, (size_t)M, bits_of((uint64_t)TT - 1), rtmp, &alt_b, s));
+    const uint32_t *keys = alt_b ? b_k1 : b_k0;
+    const uint32_t *vals = alt_b ? b_v1 : b_v0;
+    NA_CK(cudaMemsetAsync(ranges, 0, (size_t)TT * sizeof(uint2), s));   // tiles without entries stay empty
+    NA_CK(launch_ranges(keys, (size_t)M, ranges, s));
 
     CompositeArgs ca;
     memset(&ca, 0, sizeof(ca));

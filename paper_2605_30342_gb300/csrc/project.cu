@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(128) k_project(ProjectArgs a)
         for (int j = 0; j < KV; ++j) gm[j] = a.gamma ? ld_coef(a.gamma, (size_t)g * KV + j, a.vf_dtype) : 0.0f;
     }
     const float P = (float)a.n_train;
-    uint32_t zlo = 0xffffffffu, zhi = 0u, nvis = 0u;
+    uint32_t zlo = 0xffffffffu, zhi = 0u, nvis = 0u, ntiles = 0u;
 
     for (int v = 0; v < a.nv; ++v) {
         const gavis_camera &cam = s_cams[v];
@@ -169,7 +169,9 @@ __global__ void __launch_bounds__(128) k_project(ProjectArgs a)
             a.counts[r] = 0u;
             continue;
         }
-        a.counts[r] = (uint32_t)((p.x1 - p.x0 + 1) * (p.y1 - p.y0 + 1));
+        const uint32_t nt = (uint32_t)((p.x1 - p.x0 + 1) * (p.y1 - p.y0 + 1));
+        a.counts[r] = nt;
+        ntiles += nt;
         a.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.x1 << 16), (uint32_t)p.y0 | ((uint32_t)p.y1 << 16));
         zlo = min(zlo, __float_as_uint(p.z));
         zhi = max(zhi, __float_as_uint(p.z));
@@ -213,10 +215,12 @@ __global__ void __launch_bounds__(128) k_project(ProjectArgs a)
     const unsigned am = __activemask();
     const uint32_t wlo = __reduce_min_sync(am, zlo), whi = __reduce_max_sync(am, zhi);
     const uint32_t wvis = __reduce_add_sync(am, nvis);
+    const uint32_t wtiles = __reduce_add_sync(am, ntiles);
     if ((threadIdx.x & 31) == (unsigned)(__ffs(am) - 1) && wlo <= whi) {
         atomicMin(&a.zrange[0], wlo);
         atomicMax(&a.zrange[1], whi);
-        if (a.visible) atomicAdd(a.visible, (unsigned long long)wvis);
+        atomicAdd(a.visible, (unsigned long long)wvis);
+        atomicAdd(a.total, (unsigned long long)wtiles);
     }
 }
 

@@ -1,8 +1,9 @@
 // raster.cu -- tile binning, per-tile front-to-back compositing and the
 // reductions of the GAVIS hot path.
 //
-//   k_emit            one key per (view, Gaussian, tile of its rectangle)
-//   k_ranges          [start, end) of every (view, tile) in the sorted keys
+//   k_emit_records    stage A of binning: (view, depth) key per visible record
+//   k_emit_tiles      stage B: the record's tiles, in stage-A order
+//   k_ranges          [start, end) of every (view, tile) in the sorted entries
 //   k_composite_ua    Alg. "3DGS Uncertainty Quantification with Visibility
 //                     Field" + plain colour (eq:orig_vr), one thread per pixel
 //   k_composite_vis   Alg. "Single-view Particle Visibility", one thread per
@@ -84,44 +85,63 @@ __device__ __forceinline__ float footprint_q(float px, float py, float u, float 
     return __fmaf_rn(qb, dx, qd);
 }
 
-__global__ void k_emit(const uint2 *rect, const GeoRec *geo, const uint32_t *counts, const uint32_t *offsets,
-                       int nv, int64_t n, int TW, int TH, int zb, uint32_t zmin, uint64_t *keys, uint32_t *vals)
+// stage A: one record key per visible (view, Gaussian), in (view, index) order
+__global__ void k_emit_records(const uint32_t *counts, const uint32_t *pos, const GeoRec *geo, int nv, int64_t n,
+                               int zb, uint32_t zmin, uint64_t *keyA, uint32_t *valA)
 {
     const size_t total = (size_t)nv * (size_t)n;
     const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= total) return;
-    if (counts[r] == 0u) return;
-    const uint32_t v = (uint32_t)(r / (size_t)n);
-    const uint32_t g = (uint32_t)(r - (size_t)v * (size_t)n);
+    if (r >= total || counts[r] == 0u) return;
+    const uint64_t v = r / (size_t)n;
+    const uint32_t i = pos[r];
+    keyA[i] = (v << zb) | (uint64_t)(__float_as_uint(geo[r].b.z) - zmin);
+    valA[i] = (uint32_t)r;
+}
+
+__global__ void k_gather_counts(const uint32_t *valA, const uint32_t *counts, size_t nrec, uint32_t *cnt_sorted)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nrec) cnt_sorted[i] = counts[valA[i]];
+}
+
+// stage B: the tiles of each record, in stage-A order
+__global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect, int64_t n,
+                             int TW, int TH, uint32_t *keyB, uint32_t *valB)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrec) return;
+    const uint32_t r = valA[i];
+    const uint32_t v = (uint32_t)(r / (uint64_t)n);
+    const uint32_t g = (uint32_t)(r - (uint64_t)v * (uint64_t)n);
     const uint2 rc = rect[r];
     const uint32_t x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu, y1 = rc.y >> 16;
-    const uint32_t zl = __float_as_uint(geo[r].b.z) - zmin;
-    uint32_t off = offsets[r];
-    const uint64_t vbase = (uint64_t)v * (uint64_t)(TW * TH);
+    const uint32_t vbase = v * (uint32_t)(TW * TH);
+    uint32_t off = off_sorted[i];
     for (uint32_t ty = y0; ty <= y1; ++ty)
         for (uint32_t tx = x0; tx <= x1; ++tx) {
-            keys[off] = ((vbase + (uint64_t)(ty * (uint32_t)TW + tx)) << zb) | (uint64_t)zl;
-            vals[off] = g;
+            keyB[off] = vbase + ty * (uint32_t)TW + tx;
+            valB[off] = g;
             ++off;
         }
 }
 
-__global__ void k_ranges(const uint64_t *keys, size_t M, int zb, uint2 *ranges)
+__global__ void k_ranges(const uint32_t *keys, size_t M, uint2 *ranges)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
-    const uint32_t t = (uint32_t)(keys[i] >> zb);
-    if (i == 0 || (uint32_t)(keys[i - 1] >> zb) != t) ranges[t].x = (uint32_t)i;
-    if (i == M - 1 || (uint32_t)(keys[i + 1] >> zb) != t) ranges[t].y = (uint32_t)(i + 1);
+    const uint32_t t = keys[i];
+    if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
+    if (i == M - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
 }
 
-__global__ void k_keys_export(const uint64_t *keys, size_t M, int zb, uint32_t zmin, uint64_t *out)
+__global__ void k_keys_export(const uint32_t *keyB, const uint32_t *valB, size_t M, const GeoRec *geo, int64_t n,
+                              int tiles_per_view, uint64_t *out)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
-    const uint64_t k = keys[i];
-    const uint64_t low = zb ? (k & ((1ull << zb) - 1ull)) : 0ull;
-    out[i] = ((k >> zb) << 32) | (uint64_t)((uint32_t)low + zmin);
+    const uint32_t t = keyB[i];
+    const size_t r = (size_t)(t / (uint32_t)tiles_per_view) * (size_t)n + valB[i];
+    out[i] = ((uint64_t)t << 32) | (uint64_t)__float_as_uint(geo[r].b.z);
 }
 
 // 2^x and log2(x) on the special-function unit (PTX ex2/lg2, approximate;
@@ -557,27 +577,43 @@ inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-cudaError_t launch_emit(const uint2 *rect, const GeoRec *geo, const uint32_t *counts, const uint32_t *offsets,
-                        int nv, int64_t n, int TW, int TH, int zb, uint32_t zmin, uint64_t *keys, uint32_t *vals,
-                        cudaStream_t s)
+cudaError_t launch_emit_records(const uint32_t *counts, const uint32_t *pos, const GeoRec *geo, int nv, int64_t n,
+                                int zb, uint32_t zmin, uint64_t *keyA, uint32_t *valA, cudaStream_t s)
 {
     const size_t total = (size_t)nv * (size_t)n;
     if (total == 0) return cudaSuccess;
-    k_emit<<<nblk(total, 256), 256, 0, s>>>(rect, geo, counts, offsets, nv, n, TW, TH, zb, zmin, keys, vals); count_launch();
+    k_emit_records<<<nblk(total, 256), 256, 0, s>>>(counts, pos, geo, nv, n, zb, zmin, keyA, valA); count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_ranges(const uint64_t *keys, size_t M, int zb, uint2 *ranges, cudaStream_t s)
+cudaError_t launch_gather_counts(const uint32_t *valA, const uint32_t *counts, size_t nrec, uint32_t *cnt_sorted,
+                                 cudaStream_t s)
 {
-    if (M == 0) return cudaSuccess;
-    k_ranges<<<nblk(M, 256), 256, 0, s>>>(keys, M, zb, ranges); count_launch();
+    if (nrec == 0) return cudaSuccess;
+    k_gather_counts<<<nblk(nrec, 256), 256, 0, s>>>(valA, counts, nrec, cnt_sorted); count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_keys_export(const uint64_t *keys, size_t M, int zb, uint32_t zmin, uint64_t *out, cudaStream_t s)
+cudaError_t launch_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect,
+                              int64_t n, int TW, int TH, uint32_t *keyB, uint32_t *valB, cudaStream_t s)
+{
+    if (nrec == 0) return cudaSuccess;
+    k_emit_tiles<<<nblk(nrec, 256), 256, 0, s>>>(valA, off_sorted, nrec, rect, n, TW, TH, keyB, valB); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ranges(const uint32_t *keys, size_t M, uint2 *ranges, cudaStream_t s)
 {
     if (M == 0) return cudaSuccess;
-    k_keys_export<<<nblk(M, 256), 256, 0, s>>>(keys, M, zb, zmin, out); count_launch();
+    k_ranges<<<nblk(M, 256), 256, 0, s>>>(keys, M, ranges); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keys_export(const uint32_t *keyB, const uint32_t *valB, size_t M, const GeoRec *geo, int64_t n,
+                               int tiles_per_view, uint64_t *out, cudaStream_t s)
+{
+    if (M == 0) return cudaSuccess;
+    k_keys_export<<<nblk(M, 256), 256, 0, s>>>(keyB, valB, M, geo, n, tiles_per_view, out); count_launch();
     return cudaGetLastError();
 }
 

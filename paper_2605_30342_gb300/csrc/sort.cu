@@ -34,6 +34,7 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
     return t;   // valid in thread 0
 }
 
+template <bool FLAGS>
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *in, size_t n,
                                                               unsigned long long *partials)
 {
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *in
 #pragma unroll
     for (int r = 0; r < kScanItems; ++r) {
         size_t i = base + (size_t)r * kScanThreads + threadIdx.x;
-        if (i < n) v += in[i];
+        if (i < n) v += FLAGS ? (in[i] != 0u) : in[i];
     }
     v = block_sum_u64(v, s_warp);
     if (threadIdx.x == 0) partials[blockIdx.x] = v;
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_partials(unsigned long lo
     }
 }
 
+template <bool FLAGS>
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *in, uint32_t *out, size_t n,
                                                              const unsigned long long *partials)
 {
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *in,
 #pragma unroll
     for (int r = 0; r < kScanItems; ++r) {
         size_t i = base + r;
-        x[r] = i < n ? in[i] : 0u;
+        x[r] = i < n ? (FLAGS ? (uint32_t)(in[i] != 0u) : in[i]) : 0u;
         sum += x[r];
     }
     // exclusive scan of per-thread sums across the block
@@ -127,7 +129,8 @@ constexpr int kRsRounds = 16;
 constexpr int kRsTile = kRsThreads * kRsRounds;   // 4096 keys per block
 constexpr int kRsWarps = kRsThreads / 32;
 
-__global__ void __launch_bounds__(kRsThreads) k_radix_hist(const uint64_t *keys, size_t n, int shift,
+template <typename KeyT>
+__global__ void __launch_bounds__(kRsThreads) k_radix_hist(const KeyT *keys, size_t n, int shift,
                                                            uint32_t *hist, int nblocks)
 {
     __shared__ uint32_t s_h[256];
@@ -152,17 +155,19 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const uint64_t *keys,
 // turned into block-local digit offsets, items are placed in shared memory in
 // sorted order, and written out so that consecutive threads write consecutive
 // addresses of each digit run.
-constexpr size_t kRsSmem = (size_t)kRsTile * 12 + (size_t)(kRsWarps + 3) * 256 * 4;
+template <typename KeyT>
+constexpr size_t rs_smem() { return (size_t)kRsTile * (sizeof(KeyT) + 4) + (size_t)(kRsWarps + 3) * 256 * 4; }
 
-__global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const uint64_t *kin, const uint32_t *vin,
-                                                              uint64_t *kout, uint32_t *vout, size_t n, int shift,
+template <typename KeyT>
+__global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const KeyT *kin, const uint32_t *vin,
+                                                              KeyT *kout, uint32_t *vout, size_t n, int shift,
                                                               const uint32_t *hist, const uint32_t *offs,
                                                               int nblocks)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t *s_key = reinterpret_cast<uint64_t *>(smem);
-    uint32_t *s_val = reinterpret_cast<uint32_t *>(smem + (size_t)kRsTile * 8);
-    uint32_t *s_wc = reinterpret_cast<uint32_t *>(smem + (size_t)kRsTile * 12);   // [warps][256]
+    KeyT *s_key = reinterpret_cast<KeyT *>(smem);
+    uint32_t *s_val = reinterpret_cast<uint32_t *>(smem + (size_t)kRsTile * sizeof(KeyT));
+    uint32_t *s_wc = reinterpret_cast<uint32_t *>(smem + (size_t)kRsTile * (sizeof(KeyT) + 4));   // [warps][256]
     uint32_t *s_goff = s_wc + kRsWarps * 256;
     uint32_t *s_lstart = s_goff + 256;
     uint32_t *s_tmp = s_lstart + 256;
@@ -190,7 +195,7 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const uint64_t *ki
 
     // phase A: warp-private stable ranks
     constexpr int R = kRsTile / kRsThreads;   // 16 rounds of 32 items per warp
-    uint64_t k[R];
+    KeyT k[R];
     uint32_t v[R], rk[R];
     int d[R];
     uint32_t *wc = s_wc + warp * 256;
@@ -198,7 +203,7 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const uint64_t *ki
     for (int r = 0; r < R; ++r) {
         const size_t i = base + (size_t)warp * (32 * R) + (size_t)r * 32 + lane;
         const bool valid = i < n;
-        k[r] = valid ? kin[i] : 0ull;
+        k[r] = valid ? kin[i] : (KeyT)0;
         v[r] = valid ? vin[i] : 0u;
         d[r] = valid ? (int)((k[r] >> shift) & 255u) : 256;
     }
@@ -235,7 +240,7 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const uint64_t *ki
     // phase C: coalesced write-out
     const int cnt = (int)min((size_t)kRsTile, n - base);
     for (int i = tid; i < cnt; i += kRsThreads) {
-        const uint64_t kk = s_key[i];
+        const KeyT kk = s_key[i];
         const int dd = (int)((kk >> shift) & 255u);
         const uint32_t pos = s_goff[dd] + ((uint32_t)i - s_lstart[dd]);
         kout[pos] = kk;
@@ -252,7 +257,7 @@ size_t scan_tmp_bytes(size_t n)
 }
 
 cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, void *tmp,
-                               unsigned long long *d_total, cudaStream_t s)
+                               unsigned long long *d_total, cudaStream_t s, bool flags)
 {
     const size_t nb = (n + kScanChunk - 1) / kScanChunk;
     unsigned long long *partials = reinterpret_cast<unsigned long long *>(tmp);
@@ -260,9 +265,17 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, void
         if (d_total) return cudaMemsetAsync(d_total, 0, sizeof(unsigned long long), s);
         return cudaSuccess;
     }
-    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partials); count_launch();
+    if (flags) {
+        k_scan_reduce<true><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partials); count_launch();
+    } else {
+        k_scan_reduce<false><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partials); count_launch();
+    }
     k_scan_partials<<<1, kScanThreads, 0, s>>>(partials, (int)nb, d_total); count_launch();
-    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partials); count_launch();
+    if (flags) {
+        k_scan_apply<true><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partials); count_launch();
+    } else {
+        k_scan_apply<false><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partials); count_launch();
+    }
     return cudaGetLastError();
 }
 
@@ -274,8 +287,9 @@ size_t radix_tmp_bytes(size_t n)
     return 2 * a + scan_tmp_bytes(h) + 256;
 }
 
-cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, size_t n,
-                             int end_bit, void *tmp, bool *result_in_alt, cudaStream_t s)
+template <typename KeyT>
+cudaError_t radix_sort_pairs(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_t *vals_alt, size_t n, int end_bit,
+                             void *tmp, bool *result_in_alt, cudaStream_t s)
 {
     *result_in_alt = false;
     if (n <= 1) return cudaSuccess;
@@ -285,24 +299,30 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
     uint32_t *hist = reinterpret_cast<uint32_t *>(tmp);
     uint32_t *offs = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(tmp) + a);
     void *stmp = reinterpret_cast<char *>(tmp) + 2 * a;
+    constexpr size_t smem = rs_smem<KeyT>();
     // per device, idempotent
-    cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRsSmem);
-    uint64_t *kin = keys, *kout = keys_alt;
+    cudaFuncSetAttribute(k_radix_scatter<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    KeyT *kin = keys, *kout = keys_alt;
     uint32_t *vin = vals, *vout = vals_alt;
     bool alt = false;
     for (int shift = 0; shift < end_bit; shift += 8) {
-        k_radix_hist<<<nblocks, kRsThreads, 0, s>>>(kin, n, shift, hist, nblocks); count_launch();
+        k_radix_hist<KeyT><<<nblocks, kRsThreads, 0, s>>>(kin, n, shift, hist, nblocks); count_launch();
         cudaError_t e = exclusive_scan_u32(hist, offs, h, stmp, nullptr, s);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<nblocks, kRsThreads, kRsSmem, s>>>(kin, vin, kout, vout, n, shift, hist, offs, nblocks); count_launch();
+        k_radix_scatter<KeyT><<<nblocks, kRsThreads, smem, s>>>(kin, vin, kout, vout, n, shift, hist, offs, nblocks); count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        uint64_t *tk = kin; kin = kout; kout = tk;
+        KeyT *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;
         alt = !alt;
     }
     *result_in_alt = alt;
     return cudaSuccess;
 }
+
+template cudaError_t radix_sort_pairs<uint64_t>(uint64_t *, uint32_t *, uint64_t *, uint32_t *, size_t, int, void *,
+                                                bool *, cudaStream_t);
+template cudaError_t radix_sort_pairs<uint32_t>(uint32_t *, uint32_t *, uint32_t *, uint32_t *, size_t, int, void *,
+                                                bool *, cudaStream_t);
 
 }  // namespace gavis
