@@ -161,24 +161,27 @@ __device__ __forceinline__ float lg2_approx(float x)
 constexpr float kNegHalfLog2e = -0.72134752044448170368f;   // -log2(e) / 2
 constexpr float kLn2 = 0.69314718055994530942f;
 
-// Uncertainty + colour compositing.  Each thread owns two pixels of an 8 x 8
-// block per warp, (x, y) and (x, y + 4).  Per pixel and overlapping entry:
-// alpha = o 2^(-q log2(e)/2); colour w = alpha Tc, Tc -= w; uncertainty
-// alpha* = a1 alpha + a0 (eq:alpha_comp), w = alpha* T, wv = w V, T -= w.
-// The entropy bound (eq:huber) is assembled once per pixel from
-// sum(wv), sum(wv log2 wv) and the prior mass w0 = (1 - T) - sum(wv).
+// Uncertainty + colour compositing.  Each warp owns an 8 x 8 pixel block of
+// the tile (each thread two pixels, (x, y) and (x, y + 4)) and walks the
+// tile's depth-sorted list on its own, 32 entries at a time: every lane loads
+// one entry's footprint, the entries whose box touches the block are
+// compacted (in list order) into the warp's shared-memory slots, and the warp
+// composites them.  A warp stops as soon as all its pixels are saturated;
+// warps never wait for each other until the final tile sum.
+// Per pixel and overlapping entry: alpha = o 2^(-q log2(e)/2); colour
+// w = alpha Tc, Tc -= w; uncertainty alpha* = a1 alpha + a0 (eq:alpha_comp),
+// w = alpha* T, wv = w V, T -= w.  The entropy bound (eq:huber) is assembled
+// once per pixel from sum(wv), sum(wv log2 wv) and the prior mass
+// w0 = (1 - T) - sum(wv).
 template <int TILE>
 __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a)
 {
     constexpr int NT = TILE * TILE / 2;
-    constexpr int NB = 256;   // entries staged per batch
     constexpr int NW = NT / 32;
-    __shared__ float4 s_g0[NB];   // u, v, A, 2B
-    __shared__ float2 s_g1[NB];   // C, opacity
-    __shared__ float4 s_u0[NB];   // a1, a0, V, r
-    __shared__ float2 s_u1[NB];   // g, b
-    __shared__ uint32_t s_wm[NB];         // which warp blocks each entry's footprint box touches
-    __shared__ uint16_t s_list[NW][NB];   // per warp: its entries of the batch, in order
+    __shared__ float4 s_g0[NW][32];   // u, v, A, 2B
+    __shared__ float2 s_g1[NW][32];   // C, opacity
+    __shared__ float4 s_u0[NW][32];   // a1, a0, V, r
+    __shared__ float2 s_u1[NW][32];   // g, b
     __shared__ float s_red[NW];
     __shared__ uint32_t s_pairs[NW];
 
@@ -187,6 +190,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
     const int t = blockIdx.x - vb * tiles;
     const int tx = t % a.TW, ty = t / a.TW;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     const int wx = (warp % (TILE / 8)) * 8, wy = (warp / (TILE / 8)) * 8;
     const int i = tx * TILE + wx + (lane & 7);
     const int j0 = ty * TILE + wy + (lane >> 3);
@@ -209,31 +213,36 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
         rgb_on[p] = inside[p];
     }
     uint32_t npairs = 0;
+    float4 *g0s = s_g0[warp];
+    float2 *g1s = s_g1[warp];
+    float4 *u0s = s_u0[warp];
+    float2 *u1s = s_u1[warp];
 
-    for (uint32_t base = rg.x; base < rg.y; base += NB) {
-        const bool any = ua_on[0] || rgb_on[0] || ua_on[1] || rgb_on[1];
-        if (__syncthreads_count(any) == 0) break;
-        for (int k = tid; k < NB; k += NT) {
-            const uint32_t e = base + k;
-            uint32_t wm = 0u;
-            if (e < rg.y) {
-                const size_t r = vrow + a.vals[e];
-                const GeoRec gr = a.geo[r];
-                const UaRec ur = a.ua[r];
-                s_g0[k] = gr.a;
-                s_g1[k] = make_float2(gr.b.x, gr.b.y);
-                s_u0[k] = ur.a;
-                s_u1[k] = make_float2(ur.b.x, ur.b.y);
-                wm = warp_block_mask<TILE>(footprint_box(gr.a.x, gr.a.y, gr.b.w), tx, ty);
-            }
-            s_wm[k] = wm;
+    for (uint32_t base = rg.x; base < rg.y; base += 32) {
+        if (!__any_sync(0xffffffffu, ua_on[0] || rgb_on[0] || ua_on[1] || rgb_on[1])) break;
+        const uint32_t e = base + lane;
+        bool mine = false;
+        GeoRec gr;
+        size_t r = 0;
+        if (e < rg.y) {
+            r = vrow + a.vals[e];
+            gr = a.geo[r];
+            mine = !box_misses(footprint_box(gr.a.x, gr.a.y, gr.b.w), bx0, bx1, by0, by1);
         }
-        __syncthreads();
-        const int nk = build_warp_list<NB>(s_wm, warp, lane, s_list[warp]);
-        for (int idx = 0; idx < nk && (ua_on[0] || rgb_on[0] || ua_on[1] || rgb_on[1]); ++idx) {
-            const int k = s_list[warp][idx];
-            const float4 g0 = s_g0[k];
-            const float2 g1 = s_g1[k];
+        const unsigned m = __ballot_sync(0xffffffffu, mine);
+        if (mine) {
+            const int slot = __popc(m & lt);
+            const UaRec ur = a.ua[r];
+            g0s[slot] = gr.a;
+            g1s[slot] = make_float2(gr.b.x, gr.b.y);
+            u0s[slot] = ur.a;
+            u1s[slot] = make_float2(ur.b.x, ur.b.y);
+        }
+        __syncwarp();
+        const int nk = __popc(m);
+        for (int k = 0; k < nk && (ua_on[0] || rgb_on[0] || ua_on[1] || rgb_on[1]); ++k) {
+            const float4 g0 = g0s[k];
+            const float2 g1 = g1s[k];
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
                 if (!(ua_on[p] || rgb_on[p])) continue;
@@ -241,9 +250,9 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
                 if (!(q <= rc.q_cut)) continue;
                 ++npairs;
                 const float alpha = g1.y * ex2_approx(q * kNegHalfLog2e);
-                const float4 u0 = s_u0[k];
+                const float4 u0 = u0s[k];
                 if (rgb_on[p]) {
-                    const float2 u1 = s_u1[k];
+                    const float2 u1 = u1s[k];
                     const float w = alpha * Tc[p];
                     cr[p] = fmaf(w, u0.w, cr[p]);
                     cg[p] = fmaf(w, u1.x, cg[p]);
@@ -262,6 +271,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
                 }
             }
         }
+        __syncwarp();
     }
     float h = 0.0f;
     const size_t vg = (size_t)(a.v0 + vb);
