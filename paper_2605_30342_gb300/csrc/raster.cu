@@ -313,29 +313,28 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
     }
 }
 
-// Single-view particle visibility.  Each thread owns two pixels of an 8 x 8
-// block per warp.  Per overlapping entry a pixel contributes its current T
-// (fixed point, 2^-24) and a count of one to the Gaussian's sums; the warp
-// adds its 64 pixels with one redux, the block in shared memory, and one
-// global atomic per (tile, Gaussian) follows each batch.
+// Single-view particle visibility.  Each warp owns an 8 x 8 pixel block of
+// the tile (each thread two pixels) and walks the tile's depth-sorted list on
+// its own, 32 entries at a time, compacting the entries whose footprint box
+// touches the block.  Per overlapping entry a pixel contributes its current T
+// (fixed point, 2^-24) and a count of one to the Gaussian's sums; the warp adds
+// its 64 pixels with one redux and lane 0 adds them to the Gaussian's
+// accumulators with one atomic each.  A warp stops when its pixels saturate.
 template <int TILE>
 __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs a)
 {
     constexpr int NT = TILE * TILE / 2;
-    constexpr int NB = 256;
-    __shared__ float4 s_g0[NB];
-    __shared__ float2 s_g1[NB];
-    __shared__ unsigned long long s_sum[NB];
-    __shared__ uint32_t s_cnt[NB];
-    __shared__ uint32_t s_idx[NB];
-    __shared__ uint32_t s_wm[NB];
-    __shared__ uint16_t s_list[NT / 32][NB];
+    constexpr int NW = NT / 32;
+    __shared__ float4 s_g0[NW][32];
+    __shared__ float2 s_g1[NW][32];
+    __shared__ uint32_t s_idx[NW][32];
 
     const int tiles = a.TW * a.TH;
     const int vb = blockIdx.x / tiles;
     const int t = blockIdx.x - vb * tiles;
     const int tx = t % a.TW, ty = t / a.TW;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     const int wx = (warp % (TILE / 8)) * 8, wy = (warp / (TILE / 8)) * 8;
     const int i = tx * TILE + wx + (lane & 7);
     const int j0 = ty * TILE + wy + (lane >> 3);
@@ -349,34 +348,34 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
     float T0 = 1.0f, T1 = 1.0f;
     bool on0 = i < a.W && j0 < a.H, on1 = i < a.W && j0 + 4 < a.H;
     uint32_t wpairs = 0;
-    for (int k = tid; k < NB; k += NT) {
-        s_sum[k] = 0ull;
-        s_cnt[k] = 0u;
-    }
+    float4 *g0s = s_g0[warp];
+    float2 *g1s = s_g1[warp];
+    uint32_t *ids = s_idx[warp];
 
-    for (uint32_t base = rg.x; base < rg.y; base += NB) {
-        if (__syncthreads_count(on0 || on1) == 0) break;
-        for (int k = tid; k < NB; k += NT) {
-            const uint32_t e = base + k;
-            uint32_t wm = 0u;
-            if (e < rg.y) {
-                const uint32_t g = a.vals[e];
-                const GeoRec gr = a.geo[vrow + g];
-                s_g0[k] = gr.a;
-                s_g1[k] = make_float2(gr.b.x, gr.b.y);
-                s_idx[k] = g;
-                wm = warp_block_mask<TILE>(footprint_box(gr.a.x, gr.a.y, gr.b.w), tx, ty);
-            }
-            s_wm[k] = wm;
+    for (uint32_t base = rg.x; base < rg.y; base += 32) {
+        if (!__any_sync(0xffffffffu, on0 || on1)) break;
+        const uint32_t e = base + lane;
+        bool mine = false;
+        GeoRec gr;
+        uint32_t g = 0;
+        if (e < rg.y) {
+            g = a.vals[e];
+            gr = a.geo[vrow + g];
+            mine = !box_misses(footprint_box(gr.a.x, gr.a.y, gr.b.w), bx0, bx1, by0, by1);
         }
-        __syncthreads();
-        const int cnt = (int)min((uint32_t)NB, rg.y - base);
-        const int nk = build_warp_list<NB>(s_wm, warp, lane, s_list[warp]);
-        for (int idx = 0; idx < nk; ++idx) {
-            if (!__any_sync(0xffffffffu, on0 || on1)) break;          // warp-uniform
-            const int k = s_list[warp][idx];
-            const float4 g0 = s_g0[k];
-            const float2 g1 = s_g1[k];
+        const unsigned mk = __ballot_sync(0xffffffffu, mine);
+        if (mine) {
+            const int slot = __popc(mk & lt);
+            g0s[slot] = gr.a;
+            g1s[slot] = make_float2(gr.b.x, gr.b.y);
+            ids[slot] = g;
+        }
+        __syncwarp();
+        const int nk = __popc(mk);
+        for (int k = 0; k < nk; ++k) {
+            if (!__any_sync(0xffffffffu, on0 || on1)) break;   // warp-uniform
+            const float4 g0 = g0s[k];
+            const float2 g1 = g1s[k];
             const float q0 = footprint_q(px, py0, g0.x, g0.y, g0.z, g0.w, g1.x);
             const float q1 = footprint_q(px, py1, g0.x, g0.y, g0.z, g0.w, g1.x);
             const bool h0 = on0 && (q0 <= qcut), h1 = on1 && (q1 <= qcut);
@@ -387,8 +386,9 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
                 const uint32_t c = (uint32_t)(__popc(m0) + __popc(m1));
                 wpairs += c;
                 if (lane == 0) {
-                    atomicAdd(&s_sum[k], (unsigned long long)sum);
-                    atomicAdd(&s_cnt[k], c);
+                    const size_t r = vrow + ids[k];
+                    atomicAdd(&a.sumT[r], (unsigned long long)sum);
+                    atomicAdd(&a.cnt[r], c);
                 }
             }
             if (h0) {
@@ -400,16 +400,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
                 on1 = T1 >= eps;
             }
         }
-        __syncthreads();
-        for (int k = tid; k < cnt; k += NT) {
-            if (s_cnt[k] > 0u) {
-                const size_t r = vrow + s_idx[k];
-                atomicAdd(&a.sumT[r], s_sum[k]);
-                atomicAdd(&a.cnt[r], s_cnt[k]);
-                s_sum[k] = 0ull;
-                s_cnt[k] = 0u;
-            }
-        }
+        __syncwarp();
     }
     if (a.pairs && lane == 0 && wpairs) atomicAdd(a.pairs, (unsigned long long)wpairs);
 }
