@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--n-train", type=int, default=None)
     ap.add_argument("--n-cand", type=int, default=None)
     ap.add_argument("--views-per-batch", type=int, default=0)
-    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--tile", type=int, default=0, help="tile edge 8/16/32; 0 = autotune per path")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-views", type=int, default=1)
@@ -83,7 +83,7 @@ def config_json(c, args, extra=None):
         "vf_degree": c["vf_degree"],
         "coeff_storage": c["coeff_dtype"],
         "compositing": "f32",
-        "tile": args.tile,
+        "tile": args.tile if args.tile else "autotuned",
         "l2": "inputs and per-view records larger than L2 (no flush needed)",
         "parallelism": "replicas" if args.gpus > 1 else "single",
     }
@@ -266,13 +266,21 @@ def run_gavis(args):
     ctx = gv.Context(local)
     prm = gv.Params(vf_degree=L, tile=args.tile, views_per_batch=args.views_per_batch)
     vf = gv.VisibilityField(torch.zeros((sc.n, (L + 1) ** 2), dtype=cdt, device=dev), L, 0, 1.0)
+    prm_vf, prm_sc = prm, prm
+    tuned = None
+    if args.tile == 0:
+        # autotuner: tile edge per path, timed on 8 sample views (untimed here)
+        prm_vf, ms_vf = ctx.autotune(gs, train[:8], None, gv.Params(vf_degree=L, views_per_batch=args.views_per_batch))
+        ctx.vf_build(gs, train, degree=L, params=prm_vf, out=vf)
+        prm_sc, ms_sc = ctx.autotune(gs, cand[:8], vf, gv.Params(vf_degree=L, views_per_batch=args.views_per_batch))
+        tuned = {"vf_build_tile": prm_vf.tile, "score_tile": prm_sc.tile}
     W, H = cand[0].W, cand[0].H
     outs = {"rgb": torch.empty((n_cand, 3, H, W), device=dev), "unc": torch.empty((n_cand, H, W), device=dev),
             "score": torch.empty(n_cand, device=dev), "best_dev": torch.empty(1, dtype=torch.int32, device=dev)}
 
     def step():
-        ctx.vf_build(gs, train, degree=L, params=prm, out=vf)
-        return ctx.score_views(gs, vf, cand, params=prm, out=outs, sync_best=False)
+        ctx.vf_build(gs, train, degree=L, params=prm_vf, out=vf)
+        return ctx.score_views(gs, vf, cand, params=prm_sc, out=outs, sync_best=False)
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -314,10 +322,10 @@ def run_gavis(args):
 
     # ---------------- per-call work counts (one untimed instrumented pass) ----------------
     ctx.prof_enable(True)
-    ctx.vf_build(gs, train, degree=L, params=prm, out=vf)
+    ctx.vf_build(gs, train, degree=L, params=prm_vf, out=vf)
     vis_vf = ctx.prof_read()["visible"]
     ctx.prof_enable(True)
-    ctx.score_views(gs, vf, cand, params=prm, out=outs, sync_best=False)
+    ctx.score_views(gs, vf, cand, params=prm_sc, out=outs, sync_best=False)
     vis_sc = ctx.prof_read()["visible"]
     ctx.prof_enable(False)
     b = torch.tensor([], dtype=cdt).element_size()
@@ -400,7 +408,7 @@ def run_gavis(args):
             "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": config_json(c, args),
+            "config": config_json(c, args, {"autotuned": tuned} if tuned else None),
             "e2e": {"value": e2e_value, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
             "gpu_launches": int(launches),

@@ -182,6 +182,18 @@ int gavis_vf_density_control(gavis_ctx *ctx, const gavis_gaussians *gs, const fl
                              float eps_v, float *vis_out, uint8_t *keep, float *kept_means, int64_t *n_keep,
                              float *scale_out, void *stream);
 
+/* Autotuner (no counterpart in the paper): times the chain on the sample
+ * cameras with tile edges 8, 16 and 32 (one warm-up and two timed runs each,
+ * CUDA events on `stream`) and writes the fastest into p->tile.  mode 0 tunes
+ * gavis_score_views (vf required), mode 1 gavis_vf_build (vf ignored).
+ * Choices are cached per workload shape (mode, W x H, power-of-two buckets of
+ * the Gaussian and camera counts, SH degrees) in the process, and appended to
+ * the file named by the environment variable GAVIS_AUTOTUNE_CACHE when set
+ * (read back on first use); a cached choice returns at once with *best_ms =
+ * -1.  best_ms: host or NULL.  Synchronises `stream`. */
+int gavis_autotune(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf, const gavis_camera *cams, int n_cams,
+                   int mode, gavis_params *p, double *best_ms, void *stream);
+
 /* Visibility-field query alone (Alg. "Query Anisotropic Visibility Field").
  * V: device [n_cams][n] float32.  Culling is not applied: every Gaussian gets
  * a value. */

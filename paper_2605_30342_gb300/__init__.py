@@ -66,7 +66,7 @@ EXPORTS = ["gavis_ctx_create", "gavis_ctx_destroy", "gavis_last_error", "gavis_p
            "gavis_vmf_coeffs", "gavis_vf_build", "gavis_score_views", "gavis_vf_query", "gavis_debug_bins",
            "gavis_debug_visibility", "gavis_prof_enable", "gavis_prof_read", "gavis_vf_density_control",
            "gavis_server_create", "gavis_server_destroy", "gavis_server_last_error", "gavis_server_add_scene",
-           "gavis_server_submit", "gavis_server_wait", "gavis_server_stats"]
+           "gavis_server_submit", "gavis_server_wait", "gavis_server_stats", "gavis_autotune"]
 
 STAGES = ["project", "scan", "emit", "sort", "ranges", "composite_ua", "composite_vis", "reduce", "vf_accum"]
 
@@ -119,6 +119,8 @@ def load(path: str | None = None):
         lib.gavis_server_wait.argtypes = [vp, i64, i32, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
         lib.gavis_server_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                            C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+        lib.gavis_autotune.argtypes = [vp, C.POINTER(gavis_gaussians), C.POINTER(gavis_vf), C.POINTER(gavis_camera), i32,
+                                       i32, C.POINTER(gavis_params), C.POINTER(C.c_double), vp]
         lib.gavis_prof_enable.argtypes = [vp, i32]
         lib.gavis_prof_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                         C.POINTER(C.c_uint64)]
@@ -300,6 +302,18 @@ class Context:
         self._check(self._lib.gavis_vf_query(self._h, C.byref(gs.struct), C.byref(vs), camera_records(cams),
                                              len(cams), C.byref(p), C.c_void_p(V.data_ptr()), _stream_ptr(stream)))
         return V
+
+    # -------------------------------------------------------------- autotuner
+    def autotune(self, gs: Gaussians, sample_cams, vf: VisibilityField | None = None, params=None, stream=None):
+        """Pick the tile edge for scoring (vf given) or field construction
+        (vf None) on sample cameras; returns (params, best_ms)."""
+        p = params or Params(vf_degree=vf.degree if vf is not None else 2)
+        ms = C.c_double(0.0)
+        vs = vf.struct() if vf is not None else None
+        self._check(self._lib.gavis_autotune(self._h, C.byref(gs.struct), C.byref(vs) if vs is not None else None,
+                                             camera_records(sample_cams), len(sample_cams), 0 if vf is not None else 1,
+                                             C.byref(p), C.byref(ms), _stream_ptr(stream)))
+        return p, float(ms.value)
 
     # -------------------------------------------------------------- density control
     def density_control(self, gs: Gaussians, virt_means: torch.Tensor, train_cams, rho: float = 100.0,

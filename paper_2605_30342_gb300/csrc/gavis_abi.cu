@@ -13,6 +13,9 @@
 // sizes buffers, copies camera records and launches kernels.
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -43,7 +46,7 @@ struct gavis_ctx {
     size_t budget = 0;
     size_t used = 0;
     std::string err;
-    Buf rec, vis, keys, small, gamma, cams, aug;
+    Buf rec, vis, keys, small, gamma, cams, aug, tune;
     BatchInfo *h_info = nullptr;             // pinned
     int32_t *h_best = nullptr;               // pinned
     // instrumentation
@@ -573,7 +576,7 @@ void gavis_ctx_destroy(gavis_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    for (Buf *b : {&ctx->rec, &ctx->vis, &ctx->keys, &ctx->small, &ctx->gamma, &ctx->cams, &ctx->aug})
+    for (Buf *b : {&ctx->rec, &ctx->vis, &ctx->keys, &ctx->small, &ctx->gamma, &ctx->cams, &ctx->aug, &ctx->tune})
         if (b->p) cudaFree(b->p);
     if (ctx->h_info) cudaFreeHost(ctx->h_info);
     if (ctx->h_best) cudaFreeHost(ctx->h_best);
@@ -884,6 +887,115 @@ int gavis_vf_density_control(gavis_ctx *ctx, const gavis_gaussians *gs, const fl
         CK(cudaStreamSynchronize(s));
         *n_keep = (int64_t)ctx->h_info->total;
     }
+    return GAVIS_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune_cache;   // workload key -> tile edge
+
+std::string tune_key(int mode, const gavis_gaussians *gs, const gavis_vf *vf, const gavis_camera *c, int n)
+{
+    char buf[160];
+    // the Gaussian count is bucketed by powers of two
+    snprintf(buf, sizeof(buf), "m%d_w%d_h%d_n%d_sh%d_vf%d_v%d", mode, c->W, c->H, bits_of((uint64_t)gs->n),
+             gs->sh_degree, vf ? vf->degree : -1, bits_of((uint64_t)n));
+    return buf;
+}
+
+void tune_cache_load(const char *path)
+{
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char key[160];
+    int tile;
+    while (fscanf(f, "%159s %d", key, &tile) == 2) g_tune_cache[key] = tile;
+    fclose(f);
+}
+
+void tune_cache_store(const char *path, const std::string &key, int tile)
+{
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d\n", key.c_str(), tile);
+    fclose(f);
+}
+
+}  // namespace
+
+int gavis_autotune(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf, const gavis_camera *cams, int n_cams,
+                   int mode, gavis_params *p, double *best_ms, void *stream)
+{
+    if (!ctx) return GAVIS_ERR_ARG;
+    int rc;
+    if ((rc = check_params(ctx, p)) || (rc = check_gaussians(ctx, gs, mode == 0)) || (rc = check_cams(ctx, cams, n_cams)))
+        return rc;
+    if (mode != 0 && mode != 1) return fail(ctx, GAVIS_ERR_ARG, "mode must be 0 (scoring) or 1 (field construction)");
+    if (mode == 0 && (rc = check_vf(ctx, gs, vf))) return rc;
+    if (n_cams < 1 || gs->n == 0) return GAVIS_OK;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const std::string key = tune_key(mode, gs, vf, cams, n_cams);
+    const char *path = std::getenv("GAVIS_AUTOTUNE_CACHE");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        static bool loaded = false;
+        if (path && !loaded) {
+            tune_cache_load(path);
+            loaded = true;
+        }
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            p->tile = it->second;
+            if (best_ms) *best_ms = -1.0;
+            return GAVIS_OK;
+        }
+    }
+    // scratch outputs of the trial runs
+    const size_t plane = (size_t)cams[0].W * cams[0].H;
+    const int L = mode == 0 ? vf->degree : p->vf_degree;
+    const size_t K = (size_t)(L + 1) * (L + 1);
+    const size_t bytes = mode == 0 ? align256((size_t)n_cams * 4) + (size_t)n_cams * plane * 4
+                                   : (size_t)gs->n * K * 4;
+    if ((rc = ensure(ctx, ctx->tune, bytes)) != GAVIS_OK) return rc;
+    float *score = reinterpret_cast<float *>(ctx->tune.p);
+    float *unc = reinterpret_cast<float *>(reinterpret_cast<char *>(ctx->tune.p) + align256((size_t)n_cams * 4));
+    gavis_vf tv;
+    tv.n = gs->n; tv.coeffs = ctx->tune.p; tv.degree = L; tv.dtype = GAVIS_F32; tv.n_train_views = 0; tv.kappa = 0;
+    cudaEvent_t e0 = take_event(ctx), e1 = take_event(ctx);
+    const int tiles[3] = {8, 16, 32};
+    double best = 1e300;
+    int best_tile = p->tile;
+    for (int t : tiles) {
+        gavis_params q = *p;
+        q.tile = t;
+        double ms_sum = 0.0;
+        for (int rep = 0; rep < 3; ++rep) {   // the first run warms up the workspace
+            CK(cudaEventRecord(e0, s));
+            rc = mode == 0 ? gavis_score_views(ctx, gs, vf, cams, n_cams, &q, nullptr, unc, score, nullptr, nullptr, stream)
+                           : gavis_vf_build(ctx, gs, cams, n_cams, &q, &tv, 0, stream);
+            if (rc != GAVIS_OK) return rc;
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) ms_sum += ms;
+        }
+        const double ms = ms_sum / 2.0;
+        if (ms < best) {
+            best = ms;
+            best_tile = t;
+        }
+    }
+    ctx->pool.push_back(e0);
+    ctx->pool.push_back(e1);
+    p->tile = best_tile;
+    if (best_ms) *best_ms = best;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best_tile;
+    if (path) tune_cache_store(path, key, best_tile);
     return GAVIS_OK;
 }
 

@@ -326,3 +326,19 @@ def test_density_control_feeds_scoring(ctx, gv):
     err, _ = compare_views(out["unc"].cpu().numpy(), out["rgb"].cpu().numpy(), ref)
     assert err <= TOL
     assert k > 0
+
+
+def test_autotune_picks_a_tile_and_caches(ctx, gv):
+    c = case("room_small")
+    gs = gpu_scene(gv, c["scene"])
+    vf = ctx.vf_build(gs, c["train"], degree=3)
+    p, ms = ctx.autotune(gs, c["cand"][:3], vf, gv.Params(vf_degree=3))
+    assert p.tile in (8, 16, 32) and ms > 0
+    p2, ms2 = ctx.autotune(gs, c["cand"][:3], vf, gv.Params(vf_degree=3))
+    assert p2.tile == p.tile and ms2 == -1.0          # cached choice
+    pv, msv = ctx.autotune(gs, c["train"][:2], None, gv.Params(vf_degree=3))
+    assert pv.tile in (8, 16, 32)
+    # the tuned parameters give the oracle's answer (scores within tolerance)
+    out = ctx.score_views(gs, vf, c["cand"], params=p)
+    ref = ctx.score_views(gs, vf, c["cand"], params=gv.Params(vf_degree=3, tile=16))
+    assert (out["score"] - ref["score"]).abs().max().item() <= TOL
