@@ -83,6 +83,10 @@ typedef struct {
     const void *sh;              /* device [n][(sh_degree+1)^2][3], dtype sh_dtype; may be NULL for VF build */
     int32_t sh_degree;           /* 0..3 */
     int32_t sh_dtype;            /* gavis_dtype */
+    const void *sh_var;          /* device [n][(sh_degree+1)^2][3] variances of the colour coefficients
+                                    (dtype sh_dtype, > 0), or NULL.  When given, the colour covariance of a
+                                    Gaussian seen along d is diagonal with Q_k = sum_j Y_j(d)^2 var_jk
+                                    (Sec. "Integration with FisherRF"); when NULL, Q_c = sigma_c2 I_3. */
 } gavis_gaussians;
 
 typedef struct {

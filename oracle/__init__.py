@@ -79,13 +79,13 @@ def _declare(L):
     L.oracle_ranges.argtypes = [i64, vp, i64, vp]
     L.oracle_pixel_lists.argtypes = [vp, i64, vp, vp, vp, dbl, i32, i32, vp, vp, i64]
     L.oracle_pixel_lists.restype = i64
-    L.oracle_composite.argtypes = [i64, vp, vp, vp, vp, vp]
+    L.oracle_composite.argtypes = [i64, vp, vp, vp, vp, vp, vp]
     L.oracle_vf_query.argtypes = [i64, vp, i32, i64, vp, vp, vp, vp]
     L.oracle_vf_exact.argtypes = [i64, i32, vp, vp, dbl, vp, vp]
     L.oracle_visibility_view.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     L.oracle_visibility_view.restype = i64
     L.oracle_vf_build.argtypes = [i32, vp, i64, vp, vp, vp, vp, i32, vp, vp, vp, vp]
-    L.oracle_render_view.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]
+    L.oracle_render_view.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]
     L.oracle_density_control.argtypes = [i32, vp, i64, vp, vp, vp, vp, i64, vp, dbl, dbl, dbl, vp, vp, vp, vp]
     L.oracle_density_control.restype = i64
 
@@ -200,13 +200,16 @@ def pixel_lists(cam, scene, q_cut=9.0, tile=16, brute=False):
 # compositing, visibility field
 # ----------------------------------------------------------------------------
 
-def composite(alpha, V, col, prm=None):
-    """One pixel over an explicit list; returns dict of the outputs."""
+def composite(alpha, V, col, prm=None, kc=None):
+    """One pixel over an explicit list; returns dict of the outputs.  kc:
+    optional per-entry 1/2 log((2 pi e)^3 |Q_c|)."""
     prm = params() if prm is None else prm
     alpha, V = _f64(alpha), _f64(V)
     col = _f64(np.asarray(col).reshape(-1, 3))
+    kc = None if kc is None else _f64(kc)
     res = np.zeros(11)
-    lib().oracle_composite(len(alpha), _p(alpha), _p(V), _p(col), _p(prm), _p(res))
+    lib().oracle_composite(len(alpha), _p(alpha), _p(V), _p(col), _p(prm), _p(kc) if kc is not None else None,
+                           _p(res))
     return dict(H=res[0], rgb=res[1:4].copy(), T=res[4], Tc=res[5], sum_w=res[6], sum_wc=res[7],
                 w0=res[8], used=int(res[9]), amb=bool(res[10]))
 
@@ -277,30 +280,33 @@ def density_control(cams, scene, vmeans, rho=100.0, eta=0.5, eps_v=0.95, prm=Non
     return vis, keep.astype(bool), amb.astype(bool)
 
 
-def render_view(cam, scene, V, prm=None, sh=None):
-    """rgb (3,H,W), unc (H,W), amb (H,W) bool, used (H,W)."""
+def render_view(cam, scene, V, prm=None, sh=None, sh_var=None):
+    """rgb (3,H,W), unc (H,W), amb (H,W) bool, used (H,W).  sh_var: optional
+    per-coefficient colour variances (FisherRF variant of Q_c)."""
     prm = params() if prm is None else prm
     n = scene.n
     sh = _f64(scene.sh if sh is None else sh)
+    var = None if sh_var is None else _f64(sh_var)
     Lc = int(round(np.sqrt(sh.shape[1]))) - 1
     rgb = np.zeros((3, cam.H, cam.W))
     unc = np.zeros((cam.H, cam.W))
     amb = np.zeros((cam.H, cam.W), np.uint8)
     used = np.zeros((cam.H, cam.W), np.int32)
     lib().oracle_render_view(_p(cam_record(cam)), n, _p(_f32(scene.means)), _p(_f32(scene.scales)),
-                             _p(_f32(scene.rots)), _p(_f32(scene.opac)), _p(sh), Lc, _p(_f64(V)), _p(prm),
+                             _p(_f32(scene.rots)), _p(_f32(scene.opac)), _p(sh), _p(var) if var is not None else None,
+                             Lc, _p(_f64(V)), _p(prm),
                              _p(rgb), _p(unc), _p(amb), _p(used))
     return rgb, unc, amb.astype(bool), used
 
 
-def score_views(scene, gamma, L, P, cams, prm=None, sh=None, keep_images=True):
+def score_views(scene, gamma, L, P, cams, prm=None, sh=None, keep_images=True, sh_var=None):
     """Per-view mean entropy score S_v (eq:id with f_corr = 0) and the argmax
     of eq:i_gain (ties to the lowest index)."""
     prm = params() if prm is None else prm
     out = dict(rgb=[], unc=[], amb=[], used=[], score=np.zeros(len(cams)))
     for v, cam in enumerate(cams):
         V, _ = vf_query(gamma, L, P, cam, scene.means)
-        rgb, unc, amb, used = render_view(cam, scene, V, prm, sh)
+        rgb, unc, amb, used = render_view(cam, scene, V, prm, sh, sh_var)
         out["score"][v] = unc.mean()
         if keep_images:
             out["rgb"].append(rgb)

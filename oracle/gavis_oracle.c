@@ -34,6 +34,10 @@
  *   oracle_bins          the (view, tile, depth) keys a tile rasterizer sorts
  *                        by, in canonical order (stable, ties by index).
  *   oracle_composite     one pixel's compositing over a given list (pins).
+ *   (colour covariance)  with per-Gaussian coefficient variances, the
+ *                        FisherRF variant Q_c,k(d) = sum_j Y_j(d)^2 var_jk
+ *                        (Sec. "Integration with FisherRF") replaces the
+ *                        constant sigma_c^2 I in eq:huber.
  *   oracle_visibility_view  Alg. "Single-view Particle Visibility" alone.
  *   oracle_density_control  Alg. "Visibility Field Density Control": virtual
  *                        particles, product visibility over views, pruning.
@@ -485,16 +489,18 @@ static int near_thresh(double T, double eps, double margin)
 
 /* One pixel of Alg. "3DGS Uncertainty Quantification with Visibility Field"
  * together with the plain colour of eq:orig_vr.
- * in:  n entries with alpha[i] (effective opacity o*exp(-q/2)), V[i], col[3i..]
+ * in:  n entries with alpha[i] (effective opacity o*exp(-q/2)), V[i], col[3i..],
+ *      kc_each[i] (optional) = 1/2 log((2 pi e)^3 |Q_c|) of entry i, else the
+ *      constant Q_c = sigma_c2 I_3
  * out: res[0] = H, res[1..3] = rgb, res[4] = T_end, res[5] = Tc_end,
  *      res[6] = sum of w*, res[7] = sum of colour weights, res[8] = w0bar,
  *      res[9] = entries consumed, res[10] = 1 if a transmittance test landed
  *      within margin*eps of eps. */
 void oracle_composite(int64_t n, const double *alpha, const double *V, const double *col,
-                      const double *prm, double *res)
+                      const double *prm, const double *kc_each, double *res)
 {
     const double eps = prm[P_EPS_T], beta = prm[P_BETA], o0 = prm[P_O0];
-    const double kc = 0.5 * 3.0 * log(prm[P_SIGMA_C2]) + 1.5 * (log(2.0 * M_PI) + 1.0);
+    const double kc_const = 0.5 * 3.0 * log(prm[P_SIGMA_C2]) + 1.5 * (log(2.0 * M_PI) + 1.0);
     const double k0 = 0.5 * prm[P_LOGDET_Q0] + 1.5 * (log(2.0 * M_PI) + 1.0);
     const double margin = prm[P_MARGIN];
     double T = 1.0, Tc = 1.0, H = 0.0, w0 = 0.0, sw = 0.0, swc = 0.0;
@@ -517,7 +523,8 @@ void oracle_composite(int64_t n, const double *alpha, const double *V, const dou
             double as = (v + beta * (1.0 - v)) * a + o0 * (1.0 - beta) * (1.0 - v);  /* eq:alpha_comp */
             double w = as * T;
             double wv = w * v;
-            H += phi(wv) + wv * kc;          /* visible component of eq:huber */
+            double kc = kc_each ? kc_each[i] : kc_const;   /* 1/2 log((2 pi e)^3 |Q_c|) */
+            if (wv > 0.0) H += phi(wv) + wv * kc;          /* visible component of eq:huber */
             w0 += w * (1.0 - v);             /* mass of the prior component */
             sw += w;
             T = T * (1.0 - as);
@@ -690,7 +697,7 @@ void oracle_vf_build(int nview, const float *cams, int64_t n, const float *means
  * consumed.  V: per-Gaussian visibility for this view (from oracle_vf_query).
  * sh: n x (Lc+1)^2 x 3 colour coefficients. */
 void oracle_render_view(const float *cam, int64_t n, const float *means, const float *scales,
-                        const float *rots, const float *opac, const double *sh, int Lc,
+                        const float *rots, const float *opac, const double *sh, const double *sh_var, int Lc,
                         const double *V, const double *prm, double *rgb, double *unc,
                         uint8_t *amb, int32_t *used)
 {
@@ -699,6 +706,7 @@ void oracle_render_view(const float *cam, int64_t n, const float *means, const f
     const int Kc = (Lc + 1) * (Lc + 1);
     oproj *P = (oproj *)malloc(sizeof(oproj) * (size_t)(n > 0 ? n : 1));
     double *col = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double *kcg = sh_var ? (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1)) : NULL;
     #pragma omp parallel for schedule(static)
     for (int64_t g = 0; g < n; ++g) {
         project_fp32(cam, means + 3 * g, scales + 3 * g, rots + 4 * g, (float)qcut, tile, &P[g]);
@@ -710,6 +718,16 @@ void oracle_render_view(const float *cam, int64_t n, const float *means, const f
             for (int j = 0; j < Kc; ++j) c += sh[((size_t)g * Kc + j) * 3 + k] * Y[j];   /* eq:rgb_sh */
             col[3 * g + k] = c;
         }
+        if (kcg) {
+            /* FisherRF variant: Q_c,k(d) = sum_j Y_j(d)^2 var_jk (diagonal) */
+            double lq = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                double q = 0.0;
+                for (int j = 0; j < Kc; ++j) q += Y[j] * Y[j] * sh_var[((size_t)g * Kc + j) * 3 + k];
+                lq += log(q);
+            }
+            kcg[g] = 0.5 * lq + 1.5 * (log(2.0 * M_PI) + 1.0);
+        }
     }
     plist Lst;
     build_lists(cam, n, P, qcut, 0, &Lst);
@@ -718,7 +736,7 @@ void oracle_render_view(const float *cam, int64_t n, const float *means, const f
     #pragma omp parallel
     {
         int64_t capn = 0;
-        double *al = NULL, *vv = NULL, *cc = NULL;
+        double *al = NULL, *vv = NULL, *cc = NULL, *kk = NULL;
         #pragma omp for schedule(dynamic, 64)
         for (int64_t p = 0; p < npix; ++p) {
             int i = (int)(p % W), j = (int)(p / W);
@@ -728,6 +746,7 @@ void oracle_render_view(const float *cam, int64_t n, const float *means, const f
                 al = (double *)realloc(al, sizeof(double) * (size_t)capn);
                 vv = (double *)realloc(vv, sizeof(double) * (size_t)capn);
                 cc = (double *)realloc(cc, sizeof(double) * 3 * (size_t)capn);
+                kk = (double *)realloc(kk, sizeof(double) * (size_t)capn);
             }
             for (int64_t k = 0; k < m; ++k) {
                 uint32_t g = (uint32_t)(Lst.ent[s + k] & 0xffffffffu);
@@ -735,9 +754,10 @@ void oracle_render_view(const float *cam, int64_t n, const float *means, const f
                 al[k] = (double)opac[g] * exp(-0.5 * q);
                 vv[k] = V[g];
                 cc[3 * k] = col[3 * g]; cc[3 * k + 1] = col[3 * g + 1]; cc[3 * k + 2] = col[3 * g + 2];
+                if (kcg) kk[k] = kcg[g];
             }
             double res[11];
-            oracle_composite(m, al, vv, cc, prm, res);
+            oracle_composite(m, al, vv, cc, prm, kcg ? kk : NULL, res);
             unc[p] = res[0];
             rgb[p] = res[1];
             rgb[npix + p] = res[2];
@@ -745,10 +765,11 @@ void oracle_render_view(const float *cam, int64_t n, const float *means, const f
             if (amb) amb[p] = (uint8_t)res[10];
             if (used) used[p] = (int32_t)res[9];
         }
-        free(al); free(vv); free(cc);
+        free(al); free(vv); free(cc); free(kk);
     }
     free_lists(&Lst);
     free(col);
+    free(kcg);
     free(P);
 }
 

@@ -48,7 +48,8 @@ class gavis_camera(C.Structure):
 
 class gavis_gaussians(C.Structure):
     _fields_ = [("n", C.c_int64), ("means", C.c_void_p), ("scales", C.c_void_p), ("rots", C.c_void_p),
-                ("opac", C.c_void_p), ("sh", C.c_void_p), ("sh_degree", C.c_int32), ("sh_dtype", C.c_int32)]
+                ("opac", C.c_void_p), ("sh", C.c_void_p), ("sh_degree", C.c_int32), ("sh_dtype", C.c_int32),
+                ("sh_var", C.c_void_p)]
 
 
 class gavis_vf(C.Structure):
@@ -181,8 +182,10 @@ def _dev(t: torch.Tensor, name: str, dtype=None) -> int:
 class Gaussians:
     """Structure-of-arrays Gaussian scene resident on the device."""
 
-    def __init__(self, means, scales, rots, opac, sh=None, sh_degree=None):
-        self.means, self.scales, self.rots, self.opac, self.sh = means, scales, rots, opac, sh
+    def __init__(self, means, scales, rots, opac, sh=None, sh_degree=None, sh_var=None):
+        """sh_var: optional variances of the colour coefficients (same shape and
+        dtype as sh) for the per-Gaussian colour covariance."""
+        self.means, self.scales, self.rots, self.opac, self.sh, self.sh_var = means, scales, rots, opac, sh, sh_var
         self.n = int(means.shape[0])
         if sh is not None and sh_degree is None:
             sh_degree = int(round(sh.shape[1] ** 0.5)) - 1
@@ -196,6 +199,12 @@ class Gaussians:
         s.sh = _dev(sh, "sh") if sh is not None else None
         s.sh_degree = self.sh_degree
         s.sh_dtype = _DTYPE_CODE[sh.dtype] if sh is not None else 0
+        if sh_var is not None:
+            if sh is None or sh_var.shape != sh.shape or sh_var.dtype != sh.dtype:
+                raise ValueError("sh_var must match sh in shape and dtype")
+            s.sh_var = _dev(sh_var, "sh_var")
+        else:
+            s.sh_var = None
         self.struct = s
 
     @classmethod
@@ -348,8 +357,12 @@ class Context:
         opac = torch.cat([gs.opac, torch.zeros(k, device=dev)])
         sh = torch.cat([gs.sh, torch.zeros((k,) + tuple(gs.sh.shape[1:]), dtype=gs.sh.dtype, device=dev)])
         coeffs = torch.cat([vf.coeffs, torch.zeros((k, vf.coeffs.shape[1]), dtype=vf.coeffs.dtype, device=dev)])
+        var = None
+        if gs.sh_var is not None:   # any positive variance: virtual particles have V = 0
+            var = torch.cat([gs.sh_var, torch.ones((k,) + tuple(gs.sh_var.shape[1:]), dtype=gs.sh_var.dtype,
+                                                   device=dev)]).contiguous()
         return (Gaussians(means.contiguous(), scales.contiguous(), rots.contiguous(), opac.contiguous(),
-                          sh.contiguous(), gs.sh_degree),
+                          sh.contiguous(), gs.sh_degree, var),
                 VisibilityField(coeffs.contiguous(), vf.degree, vf.n_train_views, vf.kappa))
 
     # -------------------------------------------------------------- instrumentation

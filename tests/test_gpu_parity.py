@@ -342,3 +342,22 @@ def test_autotune_picks_a_tile_and_caches(ctx, gv):
     out = ctx.score_views(gs, vf, c["cand"], params=p)
     ref = ctx.score_views(gs, vf, c["cand"], params=gv.Params(vf_degree=3, tile=16))
     assert (out["score"] - ref["score"]).abs().max().item() <= TOL
+
+
+@pytest.mark.parametrize("tile", [16, 32])
+def test_colour_variance_variant_parity(ctx, gv, tile):
+    """Per-Gaussian colour covariance (FisherRF variant) against the oracle."""
+    c = case("room_small")
+    sc = c["scene"]
+    var = np.random.default_rng(21).uniform(0.001, 0.05, sc.sh.shape).astype(np.float32)
+    g32 = oracle_gamma(c)
+    vf = gv.VisibilityField(torch.as_tensor(g32).cuda(), 3, len(c["train"]), 1.0)
+    gs = gv.Gaussians(*(torch.as_tensor(x).cuda().contiguous() for x in (sc.means, sc.scales, sc.rots, sc.opac, sc.sh)),
+                      sc.sh_degree, torch.as_tensor(var).cuda().contiguous())
+    out = ctx.score_views(gs, vf, c["cand"], params=gv.Params(tile=tile, vf_degree=3))
+    ref = oracle.score_views(sc, g32.astype(np.float64), 3, len(c["train"]), c["cand"], sh_var=var.astype(np.float64))
+    err, _ = compare_views(out["unc"].cpu().numpy(), out["rgb"].cpu().numpy(), ref)
+    assert err <= TOL
+    # it differs from the constant-covariance render
+    const = ctx.score_views(gpu_scene(gv, sc), vf, c["cand"], params=gv.Params(tile=tile, vf_degree=3))
+    assert (const["score"] - out["score"]).abs().max().item() > 1e-2

@@ -515,3 +515,41 @@ def test_density_control_product_over_views():
     assert vis[0] == 0.0 and keep[0]
     vis, keep, _ = oracle.density_control([cam_a], empty, vm, eps_v=1.0)
     assert keep[0]   # visibility 1 <= eps_v = 1
+
+
+# --------------------------------------------------------------------------- FisherRF colour covariance
+
+def test_uniform_coefficient_variance_is_isotropic():
+    """Q_c,k(d) = sum_j Y_j(d)^2 var_jk: with var_jk = s2 4 pi / (Lc+1)^2 the
+    addition theorem gives Q_c = s2 I for every direction, so the render
+    equals the constant-covariance one with sigma_c^2 = s2."""
+    c = sg.config(1, n=300, n_cand=2, cand_wh=(40, 40))
+    sc = c["scene"]
+    gamma, _, _ = oracle.vf_build(c["train"][:3], sc, 2)
+    s2 = 0.02
+    var = np.full(sc.sh.shape, s2 * 4 * math.pi / 4.0)      # Lc = 1: 4 coefficients
+    for cam in c["cand"]:
+        V, _ = oracle.vf_query(gamma, 2, 3, cam, sc.means)
+        _, u1, _, _ = oracle.render_view(cam, sc, V, oracle.params(sigma_c2=s2), sh_var=var)
+        _, u2, _, _ = oracle.render_view(cam, sc, V, oracle.params(sigma_c2=s2))
+        np.testing.assert_allclose(u1, u2, atol=1e-12)
+        assert np.abs(u2).max() > 0.1
+
+
+def test_coefficient_variance_single_gaussian_closed_form():
+    """One Gaussian seen head-on, d = +z: Y_00 = 1/(2 sqrt(pi)), Y_10 = sqrt(3/(4 pi)),
+    the other degree-1 terms vanish, so Q_k = Y_00^2 var_0k + Y_10^2 var_2k and
+    the visible component carries 1/2 sum_k ln Q_k + 3/2 ln(2 pi e)."""
+    o, V = 0.8, 0.6
+    sc = single_gaussian_scene((0, 0, 2.0), 0.05, o)
+    var = np.zeros((1, 4, 3))
+    var[0, 0] = [0.01, 0.02, 0.05]
+    var[0, 2] = [0.03, 0.001, 0.002]
+    var[0, 1] = var[0, 3] = [7.0, 7.0, 7.0]                # multiplied by Y^2 = 0 here
+    rgb, unc, _, _ = oracle.render_view(axis_camera(), sc, np.array([V]), sh_var=var)
+    y00, y10 = 0.25 / math.pi, 3 / (4 * math.pi)
+    Q = y00 * var[0, 0] + y10 * var[0, 2]
+    kc = 0.5 * float(np.log(Q).sum()) + 1.5 * math.log(2 * math.pi * math.e)
+    a_s = (V + 0.5 * (1 - V)) * o + 0.15 * 0.5 * (1 - V)
+    w1, w0 = a_s * V, a_s * (1 - V)
+    assert unc[7, 7] == pytest.approx(phi(w1) + w1 * kc + phi(w0) + w0 * K0, abs=1e-6)
