@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-views", type=int, default=1)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain unbatched f32 comparison step")
     ap.add_argument("--serving", action="store_true", help="serving workload: Poisson requests over 4 resident scenes")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean request rate (req/s)")
     ap.add_argument("--requests", type=int, default=300, help="serving: number of requests")
@@ -156,6 +157,24 @@ class ClockSampler:
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "power_w_max": max(pw),
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over the ranks of the default process group (x when
+    there is none): the job's time is its slowest replica's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job units per second: every replica processes units_per_rank in
+    the max-over-ranks time ms (weak scaling)."""
+    return world * units_per_rank / (ms / 1e3)
 
 
 def percentile(xs, q):
@@ -269,10 +288,10 @@ def run_gavis(args):
     prm_vf, prm_sc = prm, prm
     tuned = None
     if args.tile == 0:
-        # autotuner: tile edge per path, timed on 8 sample views (untimed here)
-        prm_vf, ms_vf = ctx.autotune(gs, train[:8], None, gv.Params(vf_degree=L, views_per_batch=args.views_per_batch))
+        # autotuner: tile edge per path, timed on 16 training / 32 candidate views (untimed here)
+        prm_vf, ms_vf = ctx.autotune(gs, train[:16], None, gv.Params(vf_degree=L, views_per_batch=args.views_per_batch))
         ctx.vf_build(gs, train, degree=L, params=prm_vf, out=vf)
-        prm_sc, ms_sc = ctx.autotune(gs, cand[:8], vf, gv.Params(vf_degree=L, views_per_batch=args.views_per_batch))
+        prm_sc, ms_sc = ctx.autotune(gs, cand[:32], vf, gv.Params(vf_degree=L, views_per_batch=args.views_per_batch))
         tuned = {"vf_build_tile": prm_vf.tile, "score_tile": prm_sc.tile}
     W, H = cand[0].W, cand[0].H
     outs = {"rgb": torch.empty((n_cand, 3, H, W), device=dev), "unc": torch.empty((n_cand, H, W), device=dev),
@@ -313,12 +332,9 @@ def run_gavis(args):
     ctx.prof_enable(False)
     best = int(outs["best_dev"].item())
 
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dev)
     ms_per_step = total_ms / args.steps
-    value = world * n_cand / (ms_per_step / 1e3)
+    value = job_throughput(n_cand, world, ms_per_step)
 
     # ---------------- per-call work counts (one untimed instrumented pass) ----------------
     ctx.prof_enable(True)
@@ -342,6 +358,34 @@ def run_gavis(args):
            "note": "per-view algorithmic bytes (Gaussian data counted once per view; the batched chain "
                    "reads it once per batch), divided by the device time of the step"}
 
+    # ---------------- the plain unbatched f32 path, for comparison ----------------
+    plain = None
+    if not args.no_plain:
+        sh32 = devt["sh"].float().contiguous()
+        gs32 = gv.Gaussians(devt["means"], devt["scales"], devt["rots"], devt["opac"], sh32, sc.sh_degree)
+        vf32 = gv.VisibilityField(torch.zeros((sc.n, (L + 1) ** 2), device=dev), L, 0, 1.0)
+        pp = gv.Params(vf_degree=L, tile=16, views_per_batch=1)
+
+        def plain_step():
+            ctx.vf_build(gs32, train, degree=L, params=pp, out=vf32)
+            return ctx.score_views(gs32, vf32, cand, params=pp, out=outs, sync_best=False)
+
+        plain_step()
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        plain_step()
+        p1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = p0.elapsed_time(p1)
+        plain = {"ms_per_step": plain_ms, "views_per_s": n_cand / (plain_ms / 1e3),
+                 "speedup_of_batched": plain_ms / ms_per_step,
+                 "what": "f32 colour and field coefficients, one view per kernel chain, tile 16, one step; "
+                         "both paths pass the same oracle parity gate"}
+        del sh32, gs32, vf32
+        # restore the benchmark's field (the plain step overwrote the outputs only)
+        ctx.score_views(gs, vf, cand, params=prm_sc, out=outs, sync_best=False)
+
     # ---------------- end to end through host buffers ----------------
     e2e_steps = max(1, args.e2e_steps)
     h2d = sum(v.numel() * v.element_size() for v in host.values()) + gv.camera_records(train)._length_ * 96 \
@@ -362,12 +406,8 @@ def run_gavis(args):
         best_h.copy_(outs["best_dev"], non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * n_cand / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dev)
+    e2e_value = job_throughput(n_cand, world, e2e_ms)
 
     # ---------------- roofline of the dominant kernel ----------------
     st = prof["stages"]
@@ -420,6 +460,7 @@ def run_gavis(args):
             "pairs_per_step": {"uncertainty": pairs_ua // args.steps, "visibility": pairs_vis // args.steps},
             "tile_keys_per_step": prof["keys"] // args.steps,
             "hbm": hbm,
+            "plain_unbatched_f32": plain,
             "best_view": best,
         }
         print(json.dumps(line), flush=True)

@@ -305,6 +305,7 @@ KeyLayout key_layout(void *base, size_t nrec, size_t M)
 struct SmallLayout {
     uint2 *ranges;
     float *tile_sums;
+    uint32_t *pair_counts;
     BatchInfo *info;
     int32_t *best;
     size_t bytes;
@@ -318,6 +319,7 @@ SmallLayout small_layout(void *base, size_t nvt)
     auto take = [&](size_t b) { char *q = p ? p + off : nullptr; off += align256(b); return q; };
     L.ranges = reinterpret_cast<uint2 *>(take(nvt * sizeof(uint2)));
     L.tile_sums = reinterpret_cast<float *>(take(nvt * sizeof(float)));
+    L.pair_counts = reinterpret_cast<uint32_t *>(take(nvt * sizeof(uint32_t)));
     L.info = reinterpret_cast<BatchInfo *>(take(sizeof(BatchInfo)));
     L.best = reinterpret_cast<int32_t *>(take(sizeof(int32_t)));
     L.bytes = off;
@@ -380,6 +382,8 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     ProjectArgs pa;
     pa.means = gs->means; pa.scales = gs->scales; pa.rots = gs->rots; pa.opac = gs->opac;
     pa.sh = gs->sh; pa.sh_degree = gs->sh_degree; pa.sh_dtype = gs->sh_dtype;
+    pa.sh_var = mode == MODE_SCORE ? gs->sh_var : nullptr;
+    pa.k_c = (float)(1.5 * std::log((double)p->sigma_c2) + 1.5 * (std::log(2.0 * M_PI) + 1.0));
     pa.gamma = (mode == MODE_SCORE && vf) ? vf->coeffs : nullptr;
     pa.vf_degree = (mode == MODE_SCORE && vf) ? vf->degree : 0;
     pa.vf_dtype = (mode == MODE_SCORE && vf) ? vf->dtype : 0;
@@ -471,11 +475,13 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     ca.tile_sums = SL.tile_sums;
     if (mode == MODE_SCORE) {
         ca.rgb = out.rgb; ca.unc = out.unc;
-        ca.pairs = ctx->prof_on ? ctx->d_pairs : nullptr;
+        ca.per_entry_kc = gs->sh_var != nullptr;
+        ca.pair_counts = ctx->prof_on ? SL.pair_counts : nullptr;
         {
             Stage st(ctx, GAVIS_STAGE_COMPOSITE_UA, s);
             CK(launch_composite_ua(ca, s));
         }
+        if (ca.pair_counts) CK(launch_sum_counts(SL.pair_counts, nvt, ctx->d_pairs, s));
         Stage st(ctx, GAVIS_STAGE_REDUCE, s);
         CK(launch_view_reduce(SL.tile_sums, nv, G.TT, 1.0f / ((float)G.W * (float)G.H), out.score + v0, s));
     } else {

@@ -4,10 +4,11 @@
 //   GeoRec  32 B  a = (u, v, A, 2B)  b = (C, opacity, depth z, ext)
 //           image-space centre and conic of the projected Gaussian; ext packs
 //           the footprint half-extents (ex, ey) as two halves rounded up.
-//   UaRec   32 B  a = (a1, a0, V, r)  b = (g, b, 0, 0)
+//   UaRec   32 B  a = (a1, a0, V, r)  b = (g, b, kc, 0)
 //           alpha* = a1 * alpha + a0 (eq:alpha_comp, a1 = V + beta(1-V),
 //           a0 = o0(1-beta)(1-V)), the queried visibility V (eq:vis_bound) and
-//           the SH colour (eq:rgb_sh).
+//           the SH colour (eq:rgb_sh); kc = 1/2 log((2 pi e)^3 |Q_c|) of
+//           the Gaussian in that view (eq:huber).
 //   rect    8 B   (x0 | x1 << 16, y0 | y1 << 16) inclusive tile rectangle.
 //   counts  4 B   tiles touched (0 = culled).
 // Canonical order of a batch's tile lists: by key ((view * TW*TH + tile) << 32)
@@ -51,6 +52,8 @@ struct ProjectArgs {
     const float *means, *scales, *rots, *opac;
     const void *sh;
     int sh_degree, sh_dtype;
+    const void *sh_var;     // colour coefficient variances or NULL (constant Q_c)
+    float k_c;              // 1/2 log((2 pi e)^3 |Q_c|) for the constant Q_c
     const void *gamma;      // VF coefficients (NULL -> V = 0)
     int vf_degree, vf_dtype, n_train;
     float q_cut, beta, o0;
@@ -137,15 +140,20 @@ struct CompositeArgs {
     RasterConsts rc;
     float *rgb, *unc;      // may be NULL
     float *tile_sums;      // [nv * TW*TH]
+    bool per_entry_kc;     // use the per-Gaussian kc of the UaRec (colour variances given)
     // visibility pass
     unsigned long long *sumT;  // [nv * n] fixed point 2^-24
     uint32_t *cnt;             // [nv * n]
-    // optional instrumentation: (pixel, Gaussian) pairs composited
+    // optional instrumentation: (pixel, Gaussian) pairs composited; the
+    // uncertainty pass writes one count per tile (summed by launch_sum_counts),
+    // the visibility pass adds per warp into *pairs
+    uint32_t *pair_counts;
     unsigned long long *pairs;
 };
 cudaError_t launch_composite_ua(const CompositeArgs &a, cudaStream_t s);
 cudaError_t launch_composite_vis(const CompositeArgs &a, cudaStream_t s);
-cudaError_t launch_view_reduce(const float *tile_sums, int nv, int tiles_per_view, float inv_pixels,
+cudaError_t launch_sum_counts(const uint32_t *c, size_t count, unsigned long long *out, cudaStream_t s);
+cudaError_t launch_view_reduce(const float *tile_sums, int nv, int sums_per_view, float inv_pixels,
                                float *score, cudaStream_t s);
 cudaError_t launch_argmax(const float *score, int n, int32_t *best, cudaStream_t s);
 

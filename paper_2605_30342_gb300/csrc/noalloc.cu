@@ -147,6 +147,8 @@ extern "C" int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_v
     ProjectArgs pa;
     pa.means = gs->means; pa.scales = gs->scales; pa.rots = gs->rots; pa.opac = gs->opac;
     pa.sh = gs->sh; pa.sh_degree = gs->sh_degree; pa.sh_dtype = gs->sh_dtype;
+    pa.sh_var = gs->sh_var;
+    pa.k_c = (float)(1.5 * std::log((double)p->sigma_c2) + 1.5 * (std::log(2.0 * M_PI) + 1.0));
     pa.gamma = vf->coeffs; pa.vf_degree = vf->degree; pa.vf_dtype = vf->dtype; pa.n_train = vf->n_train_views;
     pa.q_cut = p->q_cut; pa.beta = p->beta; pa.o0 = p->o0;
     pa.tile = p->tile; pa.TW = TW; pa.TH = TH;
@@ -209,6 +211,7 @@ extern "C" int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_v
     ca.rc.k_c = (float)(1.5 * std::log((double)p->sigma_c2) + 1.5 * l2pie);
     ca.rc.k_0 = (float)(0.5 * (double)p->logdet_Q0 + 1.5 * l2pie);
     ca.rgb = rgb; ca.unc = unc; ca.tile_sums = tile_sums;
+    ca.per_entry_kc = gs->sh_var != nullptr;
     NA_CK(launch_composite_ua(ca, s));
     NA_CK(launch_view_reduce(tile_sums, 1, TT, 1.0f / ((float)cam->W * (float)cam->H), score, s));
     return GAVIS_OK;

@@ -131,8 +131,9 @@ __device__ __forceinline__ Proj project_one(const gavis_camera &cam, float x, fl
     return o;
 }
 
-template <int LC, int LV, bool UA>
-__global__ void __launch_bounds__(128) k_project(ProjectArgs a)
+// VAR: per-Gaussian colour covariance from coefficient variances
+template <int LC, int LV, bool UA, bool VAR>
+__global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
 {
     extern __shared__ gavis_camera s_cams[];
     for (int i = threadIdx.x; i < a.nv; i += blockDim.x) s_cams[i] = a.cams[i];
@@ -205,9 +206,22 @@ __global__ void __launch_bounds__(128) k_project(ProjectArgs a)
                 V = fminf(fmaxf(V, 0.0f), 1.0f);
             }
             const float nv1 = 1.0f - V;
+            float kc = 0.0f;   // unused by the constant-covariance composite
+            if (VAR) {
+                // FisherRF variant: Q_k(d) = sum_j Y_j(d)^2 var_jk, diagonal
+                float lq = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    float q = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < KC; ++j) q = fmaf(Y[j] * Y[j], ld_coef(a.sh_var, ((size_t)g * KC + j) * 3 + k, a.sh_dtype), q);
+                    lq += logf(fmaxf(q, 1e-30f));
+                }
+                kc = fmaf(0.5f, lq, 4.256815599614018f);   // + 3/2 log(2 pi e)
+            }
             UaRec ur;
             ur.a = make_float4(V + a.beta * nv1, a.o0 * (1.0f - a.beta) * nv1, V, col[0]);
-            ur.b = make_float4(col[1], col[2], 0.0f, 0.0f);
+            ur.b = make_float4(col[1], col[2], kc, 0.0f);
             a.ua[r] = ur;
         }
     }
@@ -259,7 +273,16 @@ __global__ void __launch_bounds__(128) k_query(QueryArgs a)
 template <int LC, int LV>
 cudaError_t launch_ua(const ProjectArgs &a, cudaStream_t s, int blocks, size_t smem)
 {
-    k_project<LC, LV, true><<<blocks, 128, smem, s>>>(a); count_launch();
+    if (a.sh_var) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_project<LC, LV, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_project<LC, LV, true, true><<<blocks, 128, smem, s>>>(a);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_project<LC, LV, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_project<LC, LV, true, false><<<blocks, 128, smem, s>>>(a);
+    }
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -272,17 +295,14 @@ cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s)
     const size_t smem = sizeof(gavis_camera) * (size_t)a.nv;
     if (smem > 48 * 1024) {
         // opt in to larger dynamic shared memory for big batches
-        cudaFuncSetAttribute(k_project<0, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_project<0, 0, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
     if (!a.ua) {
-        k_project<0, 0, false><<<blocks, 128, smem, s>>>(a); count_launch();
+        k_project<0, 0, false, false><<<blocks, 128, smem, s>>>(a); count_launch();
         return cudaGetLastError();
     }
 #define GAVIS_UA_CASE(LC, LV)                                                                            \
     if (a.sh_degree == LC && a.vf_degree == LV) {                                                        \
-        if (smem > 48 * 1024)                                                                            \
-            cudaFuncSetAttribute(k_project<LC, LV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                 (int)smem);                                                             \
         return launch_ua<LC, LV>(a, s, blocks, smem);                                                    \
     }
     GAVIS_UA_CASE(0, 0) GAVIS_UA_CASE(0, 1) GAVIS_UA_CASE(0, 2) GAVIS_UA_CASE(0, 3)

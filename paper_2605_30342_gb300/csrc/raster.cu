@@ -173,7 +173,9 @@ constexpr float kLn2 = 0.69314718055994530942f;
 // w = alpha* T, wv = w V, T -= w.  The entropy bound (eq:huber) is assembled
 // once per pixel from sum(wv), sum(wv log2 wv) and the prior mass
 // w0 = (1 - T) - sum(wv).
-template <int TILE>
+// KC: the visible components carry per-Gaussian kc (colour variances given);
+// otherwise the constant k_c is applied to sum(wv) once per pixel.
+template <int TILE, bool KC>
 __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a)
 {
     constexpr int NT = TILE * TILE / 2;
@@ -182,6 +184,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
     __shared__ float2 s_g1[NW][32];   // C, opacity
     __shared__ float4 s_u0[NW][32];   // a1, a0, V, r
     __shared__ float2 s_u1[NW][32];   // g, b
+    __shared__ float s_kc[KC ? NW : 1][32];
     __shared__ float s_red[NW];
     __shared__ uint32_t s_pairs[NW];
 
@@ -201,18 +204,19 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
     const size_t vrow = (size_t)vb * (size_t)a.n;
     const RasterConsts rc = a.rc;
 
-    float T[2], Tc[2], sl[2], swv[2], cr[2], cg[2], cb[2], py[2];
+    float T[2], Tc[2], sl[2], swv[2], skc[2], cr[2], cg[2], cb[2], py[2];
     bool ua_on[2], rgb_on[2], inside[2];
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         const int j = j0 + 4 * p;
         inside[p] = i < a.W && j < a.H;
         py[p] = (float)j + 0.5f;
-        T[p] = 1.0f; Tc[p] = 1.0f; sl[p] = 0.0f; swv[p] = 0.0f; cr[p] = 0.0f; cg[p] = 0.0f; cb[p] = 0.0f;
+        T[p] = 1.0f; Tc[p] = 1.0f; sl[p] = 0.0f; swv[p] = 0.0f; skc[p] = 0.0f; cr[p] = 0.0f; cg[p] = 0.0f; cb[p] = 0.0f;
         ua_on[p] = inside[p];
         rgb_on[p] = inside[p];
     }
     uint32_t npairs = 0;
+    float *kcs = s_kc[KC ? warp : 0];
     float4 *g0s = s_g0[warp];
     float2 *g1s = s_g1[warp];
     float4 *u0s = s_u0[warp];
@@ -237,6 +241,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
             g1s[slot] = make_float2(gr.b.x, gr.b.y);
             u0s[slot] = ur.a;
             u1s[slot] = make_float2(ur.b.x, ur.b.y);
+            if (KC) kcs[slot] = ur.b.z;
         }
         __syncwarp();
         const int nk = __popc(m);
@@ -266,6 +271,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
                     const float wv = w * u0.z;                   // weight of the visible component
                     sl[p] = fmaf(wv, lg2_approx(fmaxf(wv, 1e-30f)), sl[p]);
                     swv[p] += wv;
+                    if (KC) skc[p] = fmaf(wv, kcs[k], skc[p]);
                     T[p] -= w;
                     ua_on[p] = T[p] >= rc.eps_T;
                 }
@@ -281,7 +287,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
         if (!inside[p]) continue;
         // eq:huber: visible components sum wv (k_c - ln wv); prior w0 (k_0 - ln w0)
         const float w0 = fmaxf((1.0f - T[p]) - swv[p], 0.0f);
-        float Hs = fmaf(rc.k_c, swv[p], -kLn2 * sl[p]);
+        float Hs = (KC ? skc[p] : rc.k_c * swv[p]) - kLn2 * sl[p];
         if (w0 > 1e-30f) Hs = fmaf(w0, rc.k_0 - kLn2 * lg2_approx(w0), Hs);
         const size_t pix = (size_t)(j0 + 4 * p) * a.W + i;
         if (a.unc) a.unc[vg * plane + pix] = Hs;
@@ -303,13 +309,13 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
     __syncthreads();
     if (tid == 0) {
         float sum = 0.0f;
-        unsigned long long np = 0;
+        uint32_t np = 0;
         for (int w = 0; w < NW; ++w) {
             sum += s_red[w];
             np += s_pairs[w];
         }
         a.tile_sums[blockIdx.x] = sum;
-        if (a.pairs && np) atomicAdd(a.pairs, np);
+        if (a.pair_counts) a.pair_counts[blockIdx.x] = np;
     }
 }
 
@@ -403,6 +409,21 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
         __syncwarp();
     }
     if (a.pairs && lane == 0 && wpairs) atomicAdd(a.pairs, (unsigned long long)wpairs);
+}
+
+// instrumentation: sum of the per-warp pair counts into one counter
+__global__ void k_sum_counts(const uint32_t *c, size_t count, unsigned long long *out)
+{
+    __shared__ unsigned long long s[256];
+    unsigned long long acc = 0;
+    for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i < count; i += (size_t)gridDim.x * 256) acc += c[i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && s[0]) atomicAdd(out, s[0]);
 }
 
 __global__ void k_view_reduce(const float *tile_sums, int tiles, float inv_pixels, float *score)
@@ -513,7 +534,7 @@ __global__ void k_vis_export(const unsigned long long *sumT, const uint32_t *cnt
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
-    if (sumT_f) sumT_f[i] = (float)((double)sumT[i] * (1.0 / 16777216.0));
+    if (sumT_f) sumT_f[i] = (float)((double)sumT[i] / (double)kTScale);
     if (cnt_out) cnt_out[i] = cnt[i];
 }
 
@@ -623,9 +644,21 @@ cudaError_t launch_composite_ua(const CompositeArgs &a, cudaStream_t s)
     const unsigned blocks = (unsigned)(a.nv * a.TW * a.TH);
     if (blocks == 0) return cudaSuccess;
     switch (a.tile) {
-    case 8: k_composite_ua<8><<<blocks, 32, 0, s>>>(a); count_launch(); break;
-    case 16: k_composite_ua<16><<<blocks, 128, 0, s>>>(a); count_launch(); break;
-    case 32: k_composite_ua<32><<<blocks, 512, 0, s>>>(a); count_launch(); break;
+    case 8:
+        if (a.per_entry_kc) k_composite_ua<8, true><<<blocks, 32, 0, s>>>(a);
+        else k_composite_ua<8, false><<<blocks, 32, 0, s>>>(a);
+        count_launch();
+        break;
+    case 16:
+        if (a.per_entry_kc) k_composite_ua<16, true><<<blocks, 128, 0, s>>>(a);
+        else k_composite_ua<16, false><<<blocks, 128, 0, s>>>(a);
+        count_launch();
+        break;
+    case 32:
+        if (a.per_entry_kc) k_composite_ua<32, true><<<blocks, 512, 0, s>>>(a);
+        else k_composite_ua<32, false><<<blocks, 512, 0, s>>>(a);
+        count_launch();
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -644,11 +677,20 @@ cudaError_t launch_composite_vis(const CompositeArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_view_reduce(const float *tile_sums, int nv, int tiles_per_view, float inv_pixels, float *score,
+cudaError_t launch_sum_counts(const uint32_t *c, size_t count, unsigned long long *out, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    unsigned blocks = nblk(count, 256);
+    if (blocks > 1024) blocks = 1024;
+    k_sum_counts<<<blocks, 256, 0, s>>>(c, count, out); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_view_reduce(const float *tile_sums, int nv, int sums_per_view, float inv_pixels, float *score,
                                cudaStream_t s)
 {
     if (nv == 0) return cudaSuccess;
-    k_view_reduce<<<nv, 256, 0, s>>>(tile_sums, tiles_per_view, inv_pixels, score); count_launch();
+    k_view_reduce<<<nv, 256, 0, s>>>(tile_sums, sums_per_view, inv_pixels, score); count_launch();
     return cudaGetLastError();
 }
 

@@ -112,7 +112,7 @@ def test_single_view_visibility_parity(ctx, gv, name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16])
 def test_vf_build_parity(ctx, gv, name, dtype):
     c = case(name)
     sc, train = c["scene"], c["train"]
@@ -124,8 +124,9 @@ def test_vf_build_parity(ctx, gv, name, dtype):
     ref, amb, _ = oracle.vf_build(train, sc, L)
     ok = ~amb
     P = len(train)
-    # float16 storage rounds |gamma| <= ~1.6 P to 2^-11 relative: state it and gate on it
-    tol = TOL if dtype == torch.float32 else TOL + 2.0 ** -11 * np.abs(ref[ok]).max() / P
+    # half-precision storage rounds gamma to 2^-11 (f16) or 2^-8 (bf16) relative: state it and gate on it
+    rel = {torch.float32: 0.0, torch.float16: 2.0 ** -11, torch.bfloat16: 2.0 ** -8}[dtype]
+    tol = TOL + rel * np.abs(ref[ok]).max() / P
     err = np.abs(g[ok] - ref[ok]).max() / P
     assert err <= tol, (err, tol)
     assert ok.mean() > 0.8   # at least 80% of Gaussians are clear of the eps_T rounding margin
