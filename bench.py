@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-views", type=int, default=1)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain unbatched f32 comparison step")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph scoring comparison")
     ap.add_argument("--serving", action="store_true", help="serving workload: Poisson requests over 4 resident scenes")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean request rate (req/s)")
     ap.add_argument("--requests", type=int, default=300, help="serving: number of requests")
@@ -342,7 +343,7 @@ def run_gavis(args):
     vis_vf = ctx.prof_read()["visible"]
     ctx.prof_enable(True)
     ctx.score_views(gs, vf, cand, params=prm_sc, out=outs, sync_best=False)
-    vis_sc = ctx.prof_read()["visible"]
+    vis_sc, keys_sc = ctx.prof_read()["visible"], ctx.prof_read()["keys"]
     ctx.prof_enable(False)
     b = torch.tensor([], dtype=cdt).element_size()
     K, Kc = (L + 1) ** 2, (sc.sh_degree + 1) ** 2
@@ -385,6 +386,33 @@ def run_gavis(args):
         del sh32, gs32, vf32
         # restore the benchmark's field (the plain step overwrote the outputs only)
         ctx.score_views(gs, vf, cand, params=prm_sc, out=outs, sync_best=False)
+
+    # ---------------- scoring replayed as one CUDA graph ----------------
+    graph = None
+    if not args.no_graph:
+        plan = ctx.plan(gs, vf, n_cand, W, H, int(keys_sc * 1.25) + 1024, record_capacity=int(vis_sc * 1.25) + 1024,
+                        params=prm_sc)
+        recs = gv.camera_records(cand)
+        for _ in range(3):
+            plan.launch(recs)
+            ctx.score_views(gs, vf, cand, params=prm_sc, out=outs, sync_best=False)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(plan.score, outs["score"])) and int(plan.best_dev.item()) == int(outs["best_dev"].item())
+        g0, g1, g2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        g0.record(stream)
+        for _ in range(args.steps):
+            plan.launch(recs)
+        g1.record(stream)
+        for _ in range(args.steps):
+            ctx.score_views(gs, vf, cand, params=prm_sc, out=outs, sync_best=False)
+        g2.record(stream)
+        torch.cuda.synchronize()
+        graph = {"ms_per_scoring": g0.elapsed_time(g1) / args.steps,
+                 "score_views_ms": g1.elapsed_time(g2) / args.steps, "identical_to_score_views": same,
+                 "overflowed": plan.overflowed()[0], "kernels_per_launch": plan.kernels,
+                 "what": "the candidate-scoring chain captured once (gavis_plan_create) and replayed per step"}
+        plan.close()
+        del plan
 
     # ---------------- end to end through host buffers ----------------
     e2e_steps = max(1, args.e2e_steps)
@@ -461,6 +489,7 @@ def run_gavis(args):
             "tile_keys_per_step": prof["keys"] // args.steps,
             "hbm": hbm,
             "plain_unbatched_f32": plain,
+            "graph_scoring": graph,
             "best_view": best,
         }
         print(json.dumps(line), flush=True)

@@ -251,6 +251,57 @@ int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_vf *vf, cons
                              size_t err_len, void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Scoring plans (no counterpart in the paper): the candidate-scoring chain  */
+/* of gavis_score_views (projection with VF QUERY, Eq. for alpha*, the        */
+/* Huber entropy bound, the per-view mean and the argmax of Eq. for i*)      */
+/* captured once as a CUDA graph and replayed for new candidate poses.       */
+/* ---------------------------------------------------------------------- */
+typedef struct gavis_plan gavis_plan;
+
+/* Build a plan for n_cams (1..1024) candidate views of W x H pixels over one
+ * scene and field.  The plan allocates all its device memory here: one
+ * projected record per (view, Gaussian), sort space for record_capacity
+ * visible (view, Gaussian) records (0 = n_cams x n, always enough) and for
+ * entry_capacity tile entries.  Good values are 1.25 x the visible-record and
+ * tile-key counts gavis_prof_read reports for comparable poses; grids are
+ * sized by the capacities, so oversizing them costs time.  gs, vf, p: as for gavis_score_views; gs and vf stay owned by the
+ * caller and must stay alive at the same addresses while the plan is used.
+ * The plan captures the sizes, dtypes and |P| (vf->n_train_views); the
+ * values behind the pointers are read at every launch, so they may be
+ * rewritten between launches (e.g. Gaussians refined in place).  rgb (device [n_cams][3][H][W] or NULL), unc (device
+ * [n_cams][H][W] or NULL), score (device [n_cams]) and best_dev (device [1]
+ * int32 or NULL) are written by every launch.  *out receives the plan.
+ * Errors: GAVIS_ERR_ARG for invalid sizes or parameters (tile must be 8, 16
+ * or 32: no autotuning), GAVIS_ERR_CUDA if allocation or capture fails; the
+ * message is in gavis_last_error(ctx). */
+int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf, int n_cams, int W, int H,
+                      const gavis_params *p, int64_t record_capacity, int64_t entry_capacity, float *rgb,
+                      float *unc, float *score, int32_t *best_dev, gavis_plan **out);
+
+/* Score the poses cams (host [n_cams], each W x H as at creation) by
+ * replaying the graph on `stream`.  The poses are copied into the plan's
+ * pinned staging buffer first, after waiting for the previous launch of this
+ * plan to finish; the call does not otherwise wait for the GPU.  Results
+ * equal gavis_score_views' for the same inputs bit for bit, unless the launch
+ * needed more visible records or tile entries than the capacities: then the
+ * excess is dropped (the results are incomplete) and gavis_plan_overflowed
+ * reports it.  One plan is used from one thread at a
+ * time. */
+int gavis_plan_launch(gavis_plan *plan, const gavis_camera *cams, void *stream);
+
+/* After the last launch finishes (the call waits for it): *overflowed = 1 if
+ * it needed more visible records or tile entries than the capacities;
+ * *records_needed and *entries_needed = the numbers it needed.  Any pointer
+ * may be NULL. */
+int gavis_plan_overflowed(gavis_plan *plan, int *overflowed, int64_t *records_needed, int64_t *entries_needed);
+
+/* Kernels one launch runs (for launch accounting). */
+int64_t gavis_plan_kernels(const gavis_plan *plan);
+
+/* Waits for the last launch and frees the plan.  NULL is ignored. */
+void gavis_plan_destroy(gavis_plan *plan);
+
+/* ---------------------------------------------------------------------- */
 /* Serving (no counterpart in the paper): continuous batching of scoring     */
 /* requests over resident scenes.                                             */
 /* ---------------------------------------------------------------------- */

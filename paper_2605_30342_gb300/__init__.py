@@ -67,7 +67,9 @@ EXPORTS = ["gavis_ctx_create", "gavis_ctx_destroy", "gavis_last_error", "gavis_p
            "gavis_vmf_coeffs", "gavis_vf_build", "gavis_score_views", "gavis_vf_query", "gavis_debug_bins",
            "gavis_debug_visibility", "gavis_prof_enable", "gavis_prof_read", "gavis_vf_density_control",
            "gavis_server_create", "gavis_server_destroy", "gavis_server_last_error", "gavis_server_add_scene",
-           "gavis_server_submit", "gavis_server_wait", "gavis_server_stats", "gavis_autotune"]
+           "gavis_server_submit", "gavis_server_wait", "gavis_server_stats", "gavis_autotune",
+           "gavis_plan_create", "gavis_plan_launch", "gavis_plan_overflowed", "gavis_plan_kernels",
+           "gavis_plan_destroy"]
 
 STAGES = ["project", "scan", "emit", "sort", "ranges", "composite_ua", "composite_vis", "reduce", "vf_accum"]
 
@@ -122,6 +124,14 @@ def load(path: str | None = None):
                                            C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
         lib.gavis_autotune.argtypes = [vp, C.POINTER(gavis_gaussians), C.POINTER(gavis_vf), C.POINTER(gavis_camera), i32,
                                        i32, C.POINTER(gavis_params), C.POINTER(C.c_double), vp]
+        lib.gavis_plan_create.argtypes = [vp, C.POINTER(gavis_gaussians), C.POINTER(gavis_vf), i32, i32, i32,
+                                          C.POINTER(gavis_params), i64, i64, vp, vp, vp, vp, C.POINTER(vp)]
+        lib.gavis_plan_launch.argtypes = [vp, C.POINTER(gavis_camera), vp]
+        lib.gavis_plan_overflowed.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        lib.gavis_plan_kernels.argtypes = [vp]
+        lib.gavis_plan_kernels.restype = i64
+        lib.gavis_plan_destroy.argtypes = [vp]
+        lib.gavis_plan_destroy.restype = None
         lib.gavis_prof_enable.argtypes = [vp, i32]
         lib.gavis_prof_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                         C.POINTER(C.c_uint64)]
@@ -304,6 +314,11 @@ class Context:
         return dict(score=score, best=int(best_host.value) if sync_best else best_dev, rgb=rgb, unc=unc,
                     best_dev=best_dev)
 
+    def plan(self, gs: Gaussians, vf: VisibilityField, n_cams: int, W: int, H: int, entry_capacity: int,
+             record_capacity: int = 0, params=None, want_rgb=False, want_unc=False) -> "Plan":
+        """Candidate scoring captured as a CUDA graph (gavis_plan_create)."""
+        return Plan(self, gs, vf, n_cams, W, H, record_capacity, entry_capacity, params, want_rgb, want_unc)
+
     def vf_query(self, gs: Gaussians, vf: VisibilityField, cams, params=None, stream=None):
         p = params or Params(vf_degree=vf.degree)
         V = torch.empty((len(cams), gs.n), device=gs.means.device)
@@ -406,6 +421,64 @@ class Context:
                                                      C.byref(p), C.c_void_p(sumT.data_ptr()),
                                                      C.c_void_p(cnt.data_ptr()), _stream_ptr(stream)))
         return sumT, cnt
+
+
+class Plan:
+    """A replayable scoring graph for n_cams candidate views of W x H pixels.
+    Owns its output tensors (score [n], best_dev [1], optional rgb/unc) and
+    keeps the scene, field and parameters it was built on alive."""
+
+    def __init__(self, ctx: Context, gs: Gaussians, vf: VisibilityField, n_cams, W, H, record_capacity,
+                 entry_capacity, params, want_rgb, want_unc):
+        self._lib, self._ctx = ctx._lib, ctx
+        self.gs, self.vf = gs, vf
+        self.params = params or Params(vf_degree=vf.degree)
+        if self.params.tile == 0:
+            raise ValueError("a plan needs a fixed tile edge (8, 16 or 32)")
+        dev = gs.means.device
+        self.n_cams, self.W, self.H = int(n_cams), int(W), int(H)
+        self.score = torch.empty(self.n_cams, device=dev)
+        self.best_dev = torch.empty(1, dtype=torch.int32, device=dev)
+        self.rgb = torch.empty((self.n_cams, 3, self.H, self.W), device=dev) if want_rgb else None
+        self.unc = torch.empty((self.n_cams, self.H, self.W), device=dev) if want_unc else None
+        self._vs = vf.struct()
+        self._h = C.c_void_p()
+        ctx._check(self._lib.gavis_plan_create(
+            ctx._h, C.byref(gs.struct), C.byref(self._vs), self.n_cams, self.W, self.H, C.byref(self.params),
+            int(record_capacity), int(entry_capacity), C.c_void_p(self.rgb.data_ptr() if self.rgb is not None else None),
+            C.c_void_p(self.unc.data_ptr() if self.unc is not None else None), C.c_void_p(self.score.data_ptr()),
+            C.c_void_p(self.best_dev.data_ptr()), C.byref(self._h)))
+        self.kernels = int(self._lib.gavis_plan_kernels(self._h))
+
+    def launch(self, cams, stream=None):
+        """Score the poses `cams` (n_cams cameras of W x H, or their
+        camera_records array) asynchronously."""
+        if len(cams) != self.n_cams:
+            raise ValueError(f"plan expects {self.n_cams} cameras, got {len(cams)}")
+        recs = cams if isinstance(cams, C.Array) else camera_records(cams)
+        rc = self._lib.gavis_plan_launch(self._h, recs, _stream_ptr(stream))
+        if rc != OK:
+            raise GavisError(rc, "gavis_plan_launch")
+
+    def overflowed(self):
+        """(overflowed, records_needed, entries_needed) of the last launch;
+        waits for it."""
+        o, r, m = C.c_int(0), C.c_int64(0), C.c_int64(0)
+        rc = self._lib.gavis_plan_overflowed(self._h, C.byref(o), C.byref(r), C.byref(m))
+        if rc != OK:
+            raise GavisError(rc, "gavis_plan_overflowed")
+        return bool(o.value), int(r.value), int(m.value)
+
+    def close(self):
+        if self._h:
+            self._lib.gavis_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -548,6 +548,13 @@ int check_vf(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf)
 
 }  // namespace
 
+namespace gavis {
+void set_error(gavis_ctx *c, const char *msg)
+{
+    if (c) c->err = msg;
+}
+}  // namespace gavis
+
 extern "C" {
 
 int gavis_ctx_create(gavis_ctx **out, int device, size_t hbm_budget_bytes)

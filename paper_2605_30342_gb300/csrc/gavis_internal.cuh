@@ -28,6 +28,8 @@ namespace gavis {
 // number of kernels this library has launched (all contexts)
 extern std::atomic<long long> g_launches;
 inline void count_launch(long long k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+// sets the text gavis_last_error returns
+void set_error(gavis_ctx *c, const char *msg);
 
 struct __align__(16) GeoRec {
     float4 a;
@@ -85,18 +87,25 @@ cudaError_t launch_query(const QueryArgs &a, cudaStream_t s);
 // ---------------------------------------------------------------- sort.cu
 // exclusive scan of n uint32 into out (may alias in); writes the total (u64)
 // to *d_total (device).  flags = true scans (in[i] != 0) instead of in[i].
-// tmp: scan_tmp_bytes(n) bytes.
+// tmp: scan_tmp_bytes(n) bytes.  d_n (optional): the actual count in device
+// memory (<= n); out is then written for the first *d_n items only.
 size_t scan_tmp_bytes(size_t n);
 cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, void *tmp,
-                               unsigned long long *d_total, cudaStream_t s, bool flags = false);
+                               unsigned long long *d_total, cudaStream_t s, bool flags = false,
+                               const unsigned long long *d_n = nullptr);
 
 // stable LSD radix sort of (keys, vals) on bits [0, end_bit); ping-pong
 // buffers; *result_in_alt tells which buffer holds the result.  KeyT is
 // uint64_t or uint32_t.
 size_t radix_tmp_bytes(size_t n);
+// d_n (optional): the actual item count in device memory (<= n), for chains
+// captured in a CUDA graph; the grids are sized by n.
 template <typename KeyT>
 cudaError_t radix_sort_pairs(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_t *vals_alt, size_t n, int end_bit,
-                             void *tmp, bool *result_in_alt, cudaStream_t s);
+                             void *tmp, bool *result_in_alt, cudaStream_t s,
+                             const unsigned long long *d_n = nullptr);
+// kernel attributes the sort sets on first use; call before stream capture
+void radix_prepare();
 
 // ---------------------------------------------------------------- raster.cu
 struct BatchInfo {                // device, read back once per batch
@@ -118,13 +127,20 @@ inline int depth_bits(uint32_t zmin, uint32_t zmax) { return bits_of(zmax > zmin
 // Stage B: in that order, one entry per tile of the record's rectangle with
 // key view * TW*TH + tile and value g, stably sorted by tile: each tile's list
 // ends up in (depth, index) order.
+// Records at positions >= cap_R are not written and set *overflow (when given).
 cudaError_t launch_emit_records(const uint32_t *counts, const uint32_t *pos, const GeoRec *geo, int nv, int64_t n,
-                                int zb, uint32_t zmin, uint64_t *keyA, uint32_t *valA, cudaStream_t s);
+                                int zb, uint32_t zmin, uint64_t *keyA, uint32_t *valA, cudaStream_t s,
+                                size_t cap_R = ~(size_t)0, uint32_t *overflow = nullptr);
+// d_nrec / d_M (optional): actual counts in device memory for graph replays;
+// entries past cap_M are not written and set *overflow (when given).
 cudaError_t launch_gather_counts(const uint32_t *valA, const uint32_t *counts, size_t nrec, uint32_t *cnt_sorted,
-                                 cudaStream_t s);
+                                 cudaStream_t s, const unsigned long long *d_nrec = nullptr);
 cudaError_t launch_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect,
-                              int64_t n, int TW, int TH, uint32_t *keyB, uint32_t *valB, cudaStream_t s);
-cudaError_t launch_ranges(const uint32_t *keys, size_t M, uint2 *ranges, cudaStream_t s);
+                              int64_t n, int TW, int TH, uint32_t *keyB, uint32_t *valB, cudaStream_t s,
+                              const unsigned long long *d_nrec = nullptr, size_t cap_M = ~(size_t)0,
+                              uint32_t *overflow = nullptr);
+cudaError_t launch_ranges(const uint32_t *keys, size_t M, uint2 *ranges, cudaStream_t s,
+                          const unsigned long long *d_M = nullptr);
 // canonical keys ((view*tiles + tile) << 32) | depth bits, for verification
 cudaError_t launch_keys_export(const uint32_t *keyB, const uint32_t *valB, size_t M, const GeoRec *geo, int64_t n,
                                int tiles_per_view, uint64_t *out, cudaStream_t s);

@@ -1,0 +1,263 @@
+// plan.cu -- candidate-view scoring captured once as a CUDA graph and
+// replayed (no counterpart in the paper: it removes the per-call host work of
+// the paper's per-planning-step scoring).
+//
+// A plan fixes the scene, the field, the number of candidate views, their
+// resolution, the parameters and the output buffers.  Its buffers are sized
+// statically: projected records for every (view, Gaussian), sort space for
+// `record_capacity` visible records and `entry_capacity` tile entries.  The
+// kernels after the projection read the actual numbers of visible records
+// and tile entries from device memory (grids are sized by the capacities),
+// so nothing in the chain waits for the host; if a replay needs more than a
+// capacity, the excess is dropped, a device flag is set, and
+// gavis_plan_overflowed reports it (the caller then rebuilds the plan with
+// larger capacities).
+// The stage-A keys keep all 32 depth bits (the per-batch path subtracts the
+// batch's minimum and keeps only the bits that vary), so the record sort may
+// take one more 8-bit pass; the resulting order is the same.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "gavis_internal.cuh"
+
+using namespace gavis;
+
+namespace {
+
+struct PlanInfo {              // device
+    BatchInfo b;
+    uint32_t entries_over;     // a launch needed more tile entries than the capacity
+    uint32_t records_over;     // ... more visible records than the capacity
+};
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct gavis_plan {
+    int device = 0;
+    int n_cams = 0, W = 0, H = 0;
+    size_t record_cap = 0, entry_cap = 0;
+    void *buf = nullptr;                // one device allocation for everything
+    gavis_camera *h_cams = nullptr;     // pinned staging of the poses
+    gavis_camera *d_cams = nullptr;
+    PlanInfo *d_info = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    long long kernels = 0;              // kernels per replay
+    bool launched = false;
+};
+
+namespace {
+
+void plan_free(gavis_plan *pl)
+{
+    if (!pl) return;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->done) cudaEventDestroy(pl->done);
+    if (pl->h_cams) cudaFreeHost(pl->h_cams);
+    if (pl->buf) cudaFree(pl->buf);
+    delete pl;
+}
+
+#define PK(call)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            char m_[320];                                                                              \
+            snprintf(m_, sizeof(m_), "%s: %s", #call, cudaGetErrorString(e_));                         \
+            set_error(ctx, m_);                                                                        \
+            if (capturing) {                                                                           \
+                cudaGraph_t g_ = nullptr;                                                              \
+                cudaStreamEndCapture(cs, &g_);                                                         \
+                if (g_) cudaGraphDestroy(g_);                                                          \
+            }                                                                                          \
+            if (cs) cudaStreamDestroy(cs);                                                             \
+            plan_free(pl);                                                                             \
+            cudaGetLastError();                                                                        \
+            return GAVIS_ERR_CUDA;                                                                     \
+        }                                                                                              \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf, int n_cams, int W, int H,
+                      const gavis_params *p, int64_t record_capacity, int64_t entry_capacity, float *rgb,
+                      float *unc, float *score, int32_t *best_dev, gavis_plan **out)
+{
+    if (!out) return GAVIS_ERR_ARG;
+    *out = nullptr;
+    if (!gs || !vf || !p || !score || n_cams < 1 || n_cams > 1024 || W < 1 || H < 1 || W > 16384 || H > 16384 ||
+        entry_capacity < 1 || record_capacity < 0 || gs->n < 1 || gs->n >= ((int64_t)1 << 31) || !gs->sh || vf->n != gs->n ||
+        !(p->tile == 8 || p->tile == 16 || p->tile == 32) || ((uintptr_t)gs->rots & 15u)) {
+        set_error(ctx, "gavis_plan_create: invalid argument (sizes, tile must be 8/16/32, rots 16-byte aligned)");
+        return GAVIS_ERR_ARG;
+    }
+    const int64_t n = gs->n;
+    const int TW = (W + p->tile - 1) / p->tile, TH = (H + p->tile - 1) / p->tile, TT = TW * TH;
+    const size_t nvn = (size_t)n_cams * (size_t)n, nvt = (size_t)n_cams * (size_t)TT;
+    const size_t M = (size_t)entry_capacity;
+    const size_t R = record_capacity == 0 || (size_t)record_capacity > nvn ? nvn : (size_t)record_capacity;
+    if (nvn >= ((size_t)1 << 32) || M >= ((size_t)1 << 32)) {
+        set_error(ctx, "gavis_plan_create: n_cams x n and entry_capacity must each be below 2^32");
+        return GAVIS_ERR_ARG;
+    }
+
+    gavis_plan *pl = new gavis_plan();
+    cudaStream_t cs = nullptr;
+    bool capturing = false;
+    PK(cudaGetDevice(&pl->device));
+    pl->n_cams = n_cams;
+    pl->W = W;
+    pl->H = H;
+    pl->record_cap = R;
+    pl->entry_cap = M;
+
+    // static layout
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off += up256(b ? b : 1); return o; };
+    const size_t o_cams = take((size_t)n_cams * sizeof(gavis_camera)), o_info = take(sizeof(PlanInfo));
+    const size_t o_geo = take(nvn * sizeof(GeoRec)), o_ua = take(nvn * sizeof(UaRec)), o_rect = take(nvn * 8);
+    const size_t o_cnt = take(nvn * 4), o_pos = take(nvn * 4), o_scan = take(scan_tmp_bytes(nvn) + 64);
+    const size_t o_ak0 = take(R * 8), o_ak1 = take(R * 8), o_av0 = take(R * 4), o_av1 = take(R * 4);
+    const size_t o_acnt = take(R * 4), o_aoff = take(R * 4);
+    const size_t o_bk0 = take(M * 4), o_bk1 = take(M * 4), o_bv0 = take(M * 4), o_bv1 = take(M * 4);
+    const size_t big = R > M ? R : M;
+    const size_t o_tmp = take(radix_tmp_bytes(big) + scan_tmp_bytes(big) + 64);
+    const size_t o_rng = take(nvt * sizeof(uint2)), o_ts = take(nvt * sizeof(float));
+    PK(cudaMalloc(&pl->buf, off));
+    PK(cudaMallocHost(&pl->h_cams, (size_t)n_cams * sizeof(gavis_camera)));
+    std::memset(pl->h_cams, 0, (size_t)n_cams * sizeof(gavis_camera));
+    for (int k = 0; k < n_cams; ++k) {   // placeholder poses until the first launch
+        pl->h_cams[k].W = W;
+        pl->h_cams[k].H = H;
+    }
+    PK(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
+    char *b = reinterpret_cast<char *>(pl->buf);
+    pl->d_cams = reinterpret_cast<gavis_camera *>(b + o_cams);
+    pl->d_info = reinterpret_cast<PlanInfo *>(b + o_info);
+    GeoRec *geo = reinterpret_cast<GeoRec *>(b + o_geo);
+    UaRec *ua = reinterpret_cast<UaRec *>(b + o_ua);
+    uint2 *rect = reinterpret_cast<uint2 *>(b + o_rect);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(b + o_cnt), *pos = reinterpret_cast<uint32_t *>(b + o_pos);
+    uint64_t *ak0 = reinterpret_cast<uint64_t *>(b + o_ak0), *ak1 = reinterpret_cast<uint64_t *>(b + o_ak1);
+    uint32_t *av0 = reinterpret_cast<uint32_t *>(b + o_av0), *av1 = reinterpret_cast<uint32_t *>(b + o_av1);
+    uint32_t *acnt = reinterpret_cast<uint32_t *>(b + o_acnt), *aoff = reinterpret_cast<uint32_t *>(b + o_aoff);
+    uint32_t *bk0 = reinterpret_cast<uint32_t *>(b + o_bk0), *bk1 = reinterpret_cast<uint32_t *>(b + o_bk1);
+    uint32_t *bv0 = reinterpret_cast<uint32_t *>(b + o_bv0), *bv1 = reinterpret_cast<uint32_t *>(b + o_bv1);
+    void *tmp = b + o_tmp, *scan_tmp = b + o_scan;
+    uint2 *ranges = reinterpret_cast<uint2 *>(b + o_rng);
+    float *tile_sums = reinterpret_cast<float *>(b + o_ts);
+    PlanInfo *info = pl->d_info;
+
+    ProjectArgs pa;
+    pa.means = gs->means; pa.scales = gs->scales; pa.rots = gs->rots; pa.opac = gs->opac;
+    pa.sh = gs->sh; pa.sh_degree = gs->sh_degree; pa.sh_dtype = gs->sh_dtype;
+    pa.sh_var = gs->sh_var;
+    pa.k_c = (float)(1.5 * std::log((double)p->sigma_c2) + 1.5 * (std::log(2.0 * M_PI) + 1.0));
+    pa.gamma = vf->coeffs; pa.vf_degree = vf->degree; pa.vf_dtype = vf->dtype; pa.n_train = vf->n_train_views;
+    pa.q_cut = p->q_cut; pa.beta = p->beta; pa.o0 = p->o0;
+    pa.tile = p->tile; pa.TW = TW; pa.TH = TH;
+    pa.cams = pl->d_cams; pa.nv = n_cams; pa.n = n;
+    pa.geo = geo; pa.ua = ua; pa.rect = rect; pa.counts = counts;
+    pa.zrange = info->b.zrange;
+    pa.visible = &info->b.visible;
+    pa.total = &info->b.total;
+    CompositeArgs ca;
+    std::memset(&ca, 0, sizeof(ca));
+    ca.ranges = ranges; ca.geo = geo; ca.ua = ua;
+    ca.n = n; ca.nv = n_cams; ca.v0 = 0; ca.W = W; ca.H = H; ca.tile = p->tile; ca.TW = TW; ca.TH = TH;
+    ca.rc.eps_T = p->eps_T; ca.rc.q_cut = p->q_cut; ca.rc.beta = p->beta; ca.rc.o0 = p->o0;
+    const double l2pie = std::log(2.0 * M_PI) + 1.0;
+    ca.rc.k_c = pa.k_c;
+    ca.rc.k_0 = (float)(0.5 * (double)p->logdet_Q0 + 1.5 * l2pie);
+    ca.rgb = rgb; ca.unc = unc; ca.tile_sums = tile_sums;
+    ca.per_entry_kc = gs->sh_var != nullptr;
+
+    // the chain, captured on a private stream
+    radix_prepare();
+    PK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const long long k0 = g_launches.load();
+    PK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    capturing = true;
+    PK(cudaMemcpyAsync(pl->d_cams, pl->h_cams, (size_t)n_cams * sizeof(gavis_camera), cudaMemcpyHostToDevice, cs));
+    PK(cudaMemsetAsync(info, 0, sizeof(PlanInfo), cs));
+    PK(cudaMemsetAsync(&info->b.zrange[0], 0xff, sizeof(uint32_t), cs));
+    PK(launch_project(pa, cs));
+    PK(exclusive_scan_u32(counts, pos, nvn, scan_tmp, nullptr, cs, true));
+    PK(launch_emit_records(counts, pos, geo, n_cams, n, 32, 0u, ak0, av0, cs, R, &info->records_over));
+    bool alt_a = false, alt_b = false;
+    PK(radix_sort_pairs<uint64_t>(ak0, av0, ak1, av1, R, bits_of((uint64_t)n_cams - 1) + 32, tmp, &alt_a, cs,
+                                  &info->b.visible));
+    const uint32_t *recs = alt_a ? av1 : av0;
+    PK(launch_gather_counts(recs, counts, R, acnt, cs, &info->b.visible));
+    PK(exclusive_scan_u32(acnt, aoff, R, tmp, nullptr, cs, false, &info->b.visible));
+    PK(launch_emit_tiles(recs, aoff, R, rect, n, TW, TH, bk0, bv0, cs, &info->b.visible, M, &info->entries_over));
+    PK(radix_sort_pairs<uint32_t>(bk0, bv0, bk1, bv1, M, bits_of((uint64_t)nvt - 1), tmp, &alt_b, cs,
+                                  &info->b.total));
+    const uint32_t *keys = alt_b ? bk1 : bk0;
+    ca.vals = alt_b ? bv1 : bv0;
+    PK(cudaMemsetAsync(ranges, 0, nvt * sizeof(uint2), cs));
+    PK(launch_ranges(keys, M, ranges, cs, &info->b.total));
+    PK(launch_composite_ua(ca, cs));
+    PK(launch_view_reduce(tile_sums, n_cams, TT, 1.0f / ((float)W * (float)H), score, cs));
+    if (best_dev) PK(launch_argmax(score, n_cams, best_dev, cs));
+    PK(cudaStreamEndCapture(cs, &pl->graph));
+    capturing = false;
+    pl->kernels = g_launches.load() - k0;
+    g_launches.fetch_sub(pl->kernels);   // captured, not run: counted per replay
+    PK(cudaGraphInstantiate(&pl->exec, pl->graph, 0));
+    cudaStreamDestroy(cs);
+    *out = pl;
+    return GAVIS_OK;
+}
+
+int gavis_plan_launch(gavis_plan *pl, const gavis_camera *cams, void *stream)
+{
+    if (!pl || !cams) return GAVIS_ERR_ARG;
+    for (int k = 0; k < pl->n_cams; ++k)
+        if (cams[k].W != pl->W || cams[k].H != pl->H || !(cams[k].fx > 0.0f) || !(cams[k].fy > 0.0f) ||
+            !(cams[k].znear > 0.0f))
+            return GAVIS_ERR_ARG;
+    // the previous replay must have read the staged poses before they change
+    if (pl->launched && cudaEventSynchronize(pl->done) != cudaSuccess) return GAVIS_ERR_CUDA;
+    std::memcpy(pl->h_cams, cams, (size_t)pl->n_cams * sizeof(gavis_camera));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaGraphLaunch(pl->exec, s) != cudaSuccess || cudaEventRecord(pl->done, s) != cudaSuccess) {
+        cudaGetLastError();
+        return GAVIS_ERR_CUDA;
+    }
+    pl->launched = true;
+    count_launch(pl->kernels);
+    return GAVIS_OK;
+}
+
+int gavis_plan_overflowed(gavis_plan *pl, int *overflowed, int64_t *records_needed, int64_t *entries_needed)
+{
+    if (!pl) return GAVIS_ERR_ARG;
+    if (pl->launched && cudaEventSynchronize(pl->done) != cudaSuccess) return GAVIS_ERR_CUDA;
+    PlanInfo h;
+    if (cudaMemcpy(&h, pl->d_info, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return GAVIS_ERR_CUDA;
+    const bool over = h.entries_over != 0u || h.records_over != 0u || h.b.total > pl->entry_cap ||
+                      h.b.visible > pl->record_cap;
+    if (overflowed) *overflowed = pl->launched ? (int)over : 0;
+    if (records_needed) *records_needed = pl->launched ? (int64_t)h.b.visible : 0;
+    if (entries_needed) *entries_needed = pl->launched ? (int64_t)h.b.total : 0;
+    return GAVIS_OK;
+}
+
+int64_t gavis_plan_kernels(const gavis_plan *pl) { return pl ? (int64_t)pl->kernels : 0; }
+
+void gavis_plan_destroy(gavis_plan *pl)
+{
+    if (!pl) return;
+    if (pl->launched) cudaEventSynchronize(pl->done);
+    plan_free(pl);
+}
+
+}  // extern "C"

@@ -87,29 +87,37 @@ __device__ __forceinline__ float footprint_q(float px, float py, float u, float 
 
 // stage A: one record key per visible (view, Gaussian), in (view, index) order
 __global__ void k_emit_records(const uint32_t *counts, const uint32_t *pos, const GeoRec *geo, int nv, int64_t n,
-                               int zb, uint32_t zmin, uint64_t *keyA, uint32_t *valA)
+                               int zb, uint32_t zmin, uint64_t *keyA, uint32_t *valA, size_t cap_R,
+                               uint32_t *overflow)
 {
     const size_t total = (size_t)nv * (size_t)n;
     const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= total || counts[r] == 0u) return;
     const uint64_t v = r / (size_t)n;
     const uint32_t i = pos[r];
+    if ((size_t)i >= cap_R) {
+        if (overflow) *overflow = 1u;
+        return;
+    }
     keyA[i] = (v << zb) | (uint64_t)(__float_as_uint(geo[r].b.z) - zmin);
     valA[i] = (uint32_t)r;
 }
 
-__global__ void k_gather_counts(const uint32_t *valA, const uint32_t *counts, size_t nrec, uint32_t *cnt_sorted)
+__global__ void k_gather_counts(const uint32_t *valA, const uint32_t *counts, size_t nrec, uint32_t *cnt_sorted,
+                                const unsigned long long *d_nrec)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nrec) cnt_sorted[i] = counts[valA[i]];
+    if (i >= nrec || (d_nrec && i >= (size_t)*d_nrec)) return;
+    cnt_sorted[i] = counts[valA[i]];
 }
 
 // stage B: the tiles of each record, in stage-A order
 __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect, int64_t n,
-                             int TW, int TH, uint32_t *keyB, uint32_t *valB)
+                             int TW, int TH, uint32_t *keyB, uint32_t *valB, const unsigned long long *d_nrec,
+                             size_t cap_M, uint32_t *overflow)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nrec) return;
+    if (i >= nrec || (d_nrec && i >= (size_t)*d_nrec)) return;
     const uint32_t r = valA[i];
     const uint32_t v = (uint32_t)(r / (uint64_t)n);
     const uint32_t g = (uint32_t)(r - (uint64_t)v * (uint64_t)n);
@@ -117,16 +125,20 @@ __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, s
     const uint32_t x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu, y1 = rc.y >> 16;
     const uint32_t vbase = v * (uint32_t)(TW * TH);
     uint32_t off = off_sorted[i];
+    if ((size_t)off + (size_t)((x1 - x0 + 1) * (y1 - y0 + 1)) > cap_M && overflow) *overflow = 1u;
     for (uint32_t ty = y0; ty <= y1; ++ty)
         for (uint32_t tx = x0; tx <= x1; ++tx) {
-            keyB[off] = vbase + ty * (uint32_t)TW + tx;
-            valB[off] = g;
+            if ((size_t)off < cap_M) {
+                keyB[off] = vbase + ty * (uint32_t)TW + tx;
+                valB[off] = g;
+            }
             ++off;
         }
 }
 
-__global__ void k_ranges(const uint32_t *keys, size_t M, uint2 *ranges)
+__global__ void k_ranges(const uint32_t *keys, size_t M, uint2 *ranges, const unsigned long long *d_M)
 {
+    if (d_M && *d_M < M) M = (size_t)*d_M;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     const uint32_t t = keys[i];
@@ -600,34 +612,38 @@ inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 }  // namespace
 
 cudaError_t launch_emit_records(const uint32_t *counts, const uint32_t *pos, const GeoRec *geo, int nv, int64_t n,
-                                int zb, uint32_t zmin, uint64_t *keyA, uint32_t *valA, cudaStream_t s)
+                                int zb, uint32_t zmin, uint64_t *keyA, uint32_t *valA, cudaStream_t s,
+                                size_t cap_R, uint32_t *overflow)
 {
     const size_t total = (size_t)nv * (size_t)n;
     if (total == 0) return cudaSuccess;
-    k_emit_records<<<nblk(total, 256), 256, 0, s>>>(counts, pos, geo, nv, n, zb, zmin, keyA, valA); count_launch();
+    k_emit_records<<<nblk(total, 256), 256, 0, s>>>(counts, pos, geo, nv, n, zb, zmin, keyA, valA, cap_R, overflow);
+    count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather_counts(const uint32_t *valA, const uint32_t *counts, size_t nrec, uint32_t *cnt_sorted,
-                                 cudaStream_t s)
+                                 cudaStream_t s, const unsigned long long *d_nrec)
 {
     if (nrec == 0) return cudaSuccess;
-    k_gather_counts<<<nblk(nrec, 256), 256, 0, s>>>(valA, counts, nrec, cnt_sorted); count_launch();
+    k_gather_counts<<<nblk(nrec, 256), 256, 0, s>>>(valA, counts, nrec, cnt_sorted, d_nrec); count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect,
-                              int64_t n, int TW, int TH, uint32_t *keyB, uint32_t *valB, cudaStream_t s)
+                              int64_t n, int TW, int TH, uint32_t *keyB, uint32_t *valB, cudaStream_t s,
+                              const unsigned long long *d_nrec, size_t cap_M, uint32_t *overflow)
 {
     if (nrec == 0) return cudaSuccess;
-    k_emit_tiles<<<nblk(nrec, 256), 256, 0, s>>>(valA, off_sorted, nrec, rect, n, TW, TH, keyB, valB); count_launch();
+    k_emit_tiles<<<nblk(nrec, 256), 256, 0, s>>>(valA, off_sorted, nrec, rect, n, TW, TH, keyB, valB, d_nrec, cap_M,
+                                                 overflow); count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_ranges(const uint32_t *keys, size_t M, uint2 *ranges, cudaStream_t s)
+cudaError_t launch_ranges(const uint32_t *keys, size_t M, uint2 *ranges, cudaStream_t s, const unsigned long long *d_M)
 {
     if (M == 0) return cudaSuccess;
-    k_ranges<<<nblk(M, 256), 256, 0, s>>>(keys, M, ranges); count_launch();
+    k_ranges<<<nblk(M, 256), 256, 0, s>>>(keys, M, ranges, d_M); count_launch();
     return cudaGetLastError();
 }
 

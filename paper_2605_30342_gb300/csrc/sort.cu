@@ -34,12 +34,20 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
     return t;   // valid in thread 0
 }
 
+// d_n (optional): the actual item count in device memory, <= n (graph
+// replays); blocks past it only write a zero partial.
 template <bool FLAGS>
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *in, size_t n,
-                                                              unsigned long long *partials)
+                                                              unsigned long long *partials,
+                                                              const unsigned long long *d_n)
 {
     __shared__ unsigned long long s_warp[32];
+    if (d_n && *d_n < n) n = (size_t)*d_n;
     const size_t base = (size_t)blockIdx.x * kScanChunk;
+    if (base >= n) {
+        if (threadIdx.x == 0) partials[blockIdx.x] = 0ull;
+        return;
+    }
     unsigned long long v = 0;
 #pragma unroll
     for (int r = 0; r < kScanItems; ++r) {
@@ -83,9 +91,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_partials(unsigned long lo
 
 template <bool FLAGS>
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *in, uint32_t *out, size_t n,
-                                                             const unsigned long long *partials)
+                                                             const unsigned long long *partials,
+                                                             const unsigned long long *d_n)
 {
     __shared__ uint32_t s_warp[32];
+    if (d_n && *d_n < n) n = (size_t)*d_n;
+    if ((size_t)blockIdx.x * kScanChunk >= n) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t base = (size_t)blockIdx.x * kScanChunk + (size_t)threadIdx.x * kScanItems;
     uint32_t x[kScanItems];
@@ -129,14 +140,21 @@ constexpr int kRsRounds = 16;
 constexpr int kRsTile = kRsThreads * kRsRounds;   // 4096 keys per block
 constexpr int kRsWarps = kRsThreads / 32;
 
+// d_n (optional): the actual item count in device memory, <= n (graph replays)
 template <typename KeyT>
 __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const KeyT *keys, size_t n, int shift,
-                                                           uint32_t *hist, int nblocks)
+                                                           uint32_t *hist, int nblocks,
+                                                           const unsigned long long *d_n)
 {
+    if (d_n && *d_n < n) n = (size_t)*d_n;
     __shared__ uint32_t s_h[256];
+    const size_t base = (size_t)blockIdx.x * kRsTile;
+    if (base >= n) {   // whole block past the live items (graph replays)
+        hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = 0u;
+        return;
+    }
     s_h[threadIdx.x] = 0;
     __syncthreads();
-    const size_t base = (size_t)blockIdx.x * kRsTile;
     const int lane = threadIdx.x & 31;
 #pragma unroll 4
     for (int r = 0; r < kRsRounds; ++r) {
@@ -162,8 +180,10 @@ template <typename KeyT>
 __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const KeyT *kin, const uint32_t *vin,
                                                               KeyT *kout, uint32_t *vout, size_t n, int shift,
                                                               const uint32_t *hist, const uint32_t *offs,
-                                                              int nblocks)
+                                                              int nblocks, const unsigned long long *d_n)
 {
+    if (d_n && *d_n < n) n = (size_t)*d_n;
+    if ((size_t)blockIdx.x * kRsTile >= n) return;   // nothing of this block is live
     extern __shared__ __align__(16) unsigned char smem[];
     KeyT *s_key = reinterpret_cast<KeyT *>(smem);
     uint32_t *s_val = reinterpret_cast<uint32_t *>(smem + (size_t)kRsTile * sizeof(KeyT));
@@ -238,7 +258,7 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const KeyT *kin, c
     }
     __syncthreads();
     // phase C: coalesced write-out
-    const int cnt = (int)min((size_t)kRsTile, n - base);
+    const int cnt = base < n ? (int)min((size_t)kRsTile, n - base) : 0;
     for (int i = tid; i < cnt; i += kRsThreads) {
         const KeyT kk = s_key[i];
         const int dd = (int)((kk >> shift) & 255u);
@@ -257,7 +277,8 @@ size_t scan_tmp_bytes(size_t n)
 }
 
 cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, void *tmp,
-                               unsigned long long *d_total, cudaStream_t s, bool flags)
+                               unsigned long long *d_total, cudaStream_t s, bool flags,
+                               const unsigned long long *d_n)
 {
     const size_t nb = (n + kScanChunk - 1) / kScanChunk;
     unsigned long long *partials = reinterpret_cast<unsigned long long *>(tmp);
@@ -266,15 +287,15 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, void
         return cudaSuccess;
     }
     if (flags) {
-        k_scan_reduce<true><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partials); count_launch();
+        k_scan_reduce<true><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partials, d_n); count_launch();
     } else {
-        k_scan_reduce<false><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partials); count_launch();
+        k_scan_reduce<false><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partials, d_n); count_launch();
     }
     k_scan_partials<<<1, kScanThreads, 0, s>>>(partials, (int)nb, d_total); count_launch();
     if (flags) {
-        k_scan_apply<true><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partials); count_launch();
+        k_scan_apply<true><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partials, d_n); count_launch();
     } else {
-        k_scan_apply<false><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partials); count_launch();
+        k_scan_apply<false><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partials, d_n); count_launch();
     }
     return cudaGetLastError();
 }
@@ -289,7 +310,7 @@ size_t radix_tmp_bytes(size_t n)
 
 template <typename KeyT>
 cudaError_t radix_sort_pairs(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_t *vals_alt, size_t n, int end_bit,
-                             void *tmp, bool *result_in_alt, cudaStream_t s)
+                             void *tmp, bool *result_in_alt, cudaStream_t s, const unsigned long long *d_n)
 {
     *result_in_alt = false;
     if (n <= 1) return cudaSuccess;
@@ -300,16 +321,17 @@ cudaError_t radix_sort_pairs(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_
     uint32_t *offs = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(tmp) + a);
     void *stmp = reinterpret_cast<char *>(tmp) + 2 * a;
     constexpr size_t smem = rs_smem<KeyT>();
-    // per device, idempotent
-    cudaFuncSetAttribute(k_radix_scatter<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!d_n) {   // per device, idempotent (done beforehand when capturing)
+        cudaFuncSetAttribute(k_radix_scatter<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
     KeyT *kin = keys, *kout = keys_alt;
     uint32_t *vin = vals, *vout = vals_alt;
     bool alt = false;
     for (int shift = 0; shift < end_bit; shift += 8) {
-        k_radix_hist<KeyT><<<nblocks, kRsThreads, 0, s>>>(kin, n, shift, hist, nblocks); count_launch();
+        k_radix_hist<KeyT><<<nblocks, kRsThreads, 0, s>>>(kin, n, shift, hist, nblocks, d_n); count_launch();
         cudaError_t e = exclusive_scan_u32(hist, offs, h, stmp, nullptr, s);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<KeyT><<<nblocks, kRsThreads, smem, s>>>(kin, vin, kout, vout, n, shift, hist, offs, nblocks); count_launch();
+        k_radix_scatter<KeyT><<<nblocks, kRsThreads, smem, s>>>(kin, vin, kout, vout, n, shift, hist, offs, nblocks, d_n); count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         KeyT *tk = kin; kin = kout; kout = tk;
@@ -321,8 +343,16 @@ cudaError_t radix_sort_pairs(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_
 }
 
 template cudaError_t radix_sort_pairs<uint64_t>(uint64_t *, uint32_t *, uint64_t *, uint32_t *, size_t, int, void *,
-                                                bool *, cudaStream_t);
+                                                bool *, cudaStream_t, const unsigned long long *);
 template cudaError_t radix_sort_pairs<uint32_t>(uint32_t *, uint32_t *, uint32_t *, uint32_t *, size_t, int, void *,
-                                                bool *, cudaStream_t);
+                                                bool *, cudaStream_t, const unsigned long long *);
+
+void radix_prepare()
+{
+    cudaFuncSetAttribute(k_radix_scatter<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)rs_smem<uint64_t>());
+    cudaFuncSetAttribute(k_radix_scatter<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)rs_smem<uint32_t>());
+}
 
 }  // namespace gavis

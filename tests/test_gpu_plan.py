@@ -1,0 +1,160 @@
+"""Scoring plans (the scoring chain captured as a CUDA graph): a replay must
+give the same bits as gavis_score_views for the same poses, pick up new poses
+and in-place scene updates, and flag an undersized tile-entry capacity."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenegen as sg
+from _util import GAP, TOL, compare_views, sorted_gap
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gv():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2605_30342_gb300 as pkg
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def ctx(gv):
+    c = gv.Context(0)
+    yield c
+    c.close()
+
+
+def setup(gv, ctx, k=2, **kw):
+    c = sg.config(k, **kw)
+    gs = gv.Gaussians.from_numpy(c["scene"])
+    vf = ctx.vf_build(gs, c["train"], degree=c["vf_degree"])
+    return c, gs, vf
+
+
+def needed(gv, ctx, gs, vf, cams, p):
+    """(visible records, tile keys) gavis_score_views used for `cams`."""
+    ctx.prof_enable(True)
+    ctx.score_views(gs, vf, cams, params=p, want_rgb=False, want_unc=False)
+    r = ctx.prof_read()
+    ctx.prof_enable(False)
+    return int(r["visible"]), int(r["keys"])
+
+
+def assert_same(plan, ref):
+    assert torch.equal(plan.score, ref["score"])
+    assert int(plan.best_dev.item()) == ref["best"]
+    if plan.rgb is not None:
+        assert torch.equal(plan.rgb, ref["rgb"])
+    if plan.unc is not None:
+        assert torch.equal(plan.unc, ref["unc"])
+
+
+@pytest.mark.parametrize("tile", [16, 8, 32])
+def test_plan_equals_score_views(ctx, gv, tile):
+    c, gs, vf = setup(gv, ctx, n=20000, n_train=4, n_cand=6, train_wh=(160, 120), cand_wh=(200, 136))
+    cand = c["cand"]
+    p = gv.Params(tile=tile, vf_degree=c["vf_degree"])
+    rec, cap = needed(gv, ctx, gs, vf, cand, p)
+    plan = ctx.plan(gs, vf, len(cand), cand[0].W, cand[0].H, cap, record_capacity=rec, params=p, want_rgb=True,
+                    want_unc=True)
+    assert plan.kernels > 10
+    plan.launch(cand)
+    torch.cuda.synchronize()
+    assert plan.overflowed() == (False, rec, cap)
+    assert_same(plan, ctx.score_views(gs, vf, cand, params=p))
+    plan.close()
+
+
+def test_plan_matches_oracle(ctx, gv):
+    c = sg.config(1, n=900, n_train=3, n_cand=5, train_wh=(100, 75), cand_wh=(100, 75))
+    sc, cand, L = c["scene"], c["cand"], c["vf_degree"]
+    g, _, _ = oracle.vf_build(c["train"], sc, L)
+    g32 = g.astype(np.float32)
+    gs = gv.Gaussians.from_numpy(sc)
+    vf = gv.VisibilityField(torch.as_tensor(g32).cuda(), L, len(c["train"]), 1.0)
+    p = gv.Params(tile=16, vf_degree=L)
+    plan = ctx.plan(gs, vf, len(cand), cand[0].W, cand[0].H, 1 << 20, params=p, want_rgb=True, want_unc=True)
+    plan.launch(cand)
+    torch.cuda.synchronize()
+    ref = oracle.score_views(sc, g32.astype(np.float64), L, len(c["train"]), cand)
+    err, n_amb = compare_views(plan.unc.cpu().numpy(), plan.rgb.cpu().numpy(), ref)
+    assert err <= TOL, err
+    assert n_amb <= 0.01 * len(cand) * cand[0].W * cand[0].H
+    score = plan.score.cpu().numpy()
+    unc = plan.unc.cpu().numpy()
+    amb_slack = np.array([np.abs(unc[v] - ref["unc"][v])[ref["amb"][v]].sum() / unc[v].size for v in range(len(cand))])
+    assert np.all(np.abs(score - ref["score"]) <= TOL + amb_slack)
+    if sorted_gap(ref["score"]) > GAP:
+        assert int(plan.best_dev.item()) == ref["best"]
+
+
+def test_plan_relaunch_with_new_poses(ctx, gv):
+    c, gs, vf = setup(gv, ctx, n=20000, n_train=4, n_cand=8, train_wh=(160, 120), cand_wh=(160, 120))
+    a, b = c["cand"][:4], c["cand"][4:]
+    p = gv.Params(tile=16, vf_degree=c["vf_degree"])
+    cap = 2 * max(needed(gv, ctx, gs, vf, a, p)[1], needed(gv, ctx, gs, vf, b, p)[1])
+    plan = ctx.plan(gs, vf, 4, 160, 120, cap, params=p, want_unc=True)
+    for poses in (a, b, a, b):
+        plan.launch(gv.camera_records(poses))
+        assert_same(plan, ctx.score_views(gs, vf, poses, params=p, want_rgb=False))
+    assert not plan.overflowed()[0]
+    plan.close()
+
+
+def test_plan_reads_scene_values_at_launch(ctx, gv):
+    c, gs, vf = setup(gv, ctx, n=20000, n_train=4, n_cand=4, train_wh=(160, 120), cand_wh=(160, 120))
+    cand = c["cand"]
+    p = gv.Params(tile=16, vf_degree=c["vf_degree"])
+    cap = 2 * needed(gv, ctx, gs, vf, cand, p)[1]
+    plan = ctx.plan(gs, vf, len(cand), 160, 120, cap, params=p)
+    plan.launch(cand)
+    torch.cuda.synchronize()
+    before = plan.score.clone()
+    with torch.no_grad():
+        gs.opac.mul_(0.5)          # in place: same addresses
+        vf.coeffs.mul_(0.25)
+    torch.cuda.synchronize()
+    plan.launch(cand)
+    ref = ctx.score_views(gs, vf, cand, params=p, want_rgb=False, want_unc=False)
+    assert_same(plan, ref)
+    assert not torch.equal(before, plan.score)
+    plan.close()
+
+
+def test_plan_flags_overflow(ctx, gv):
+    c, gs, vf = setup(gv, ctx, n=20000, n_train=4, n_cand=4, train_wh=(160, 120), cand_wh=(160, 120))
+    cand = c["cand"]
+    p = gv.Params(tile=16, vf_degree=c["vf_degree"])
+    rec, need = needed(gv, ctx, gs, vf, cand, p)
+    few_entries = ctx.plan(gs, vf, len(cand), 160, 120, need // 3, params=p)
+    few_entries.launch(cand)
+    assert few_entries.overflowed() == (True, rec, need)
+    few_records = ctx.plan(gs, vf, len(cand), 160, 120, need, record_capacity=rec - 1, params=p)
+    few_records.launch(cand)
+    assert few_records.overflowed() == (True, rec, need)
+    exact = ctx.plan(gs, vf, len(cand), 160, 120, need, record_capacity=rec, params=p)
+    exact.launch(cand)
+    assert exact.overflowed() == (False, rec, need)
+    assert_same(exact, ctx.score_views(gs, vf, cand, params=p, want_rgb=False, want_unc=False))
+    for pl in (few_entries, few_records, exact):
+        pl.close()
+
+
+def test_plan_rejects_bad_arguments(ctx, gv):
+    c, gs, vf = setup(gv, ctx, k=1)
+    cand = c["cand"]
+    W, H = cand[0].W, cand[0].H
+    with pytest.raises(ValueError):
+        ctx.plan(gs, vf, len(cand), W, H, 1 << 16, params=gv.Params(tile=0, vf_degree=c["vf_degree"]))
+    with pytest.raises(gv.GavisError):
+        ctx.plan(gs, vf, len(cand), W, H, 0, params=gv.Params(tile=16, vf_degree=c["vf_degree"]))
+    plan = ctx.plan(gs, vf, len(cand), W, H, 1 << 16, params=gv.Params(tile=16, vf_degree=c["vf_degree"]))
+    with pytest.raises(ValueError):
+        plan.launch(cand[:-1])
+    other = sg.config(1, cand_wh=(W + 8, H))["cand"][:len(cand)]
+    with pytest.raises(gv.GavisError):
+        plan.launch(other)
+    plan.close()
