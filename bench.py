@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--tile", type=int, default=0, help="tile edge 8/16/32; 0 = autotune per path")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-views", type=int, default=1)
+    ap.add_argument("--cpu-sample-views", type=int, default=16,
+                    help="cpu_baseline: training and candidate views of the oracle sample (about 10 s of CPU work)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain unbatched f32 comparison step")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph scoring comparison")
     ap.add_argument("--serving", action="store_true", help="serving workload: Poisson requests over 4 resident scenes")

@@ -12,13 +12,16 @@
 //   k_argmax          next-best view (eq:i_gain)
 //   k_vf_accumulate   gamma_lm += v a_l Y_lm(d_p) (eq:vis_gamma)
 //
-// Compositing stages the tile's list in shared memory in batches of one entry
-// per thread (gathered from the per-view records by Gaussian index) and loops
-// over the batch per pixel.  Each warp covers an 8 x 4 pixel block and skips,
-// as a whole, the entries whose footprint box (half-extents rounded up) misses
-// the block's pixel centres; those entries have q > q_cut at all its pixels.  The footprint value q of a (pixel, Gaussian) pair
-// uses explicit round-to-nearest operations in a fixed order, so the overlap
-// decision q <= q_cut is reproducible bit for bit.
+// Compositing: each warp owns an 8 x 8 pixel block of the tile (two pixels
+// per thread, rows j and j + 4) and walks the tile's list on its own, in
+// chunks of 32 entries: every lane gathers one entry's record (by Gaussian
+// index from the per-view records), drops it if the footprint box
+// (half-extents rounded up) or the ellipse itself misses the block's pixel
+// centres, and the survivors are compacted in order into warp-private shared
+// memory and composited front to back.  The footprint value q of a
+// (pixel, Gaussian) pair uses explicit round-to-nearest operations in a fixed
+// order, so the overlap decision q <= q_cut is reproducible bit for bit; the
+// culling tests are conservative and never change a pixel's result.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -42,37 +45,36 @@ __device__ __forceinline__ bool box_misses(const float4 b, float bx0, float bx1,
     return b.y < bx0 || b.x > bx1 || b.w < by0 || b.z > by1;
 }
 
-// Bit w set iff the footprint box touches the pixel centres of warp block w
-// (8 x 8 pixels, TILE/8 blocks per row) of tile (tx, ty).
-template <int TILE>
-__device__ __forceinline__ uint32_t warp_block_mask(const float4 b, int tx, int ty)
+// True only if q(d) = A dx^2 + B2 dx dy + C dy^2 (d = p - (u, v)) exceeds
+// q_cut at every point p of the rectangle [bx0, bx1] x [by0, by1] of a warp's
+// pixel centres, so no pixel of the warp can be covered.  The minimum of the
+// convex q over the rectangle is 0 if the centre lies inside, else it lies on
+// an edge, where q is a parabola in one variable minimised at a clamped
+// stationary point.  The decision must never cull a Gaussian that
+// footprint_q admits at some pixel: both evaluations err by a few float32
+// ulps of S = A dx^2 + |B2 dx dy| + C dy^2 <= 2 (A dx^2 + C dy^2), so the
+// test keeps a margin of 2^-16 times that bound over the rectangle
+// (8 times the worst-case error) plus 2^-10 q_cut.
+__device__ __forceinline__ bool ellipse_misses(float u, float v, float A, float B2, float C, float bx0, float bx1,
+                                               float by0, float by1, float qcut)
 {
-    constexpr int WPR = TILE / 8;
-    uint32_t m = 0u;
+    const float X0 = bx0 - u, X1 = bx1 - u, Y0 = by0 - v, Y1 = by1 - v;
+    if (X0 <= 0.0f && X1 >= 0.0f && Y0 <= 0.0f && Y1 >= 0.0f) return false;
+    // stationary points per unit offset (any point of an edge gives a valid
+    // upper bound on its minimum, so an approximate quotient is enough)
+    const float hA = __fdividef(-0.5f * B2, A), hC = __fdividef(-0.5f * B2, C);
+    float m = INFINITY;
 #pragma unroll
-    for (int w = 0; w < WPR * WPR; ++w) {
-        const float x0 = (float)(tx * TILE + (w % WPR) * 8) + 0.5f, y0 = (float)(ty * TILE + (w / WPR) * 8) + 0.5f;
-        if (!box_misses(b, x0, x0 + 7.0f, y0, y0 + 7.0f)) m |= 1u << w;
+    for (int e = 0; e < 2; ++e) {
+        const float X = e ? X1 : X0, Y = e ? Y1 : Y0;
+        const float dy = fminf(fmaxf(hC * X, Y0), Y1);    // vertical edge dx = X
+        m = fminf(m, fmaf(fmaf(A, X, B2 * dy), X, C * dy * dy));
+        const float dx = fminf(fmaxf(hA * Y, X0), X1);    // horizontal edge dy = Y
+        m = fminf(m, fmaf(fmaf(A, dx, B2 * Y), dx, C * Y * Y));
     }
-    return m;
-}
-
-// The warp's entries of a staged batch (bit `warp` of s_wm), compacted in
-// order into list; returns their number (warp-uniform).
-template <int NB>
-__device__ __forceinline__ int build_warp_list(const uint32_t *s_wm, int warp, int lane, uint16_t *list)
-{
-    int n = 0;
-    const unsigned lt = (1u << lane) - 1u;
-#pragma unroll
-    for (int c = 0; c < NB; c += 32) {
-        const bool mine = (s_wm[c + lane] >> warp) & 1u;
-        const unsigned b = __ballot_sync(0xffffffffu, mine);
-        if (mine) list[n + __popc(b & lt)] = (uint16_t)(c + lane);
-        n += __popc(b);
-    }
-    __syncwarp();
-    return n;
+    const float Dx = fmaxf(fabsf(X0), fabsf(X1)), Dy = fmaxf(fabsf(Y0), fabsf(Y1));
+    const float smax = 2.0f * fmaf(A, Dx * Dx, C * Dy * Dy);
+    return m > fmaf(smax, 1.52587890625e-5f, qcut * (1.0f + 9.765625e-4f));
 }
 
 __device__ __forceinline__ float footprint_q(float px, float py, float u, float v, float A, float B2, float C)
@@ -84,6 +86,7 @@ __device__ __forceinline__ float footprint_q(float px, float py, float u, float 
     const float qd = __fmul_rn(qc, dy);
     return __fmaf_rn(qb, dx, qd);
 }
+
 
 // stage A: one record key per visible (view, Gaussian), in (view, index) order
 __global__ void k_emit_records(const uint32_t *counts, const uint32_t *pos, const GeoRec *geo, int nv, int64_t n,
@@ -243,7 +246,8 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
         if (e < rg.y) {
             r = vrow + a.vals[e];
             gr = a.geo[r];
-            mine = !box_misses(footprint_box(gr.a.x, gr.a.y, gr.b.w), bx0, bx1, by0, by1);
+            mine = !box_misses(footprint_box(gr.a.x, gr.a.y, gr.b.w), bx0, bx1, by0, by1) &&
+                   !ellipse_misses(gr.a.x, gr.a.y, gr.a.z, gr.a.w, gr.b.x, bx0, bx1, by0, by1, rc.q_cut);
         }
         const unsigned m = __ballot_sync(0xffffffffu, mine);
         if (mine) {
@@ -379,7 +383,8 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
         if (e < rg.y) {
             g = a.vals[e];
             gr = a.geo[vrow + g];
-            mine = !box_misses(footprint_box(gr.a.x, gr.a.y, gr.b.w), bx0, bx1, by0, by1);
+            mine = !box_misses(footprint_box(gr.a.x, gr.a.y, gr.b.w), bx0, bx1, by0, by1) &&
+                   !ellipse_misses(gr.a.x, gr.a.y, gr.a.z, gr.a.w, gr.b.x, bx0, bx1, by0, by1, qcut);
         }
         const unsigned mk = __ballot_sync(0xffffffffu, mine);
         if (mine) {
