@@ -48,6 +48,8 @@ struct gavis_ctx {
     std::string err;
     Buf rec, vis, keys, small, gamma, cams, aug, tune;
     BatchInfo *h_info = nullptr;             // pinned
+    uint32_t *h_voff = nullptr;              // pinned, per-view record offsets of a batch
+    size_t h_voff_cap = 0;
     int32_t *h_best = nullptr;               // pinned
     // instrumentation
     bool prof_on = false;
@@ -308,10 +310,11 @@ struct SmallLayout {
     uint32_t *pair_counts;
     BatchInfo *info;
     int32_t *best;
+    uint32_t *voff;   // [nv + 1]
     size_t bytes;
 };
 
-SmallLayout small_layout(void *base, size_t nvt)
+SmallLayout small_layout(void *base, size_t nvt, size_t nv = 0)
 {
     SmallLayout L;
     char *p = reinterpret_cast<char *>(base);
@@ -322,6 +325,7 @@ SmallLayout small_layout(void *base, size_t nvt)
     L.pair_counts = reinterpret_cast<uint32_t *>(take(nvt * sizeof(uint32_t)));
     L.info = reinterpret_cast<BatchInfo *>(take(sizeof(BatchInfo)));
     L.best = reinterpret_cast<int32_t *>(take(sizeof(int32_t)));
+    L.voff = reinterpret_cast<uint32_t *>(take((nv + 1) * sizeof(uint32_t)));
     L.bytes = off;
     return L;
 }
@@ -375,9 +379,16 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     RecLayout RL = rec_layout(nullptr, nvn, mode == MODE_SCORE);
     if ((rc = ensure(ctx, ctx->rec, RL.bytes)) != GAVIS_OK) return rc;
     RL = rec_layout(ctx->rec.p, nvn, mode == MODE_SCORE);
-    SmallLayout SL = small_layout(nullptr, nvt);
+    SmallLayout SL = small_layout(nullptr, nvt, (size_t)nv);
     if ((rc = ensure(ctx, ctx->small, SL.bytes)) != GAVIS_OK) return rc;
-    SL = small_layout(ctx->small.p, nvt);
+    SL = small_layout(ctx->small.p, nvt, (size_t)nv);
+    if (ctx->h_voff_cap < (size_t)nv + 1) {
+        if (ctx->h_voff) cudaFreeHost(ctx->h_voff);
+        ctx->h_voff = nullptr;
+        ctx->h_voff_cap = 0;
+        CK(cudaMallocHost(&ctx->h_voff, ((size_t)nv + 1) * sizeof(uint32_t)));
+        ctx->h_voff_cap = (size_t)nv + 1;
+    }
 
     ProjectArgs pa;
     pa.means = gs->means; pa.scales = gs->scales; pa.rots = gs->rots; pa.opac = gs->opac;
@@ -406,7 +417,9 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
         Stage st(ctx, GAVIS_STAGE_SCAN, s);
         CK(exclusive_scan_u32(RL.counts, RL.offsets, nvn, RL.scan_tmp, nullptr, s, true));
     }
+    CK(launch_view_offsets(RL.offsets, RL.counts, n, nv, SL.voff, s));
     CK(cudaMemcpyAsync(ctx->h_info, SL.info, sizeof(BatchInfo), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_voff, SL.voff, ((size_t)nv + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const unsigned long long M = ctx->h_info->total, nrec = ctx->h_info->visible;
     const uint32_t zmin = ctx->h_info->zrange[0];
@@ -421,15 +434,42 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     if ((rc = ensure(ctx, ctx->keys, KL.bytes)) != GAVIS_OK) return rc;
     KL = key_layout(ctx->keys.p, (size_t)nrec, (size_t)M);
     bool alt_a = false, alt_b = false;
-    {
-        // stage A: records sorted by (view, depth), ties in index order
-        Stage st(ctx, GAVIS_STAGE_EMIT, s);
-        CK(launch_emit_records(RL.counts, RL.offsets, RL.geo, nv, n, zb, zmin, KL.a_k0, KL.a_v0, s));
-    }
-    {
+    // stage A: records sorted by (view, depth), ties in index order.  With
+    // 32-bit keys, groups of 2^gb views (gb + zb <= 32) are sorted one after
+    // another, each over its contiguous range of records (they are emitted in
+    // view order); only if zb leaves no room for a view bit do the keys take
+    // 64 bits.
+    const int vb = bits_of((uint64_t)nv - 1);
+    const int gb = vb + zb <= 32 ? vb : 32 - zb;
+    if (zb < 32) {
+        uint32_t *k0 = reinterpret_cast<uint32_t *>(KL.a_k0), *k1 = reinterpret_cast<uint32_t *>(KL.a_k1);
+        {
+            Stage st(ctx, GAVIS_STAGE_EMIT, s);
+            CK(launch_emit_records32(RL.counts, RL.offsets, RL.geo, nv, n, zb, zmin, (1u << gb) - 1u, k0, KL.a_v0,
+                                     s));
+        }
         Stage st(ctx, GAVIS_STAGE_SORT, s);
-        CK(radix_sort_pairs<uint64_t>(KL.a_k0, KL.a_v0, KL.a_k1, KL.a_v1, (size_t)nrec, bits_of((uint64_t)nv - 1) + zb,
-                                      KL.tmp, &alt_a, s));
+        const int end_bit = gb + zb;
+        const bool want_alt = ((end_bit + 7) / 8) % 2 == 1;   // every group takes the same number of passes
+        const int G = 1 << gb;
+        for (int g0 = 0; g0 < nv; g0 += G) {
+            const uint32_t a = ctx->h_voff[g0], b = ctx->h_voff[g0 + G < nv ? g0 + G : nv];
+            if (b <= a) continue;
+            bool alt = false;
+            CK(radix_sort_pairs<uint32_t>(k0 + a, KL.a_v0 + a, k1 + a, KL.a_v1 + a, (size_t)(b - a), end_bit, KL.tmp,
+                                          &alt, s));
+            if (alt != want_alt)   // a group too small to sort stays where it was emitted
+                CK(cudaMemcpyAsync((want_alt ? KL.a_v1 : KL.a_v0) + a, (alt ? KL.a_v1 : KL.a_v0) + a,
+                                   (size_t)(b - a) * 4, cudaMemcpyDeviceToDevice, s));
+        }
+        alt_a = want_alt;
+    } else {
+        {
+            Stage st(ctx, GAVIS_STAGE_EMIT, s);
+            CK(launch_emit_records(RL.counts, RL.offsets, RL.geo, nv, n, zb, zmin, KL.a_k0, KL.a_v0, s));
+        }
+        Stage st(ctx, GAVIS_STAGE_SORT, s);
+        CK(radix_sort_pairs<uint64_t>(KL.a_k0, KL.a_v0, KL.a_k1, KL.a_v1, (size_t)nrec, vb + zb, KL.tmp, &alt_a, s));
     }
     const uint32_t *recs = alt_a ? KL.a_v1 : KL.a_v0;
     {
@@ -577,6 +617,7 @@ int gavis_ctx_create(gavis_ctx **out, int device, size_t hbm_budget_bytes)
     ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : fr / 10 * 6;
     if (cudaMallocHost(&ctx->h_info, sizeof(BatchInfo)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_best, sizeof(int32_t)) != cudaSuccess) {
+        if (ctx->h_info) cudaFreeHost(ctx->h_info);
         delete ctx;
         return GAVIS_ERR_CUDA;
     }
@@ -592,6 +633,7 @@ void gavis_ctx_destroy(gavis_ctx *ctx)
     for (Buf *b : {&ctx->rec, &ctx->vis, &ctx->keys, &ctx->small, &ctx->gamma, &ctx->cams, &ctx->aug, &ctx->tune})
         if (b->p) cudaFree(b->p);
     if (ctx->h_info) cudaFreeHost(ctx->h_info);
+    if (ctx->h_voff) cudaFreeHost(ctx->h_voff);
     if (ctx->h_best) cudaFreeHost(ctx->h_best);
     if (ctx->d_pairs) cudaFree(ctx->d_pairs);
     for (auto &r : ctx->pending) {

@@ -131,6 +131,15 @@ inline int depth_bits(uint32_t zmin, uint32_t zmax) { return bits_of(zmax > zmin
 cudaError_t launch_emit_records(const uint32_t *counts, const uint32_t *pos, const GeoRec *geo, int nv, int64_t n,
                                 int zb, uint32_t zmin, uint64_t *keyA, uint32_t *valA, cudaStream_t s,
                                 size_t cap_R = ~(size_t)0, uint32_t *overflow = nullptr);
+// 32-bit record keys ((v & vmask) << zb) | (depth bits - zmin), for sorting
+// the records of each group of vmask + 1 views separately.
+cudaError_t launch_emit_records32(const uint32_t *counts, const uint32_t *pos, const GeoRec *geo, int nv, int64_t n,
+                                  int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA, uint32_t *valA,
+                                  cudaStream_t s);
+// voff[v] (v = 0..nv) = visible records of the views before v, from the
+// flag scan pos and the counts (device [nv + 1]).
+cudaError_t launch_view_offsets(const uint32_t *pos, const uint32_t *counts, int64_t n, int nv, uint32_t *voff,
+                                cudaStream_t s);
 // d_nrec / d_M (optional): actual counts in device memory for graph replays;
 // entries past cap_M are not written and set *overflow (when given).
 cudaError_t launch_gather_counts(const uint32_t *valA, const uint32_t *counts, size_t nrec, uint32_t *cnt_sorted,

@@ -5,10 +5,10 @@
 // is (1) a per-block digit histogram over a tile of 4096 keys, (2) an
 // exclusive scan of the histograms in digit-major order, which gives every
 // (digit, block) its output offset, and (3) a stable scatter: items are
-// ranked within a warp with __match_any_sync, warps are ordered by a shared
-// prefix, rounds of 256 items in input order, so equal digits keep their
-// input order.  Starting from index-ascending input this yields the canonical
-// (key, index) order.
+// ranked within a warp (lanes with equal digits found by __match_any_sync or
+// by per-bit ballots), warps are ordered by a shared prefix, rounds of 256
+// items in input order, so equal digits keep their input order.  Starting
+// from index-ascending input this yields the canonical (key, index) order.
 #include "gavis_internal.cuh"
 
 namespace gavis {
@@ -140,6 +140,27 @@ constexpr int kRsRounds = 16;
 constexpr int kRsTile = kRsThreads * kRsRounds;   // 4096 keys per block
 constexpr int kRsWarps = kRsThreads / 32;
 
+// Lanes of the warp holding the same digit d as this lane (d = 256 marks an
+// invalid item and matches only other invalid items).  BALLOT builds the
+// mask from one ballot per digit bit, which is cheaper than __match_any_sync
+// when the 32 digits are mostly distinct (low digits of unsorted keys);
+// __match_any_sync wins when they are few (high digits).
+template <bool BALLOT>
+__device__ __forceinline__ unsigned digit_peers(int d)
+{
+    if (!BALLOT) return __match_any_sync(0xffffffffu, d);
+    unsigned p = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+        const bool bit = (d >> b) & 1;
+        const unsigned bal = __ballot_sync(0xffffffffu, bit);
+        p &= bit ? bal : ~bal;
+    }
+    return p;
+}
+
+// Per-block digit histogram: warp-private counters with plain shared atomics
+// (rounds in which the whole warp holds one digit add 32 once).
 // d_n (optional): the actual item count in device memory, <= n (graph replays)
 template <typename KeyT>
 __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const KeyT *keys, size_t n, int shift,
@@ -147,24 +168,31 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const KeyT *keys, siz
                                                            const unsigned long long *d_n)
 {
     if (d_n && *d_n < n) n = (size_t)*d_n;
-    __shared__ uint32_t s_h[256];
+    __shared__ uint32_t s_h[kRsWarps][257];
     const size_t base = (size_t)blockIdx.x * kRsTile;
     if (base >= n) {   // whole block past the live items (graph replays)
         hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = 0u;
         return;
     }
-    s_h[threadIdx.x] = 0;
+    for (int i = threadIdx.x; i < kRsWarps * 257; i += kRsThreads) (&s_h[0][0])[i] = 0u;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll 4
     for (int r = 0; r < kRsRounds; ++r) {
-        size_t i = base + (size_t)r * kRsThreads + threadIdx.x;
-        int d = i < n ? (int)((keys[i] >> shift) & 255u) : 256;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (d < 256 && lane == __ffs(peers) - 1) atomicAdd(&s_h[d], (uint32_t)__popc(peers));
+        const size_t i = base + (size_t)r * kRsThreads + threadIdx.x;
+        const int d = i < n ? (int)((keys[i] >> shift) & 255u) : 256;
+        const int d0 = __shfl_sync(0xffffffffu, d, 0);
+        if (__all_sync(0xffffffffu, d == d0)) {
+            if (lane == 0) atomicAdd(&s_h[warp][d0], 32u);
+        } else {
+            atomicAdd(&s_h[warp][d], 1u);
+        }
     }
     __syncthreads();
-    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = s_h[threadIdx.x];
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < kRsWarps; ++w) c += s_h[w][threadIdx.x];
+    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = c;
 }
 
 // Stable scatter of one 4096-item tile.  Warp w owns the contiguous items
@@ -176,8 +204,8 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const KeyT *keys, siz
 template <typename KeyT>
 constexpr size_t rs_smem() { return (size_t)kRsTile * (sizeof(KeyT) + 4) + (size_t)(kRsWarps + 3) * 256 * 4; }
 
-template <typename KeyT>
-__global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const KeyT *kin, const uint32_t *vin,
+template <typename KeyT, bool BALLOT>
+__global__ void __launch_bounds__(kRsThreads, 2) k_radix_scatter(const KeyT *kin, const uint32_t *vin,
                                                               KeyT *kout, uint32_t *vout, size_t n, int shift,
                                                               const uint32_t *hist, const uint32_t *offs,
                                                               int nblocks, const unsigned long long *d_n)
@@ -229,7 +257,7 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const KeyT *kin, c
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
+        const unsigned peers = digit_peers<BALLOT>(d[r]);
         const uint32_t prior = d[r] < 256 ? wc[d[r]] : 0u;
         rk[r] = prior + (uint32_t)__popc(peers & lt);
         __syncwarp();
@@ -322,7 +350,8 @@ cudaError_t radix_sort_pairs(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_
     void *stmp = reinterpret_cast<char *>(tmp) + 2 * a;
     constexpr size_t smem = rs_smem<KeyT>();
     if (!d_n) {   // per device, idempotent (done beforehand when capturing)
-        cudaFuncSetAttribute(k_radix_scatter<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_radix_scatter<KeyT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_radix_scatter<KeyT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
     KeyT *kin = keys, *kout = keys_alt;
     uint32_t *vin = vals, *vout = vals_alt;
@@ -331,7 +360,14 @@ cudaError_t radix_sort_pairs(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_
         k_radix_hist<KeyT><<<nblocks, kRsThreads, 0, s>>>(kin, n, shift, hist, nblocks, d_n); count_launch();
         cudaError_t e = exclusive_scan_u32(hist, offs, h, stmp, nullptr, s);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<KeyT><<<nblocks, kRsThreads, smem, s>>>(kin, vin, kout, vout, n, shift, hist, offs, nblocks, d_n); count_launch();
+        // digits below the top two passes are close to uniformly distributed
+        if (shift + 8 < end_bit - 8)
+            k_radix_scatter<KeyT, true><<<nblocks, kRsThreads, smem, s>>>(kin, vin, kout, vout, n, shift, hist, offs,
+                                                                         nblocks, d_n);
+        else
+            k_radix_scatter<KeyT, false><<<nblocks, kRsThreads, smem, s>>>(kin, vin, kout, vout, n, shift, hist,
+                                                                          offs, nblocks, d_n);
+        count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         KeyT *tk = kin; kin = kout; kout = tk;
@@ -349,9 +385,13 @@ template cudaError_t radix_sort_pairs<uint32_t>(uint32_t *, uint32_t *, uint32_t
 
 void radix_prepare()
 {
-    cudaFuncSetAttribute(k_radix_scatter<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_radix_scatter<uint64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)rs_smem<uint64_t>());
-    cudaFuncSetAttribute(k_radix_scatter<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_radix_scatter<uint64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)rs_smem<uint64_t>());
+    cudaFuncSetAttribute(k_radix_scatter<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)rs_smem<uint32_t>());
+    cudaFuncSetAttribute(k_radix_scatter<uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)rs_smem<uint32_t>());
 }
 
