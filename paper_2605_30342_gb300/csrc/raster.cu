@@ -412,6 +412,9 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
         }
         __syncwarp();
         const int nk = __popc(mk);
+        // the warp's sums for the entry in slot k are kept by lane k and
+        // added to the per-Gaussian totals once per chunk, all lanes at once
+        uint32_t my_sum = 0u, my_cnt = 0u;
         for (int k = 0; k < nk; ++k) {
             if (!__any_sync(0xffffffffu, on0 || on1)) break;   // warp-uniform
             const float4 g0 = g0s[k];
@@ -424,11 +427,9 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
                 const uint32_t tq = (h0 ? __float2uint_rn(T0 * kTScale) : 0u) + (h1 ? __float2uint_rn(T1 * kTScale) : 0u);
                 const uint32_t sum = __reduce_add_sync(0xffffffffu, tq);
                 const uint32_t c = (uint32_t)(__popc(m0) + __popc(m1));
-                wpairs += c;
-                if (lane == 0) {
-                    const size_t r = vrow + ids[k];
-                    atomicAdd(&a.sumT[r], (unsigned long long)sum);
-                    atomicAdd(&a.cnt[r], c);
+                if (lane == k) {
+                    my_sum = sum;
+                    my_cnt = c;
                 }
             }
             if (h0) {
@@ -440,9 +441,18 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
                 on1 = T1 >= eps;
             }
         }
+        if (my_cnt) {
+            const size_t r = vrow + ids[lane];
+            atomicAdd(&a.sumT[r], (unsigned long long)my_sum);
+            atomicAdd(&a.cnt[r], my_cnt);
+            wpairs += my_cnt;
+        }
         __syncwarp();
     }
-    if (a.pairs && lane == 0 && wpairs) atomicAdd(a.pairs, (unsigned long long)wpairs);
+    if (a.pairs) {
+        const uint32_t wp = __reduce_add_sync(0xffffffffu, wpairs);
+        if (lane == 0 && wp) atomicAdd(a.pairs, (unsigned long long)wp);
+    }
 }
 
 // instrumentation: sum of the per-warp pair counts into one counter
