@@ -310,7 +310,8 @@ struct SmallLayout {
     uint32_t *pair_counts;
     BatchInfo *info;
     int32_t *best;
-    uint32_t *voff;   // [nv + 1]
+    uint32_t *voff;   // [nv + 1] visible records before each view, then [nv + 1] tile entries before each view
+    uint32_t *eoff;
     size_t bytes;
 };
 
@@ -325,7 +326,8 @@ SmallLayout small_layout(void *base, size_t nvt, size_t nv = 0)
     L.pair_counts = reinterpret_cast<uint32_t *>(take(nvt * sizeof(uint32_t)));
     L.info = reinterpret_cast<BatchInfo *>(take(sizeof(BatchInfo)));
     L.best = reinterpret_cast<int32_t *>(take(sizeof(int32_t)));
-    L.voff = reinterpret_cast<uint32_t *>(take((nv + 1) * sizeof(uint32_t)));
+    L.voff = reinterpret_cast<uint32_t *>(take((2 * nv + 2) * sizeof(uint32_t)));
+    L.eoff = L.voff ? L.voff + nv + 1 : nullptr;
     L.bytes = off;
     return L;
 }
@@ -382,15 +384,16 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     SmallLayout SL = small_layout(nullptr, nvt, (size_t)nv);
     if ((rc = ensure(ctx, ctx->small, SL.bytes)) != GAVIS_OK) return rc;
     SL = small_layout(ctx->small.p, nvt, (size_t)nv);
-    if (ctx->h_voff_cap < (size_t)nv + 1) {
+    if (ctx->h_voff_cap < 2 * (size_t)nv + 2) {
         if (ctx->h_voff) cudaFreeHost(ctx->h_voff);
         ctx->h_voff = nullptr;
         ctx->h_voff_cap = 0;
-        CK(cudaMallocHost(&ctx->h_voff, ((size_t)nv + 1) * sizeof(uint32_t)));
-        ctx->h_voff_cap = (size_t)nv + 1;
+        CK(cudaMallocHost(&ctx->h_voff, (2 * (size_t)nv + 2) * sizeof(uint32_t)));
+        ctx->h_voff_cap = 2 * (size_t)nv + 2;
     }
+    uint32_t *h_eoff = ctx->h_voff + nv + 1;
 
-    ProjectArgs pa;
+    ProjectArgs pa{};
     pa.means = gs->means; pa.scales = gs->scales; pa.rots = gs->rots; pa.opac = gs->opac;
     pa.sh = gs->sh; pa.sh_degree = gs->sh_degree; pa.sh_dtype = gs->sh_dtype;
     pa.sh_var = mode == MODE_SCORE ? gs->sh_var : nullptr;
@@ -451,9 +454,9 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
         Stage st(ctx, GAVIS_STAGE_SORT, s);
         const int end_bit = gb + zb;
         const bool want_alt = ((end_bit + 7) / 8) % 2 == 1;   // every group takes the same number of passes
-        const int G = 1 << gb;
-        for (int g0 = 0; g0 < nv; g0 += G) {
-            const uint32_t a = ctx->h_voff[g0], b = ctx->h_voff[g0 + G < nv ? g0 + G : nv];
+        const int gsz = 1 << gb;
+        for (int g0 = 0; g0 < nv; g0 += gsz) {
+            const uint32_t a = ctx->h_voff[g0], b = ctx->h_voff[g0 + gsz < nv ? g0 + gsz : nv];
             if (b <= a) continue;
             bool alt = false;
             CK(radix_sort_pairs<uint32_t>(k0 + a, KL.a_v0 + a, k1 + a, KL.a_v1 + a, (size_t)(b - a), end_bit, KL.tmp,
@@ -472,24 +475,57 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
         CK(radix_sort_pairs<uint64_t>(KL.a_k0, KL.a_v0, KL.a_k1, KL.a_v1, (size_t)nrec, vb + zb, KL.tmp, &alt_a, s));
     }
     const uint32_t *recs = alt_a ? KL.a_v1 : KL.a_v0;
+    // stage B: tile entries in stage-A order, i.e. view by view.  When the
+    // tile index fits in tb <= 16 bits the keys are (view << tb) | tile and
+    // each group of 2^(16 - tb) views is sorted on 16 bits (two passes) over
+    // its contiguous entries; otherwise keys are view * TT + tile, one sort.
+    const int tbits = bits_of((uint64_t)G.TT - 1);
+    int tb = -1, gbb = 0;
+    if (tbits + vb > 16 && tbits <= 16 && ((nv - 1) >> (16 - tbits)) < 64) {
+        tb = tbits;
+        gbb = 16 - tbits;
+    }
     {
-        // stage B: tile entries in stage-A order
         Stage st(ctx, GAVIS_STAGE_EMIT, s);
         CK(launch_gather_counts(recs, RL.counts, (size_t)nrec, KL.a_cnt, s));
         CK(exclusive_scan_u32(KL.a_cnt, KL.a_off, (size_t)nrec, KL.tmp, nullptr, s));
-        CK(launch_emit_tiles(recs, KL.a_off, (size_t)nrec, RL.rect, n, G.TW, G.TH, KL.b_k0, KL.b_v0, s));
+        CK(launch_emit_tiles(recs, KL.a_off, (size_t)nrec, RL.rect, n, G.TW, G.TH, KL.b_k0, KL.b_v0, s, nullptr,
+                             ~(size_t)0, nullptr, tb));
+        if (tb >= 0) {   // tile entries before each view: a second read-back
+            CK(launch_entry_offsets(KL.a_off, SL.voff, nv, (uint32_t)M, SL.eoff, s));
+            CK(cudaMemcpyAsync(h_eoff, SL.eoff, ((size_t)nv + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
     }
     {
         Stage st(ctx, GAVIS_STAGE_SORT, s);
-        CK(radix_sort_pairs<uint32_t>(KL.b_k0, KL.b_v0, KL.b_k1, KL.b_v1, (size_t)M, bits_of((uint64_t)nvt - 1),
-                                      KL.tmp, &alt_b, s));
+        if (tb < 0) {
+            CK(radix_sort_pairs<uint32_t>(KL.b_k0, KL.b_v0, KL.b_k1, KL.b_v1, (size_t)M, bits_of((uint64_t)nvt - 1),
+                                          KL.tmp, &alt_b, s));
+        } else {
+            const int gsz = 1 << gbb;
+            for (int g0 = 0; g0 < nv; g0 += gsz) {
+                const uint64_t e0 = h_eoff[g0], e1 = h_eoff[g0 + gsz < nv ? g0 + gsz : nv];
+                if (e1 < e0 || e1 > M) return fail(ctx, GAVIS_ERR_CUDA, "internal: inconsistent per-view entry offsets");
+                const uint64_t len = e1 - e0;
+                bool alt = false;
+                if (len > 0)
+                    CK(radix_sort_pairs<uint32_t>(KL.b_k0 + e0, KL.b_v0 + e0, KL.b_k1 + e0, KL.b_v1 + e0, (size_t)len, 16,
+                                                  KL.tmp, &alt, s));
+                if (alt) {   // two passes end in the first buffer; a group too small to sort already is there
+                    CK(cudaMemcpyAsync(KL.b_k0 + e0, KL.b_k1 + e0, (size_t)len * 4, cudaMemcpyDeviceToDevice, s));
+                    CK(cudaMemcpyAsync(KL.b_v0 + e0, KL.b_v1 + e0, (size_t)len * 4, cudaMemcpyDeviceToDevice, s));
+                }
+            }
+            alt_b = false;
+        }
     }
     const uint32_t *keys = alt_b ? KL.b_k1 : KL.b_k0;
     const uint32_t *vals = alt_b ? KL.b_v1 : KL.b_v0;
     {
         Stage st(ctx, GAVIS_STAGE_RANGES, s);
         CK(cudaMemsetAsync(SL.ranges, 0, nvt * sizeof(uint2), s));
-        CK(launch_ranges(keys, (size_t)M, SL.ranges, s));
+        CK(launch_ranges(keys, (size_t)M, SL.ranges, s, nullptr, tb, (uint32_t)G.TT));
     }
 
     if (mode == MODE_BINS) {
@@ -497,7 +533,7 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
         if (off < out.cap && out.keys) {
             const int64_t m = (int64_t)M < out.cap - off ? (int64_t)M : out.cap - off;
             // canonical keys; one batch, so the view index is the call's
-            CK(launch_keys_export(keys, vals, (size_t)m, RL.geo, n, G.TT, out.keys + off, s));
+            CK(launch_keys_export(keys, vals, (size_t)m, RL.geo, n, G.TT, out.keys + off, s, tb));
             CK(cudaMemcpyAsync(out.vals + off, vals, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
         }
         if (out.ranges)

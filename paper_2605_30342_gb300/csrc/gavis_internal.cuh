@@ -140,19 +140,25 @@ cudaError_t launch_emit_records32(const uint32_t *counts, const uint32_t *pos, c
 // flag scan pos and the counts (device [nv + 1]).
 cudaError_t launch_view_offsets(const uint32_t *pos, const uint32_t *counts, int64_t n, int nv, uint32_t *voff,
                                 cudaStream_t s);
+// eoff[v] (v = 0..nv) = stage-B tile entries of the views before v, from the
+// stage-B offsets of the records (stage-A order) and voff (device [nv + 1]).
+cudaError_t launch_entry_offsets(const uint32_t *off_sorted, const uint32_t *voff, int nv, uint32_t M,
+                                 uint32_t *eoff, cudaStream_t s);
 // d_nrec / d_M (optional): actual counts in device memory for graph replays;
 // entries past cap_M are not written and set *overflow (when given).
 cudaError_t launch_gather_counts(const uint32_t *valA, const uint32_t *counts, size_t nrec, uint32_t *cnt_sorted,
                                  cudaStream_t s, const unsigned long long *d_nrec = nullptr);
+// tb: tile keys are v * TT + tile (tb < 0) or (v << tb) | tile (2^tb >= TT),
+// which lets a group of 2^g views be sorted on its low tb + g bits.
 cudaError_t launch_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect,
                               int64_t n, int TW, int TH, uint32_t *keyB, uint32_t *valB, cudaStream_t s,
                               const unsigned long long *d_nrec = nullptr, size_t cap_M = ~(size_t)0,
-                              uint32_t *overflow = nullptr);
+                              uint32_t *overflow = nullptr, int tb = -1);
 cudaError_t launch_ranges(const uint32_t *keys, size_t M, uint2 *ranges, cudaStream_t s,
-                          const unsigned long long *d_M = nullptr);
+                          const unsigned long long *d_M = nullptr, int tb = -1, uint32_t TT = 0);
 // canonical keys ((view*tiles + tile) << 32) | depth bits, for verification
 cudaError_t launch_keys_export(const uint32_t *keyB, const uint32_t *valB, size_t M, const GeoRec *geo, int64_t n,
-                               int tiles_per_view, uint64_t *out, cudaStream_t s);
+                               int tiles_per_view, uint64_t *out, cudaStream_t s, int tb = -1);
 
 struct CompositeArgs {
     const uint2 *ranges;

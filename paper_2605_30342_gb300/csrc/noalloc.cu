@@ -144,7 +144,7 @@ extern "C" int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_v
         return report(err, err_len, GAVIS_ERR_BUDGET, "scratch layout exceeds %zu bytes", kNoAllocScratchBytes);
 
     NA_CK(cudaMemcpyAsync(d_cam, cam, sizeof(gavis_camera), cudaMemcpyHostToDevice, s));
-    ProjectArgs pa;
+    ProjectArgs pa{};
     pa.means = gs->means; pa.scales = gs->scales; pa.rots = gs->rots; pa.opac = gs->opac;
     pa.sh = gs->sh; pa.sh_degree = gs->sh_degree; pa.sh_dtype = gs->sh_dtype;
     pa.sh_var = gs->sh_var;

@@ -155,7 +155,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     float *tile_sums = reinterpret_cast<float *>(b + o_ts);
     PlanInfo *info = pl->d_info;
 
-    ProjectArgs pa;
+    ProjectArgs pa{};
     pa.means = gs->means; pa.scales = gs->scales; pa.rots = gs->rots; pa.opac = gs->opac;
     pa.sh = gs->sh; pa.sh_degree = gs->sh_degree; pa.sh_dtype = gs->sh_dtype;
     pa.sh_var = gs->sh_var;

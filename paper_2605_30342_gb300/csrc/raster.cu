@@ -123,6 +123,16 @@ __global__ void k_view_offsets(const uint32_t *pos, const uint32_t *counts, int6
     }
 }
 
+// eoff[v] = tile entries of the views before v (v = 0..nv): the stage-B
+// offset of each view's first record (records are in view order)
+__global__ void k_entry_offsets(const uint32_t *off_sorted, const uint32_t *voff, int nv, uint32_t M, uint32_t *eoff)
+{
+    for (int v = threadIdx.x; v <= nv; v += blockDim.x) {
+        const uint32_t r = voff[v];
+        eoff[v] = v < nv && r < voff[nv] ? off_sorted[r] : M;
+    }
+}
+
 __global__ void k_gather_counts(const uint32_t *valA, const uint32_t *counts, size_t nrec, uint32_t *cnt_sorted,
                                 const unsigned long long *d_nrec)
 {
@@ -131,10 +141,17 @@ __global__ void k_gather_counts(const uint32_t *valA, const uint32_t *counts, si
     cnt_sorted[i] = counts[valA[i]];
 }
 
+// Tile keys: v * TT + tile (tb < 0), or (v << tb) | tile with 2^tb >= TT, so
+// that the keys of a group of 2^g views differ only in their low tb + g bits.
+__device__ __forceinline__ uint32_t tile_index(uint32_t key, int tb, uint32_t TT)
+{
+    return tb < 0 ? key : (key >> tb) * TT + (key & ((1u << tb) - 1u));
+}
+
 // stage B: the tiles of each record, in stage-A order
 __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect, int64_t n,
                              int TW, int TH, uint32_t *keyB, uint32_t *valB, const unsigned long long *d_nrec,
-                             size_t cap_M, uint32_t *overflow)
+                             size_t cap_M, uint32_t *overflow, int tb)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nrec || (d_nrec && i >= (size_t)*d_nrec)) return;
@@ -143,7 +160,7 @@ __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, s
     const uint32_t g = (uint32_t)(r - (uint64_t)v * (uint64_t)n);
     const uint2 rc = rect[r];
     const uint32_t x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu, y1 = rc.y >> 16;
-    const uint32_t vbase = v * (uint32_t)(TW * TH);
+    const uint32_t vbase = tb < 0 ? v * (uint32_t)(TW * TH) : v << tb;
     uint32_t off = off_sorted[i];
     if ((size_t)off + (size_t)((x1 - x0 + 1) * (y1 - y0 + 1)) > cap_M && overflow) *overflow = 1u;
     for (uint32_t ty = y0; ty <= y1; ++ty)
@@ -156,22 +173,24 @@ __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, s
         }
 }
 
-__global__ void k_ranges(const uint32_t *keys, size_t M, uint2 *ranges, const unsigned long long *d_M)
+__global__ void k_ranges(const uint32_t *keys, size_t M, uint2 *ranges, const unsigned long long *d_M, int tb,
+                         uint32_t TT)
 {
     if (d_M && *d_M < M) M = (size_t)*d_M;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     const uint32_t t = keys[i];
-    if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
-    if (i == M - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+    const uint32_t ti = tile_index(t, tb, TT);
+    if (i == 0 || keys[i - 1] != t) ranges[ti].x = (uint32_t)i;
+    if (i == M - 1 || keys[i + 1] != t) ranges[ti].y = (uint32_t)(i + 1);
 }
 
 __global__ void k_keys_export(const uint32_t *keyB, const uint32_t *valB, size_t M, const GeoRec *geo, int64_t n,
-                              int tiles_per_view, uint64_t *out)
+                              int tiles_per_view, uint64_t *out, int tb)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
-    const uint32_t t = keyB[i];
+    const uint32_t t = tile_index(keyB[i], tb, (uint32_t)tiles_per_view);
     const size_t r = (size_t)(t / (uint32_t)tiles_per_view) * (size_t)n + valB[i];
     out[i] = ((uint64_t)t << 32) | (uint64_t)__float_as_uint(geo[r].b.z);
 }
@@ -667,6 +686,14 @@ cudaError_t launch_emit_records32(const uint32_t *counts, const uint32_t *pos, c
     return cudaGetLastError();
 }
 
+cudaError_t launch_entry_offsets(const uint32_t *off_sorted, const uint32_t *voff, int nv, uint32_t M,
+                                 uint32_t *eoff, cudaStream_t s)
+{
+    if (nv <= 0) return cudaSuccess;
+    k_entry_offsets<<<1, 256, 0, s>>>(off_sorted, voff, nv, M, eoff); count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_view_offsets(const uint32_t *pos, const uint32_t *counts, int64_t n, int nv, uint32_t *voff,
                                 cudaStream_t s)
 {
@@ -685,26 +712,27 @@ cudaError_t launch_gather_counts(const uint32_t *valA, const uint32_t *counts, s
 
 cudaError_t launch_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect,
                               int64_t n, int TW, int TH, uint32_t *keyB, uint32_t *valB, cudaStream_t s,
-                              const unsigned long long *d_nrec, size_t cap_M, uint32_t *overflow)
+                              const unsigned long long *d_nrec, size_t cap_M, uint32_t *overflow, int tb)
 {
     if (nrec == 0) return cudaSuccess;
     k_emit_tiles<<<nblk(nrec, 256), 256, 0, s>>>(valA, off_sorted, nrec, rect, n, TW, TH, keyB, valB, d_nrec, cap_M,
-                                                 overflow); count_launch();
+                                                 overflow, tb); count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_ranges(const uint32_t *keys, size_t M, uint2 *ranges, cudaStream_t s, const unsigned long long *d_M)
+cudaError_t launch_ranges(const uint32_t *keys, size_t M, uint2 *ranges, cudaStream_t s, const unsigned long long *d_M,
+                          int tb, uint32_t TT)
 {
     if (M == 0) return cudaSuccess;
-    k_ranges<<<nblk(M, 256), 256, 0, s>>>(keys, M, ranges, d_M); count_launch();
+    k_ranges<<<nblk(M, 256), 256, 0, s>>>(keys, M, ranges, d_M, tb, TT); count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_keys_export(const uint32_t *keyB, const uint32_t *valB, size_t M, const GeoRec *geo, int64_t n,
-                               int tiles_per_view, uint64_t *out, cudaStream_t s)
+                               int tiles_per_view, uint64_t *out, cudaStream_t s, int tb)
 {
     if (M == 0) return cudaSuccess;
-    k_keys_export<<<nblk(M, 256), 256, 0, s>>>(keyB, valB, M, geo, n, tiles_per_view, out); count_launch();
+    k_keys_export<<<nblk(M, 256), 256, 0, s>>>(keyB, valB, M, geo, n, tiles_per_view, out, tb); count_launch();
     return cudaGetLastError();
 }
 

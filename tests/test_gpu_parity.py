@@ -70,23 +70,26 @@ def test_bins_bit_exact(ctx, gv, name, tile):
 
 
 def test_bins_bit_exact_with_view_groups(ctx, gv):
-    """600 views in one call: view bits + depth bits exceed 32, so the
-    record sort runs per group of views (here 3 groups); keys, values and
-    ranges stay bit-exact, and scoring equals the one-view-per-batch path."""
+    """600 views in one call: view bits + depth bits exceed 32 and view bits
+    + tile bits exceed 16, so both sorts run per group of views (3 groups
+    each); keys, values and ranges stay bit-exact, and scoring equals the
+    one-view-per-batch path."""
     sc = sg.tiny_scene(2000, seed=3, sh_degree=1)
-    cams = sg.fibonacci_cameras(600, 3.0, 32, 24, 60.0)
+    cams = sg.fibonacci_cameras(600, 3.0, 128, 96, 60.0)
+    TT = 16 * 12
     zbits = []
     for cam in cams:
         out, st = oracle.project(cam, sc, tile=8)
         zbits.append(out[st == 1, 0].astype(np.float32).view(np.uint32))
     zb = np.concatenate(zbits)
-    assert (len(cams) - 1).bit_length() + int(zb.max() - zb.min()).bit_length() > 32
+    vbits = (len(cams) - 1).bit_length()
+    assert vbits + int(zb.max() - zb.min()).bit_length() > 32
+    assert vbits + (TT - 1).bit_length() > 16
     gs = gpu_scene(gv, sc)
     keys, vals, ranges = ctx.debug_bins(gs, cams, gv.Params(tile=8))
     rk, rv = oracle.bins(cams, sc, tile=8)
     assert np.array_equal(keys.cpu().numpy().view(np.uint64), rk)
     assert np.array_equal(vals.cpu().numpy().view(np.uint32), rv)
-    TT = 4 * 3
     assert np.array_equal(ranges.cpu().numpy().view(np.uint32), oracle.ranges(rk, len(cams) * TT))
     vf = gv.VisibilityField(torch.zeros((sc.n, 9), device="cuda"), 2, 0, 1.0)
     a = ctx.score_views(gs, vf, cams, params=gv.Params(tile=8, views_per_batch=0))
