@@ -245,12 +245,12 @@ Geometry geometry_of(const gavis_camera *cams, int tile)
 }
 
 
-// per-batch workspace: records + counts/offsets
+// per-batch workspace: records, tile counts, flag-scan partials
 struct RecLayout {
     GeoRec *geo;
     UaRec *ua;
     uint2 *rect;
-    uint32_t *counts, *offsets;
+    uint32_t *counts;
     void *scan_tmp;
     size_t bytes;
 };
@@ -265,7 +265,6 @@ RecLayout rec_layout(void *base, size_t nvn, bool ua)
     L.ua = ua ? reinterpret_cast<UaRec *>(take(nvn * sizeof(UaRec))) : nullptr;
     L.rect = reinterpret_cast<uint2 *>(take(nvn * sizeof(uint2)));
     L.counts = reinterpret_cast<uint32_t *>(take(nvn * sizeof(uint32_t)));
-    L.offsets = reinterpret_cast<uint32_t *>(take(nvn * sizeof(uint32_t)));
     L.scan_tmp = take(scan_tmp_bytes(nvn) + 64);
     L.bytes = off;
     return L;
@@ -356,13 +355,20 @@ size_t per_view_bytes(int64_t n, int TT, Mode m)
 
 int auto_batch(gavis_ctx *ctx, int64_t n, int TT, int n_views, Mode m, int requested)
 {
-    if (requested > 0) return requested < n_views ? requested : n_views;
-    const size_t per = per_view_bytes(n, TT, m);
-    // buffers are reused across batches, so the whole budget is available
-    long long nv = (long long)((ctx->budget * 7 / 10) / (per ? per : 1));
+    // record indices v * n + g of a batch are 32-bit
+    const long long idx_cap = n > 0 ? (long long)(0xffffffffull / (unsigned long long)n) : n_views;
+    long long nv;
+    if (requested > 0) {
+        nv = requested < n_views ? requested : n_views;
+    } else {
+        const size_t per = per_view_bytes(n, TT, m);
+        // buffers are reused across batches, so the whole budget is available
+        nv = (long long)((ctx->budget * 7 / 10) / (per ? per : 1));
+        if (nv > 256) nv = 256;
+        if (nv > n_views) nv = n_views;
+    }
+    if (nv > idx_cap) nv = idx_cap;
     if (nv < 1) nv = 1;
-    if (nv > 256) nv = 256;
-    if (nv > n_views) nv = n_views;
     return (int)nv;
 }
 
@@ -416,13 +422,11 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
         CK(launch_project(pa, s));
     }
     {
-        // positions of the visible records, in (view, index) order
+        // block sums of the visibility flags, in (view, index) order
         Stage st(ctx, GAVIS_STAGE_SCAN, s);
-        CK(exclusive_scan_u32(RL.counts, RL.offsets, nvn, RL.scan_tmp, nullptr, s, true));
+        CK(scan_flags_reduce(RL.counts, nvn, RL.scan_tmp, s));
     }
-    CK(launch_view_offsets(RL.offsets, RL.counts, n, nv, SL.voff, s));
     CK(cudaMemcpyAsync(ctx->h_info, SL.info, sizeof(BatchInfo), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(ctx->h_voff, SL.voff, ((size_t)nv + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const unsigned long long M = ctx->h_info->total, nrec = ctx->h_info->visible;
     const uint32_t zmin = ctx->h_info->zrange[0];
@@ -437,26 +441,34 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     if ((rc = ensure(ctx, ctx->keys, KL.bytes)) != GAVIS_OK) return rc;
     KL = key_layout(ctx->keys.p, (size_t)nrec, (size_t)M);
     bool alt_a = false, alt_b = false;
-    // stage A: records sorted by (view, depth), ties in index order.  With
-    // 32-bit keys, groups of 2^gb views (gb + zb <= 32) are sorted one after
-    // another, each over its contiguous range of records (they are emitted in
-    // view order); only if zb leaves no room for a view bit do the keys take
-    // 64 bits.
+    // stage A: records sorted by (view, depth), ties in index order.  Keys
+    // are 32 bits, ((view & (2^gb - 1)) << zb) | (depth bits - zmin) with
+    // gb + zb <= 32 (depth bits of positive floats span zb <= 31 bits); the
+    // groups of 2^gb views are sorted one after another, each over its
+    // contiguous range of records (records are emitted in view order).  The
+    // keys are written by the apply step of the visibility-flag scan.
     const int vb = bits_of((uint64_t)nv - 1);
     const int gb = vb + zb <= 32 ? vb : 32 - zb;
-    if (zb < 32) {
-        uint32_t *k0 = reinterpret_cast<uint32_t *>(KL.a_k0), *k1 = reinterpret_cast<uint32_t *>(KL.a_k1);
-        {
-            Stage st(ctx, GAVIS_STAGE_EMIT, s);
-            CK(launch_emit_records32(RL.counts, RL.offsets, RL.geo, nv, n, zb, zmin, (1u << gb) - 1u, k0, KL.a_v0,
-                                     s));
-        }
+    const int gsz_a = 1 << gb;
+    uint32_t *k0 = reinterpret_cast<uint32_t *>(KL.a_k0), *k1 = reinterpret_cast<uint32_t *>(KL.a_k1);
+    {
+        Stage st(ctx, GAVIS_STAGE_EMIT, s);
+        CK(scan_flags_emit(RL.counts, nvn, RL.scan_tmp, RL.geo, n, zb, zmin, (uint32_t)(gsz_a - 1), k0, KL.a_v0,
+                           SL.voff, s));
+    }
+    if (gsz_a < nv) {   // group boundaries: a second read-back
+        CK(cudaMemcpyAsync(ctx->h_voff, SL.voff, ((size_t)nv + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } else {
+        ctx->h_voff[0] = 0u;
+        ctx->h_voff[nv] = (uint32_t)nrec;
+    }
+    {
         Stage st(ctx, GAVIS_STAGE_SORT, s);
         const int end_bit = gb + zb;
         const bool want_alt = ((end_bit + 7) / 8) % 2 == 1;   // every group takes the same number of passes
-        const int gsz = 1 << gb;
-        for (int g0 = 0; g0 < nv; g0 += gsz) {
-            const uint32_t a = ctx->h_voff[g0], b = ctx->h_voff[g0 + gsz < nv ? g0 + gsz : nv];
+        for (int g0 = 0; g0 < nv; g0 += gsz_a) {
+            const uint32_t a = ctx->h_voff[g0], b = ctx->h_voff[g0 + gsz_a < nv ? g0 + gsz_a : nv];
             if (b <= a) continue;
             bool alt = false;
             CK(radix_sort_pairs<uint32_t>(k0 + a, KL.a_v0 + a, k1 + a, KL.a_v1 + a, (size_t)(b - a), end_bit, KL.tmp,
@@ -466,13 +478,6 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
                                    (size_t)(b - a) * 4, cudaMemcpyDeviceToDevice, s));
         }
         alt_a = want_alt;
-    } else {
-        {
-            Stage st(ctx, GAVIS_STAGE_EMIT, s);
-            CK(launch_emit_records(RL.counts, RL.offsets, RL.geo, nv, n, zb, zmin, KL.a_k0, KL.a_v0, s));
-        }
-        Stage st(ctx, GAVIS_STAGE_SORT, s);
-        CK(radix_sort_pairs<uint64_t>(KL.a_k0, KL.a_v0, KL.a_k1, KL.a_v1, (size_t)nrec, vb + zb, KL.tmp, &alt_a, s));
     }
     const uint32_t *recs = alt_a ? KL.a_v1 : KL.a_v0;
     // stage B: tile entries in stage-A order, i.e. view by view.  When the

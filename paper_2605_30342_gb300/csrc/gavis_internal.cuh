@@ -94,6 +94,17 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, void
                                unsigned long long *d_total, cudaStream_t s, bool flags = false,
                                const unsigned long long *d_n = nullptr);
 
+// Scan of the visibility flags (counts[r] != 0, r < total = views x n)
+// fused with stage A's emission: scan_flags_reduce computes the block
+// partials into tmp (scan_tmp_bytes(total)); scan_flags_emit then writes, for
+// every visible record r = v n + g at its position p among the visible
+// records, keyA[p] = ((v & vmask) << zb) | (depth bits - zmin) and
+// valA[p] = r, and voff[v] = visible records before view v (v = 0..views).
+cudaError_t scan_flags_reduce(const uint32_t *counts, size_t total, void *tmp, cudaStream_t s);
+cudaError_t scan_flags_emit(const uint32_t *counts, size_t total, const void *tmp, const GeoRec *geo, int64_t n,
+                            int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA, uint32_t *valA, uint32_t *voff,
+                            cudaStream_t s);
+
 // stable LSD radix sort of (keys, vals) on bits [0, end_bit); ping-pong
 // buffers; *result_in_alt tells which buffer holds the result.  KeyT is
 // uint64_t or uint32_t.
@@ -131,15 +142,6 @@ inline int depth_bits(uint32_t zmin, uint32_t zmax) { return bits_of(zmax > zmin
 cudaError_t launch_emit_records(const uint32_t *counts, const uint32_t *pos, const GeoRec *geo, int nv, int64_t n,
                                 int zb, uint32_t zmin, uint64_t *keyA, uint32_t *valA, cudaStream_t s,
                                 size_t cap_R = ~(size_t)0, uint32_t *overflow = nullptr);
-// 32-bit record keys ((v & vmask) << zb) | (depth bits - zmin), for sorting
-// the records of each group of vmask + 1 views separately.
-cudaError_t launch_emit_records32(const uint32_t *counts, const uint32_t *pos, const GeoRec *geo, int nv, int64_t n,
-                                  int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA, uint32_t *valA,
-                                  cudaStream_t s);
-// voff[v] (v = 0..nv) = visible records of the views before v, from the
-// flag scan pos and the counts (device [nv + 1]).
-cudaError_t launch_view_offsets(const uint32_t *pos, const uint32_t *counts, int64_t n, int nv, uint32_t *voff,
-                                cudaStream_t s);
 // eoff[v] (v = 0..nv) = stage-B tile entries of the views before v, from the
 // stage-B offsets of the records (stage-A order) and voff (device [nv + 1]).
 cudaError_t launch_entry_offsets(const uint32_t *off_sorted, const uint32_t *voff, int nv, uint32_t M,

@@ -88,39 +88,22 @@ __device__ __forceinline__ float footprint_q(float px, float py, float u, float 
 }
 
 
-// stage A: one record key per visible (view, Gaussian), in (view, index)
-// order; the view part of the key is v & vmask (32-bit keys sorted per group
-// of views) or v (64-bit keys, vmask all ones)
-template <typename KeyT>
+// stage A: one record key per visible (view, Gaussian), in (view, index) order
 __global__ void k_emit_records(const uint32_t *counts, const uint32_t *pos, const GeoRec *geo, int nv, int64_t n,
-                               int zb, uint32_t zmin, uint32_t vmask, KeyT *keyA, uint32_t *valA, size_t cap_R,
+                               int zb, uint32_t zmin, uint64_t *keyA, uint32_t *valA, size_t cap_R,
                                uint32_t *overflow)
 {
     const size_t total = (size_t)nv * (size_t)n;
     const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= total || counts[r] == 0u) return;
-    const uint32_t v = (uint32_t)(r / (size_t)n);
+    const uint64_t v = r / (size_t)n;
     const uint32_t i = pos[r];
     if ((size_t)i >= cap_R) {
         if (overflow) *overflow = 1u;
         return;
     }
-    keyA[i] = ((KeyT)(v & vmask) << zb) | (KeyT)(__float_as_uint(geo[r].b.z) - zmin);
+    keyA[i] = (v << zb) | (uint64_t)(__float_as_uint(geo[r].b.z) - zmin);
     valA[i] = (uint32_t)r;
-}
-
-// voff[v] = number of visible records of views < v (v = 0..nv); pos is the
-// exclusive scan of the visibility flags in (view, index) order
-__global__ void k_view_offsets(const uint32_t *pos, const uint32_t *counts, int64_t n, int nv, uint32_t *voff)
-{
-    for (int v = threadIdx.x; v <= nv; v += blockDim.x) {
-        if (v < nv) {
-            voff[v] = pos[(size_t)v * (size_t)n];
-        } else {
-            const size_t last = (size_t)nv * (size_t)n - 1;
-            voff[v] = pos[last] + (counts[last] != 0u ? 1u : 0u);
-        }
-    }
 }
 
 // eoff[v] = tile entries of the views before v (v = 0..nv): the stage-B
@@ -668,20 +651,7 @@ cudaError_t launch_emit_records(const uint32_t *counts, const uint32_t *pos, con
 {
     const size_t total = (size_t)nv * (size_t)n;
     if (total == 0) return cudaSuccess;
-    k_emit_records<uint64_t><<<nblk(total, 256), 256, 0, s>>>(counts, pos, geo, nv, n, zb, zmin, 0xffffffffu, keyA,
-                                                              valA, cap_R, overflow);
-    count_launch();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_emit_records32(const uint32_t *counts, const uint32_t *pos, const GeoRec *geo, int nv, int64_t n,
-                                  int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA, uint32_t *valA,
-                                  cudaStream_t s)
-{
-    const size_t total = (size_t)nv * (size_t)n;
-    if (total == 0) return cudaSuccess;
-    k_emit_records<uint32_t><<<nblk(total, 256), 256, 0, s>>>(counts, pos, geo, nv, n, zb, zmin, vmask, keyA, valA,
-                                                              ~(size_t)0, nullptr);
+    k_emit_records<<<nblk(total, 256), 256, 0, s>>>(counts, pos, geo, nv, n, zb, zmin, keyA, valA, cap_R, overflow);
     count_launch();
     return cudaGetLastError();
 }
@@ -691,14 +661,6 @@ cudaError_t launch_entry_offsets(const uint32_t *off_sorted, const uint32_t *vof
 {
     if (nv <= 0) return cudaSuccess;
     k_entry_offsets<<<1, 256, 0, s>>>(off_sorted, voff, nv, M, eoff); count_launch();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_view_offsets(const uint32_t *pos, const uint32_t *counts, int64_t n, int nv, uint32_t *voff,
-                                cudaStream_t s)
-{
-    if (nv <= 0 || n <= 0) return cudaSuccess;
-    k_view_offsets<<<1, 256, 0, s>>>(pos, counts, n, nv, voff); count_launch();
     return cudaGetLastError();
 }
 
