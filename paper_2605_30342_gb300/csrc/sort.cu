@@ -446,8 +446,9 @@ cudaError_t radix_sort_pairs(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_
         k_radix_hist<KeyT><<<nblocks, kRsThreads, 0, s>>>(kin, n, shift, hist, nblocks, d_n); count_launch();
         cudaError_t e = exclusive_scan_u32(hist, offs, h, stmp, nullptr, s);
         if (e != cudaSuccess) return e;
-        // digits below the top two passes are close to uniformly distributed
-        if (shift + 8 < end_bit - 8)
+        // the lowest digit, and those below the top two passes, are close to
+        // uniformly distributed
+        if (shift == 0 || shift + 8 < end_bit - 8)
             k_radix_scatter<KeyT, true><<<nblocks, kRsThreads, smem, s>>>(kin, vin, kout, vout, n, shift, hist, offs,
                                                                          nblocks, d_n);
         else
