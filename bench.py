@@ -390,9 +390,14 @@ def run_gavis(args):
 
     # ---------------- scoring replayed as one CUDA graph ----------------
     graph = None
+    plan = None
     if not args.no_graph:
-        plan = ctx.plan(gs, vf, n_cand, W, H, int(keys_sc * 1.25) + 1024, record_capacity=int(vis_sc * 1.25) + 1024,
-                        params=prm_sc)
+        try:   # one plan holds the records of every (candidate, Gaussian) pair at once
+            plan = ctx.plan(gs, vf, n_cand, W, H, int(keys_sc * 1.25) + 1024,
+                            record_capacity=int(vis_sc * 1.25) + 1024, params=prm_sc)
+        except gv.GavisError as e:
+            graph = {"skipped": str(e)}
+    if plan is not None:
         recs = gv.camera_records(cand)
         for _ in range(3):
             plan.launch(recs)
