@@ -79,13 +79,13 @@ def _declare(L):
     L.oracle_ranges.argtypes = [i64, vp, i64, vp]
     L.oracle_pixel_lists.argtypes = [vp, i64, vp, vp, vp, dbl, i32, i32, vp, vp, i64]
     L.oracle_pixel_lists.restype = i64
-    L.oracle_composite.argtypes = [i64, vp, vp, vp, vp, vp, vp]
+    L.oracle_composite.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
     L.oracle_vf_query.argtypes = [i64, vp, i32, i64, vp, vp, vp, vp]
     L.oracle_vf_exact.argtypes = [i64, i32, vp, vp, dbl, vp, vp]
     L.oracle_visibility_view.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     L.oracle_visibility_view.restype = i64
     L.oracle_vf_build.argtypes = [i32, vp, i64, vp, vp, vp, vp, i32, vp, vp, vp, vp]
-    L.oracle_render_view.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]
+    L.oracle_render_view.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
     L.oracle_density_control.argtypes = [i32, vp, i64, vp, vp, vp, vp, i64, vp, dbl, dbl, dbl, vp, vp, vp, vp]
     L.oracle_density_control.restype = i64
 
@@ -200,18 +200,20 @@ def pixel_lists(cam, scene, q_cut=9.0, tile=16, brute=False):
 # compositing, visibility field
 # ----------------------------------------------------------------------------
 
-def composite(alpha, V, col, prm=None, kc=None):
+def composite(alpha, V, col, prm=None, kc=None, z=None):
     """One pixel over an explicit list; returns dict of the outputs.  kc:
-    optional per-entry 1/2 log((2 pi e)^3 |Q_c|)."""
+    optional per-entry 1/2 log((2 pi e)^3 |Q_c|); z: optional per-entry
+    camera depths (for the expected depth)."""
     prm = params() if prm is None else prm
     alpha, V = _f64(alpha), _f64(V)
     col = _f64(np.asarray(col).reshape(-1, 3))
     kc = None if kc is None else _f64(kc)
-    res = np.zeros(11)
-    lib().oracle_composite(len(alpha), _p(alpha), _p(V), _p(col), _p(prm), _p(kc) if kc is not None else None,
-                           _p(res))
+    z = None if z is None else _f64(z)
+    res = np.zeros(12)
+    lib().oracle_composite(len(alpha), _p(alpha), _p(V), _p(col), _p(z) if z is not None else None, _p(prm),
+                           _p(kc) if kc is not None else None, _p(res))
     return dict(H=res[0], rgb=res[1:4].copy(), T=res[4], Tc=res[5], sum_w=res[6], sum_wc=res[7],
-                w0=res[8], used=int(res[9]), amb=bool(res[10]))
+                w0=res[8], used=int(res[9]), amb=bool(res[10]), depth=res[11])
 
 
 def vf_query(gamma, L, P, cam, means):
@@ -280,9 +282,10 @@ def density_control(cams, scene, vmeans, rho=100.0, eta=0.5, eps_v=0.95, prm=Non
     return vis, keep.astype(bool), amb.astype(bool)
 
 
-def render_view(cam, scene, V, prm=None, sh=None, sh_var=None):
-    """rgb (3,H,W), unc (H,W), amb (H,W) bool, used (H,W).  sh_var: optional
-    per-coefficient colour variances (FisherRF variant of Q_c)."""
+def render_view(cam, scene, V, prm=None, sh=None, sh_var=None, want_depth=False):
+    """rgb (3,H,W), unc (H,W), amb (H,W) bool, used (H,W) [, depth (H,W) if
+    want_depth].  sh_var: optional per-coefficient colour variances (FisherRF
+    variant of Q_c)."""
     prm = params() if prm is None else prm
     n = scene.n
     sh = _f64(scene.sh if sh is None else sh)
@@ -292,21 +295,27 @@ def render_view(cam, scene, V, prm=None, sh=None, sh_var=None):
     unc = np.zeros((cam.H, cam.W))
     amb = np.zeros((cam.H, cam.W), np.uint8)
     used = np.zeros((cam.H, cam.W), np.int32)
+    depth = np.zeros((cam.H, cam.W)) if want_depth else None
     lib().oracle_render_view(_p(cam_record(cam)), n, _p(_f32(scene.means)), _p(_f32(scene.scales)),
                              _p(_f32(scene.rots)), _p(_f32(scene.opac)), _p(sh), _p(var) if var is not None else None,
                              Lc, _p(_f64(V)), _p(prm),
-                             _p(rgb), _p(unc), _p(amb), _p(used))
+                             _p(rgb), _p(unc), _p(depth) if want_depth else None, _p(amb), _p(used))
+    if want_depth:
+        return rgb, unc, amb.astype(bool), used, depth
     return rgb, unc, amb.astype(bool), used
 
 
-def score_views(scene, gamma, L, P, cams, prm=None, sh=None, keep_images=True, sh_var=None):
+def score_views(scene, gamma, L, P, cams, prm=None, sh=None, keep_images=True, sh_var=None, want_depth=False):
     """Per-view mean entropy score S_v (eq:id with f_corr = 0) and the argmax
     of eq:i_gain (ties to the lowest index)."""
     prm = params() if prm is None else prm
-    out = dict(rgb=[], unc=[], amb=[], used=[], score=np.zeros(len(cams)))
+    out = dict(rgb=[], unc=[], amb=[], used=[], depth=[], score=np.zeros(len(cams)))
     for v, cam in enumerate(cams):
         V, _ = vf_query(gamma, L, P, cam, scene.means)
-        rgb, unc, amb, used = render_view(cam, scene, V, prm, sh, sh_var)
+        r = render_view(cam, scene, V, prm, sh, sh_var, want_depth=want_depth)
+        rgb, unc, amb, used = r[:4]
+        if want_depth and keep_images:
+            out["depth"].append(r[4])
         out["score"][v] = unc.mean()
         if keep_images:
             out["rgb"].append(rgb)

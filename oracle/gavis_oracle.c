@@ -30,7 +30,9 @@
  *   oracle_render_view   Alg. "3DGS Uncertainty Quantification with
  *                        Visibility Field" (eq:alpha_comp, eq:huber) plus the
  *                        plain 3DGS colour of eq:orig_vr, on untiled
- *                        per-pixel depth-sorted lists.
+ *                        per-pixel depth-sorted lists; optionally the
+ *                        per-pixel expected depth d of eq:id, summed over
+ *                        the colour weights alpha_i T_c,i (background 0).
  *   oracle_bins          the (view, tile, depth) keys a tile rasterizer sorts
  *                        by, in canonical order (stable, ties by index).
  *   oracle_composite     one pixel's compositing over a given list (pins).
@@ -496,14 +498,14 @@ static int near_thresh(double T, double eps, double margin)
  *      res[6] = sum of w*, res[7] = sum of colour weights, res[8] = w0bar,
  *      res[9] = entries consumed, res[10] = 1 if a transmittance test landed
  *      within margin*eps of eps. */
-void oracle_composite(int64_t n, const double *alpha, const double *V, const double *col,
+void oracle_composite(int64_t n, const double *alpha, const double *V, const double *col, const double *z,
                       const double *prm, const double *kc_each, double *res)
 {
     const double eps = prm[P_EPS_T], beta = prm[P_BETA], o0 = prm[P_O0];
     const double kc_const = 0.5 * 3.0 * log(prm[P_SIGMA_C2]) + 1.5 * (log(2.0 * M_PI) + 1.0);
     const double k0 = 0.5 * prm[P_LOGDET_Q0] + 1.5 * (log(2.0 * M_PI) + 1.0);
     const double margin = prm[P_MARGIN];
-    double T = 1.0, Tc = 1.0, H = 0.0, w0 = 0.0, sw = 0.0, swc = 0.0;
+    double T = 1.0, Tc = 1.0, H = 0.0, w0 = 0.0, sw = 0.0, swc = 0.0, D = 0.0;
     double C[3] = {0, 0, 0};
     int ua = 1, rgb = 1, amb = 0;
     int64_t used = 0;
@@ -513,6 +515,7 @@ void oracle_composite(int64_t n, const double *alpha, const double *V, const dou
         if (rgb) {
             double w = a * Tc;
             C[0] += w * col[3 * i]; C[1] += w * col[3 * i + 1]; C[2] += w * col[3 * i + 2];
+            if (z) D += w * z[i];            /* expected depth, background at 0 */
             swc += w;
             Tc = Tc * (1.0 - a);
             if (near_thresh(Tc, eps, margin)) amb = 1;
@@ -535,7 +538,7 @@ void oracle_composite(int64_t n, const double *alpha, const double *V, const dou
     H += phi(w0) + w0 * k0;                  /* invisible component */
     res[0] = H; res[1] = C[0]; res[2] = C[1]; res[3] = C[2];
     res[4] = T; res[5] = Tc; res[6] = sw; res[7] = swc; res[8] = w0;
-    res[9] = (double)used; res[10] = (double)amb;
+    res[9] = (double)used; res[10] = (double)amb; res[11] = D;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -698,7 +701,7 @@ void oracle_vf_build(int nview, const float *cams, int64_t n, const float *means
  * sh: n x (Lc+1)^2 x 3 colour coefficients. */
 void oracle_render_view(const float *cam, int64_t n, const float *means, const float *scales,
                         const float *rots, const float *opac, const double *sh, const double *sh_var, int Lc,
-                        const double *V, const double *prm, double *rgb, double *unc,
+                        const double *V, const double *prm, double *rgb, double *unc, double *depth,
                         uint8_t *amb, int32_t *used)
 {
     const double qcut = prm[P_QCUT];
@@ -736,7 +739,7 @@ void oracle_render_view(const float *cam, int64_t n, const float *means, const f
     #pragma omp parallel
     {
         int64_t capn = 0;
-        double *al = NULL, *vv = NULL, *cc = NULL, *kk = NULL;
+        double *al = NULL, *vv = NULL, *cc = NULL, *kk = NULL, *zz = NULL;
         #pragma omp for schedule(dynamic, 64)
         for (int64_t p = 0; p < npix; ++p) {
             int i = (int)(p % W), j = (int)(p / W);
@@ -747,6 +750,7 @@ void oracle_render_view(const float *cam, int64_t n, const float *means, const f
                 vv = (double *)realloc(vv, sizeof(double) * (size_t)capn);
                 cc = (double *)realloc(cc, sizeof(double) * 3 * (size_t)capn);
                 kk = (double *)realloc(kk, sizeof(double) * (size_t)capn);
+                zz = (double *)realloc(zz, sizeof(double) * (size_t)capn);
             }
             for (int64_t k = 0; k < m; ++k) {
                 uint32_t g = (uint32_t)(Lst.ent[s + k] & 0xffffffffu);
@@ -755,17 +759,19 @@ void oracle_render_view(const float *cam, int64_t n, const float *means, const f
                 vv[k] = V[g];
                 cc[3 * k] = col[3 * g]; cc[3 * k + 1] = col[3 * g + 1]; cc[3 * k + 2] = col[3 * g + 2];
                 if (kcg) kk[k] = kcg[g];
+                zz[k] = (double)P[g].z;
             }
-            double res[11];
-            oracle_composite(m, al, vv, cc, prm, kcg ? kk : NULL, res);
+            double res[12];
+            oracle_composite(m, al, vv, cc, zz, prm, kcg ? kk : NULL, res);
             unc[p] = res[0];
             rgb[p] = res[1];
             rgb[npix + p] = res[2];
             rgb[2 * npix + p] = res[3];
+            if (depth) depth[p] = res[11];
             if (amb) amb[p] = (uint8_t)res[10];
             if (used) used[p] = (int32_t)res[9];
         }
-        free(al); free(vv); free(cc); free(kk);
+        free(al); free(vv); free(cc); free(kk); free(zz);
     }
     free_lists(&Lst);
     free(col);

@@ -553,3 +553,33 @@ def test_coefficient_variance_single_gaussian_closed_form():
     a_s = (V + 0.5 * (1 - V)) * o + 0.15 * 0.5 * (1 - V)
     w1, w0 = a_s * V, a_s * (1 - V)
     assert unc[7, 7] == pytest.approx(phi(w1) + w1 * kc + phi(w0) + w0 * K0, abs=1e-6)
+
+
+def test_expected_depth_single_gaussian_and_occlusion():
+    """Expected depth d of eq:id (colour weights alpha_i T_c,i, background 0):
+    one Gaussian on the optical axis at z = 2 gives d = o * 2 at the centre
+    pixel (alpha = o at q = 0) and 0 outside its footprint; a second Gaussian
+    straight behind it at z = 3 adds (1 - o) o2 * 3."""
+    o = 0.8
+    sc = single_gaussian_scene((0, 0, 2.0), 0.05, o)
+    cam = axis_camera()
+    rgb, unc, amb, used, depth = oracle.render_view(cam, sc, np.array([0.5]), want_depth=True)
+    assert depth[7, 7] == pytest.approx(np.float32(o) * 2.0, abs=1e-6)
+    assert depth[0, 0] == 0.0
+    o2 = 0.6
+    two = sg.Scene(np.array([[0, 0, 2.0], [0, 0, 3.0]], np.float32), np.full((2, 3), 0.05, np.float32),
+                   np.array([[1, 0, 0, 0], [1, 0, 0, 0]], np.float32), np.array([o, o2], np.float32),
+                   np.zeros((2, 4, 3), np.float32), 1)
+    _, _, _, _, d2 = oracle.render_view(cam, two, np.array([0.5, 0.5]), want_depth=True)
+    assert d2[7, 7] == pytest.approx(np.float32(o) * 2.0 + (1 - np.float32(o)) * np.float32(o2) * 3.0, abs=1e-6)
+
+
+def test_expected_depth_partition_of_unity():
+    """With every Gaussian at the same depth z, d = z (1 - T_c,end): the colour
+    weights sum to the opacity the pixel accumulated (P9 applied to d)."""
+    rng = np.random.default_rng(11)
+    for n in (1, 5, 40):
+        al = rng.uniform(0.05, 0.9, n)
+        r = oracle.composite(al, rng.uniform(0, 1, n), rng.normal(size=(n, 3)), z=np.full(n, 4.25))
+        assert r["depth"] == pytest.approx(4.25 * (1.0 - r["Tc"]), rel=1e-12, abs=1e-12)
+        assert r["depth"] == pytest.approx(4.25 * r["sum_wc"], rel=1e-12)
