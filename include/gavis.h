@@ -167,6 +167,25 @@ int gavis_score_views(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
                       float *rgb, float *unc, float *score, int32_t *best_dev, int32_t *best_host,
                       void *stream);
 
+/* Outputs of gavis_render_views.  Any pointer may be NULL except score. */
+typedef struct {
+    float *rgb;           /* device [n_cand][3][H][W], as for gavis_score_views */
+    float *unc;           /* device [n_cand][H][W] */
+    float *depth;         /* device [n_cand][H][W]: the expected depth d of eq:id, the sum over the
+                             colour weights alpha_i T_c,i of eq:orig_vr of the Gaussians' camera depths
+                             (background 0; divide by the accumulated opacity 1 - T_c for the
+                             normalised depth) */
+    float *score;         /* device [n_cand] */
+    int32_t *best_dev;    /* device [1] */
+    int32_t *best_host;   /* host [1]; if given the call synchronises `stream` */
+} gavis_views_out;
+
+/* gavis_score_views with the optional per-pixel expected depth (the input of
+ * the correction term f_corr of eq:id, which this library takes as 0).
+ * Same arguments, errors and synchronisation as gavis_score_views. */
+int gavis_render_views(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf, const gavis_camera *cand,
+                       int n_cand, const gavis_params *p, const gavis_views_out *out, void *stream);
+
 /* Visibility-field density control (Alg. "Visibility Field Density Control").
  * Virtual particles at the caller-drawn centres virt_means (device [3 n_virt],
  * uniform in the scene volume; their number is floor(rho * volume)) get an

@@ -63,13 +63,18 @@ class gavis_params(C.Structure):
                 ("tile", C.c_int32), ("views_per_batch", C.c_int32)]
 
 
+class gavis_views_out(C.Structure):
+    _fields_ = [("rgb", C.c_void_p), ("unc", C.c_void_p), ("depth", C.c_void_p), ("score", C.c_void_p),
+                ("best_dev", C.c_void_p), ("best_host", C.c_void_p)]
+
+
 EXPORTS = ["gavis_ctx_create", "gavis_ctx_destroy", "gavis_last_error", "gavis_params_default",
            "gavis_vmf_coeffs", "gavis_vf_build", "gavis_score_views", "gavis_vf_query", "gavis_debug_bins",
            "gavis_debug_visibility", "gavis_prof_enable", "gavis_prof_read", "gavis_vf_density_control",
            "gavis_server_create", "gavis_server_destroy", "gavis_server_last_error", "gavis_server_add_scene",
            "gavis_server_submit", "gavis_server_wait", "gavis_server_stats", "gavis_autotune",
            "gavis_plan_create", "gavis_plan_launch", "gavis_plan_overflowed", "gavis_plan_kernels",
-           "gavis_plan_destroy"]
+           "gavis_plan_destroy", "gavis_render_views"]
 
 STAGES = ["project", "scan", "emit", "sort", "ranges", "composite_ua", "composite_vis", "reduce", "vf_accum"]
 
@@ -124,6 +129,9 @@ def load(path: str | None = None):
                                            C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
         lib.gavis_autotune.argtypes = [vp, C.POINTER(gavis_gaussians), C.POINTER(gavis_vf), C.POINTER(gavis_camera), i32,
                                        i32, C.POINTER(gavis_params), C.POINTER(C.c_double), vp]
+        lib.gavis_render_views.argtypes = [vp, C.POINTER(gavis_gaussians), C.POINTER(gavis_vf),
+                                           C.POINTER(gavis_camera), i32, C.POINTER(gavis_params),
+                                           C.POINTER(gavis_views_out), vp]
         lib.gavis_plan_create.argtypes = [vp, C.POINTER(gavis_gaussians), C.POINTER(gavis_vf), i32, i32, i32,
                                           C.POINTER(gavis_params), i64, i64, vp, vp, vp, vp, C.POINTER(vp)]
         lib.gavis_plan_launch.argtypes = [vp, C.POINTER(gavis_camera), vp]
@@ -291,8 +299,9 @@ class Context:
 
     # -------------------------------------------------------------- scoring
     def score_views(self, gs: Gaussians, vf: VisibilityField, cand_cams, params=None, want_rgb=True,
-                    want_unc=True, out=None, sync_best=True, stream=None):
-        """Returns dict(score [n], best (int or device tensor), rgb [n,3,H,W], unc [n,H,W])."""
+                    want_unc=True, out=None, sync_best=True, stream=None, want_depth=False):
+        """Returns dict(score [n], best (int or device tensor), rgb [n,3,H,W], unc [n,H,W],
+        depth [n,H,W] (expected depth, when want_depth))."""
         p = params or Params(vf_degree=vf.degree)
         n = len(cand_cams)
         dev = gs.means.device
@@ -302,17 +311,21 @@ class Context:
         unc = out.get("unc") if "unc" in out else (torch.empty((n, H, W), device=dev) if want_unc else None)
         score = out.get("score") if "score" in out else torch.empty(n, device=dev)
         best_dev = out.get("best_dev") if "best_dev" in out else torch.empty(1, dtype=torch.int32, device=dev)
+        depth = out.get("depth") if "depth" in out else (torch.empty((n, H, W), device=dev) if want_depth else None)
         best_host = C.c_int32(-1)
         vs = vf.struct()
         cams = camera_records(cand_cams)
-        self._check(self._lib.gavis_score_views(
-            self._h, C.byref(gs.struct), C.byref(vs), cams, n, C.byref(p),
-            C.c_void_p(rgb.data_ptr() if rgb is not None else None),
-            C.c_void_p(unc.data_ptr() if unc is not None else None),
-            C.c_void_p(score.data_ptr()), C.c_void_p(best_dev.data_ptr()),
-            C.byref(best_host) if sync_best else None, _stream_ptr(stream)))
+        o = gavis_views_out()
+        o.rgb = rgb.data_ptr() if rgb is not None else None
+        o.unc = unc.data_ptr() if unc is not None else None
+        o.depth = depth.data_ptr() if depth is not None else None
+        o.score = score.data_ptr()
+        o.best_dev = best_dev.data_ptr()
+        o.best_host = C.cast(C.pointer(best_host), C.c_void_p) if sync_best else None
+        self._check(self._lib.gavis_render_views(self._h, C.byref(gs.struct), C.byref(vs), cams, n, C.byref(p),
+                                                 C.byref(o), _stream_ptr(stream)))
         return dict(score=score, best=int(best_host.value) if sync_best else best_dev, rgb=rgb, unc=unc,
-                    best_dev=best_dev)
+                    depth=depth, best_dev=best_dev)
 
     def plan(self, gs: Gaussians, vf: VisibilityField, n_cams: int, W: int, H: int, entry_capacity: int,
              record_capacity: int = 0, params=None, want_rgb=False, want_unc=False) -> "Plan":

@@ -335,7 +335,7 @@ enum Mode { MODE_SCORE, MODE_VIS, MODE_BINS };
 
 struct ChainOut {
     // score mode
-    float *rgb = nullptr, *unc = nullptr, *score = nullptr;
+    float *rgb = nullptr, *unc = nullptr, *depth = nullptr, *score = nullptr;
     // vis mode: per-batch sums land in ctx->vis; callback consumes them
     // bins mode
     uint64_t *keys = nullptr;
@@ -555,7 +555,7 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     ca.rc = raster_consts(p);
     ca.tile_sums = SL.tile_sums;
     if (mode == MODE_SCORE) {
-        ca.rgb = out.rgb; ca.unc = out.unc;
+        ca.rgb = out.rgb; ca.unc = out.unc; ca.depth = out.depth;
         ca.per_entry_kc = gs->sh_var != nullptr;
         ca.pair_counts = ctx->prof_on ? SL.pair_counts : nullptr;
         {
@@ -821,7 +821,23 @@ int gavis_score_views(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
                       int n_cand, const gavis_params *p, float *rgb, float *unc, float *score, int32_t *best_dev,
                       int32_t *best_host, void *stream)
 {
+    gavis_views_out o;
+    o.rgb = rgb;
+    o.unc = unc;
+    o.depth = nullptr;
+    o.score = score;
+    o.best_dev = best_dev;
+    o.best_host = best_host;
+    return gavis_render_views(ctx, gs, vf, cand, n_cand, p, &o, stream);
+}
+
+int gavis_render_views(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf, const gavis_camera *cand,
+                       int n_cand, const gavis_params *p, const gavis_views_out *out, void *stream)
+{
     if (!ctx) return GAVIS_ERR_ARG;
+    if (!out) return fail(ctx, GAVIS_ERR_ARG, "out is NULL");
+    float *rgb = out->rgb, *unc = out->unc, *depth = out->depth, *score = out->score;
+    int32_t *best_dev = out->best_dev, *best_host = out->best_host;
     int rc;
     if ((rc = check_params(ctx, p)) || (rc = check_gaussians(ctx, gs, true)) || (rc = check_vf(ctx, gs, vf)) ||
         (rc = check_cams(ctx, cand, n_cand)))
@@ -832,12 +848,14 @@ int gavis_score_views(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     ChainOut co;
     co.rgb = rgb;
     co.unc = unc;
+    co.depth = depth;
     co.score = score;
     if (gs->n == 0 && n_cand > 0) {
-        // empty scene: every pixel has an empty list, H = 0 and rgb = 0
+        // empty scene: every pixel has an empty list, H = 0, rgb = 0, depth = 0
         const size_t plane = (size_t)cand[0].W * cand[0].H;
         if (rgb) CK(cudaMemsetAsync(rgb, 0, (size_t)n_cand * 3 * plane * sizeof(float), s));
         if (unc) CK(cudaMemsetAsync(unc, 0, (size_t)n_cand * plane * sizeof(float), s));
+        if (depth) CK(cudaMemsetAsync(depth, 0, (size_t)n_cand * plane * sizeof(float), s));
         CK(cudaMemsetAsync(score, 0, (size_t)n_cand * sizeof(float), s));
     } else {
         rc = run_views(ctx, MODE_SCORE, gs, vf, cand, n_cand, p, co, s, [](int, int) { return GAVIS_OK; });

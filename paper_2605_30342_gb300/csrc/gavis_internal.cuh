@@ -172,6 +172,7 @@ struct CompositeArgs {
     int W, H, tile, TW, TH;
     RasterConsts rc;
     float *rgb, *unc;      // may be NULL
+    float *depth;          // expected depth (sum of colour weight x camera depth) or NULL
     float *tile_sums;      // [nv * TW*TH]
     bool per_entry_kc;     // use the per-Gaussian kc of the UaRec (colour variances given)
     // visibility pass

@@ -209,7 +209,9 @@ constexpr float kLn2 = 0.69314718055994530942f;
 // w0 = (1 - T) - sum(wv).
 // KC: the visible components carry per-Gaussian kc (colour variances given);
 // otherwise the constant k_c is applied to sum(wv) once per pixel.
-template <int TILE, bool KC>
+// DEPTH: also accumulate the expected depth sum_i alpha_i T_c,i z_i along the
+// colour path (into a.depth).
+template <int TILE, bool KC, bool DEPTH>
 __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a)
 {
     constexpr int NT = TILE * TILE / 2;
@@ -219,6 +221,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
     __shared__ float4 s_u0[NW][32];   // a1, a0, V, r
     __shared__ float2 s_u1[NW][32];   // g, b
     __shared__ float s_kc[KC ? NW : 1][32];
+    __shared__ float s_z[DEPTH ? NW : 1][32];
     __shared__ float s_red[NW];
     __shared__ uint32_t s_pairs[NW];
 
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
     const size_t vrow = (size_t)vb * (size_t)a.n;
     const RasterConsts rc = a.rc;
 
-    float T[2], Tc[2], sl[2], swv[2], skc[2], cr[2], cg[2], cb[2], py[2];
+    float T[2], Tc[2], sl[2], swv[2], skc[2], cr[2], cg[2], cb[2], py[2], dz[2];
     bool ua_on[2], rgb_on[2], inside[2];
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
@@ -246,11 +249,13 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
         inside[p] = i < a.W && j < a.H;
         py[p] = (float)j + 0.5f;
         T[p] = 1.0f; Tc[p] = 1.0f; sl[p] = 0.0f; swv[p] = 0.0f; skc[p] = 0.0f; cr[p] = 0.0f; cg[p] = 0.0f; cb[p] = 0.0f;
+        dz[p] = 0.0f;
         ua_on[p] = inside[p];
-        rgb_on[p] = inside[p] && a.rgb != nullptr;   // colour only when asked for
+        rgb_on[p] = inside[p] && (DEPTH || a.rgb != nullptr);   // colour path only when asked for
     }
     uint32_t npairs = 0;
     float *kcs = s_kc[KC ? warp : 0];
+    float *zs = s_z[DEPTH ? warp : 0];
     float4 *g0s = s_g0[warp];
     float2 *g1s = s_g1[warp];
     float4 *u0s = s_u0[warp];
@@ -277,6 +282,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
             u0s[slot] = ur.a;
             u1s[slot] = make_float2(ur.b.x, ur.b.y);
             if (KC) kcs[slot] = ur.b.z;
+            if (DEPTH) zs[slot] = gr.b.z;
         }
         __syncwarp();
         const int nk = __popc(m);
@@ -297,6 +303,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
                     cr[p] = fmaf(w, u0.w, cr[p]);
                     cg[p] = fmaf(w, u1.x, cg[p]);
                     cb[p] = fmaf(w, u1.y, cb[p]);
+                    if (DEPTH) dz[p] = fmaf(w, zs[k], dz[p]);
                     Tc[p] -= w;
                     rgb_on[p] = Tc[p] >= rc.eps_T;
                 }
@@ -326,6 +333,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
         if (w0 > 1e-30f) Hs = fmaf(w0, rc.k_0 - kLn2 * lg2_approx(w0), Hs);
         const size_t pix = (size_t)(j0 + 4 * p) * a.W + i;
         if (a.unc) a.unc[vg * plane + pix] = Hs;
+        if (DEPTH) a.depth[vg * plane + pix] = dz[p];
         if (a.rgb) {
             a.rgb[(vg * 3 + 0) * plane + pix] = cr[p];
             a.rgb[(vg * 3 + 1) * plane + pix] = cg[p];
@@ -698,26 +706,29 @@ cudaError_t launch_keys_export(const uint32_t *keyB, const uint32_t *valB, size_
     return cudaGetLastError();
 }
 
+template <int TILE>
+void launch_ua_tile(const CompositeArgs &a, unsigned blocks, cudaStream_t s)
+{
+    constexpr int NT = TILE * TILE / 2;
+    const bool d = a.depth != nullptr;
+    if (a.per_entry_kc) {
+        if (d) k_composite_ua<TILE, true, true><<<blocks, NT, 0, s>>>(a);
+        else k_composite_ua<TILE, true, false><<<blocks, NT, 0, s>>>(a);
+    } else {
+        if (d) k_composite_ua<TILE, false, true><<<blocks, NT, 0, s>>>(a);
+        else k_composite_ua<TILE, false, false><<<blocks, NT, 0, s>>>(a);
+    }
+    count_launch();
+}
+
 cudaError_t launch_composite_ua(const CompositeArgs &a, cudaStream_t s)
 {
     const unsigned blocks = (unsigned)(a.nv * a.TW * a.TH);
     if (blocks == 0) return cudaSuccess;
     switch (a.tile) {
-    case 8:
-        if (a.per_entry_kc) k_composite_ua<8, true><<<blocks, 32, 0, s>>>(a);
-        else k_composite_ua<8, false><<<blocks, 32, 0, s>>>(a);
-        count_launch();
-        break;
-    case 16:
-        if (a.per_entry_kc) k_composite_ua<16, true><<<blocks, 128, 0, s>>>(a);
-        else k_composite_ua<16, false><<<blocks, 128, 0, s>>>(a);
-        count_launch();
-        break;
-    case 32:
-        if (a.per_entry_kc) k_composite_ua<32, true><<<blocks, 512, 0, s>>>(a);
-        else k_composite_ua<32, false><<<blocks, 512, 0, s>>>(a);
-        count_launch();
-        break;
+    case 8: launch_ua_tile<8>(a, blocks, s); break;
+    case 16: launch_ua_tile<16>(a, blocks, s); break;
+    case 32: launch_ua_tile<32>(a, blocks, s); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

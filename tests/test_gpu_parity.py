@@ -211,6 +211,36 @@ def test_score_views_parity(ctx, gv, name, tile):
         assert out["best"] == ref["best"]
 
 
+@pytest.mark.parametrize("name", ["tiny", "room_small"])
+@pytest.mark.parametrize("tile", [16, 8])
+def test_expected_depth_parity(ctx, gv, name, tile):
+    """Expected depth (colour weights x camera depth, background 0) against the
+    oracle; it grows with the depths (up to ~10 here), so the gate is 1e-4
+    relative to max(1, |d|).  Asking for it leaves every other output bit for
+    bit unchanged."""
+    c = case(name)
+    sc, cand = c["scene"], c["cand"]
+    L = c["vf_degree"]
+    g32 = oracle_gamma(c)
+    vf = gv.VisibilityField(torch.as_tensor(g32).cuda(), L, len(c["train"]), 1.0)
+    gs = gpu_scene(gv, sc)
+    p = gv.Params(tile=tile, vf_degree=L)
+    a = ctx.score_views(gs, vf, cand, params=p, want_depth=True)
+    b = ctx.score_views(gs, vf, cand, params=p)
+    for k in ("unc", "rgb", "score"):
+        assert torch.equal(a[k], b[k]), k
+    ref = oracle.score_views(sc, g32.astype(np.float64), L, len(c["train"]), cand, want_depth=True)
+    d = a["depth"].cpu().numpy()
+    n_amb = 0
+    for v in range(len(cand)):
+        ok = ~ref["amb"][v]
+        n_amb += int((~ok).sum())
+        err = np.abs(d[v] - ref["depth"][v]) / np.maximum(1.0, np.abs(ref["depth"][v]))
+        assert err[ok].max() <= TOL, (v, err[ok].max())
+    assert n_amb <= 0.01 * d.size
+    assert np.abs(d).max() > 1.0   # the case exercises depths well above 1
+
+
 def test_score_batched_equals_plain(ctx, gv):
     c = case("room_small")
     g32 = oracle_gamma(c)
@@ -246,8 +276,9 @@ def test_empty_scene(ctx, gv):
     sc = c["scene"].subset(np.arange(0))
     gs = gpu_scene(gv, sc)
     vf = ctx.vf_build(gs, c["train"], degree=2)
-    out = ctx.score_views(gs, vf, c["cand"][:3])
+    out = ctx.score_views(gs, vf, c["cand"][:3], want_depth=True)
     assert torch.all(out["unc"] == 0) and torch.all(out["rgb"] == 0) and torch.all(out["score"] == 0)
+    assert torch.all(out["depth"] == 0)
     assert out["best"] == 0
 
 
