@@ -391,14 +391,30 @@ def run_gavis(args):
     # ---------------- scoring replayed as one CUDA graph ----------------
     graph = None
     plan = None
+    plan_batch = 0
     if not args.no_graph:
-        try:   # one plan holds the records of every (candidate, Gaussian) pair at once
+        recs = gv.camera_records(cand)
+        try:   # all candidates in one batch when their records fit, else batches of 64 views
             plan = ctx.plan(gs, vf, n_cand, W, H, int(keys_sc * 1.25) + 1024,
                             record_capacity=int(vis_sc * 1.25) + 1024, params=prm_sc)
-        except gv.GavisError as e:
-            graph = {"skipped": str(e)}
+        except gv.GavisError:
+            plan_batch = 64
+            nb = (n_cand + plan_batch - 1) // plan_batch
+            pb = gv.Params(**{f: getattr(prm_sc, f) for f, _ in prm_sc._fields_})
+            pb.views_per_batch = plan_batch
+            try:
+                plan = ctx.plan(gs, vf, n_cand, W, H, int(keys_sc / nb * 2) + 1024,
+                                record_capacity=int(vis_sc / nb * 2) + 1024, params=pb)
+                plan.launch(recs)
+                over, rec_need, ent_need = plan.overflowed()
+                if over:   # size the capacities from the largest batch
+                    plan.close()
+                    plan = ctx.plan(gs, vf, n_cand, W, H, int(ent_need * 1.1) + 1024,
+                                    record_capacity=int(rec_need * 1.1) + 1024, params=pb)
+            except gv.GavisError as e:
+                plan = None
+                graph = {"skipped": str(e)}
     if plan is not None:
-        recs = gv.camera_records(cand)
         for _ in range(3):
             plan.launch(recs)
             ctx.score_views(gs, vf, cand, params=prm_sc, out=outs, sync_best=False)
@@ -416,6 +432,7 @@ def run_gavis(args):
         graph = {"ms_per_scoring": g0.elapsed_time(g1) / args.steps,
                  "score_views_ms": g1.elapsed_time(g2) / args.steps, "identical_to_score_views": same,
                  "overflowed": plan.overflowed()[0], "kernels_per_launch": plan.kernels,
+                 "views_per_batch": plan_batch or n_cand,
                  "what": "the candidate-scoring chain captured once (gavis_plan_create) and replayed per step"}
         plan.close()
         del plan

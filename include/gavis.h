@@ -277,13 +277,16 @@ int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_vf *vf, cons
 /* ---------------------------------------------------------------------- */
 typedef struct gavis_plan gavis_plan;
 
-/* Build a plan for n_cams (1..1024) candidate views of W x H pixels over one
- * scene and field.  The plan allocates all its device memory here: one
- * projected record per (view, Gaussian), sort space for record_capacity
- * visible (view, Gaussian) records (0 = n_cams x n, always enough) and for
- * entry_capacity tile entries.  Good values are 1.25 x the visible-record and
- * tile-key counts gavis_prof_read reports for comparable poses; grids are
- * sized by the capacities, so oversizing them costs time.  gs, vf, p: as for gavis_score_views; gs and vf stay owned by the
+/* Build a plan for n_cams (1..16384) candidate views of W x H pixels over
+ * one scene and field.  The views go through the chain in batches of
+ * p->views_per_batch (0: all in one batch), replayed one after another over
+ * the same buffers.  The plan allocates all its device memory here, for one
+ * batch: one projected record per (view, Gaussian), sort space for
+ * record_capacity visible (view, Gaussian) records (0 = views x n, always
+ * enough) and for entry_capacity tile entries.  Good values are 1.25 x the
+ * largest batch's visible-record and tile-key counts (gavis_prof_read gives
+ * totals; gavis_plan_overflowed gives the largest batch's after a launch);
+ * grids are sized by the capacities, so oversizing them costs time.  gs, vf, p: as for gavis_score_views; gs and vf stay owned by the
  * caller and must stay alive at the same addresses while the plan is used.
  * The plan captures the sizes, dtypes and |P| (vf->n_train_views); the
  * values behind the pointers are read at every launch, so they may be
@@ -309,9 +312,9 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
 int gavis_plan_launch(gavis_plan *plan, const gavis_camera *cams, void *stream);
 
 /* After the last launch finishes (the call waits for it): *overflowed = 1 if
- * it needed more visible records or tile entries than the capacities;
- * *records_needed and *entries_needed = the numbers it needed.  Any pointer
- * may be NULL. */
+ * a batch needed more visible records or tile entries than the capacities;
+ * *records_needed and *entries_needed = the largest numbers a batch needed.
+ * Any pointer may be NULL. */
 int gavis_plan_overflowed(gavis_plan *plan, int *overflowed, int64_t *records_needed, int64_t *entries_needed);
 
 /* Kernels one launch runs (for launch accounting). */

@@ -3,8 +3,10 @@
 // the paper's per-planning-step scoring).
 //
 // A plan fixes the scene, the field, the number of candidate views, their
-// resolution, the parameters and the output buffers.  Its buffers are sized
-// statically: projected records for every (view, Gaussian), sort space for
+// resolution, the parameters and the output buffers.  The views go through
+// the chain in batches of p->views_per_batch (0: all at once), captured one
+// after another over the same buffers, which are sized statically for one
+// batch: projected records for every (view, Gaussian), sort space for
 // `record_capacity` visible records and `entry_capacity` tile entries.  The
 // kernels after the projection read the actual numbers of visible records
 // and tile entries from device memory (grids are sized by the capacities),
@@ -37,7 +39,7 @@ size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct gavis_plan {
     int device = 0;
-    int n_cams = 0, W = 0, H = 0;
+    int n_cams = 0, n_batches = 1, W = 0, H = 0;
     size_t record_cap = 0, entry_cap = 0;
     void *buf = nullptr;                // one device allocation for everything
     gavis_camera *h_cams = nullptr;     // pinned staging of the poses
@@ -92,19 +94,23 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
 {
     if (!out) return GAVIS_ERR_ARG;
     *out = nullptr;
-    if (!gs || !vf || !p || !score || n_cams < 1 || n_cams > 1024 || W < 1 || H < 1 || W > 16384 || H > 16384 ||
-        entry_capacity < 1 || record_capacity < 0 || gs->n < 1 || gs->n >= ((int64_t)1 << 31) || !gs->sh || vf->n != gs->n ||
-        !(p->tile == 8 || p->tile == 16 || p->tile == 32) || ((uintptr_t)gs->rots & 15u)) {
+    if (!gs || !vf || !p || !score || n_cams < 1 || n_cams > 16384 || W < 1 || H < 1 || W > 16384 || H > 16384 ||
+        entry_capacity < 1 || record_capacity < 0 || gs->n < 1 || gs->n >= ((int64_t)1 << 31) || !gs->sh ||
+        vf->n != gs->n || !(p->tile == 8 || p->tile == 16 || p->tile == 32) || p->views_per_batch < 0 ||
+        ((uintptr_t)gs->rots & 15u)) {
         set_error(ctx, "gavis_plan_create: invalid argument (sizes, tile must be 8/16/32, rots 16-byte aligned)");
         return GAVIS_ERR_ARG;
     }
     const int64_t n = gs->n;
     const int TW = (W + p->tile - 1) / p->tile, TH = (H + p->tile - 1) / p->tile, TT = TW * TH;
-    const size_t nvn = (size_t)n_cams * (size_t)n, nvt = (size_t)n_cams * (size_t)TT;
+    // views per batch: every batch reuses the same buffers, one after another
+    const int B = p->views_per_batch > 0 && p->views_per_batch < n_cams ? p->views_per_batch : n_cams;
+    const int nb = (n_cams + B - 1) / B;
+    const size_t nvn = (size_t)B * (size_t)n, nvt = (size_t)B * (size_t)TT;
     const size_t M = (size_t)entry_capacity;
     const size_t R = record_capacity == 0 || (size_t)record_capacity > nvn ? nvn : (size_t)record_capacity;
     if (nvn >= ((size_t)1 << 32) || M >= ((size_t)1 << 32)) {
-        set_error(ctx, "gavis_plan_create: n_cams x n and entry_capacity must each be below 2^32");
+        set_error(ctx, "gavis_plan_create: views per batch x n and entry_capacity must each be below 2^32");
         return GAVIS_ERR_ARG;
     }
 
@@ -113,6 +119,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     bool capturing = false;
     PK(cudaGetDevice(&pl->device));
     pl->n_cams = n_cams;
+    pl->n_batches = nb;
     pl->W = W;
     pl->H = H;
     pl->record_cap = R;
@@ -121,7 +128,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     // static layout
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off += up256(b ? b : 1); return o; };
-    const size_t o_cams = take((size_t)n_cams * sizeof(gavis_camera)), o_info = take(sizeof(PlanInfo));
+    const size_t o_cams = take((size_t)n_cams * sizeof(gavis_camera)), o_info = take(nb * sizeof(PlanInfo));
     const size_t o_geo = take(nvn * sizeof(GeoRec)), o_ua = take(nvn * sizeof(UaRec)), o_rect = take(nvn * 8);
     const size_t o_cnt = take(nvn * 4), o_pos = take(nvn * 4), o_scan = take(scan_tmp_bytes(nvn) + 64);
     const size_t o_ak0 = take(R * 8), o_ak1 = take(R * 8), o_av0 = take(R * 4), o_av1 = take(R * 4);
@@ -153,7 +160,6 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     void *tmp = b + o_tmp, *scan_tmp = b + o_scan;
     uint2 *ranges = reinterpret_cast<uint2 *>(b + o_rng);
     float *tile_sums = reinterpret_cast<float *>(b + o_ts);
-    PlanInfo *info = pl->d_info;
 
     ProjectArgs pa{};
     pa.means = gs->means; pa.scales = gs->scales; pa.rots = gs->rots; pa.opac = gs->opac;
@@ -163,15 +169,12 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     pa.gamma = vf->coeffs; pa.vf_degree = vf->degree; pa.vf_dtype = vf->dtype; pa.n_train = vf->n_train_views;
     pa.q_cut = p->q_cut; pa.beta = p->beta; pa.o0 = p->o0;
     pa.tile = p->tile; pa.TW = TW; pa.TH = TH;
-    pa.cams = pl->d_cams; pa.nv = n_cams; pa.n = n;
+    pa.n = n;
     pa.geo = geo; pa.ua = ua; pa.rect = rect; pa.counts = counts;
-    pa.zrange = info->b.zrange;
-    pa.visible = &info->b.visible;
-    pa.total = &info->b.total;
     CompositeArgs ca;
     std::memset(&ca, 0, sizeof(ca));
     ca.ranges = ranges; ca.geo = geo; ca.ua = ua;
-    ca.n = n; ca.nv = n_cams; ca.v0 = 0; ca.W = W; ca.H = H; ca.tile = p->tile; ca.TW = TW; ca.TH = TH;
+    ca.n = n; ca.W = W; ca.H = H; ca.tile = p->tile; ca.TW = TW; ca.TH = TH;
     ca.rc.eps_T = p->eps_T; ca.rc.q_cut = p->q_cut; ca.rc.beta = p->beta; ca.rc.o0 = p->o0;
     const double l2pie = std::log(2.0 * M_PI) + 1.0;
     ca.rc.k_c = pa.k_c;
@@ -179,33 +182,44 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     ca.rgb = rgb; ca.unc = unc; ca.tile_sums = tile_sums;
     ca.per_entry_kc = gs->sh_var != nullptr;
 
-    // the chain, captured on a private stream
+    // the chain of every batch, captured on a private stream
     radix_prepare();
     PK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     const long long k0 = g_launches.load();
     PK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     capturing = true;
     PK(cudaMemcpyAsync(pl->d_cams, pl->h_cams, (size_t)n_cams * sizeof(gavis_camera), cudaMemcpyHostToDevice, cs));
-    PK(cudaMemsetAsync(info, 0, sizeof(PlanInfo), cs));
-    PK(cudaMemsetAsync(&info->b.zrange[0], 0xff, sizeof(uint32_t), cs));
-    PK(launch_project(pa, cs));
-    PK(exclusive_scan_u32(counts, pos, nvn, scan_tmp, nullptr, cs, true));
-    PK(launch_emit_records(counts, pos, geo, n_cams, n, 32, 0u, ak0, av0, cs, R, &info->records_over));
-    bool alt_a = false, alt_b = false;
-    PK(radix_sort_pairs<uint64_t>(ak0, av0, ak1, av1, R, bits_of((uint64_t)n_cams - 1) + 32, tmp, &alt_a, cs,
-                                  &info->b.visible));
-    const uint32_t *recs = alt_a ? av1 : av0;
-    PK(launch_gather_counts(recs, counts, R, acnt, cs, &info->b.visible));
-    PK(exclusive_scan_u32(acnt, aoff, R, tmp, nullptr, cs, false, &info->b.visible));
-    PK(launch_emit_tiles(recs, aoff, R, rect, n, TW, TH, bk0, bv0, cs, &info->b.visible, M, &info->entries_over));
-    PK(radix_sort_pairs<uint32_t>(bk0, bv0, bk1, bv1, M, bits_of((uint64_t)nvt - 1), tmp, &alt_b, cs,
-                                  &info->b.total));
-    const uint32_t *keys = alt_b ? bk1 : bk0;
-    ca.vals = alt_b ? bv1 : bv0;
-    PK(cudaMemsetAsync(ranges, 0, nvt * sizeof(uint2), cs));
-    PK(launch_ranges(keys, M, ranges, cs, &info->b.total));
-    PK(launch_composite_ua(ca, cs));
-    PK(launch_view_reduce(tile_sums, n_cams, TT, 1.0f / ((float)W * (float)H), score, cs));
+    PK(cudaMemsetAsync(pl->d_info, 0, nb * sizeof(PlanInfo), cs));
+    for (int bi = 0; bi < nb; ++bi) {
+        const int v0 = bi * B, nv = n_cams - v0 < B ? n_cams - v0 : B;
+        const size_t nvn_b = (size_t)nv * (size_t)n, nvt_b = (size_t)nv * (size_t)TT;
+        PlanInfo *info = pl->d_info + bi;
+        pa.cams = pl->d_cams + v0; pa.nv = nv;
+        pa.zrange = info->b.zrange;
+        pa.visible = &info->b.visible;
+        pa.total = &info->b.total;
+        ca.nv = nv; ca.v0 = v0;
+        PK(cudaMemsetAsync(&info->b.zrange[0], 0xff, sizeof(uint32_t), cs));
+        PK(launch_project(pa, cs));
+        PK(exclusive_scan_u32(counts, pos, nvn_b, scan_tmp, nullptr, cs, true));
+        PK(launch_emit_records(counts, pos, geo, nv, n, 32, 0u, ak0, av0, cs, R, &info->records_over));
+        bool alt_a = false, alt_b = false;
+        PK(radix_sort_pairs<uint64_t>(ak0, av0, ak1, av1, R, bits_of((uint64_t)nv - 1) + 32, tmp, &alt_a, cs,
+                                      &info->b.visible));
+        const uint32_t *recs = alt_a ? av1 : av0;
+        PK(launch_gather_counts(recs, counts, R, acnt, cs, &info->b.visible));
+        PK(exclusive_scan_u32(acnt, aoff, R, tmp, nullptr, cs, false, &info->b.visible));
+        PK(launch_emit_tiles(recs, aoff, R, rect, n, TW, TH, bk0, bv0, cs, &info->b.visible, M,
+                             &info->entries_over));
+        PK(radix_sort_pairs<uint32_t>(bk0, bv0, bk1, bv1, M, bits_of((uint64_t)nvt_b - 1), tmp, &alt_b, cs,
+                                      &info->b.total));
+        const uint32_t *keys = alt_b ? bk1 : bk0;
+        ca.vals = alt_b ? bv1 : bv0;
+        PK(cudaMemsetAsync(ranges, 0, nvt_b * sizeof(uint2), cs));
+        PK(launch_ranges(keys, M, ranges, cs, &info->b.total));
+        PK(launch_composite_ua(ca, cs));
+        PK(launch_view_reduce(tile_sums, nv, TT, 1.0f / ((float)W * (float)H), score + v0, cs));
+    }
     if (best_dev) PK(launch_argmax(score, n_cams, best_dev, cs));
     PK(cudaStreamEndCapture(cs, &pl->graph));
     capturing = false;
@@ -241,13 +255,19 @@ int gavis_plan_overflowed(gavis_plan *pl, int *overflowed, int64_t *records_need
 {
     if (!pl) return GAVIS_ERR_ARG;
     if (pl->launched && cudaEventSynchronize(pl->done) != cudaSuccess) return GAVIS_ERR_CUDA;
-    PlanInfo h;
-    if (cudaMemcpy(&h, pl->d_info, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return GAVIS_ERR_CUDA;
-    const bool over = h.entries_over != 0u || h.records_over != 0u || h.b.total > pl->entry_cap ||
-                      h.b.visible > pl->record_cap;
+    bool over = false;
+    unsigned long long rec = 0, ent = 0;
+    for (int bi = 0; bi < pl->n_batches; ++bi) {   // the largest batch decides
+        PlanInfo h;
+        if (cudaMemcpy(&h, pl->d_info + bi, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return GAVIS_ERR_CUDA;
+        over = over || h.entries_over != 0u || h.records_over != 0u || h.b.total > pl->entry_cap ||
+               h.b.visible > pl->record_cap;
+        rec = h.b.visible > rec ? h.b.visible : rec;
+        ent = h.b.total > ent ? h.b.total : ent;
+    }
     if (overflowed) *overflowed = pl->launched ? (int)over : 0;
-    if (records_needed) *records_needed = pl->launched ? (int64_t)h.b.visible : 0;
-    if (entries_needed) *entries_needed = pl->launched ? (int64_t)h.b.total : 0;
+    if (records_needed) *records_needed = pl->launched ? (int64_t)rec : 0;
+    if (entries_needed) *entries_needed = pl->launched ? (int64_t)ent : 0;
     return GAVIS_OK;
 }
 

@@ -158,3 +158,24 @@ def test_plan_rejects_bad_arguments(ctx, gv):
     with pytest.raises(gv.GavisError):
         plan.launch(other)
     plan.close()
+
+
+def test_plan_in_view_batches(ctx, gv):
+    """views_per_batch: the views go through the captured chain in batches
+    over the same buffers (here 4 + 4 + 2); results equal gavis_score_views',
+    and the capacities apply per batch."""
+    c, gs, vf = setup(gv, ctx, n=20000, n_train=4, n_cand=10, train_wh=(160, 120), cand_wh=(160, 120))
+    cand = c["cand"]
+    p = gv.Params(tile=16, vf_degree=c["vf_degree"], views_per_batch=4)
+    rec, keys = needed(gv, ctx, gs, vf, cand, gv.Params(tile=16, vf_degree=c["vf_degree"]))
+    plan = ctx.plan(gs, vf, len(cand), 160, 120, keys, record_capacity=rec, params=p, want_rgb=True, want_unc=True)
+    plan.launch(cand)
+    over, rec_b, keys_b = plan.overflowed()
+    assert not over and 0 < rec_b < rec and 0 < keys_b < keys   # the largest batch needs less than all views
+    assert_same(plan, ctx.score_views(gs, vf, cand, params=gv.Params(tile=16, vf_degree=c["vf_degree"])))
+    tight = ctx.plan(gs, vf, len(cand), 160, 120, keys_b, record_capacity=rec_b, params=p)
+    tight.launch(cand)
+    assert tight.overflowed() == (False, rec_b, keys_b)
+    assert torch.equal(tight.score, plan.score)
+    plan.close()
+    tight.close()
