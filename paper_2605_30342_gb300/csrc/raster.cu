@@ -77,6 +77,13 @@ __device__ __forceinline__ bool ellipse_misses(float u, float v, float A, float 
     return m > fmaf(smax, 1.52587890625e-5f, qcut * (1.0f + 9.765625e-4f));
 }
 
+// L2 prefetch of the record a chunk will gather next (its address is known
+// one chunk ahead; the gather itself then finds it in L2)
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ float footprint_q(float px, float py, float u, float v, float A, float B2, float C)
 {
     const float dx = __fsub_rn(px, u), dy = __fsub_rn(py, v);
@@ -261,14 +268,18 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
     float4 *u0s = s_u0[warp];
     float2 *u1s = s_u1[warp];
 
+    uint32_t nval = rg.x + lane < rg.y ? a.vals[rg.x + lane] : 0u;   // this lane's entry of the next chunk
     for (uint32_t base = rg.x; base < rg.y; base += 32) {
         if (!__any_sync(0xffffffffu, ua_on[0] || rgb_on[0] || ua_on[1] || rgb_on[1])) break;
         const uint32_t e = base + lane;
+        const uint32_t val = nval;
+        const bool more = e + 32 < rg.y;
+        if (more) nval = a.vals[e + 32];
         bool mine = false;
         GeoRec gr;
         size_t r = 0;
         if (e < rg.y) {
-            r = vrow + a.vals[e];
+            r = vrow + val;
             gr = a.geo[r];
             mine = !box_misses(footprint_box(gr.a.x, gr.a.y, gr.b.w), bx0, bx1, by0, by1) &&
                    !ellipse_misses(gr.a.x, gr.a.y, gr.a.z, gr.a.w, gr.b.x, bx0, bx1, by0, by1, rc.q_cut);
@@ -285,6 +296,10 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
             if (DEPTH) zs[slot] = gr.b.z;
         }
         __syncwarp();
+        if (more) {
+            prefetch_l2(a.geo + vrow + nval);
+            prefetch_l2(a.ua + vrow + nval);
+        }
         const int nk = __popc(m);
         for (int k = 0; k < nk && (ua_on[0] || rgb_on[0] || ua_on[1] || rgb_on[1]); ++k) {
             const float4 g0 = g0s[k];
