@@ -251,11 +251,12 @@ struct RecLayout {
     UaRec *ua;
     uint2 *rect;
     uint32_t *counts;
+    uint32_t *vis_words, *woff;   // [nv][ceil(n/32)] visibility bits and their record offsets
     void *scan_tmp;
     size_t bytes;
 };
 
-RecLayout rec_layout(void *base, size_t nvn, bool ua)
+RecLayout rec_layout(void *base, size_t nvn, bool ua, size_t nwords)
 {
     RecLayout L;
     char *p = reinterpret_cast<char *>(base);
@@ -265,7 +266,9 @@ RecLayout rec_layout(void *base, size_t nvn, bool ua)
     L.ua = ua ? reinterpret_cast<UaRec *>(take(nvn * sizeof(UaRec))) : nullptr;
     L.rect = reinterpret_cast<uint2 *>(take(nvn * sizeof(uint2)));
     L.counts = reinterpret_cast<uint32_t *>(take(nvn * sizeof(uint32_t)));
-    L.scan_tmp = take(scan_tmp_bytes(nvn) + 64);
+    L.vis_words = reinterpret_cast<uint32_t *>(take(nwords * sizeof(uint32_t)));
+    L.woff = reinterpret_cast<uint32_t *>(take(nwords * sizeof(uint32_t)));
+    L.scan_tmp = take(scan_tmp_bytes(nwords) + 64);
     L.bytes = off;
     return L;
 }
@@ -384,9 +387,10 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     const size_t nvt = (size_t)nv * (size_t)G.TT;
     int rc;
 
-    RecLayout RL = rec_layout(nullptr, nvn, mode == MODE_SCORE);
+    const size_t nwords = (size_t)nv * (size_t)((n + 31) / 32);
+    RecLayout RL = rec_layout(nullptr, nvn, mode == MODE_SCORE, nwords);
     if ((rc = ensure(ctx, ctx->rec, RL.bytes)) != GAVIS_OK) return rc;
-    RL = rec_layout(ctx->rec.p, nvn, mode == MODE_SCORE);
+    RL = rec_layout(ctx->rec.p, nvn, mode == MODE_SCORE, nwords);
     SmallLayout SL = small_layout(nullptr, nvt, (size_t)nv);
     if ((rc = ensure(ctx, ctx->small, SL.bytes)) != GAVIS_OK) return rc;
     SL = small_layout(ctx->small.p, nvt, (size_t)nv);
@@ -412,6 +416,7 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     pa.tile = p->tile; pa.TW = G.TW; pa.TH = G.TH;
     pa.cams = d_cams + v0; pa.nv = nv; pa.n = n;
     pa.geo = RL.geo; pa.ua = RL.ua; pa.rect = RL.rect; pa.counts = RL.counts;
+    pa.vis_words = RL.vis_words;
     pa.zrange = SL.info->zrange;
     pa.visible = &SL.info->visible;
     pa.total = &SL.info->total;
@@ -422,9 +427,9 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
         CK(launch_project(pa, s));
     }
     {
-        // block sums of the visibility flags, in (view, index) order
+        // record offsets of the visibility words, in (view, index) order
         Stage st(ctx, GAVIS_STAGE_SCAN, s);
-        CK(scan_flags_reduce(RL.counts, nvn, RL.scan_tmp, s));
+        CK(scan_vis_words(RL.vis_words, nwords, RL.woff, RL.scan_tmp, s));
     }
     CK(cudaMemcpyAsync(ctx->h_info, SL.info, sizeof(BatchInfo), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -446,15 +451,15 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     // gb + zb <= 32 (depth bits of positive floats span zb <= 31 bits); the
     // groups of 2^gb views are sorted one after another, each over its
     // contiguous range of records (records are emitted in view order).  The
-    // keys are written by the apply step of the visibility-flag scan.
+    // keys are written from the visibility bits the projection leaves.
     const int vb = bits_of((uint64_t)nv - 1);
     const int gb = vb + zb <= 32 ? vb : 32 - zb;
     const int gsz_a = 1 << gb;
     uint32_t *k0 = reinterpret_cast<uint32_t *>(KL.a_k0), *k1 = reinterpret_cast<uint32_t *>(KL.a_k1);
     {
         Stage st(ctx, GAVIS_STAGE_EMIT, s);
-        CK(scan_flags_emit(RL.counts, nvn, RL.scan_tmp, RL.geo, n, zb, zmin, (uint32_t)(gsz_a - 1), k0, KL.a_v0,
-                           SL.voff, s));
+        CK(emit_vis_words(RL.vis_words, RL.woff, nv, n, RL.geo, zb, zmin, (uint32_t)(gsz_a - 1), k0, KL.a_v0,
+                          SL.voff, s));
     }
     if (gsz_a < nv) {   // group boundaries: a second read-back
         CK(cudaMemcpyAsync(ctx->h_voff, SL.voff, ((size_t)nv + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));

@@ -66,7 +66,8 @@ struct ProjectArgs {
     GeoRec *geo;
     UaRec *ua;              // NULL for the visibility pass
     uint2 *rect;
-    uint32_t *counts;
+    uint32_t *counts;       // tile count of each visible record (and 0 for culled ones unless vis_words is given)
+    uint32_t *vis_words;    // [nv][ceil(n/32)] visibility bits (bit g%32 of word g/32), or NULL
     uint32_t *zrange;       // [2] min and max depth bits of visible records (atomic)
     unsigned long long *visible;   // count of visible records (atomic)
     unsigned long long *total;     // count of tile entries (atomic)
@@ -94,16 +95,16 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, void
                                unsigned long long *d_total, cudaStream_t s, bool flags = false,
                                const unsigned long long *d_n = nullptr);
 
-// Scan of the visibility flags (counts[r] != 0, r < total = views x n)
-// fused with stage A's emission: scan_flags_reduce computes the block
-// partials into tmp (scan_tmp_bytes(total)); scan_flags_emit then writes, for
-// every visible record r = v n + g at its position p among the visible
-// records, keyA[p] = ((v & vmask) << zb) | (depth bits - zmin) and
-// valA[p] = r, and voff[v] = visible records before view v (v = 0..views).
-cudaError_t scan_flags_reduce(const uint32_t *counts, size_t total, void *tmp, cudaStream_t s);
-cudaError_t scan_flags_emit(const uint32_t *counts, size_t total, const void *tmp, const GeoRec *geo, int64_t n,
-                            int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA, uint32_t *valA, uint32_t *voff,
-                            cudaStream_t s);
+// Stage A from the visibility bits (nv views x nw words, nw = ceil(n/32)):
+// scan_vis_words writes woff[w] = visible records before word w (tmp:
+// scan_tmp_bytes(nv * nw)); emit_vis_words then writes, for every visible
+// record r = v n + g at its position p among the visible records,
+// keyA[p] = ((v & vmask) << zb) | (depth bits - zmin) and valA[p] = r, and
+// voff[v] = visible records before view v (v = 0..nv).
+cudaError_t scan_vis_words(const uint32_t *words, size_t nwords, uint32_t *woff, void *tmp, cudaStream_t s);
+cudaError_t emit_vis_words(const uint32_t *words, const uint32_t *woff, int nv, int64_t n, const GeoRec *geo,
+                           int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA, uint32_t *valA, uint32_t *voff,
+                           cudaStream_t s);
 
 // stable LSD radix sort of (keys, vals) on bits [0, end_bit); ping-pong
 // buffers; *result_in_alt tells which buffer holds the result.  KeyT is

@@ -161,13 +161,19 @@ __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
     }
     const float P = (float)a.n_train;
     uint32_t zlo = 0xffffffffu, zhi = 0u, nvis = 0u, ntiles = 0u;
+    const unsigned am0 = __activemask();   // the warp's lanes with g < n; each runs every view iteration
 
     for (int v = 0; v < a.nv; ++v) {
         const gavis_camera &cam = s_cams[v];
         const Proj p = project_one(cam, mx, my, mz, S, a.q_cut, rb, a.TW, a.TH);
         const size_t r = (size_t)v * (size_t)a.n + (size_t)g;
+        if (a.vis_words) {   // one visibility word per warp (32 consecutive Gaussians) and view
+            const unsigned bal = __ballot_sync(am0, p.status == 1);
+            if ((threadIdx.x & 31) == (unsigned)(__ffs(am0) - 1))
+                a.vis_words[(size_t)v * (size_t)((a.n + 31) >> 5) + (size_t)(g >> 5)] = bal;
+        }
         if (p.status != 1) {
-            a.counts[r] = 0u;
+            if (!a.vis_words) a.counts[r] = 0u;
             continue;
         }
         const uint32_t nt = (uint32_t)((p.x1 - p.x0 + 1) * (p.y1 - p.y0 + 1));

@@ -135,65 +135,32 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *in,
     }
 }
 
-// Apply step of the scan of the visibility flags (counts[r] != 0), fused
-// with stage A's emission: visible record r = v n + g (r < 2^32) gets
-// position p = (visible records before r), key ((v & vmask) << zb) |
-// (depth bits - zmin) and value r; voff[v] = visible records before view v,
-// voff[nv] = all of them.
-__global__ void __launch_bounds__(kScanThreads) k_scan_emit(const uint32_t *counts, uint32_t total,
-                                                            const unsigned long long *partials, const GeoRec *geo,
-                                                            uint32_t n, int zb, uint32_t zmin, uint32_t vmask,
-                                                            uint32_t *keyA, uint32_t *valA, uint32_t *voff)
+__global__ void k_popc_words(const uint32_t *words, size_t nwords, uint32_t *cnt)
 {
-    __shared__ uint32_t s_warp[32];
-    if ((size_t)blockIdx.x * kScanChunk >= total) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t base = blockIdx.x * (uint32_t)kScanChunk + threadIdx.x * (uint32_t)kScanItems;
-    uint32_t x[kScanItems];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int r = 0; r < kScanItems; ++r) {
-        const uint32_t i = base + r;
-        x[r] = i < total ? (uint32_t)(counts[i] != 0u) : 0u;
-        sum += x[r];
-    }
-    uint32_t inc = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_warp[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = s_warp[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        s_warp[lane] = w;
-    }
-    __syncthreads();
-    uint32_t run = (uint32_t)partials[blockIdx.x] + (warp ? s_warp[warp - 1] : 0u) + inc - sum;
-    if (base >= total) return;
-    uint32_t v = base / n;              // view of the first item; advanced at view boundaries
-    uint32_t vstart = v * n;
-#pragma unroll
-    for (int r = 0; r < kScanItems; ++r) {
-        const uint32_t i = base + r;
-        if (i >= total) break;
-        if (i - vstart >= n) {
-            ++v;
-            vstart += n;
-        }
-        if (i == vstart) voff[v] = run;
-        if (x[r]) {
-            keyA[run] = ((v & vmask) << zb) | (__float_as_uint(geo[i].b.z) - zmin);
-            valA[run] = i;
-        }
-        run += x[r];
-        if (i == total - 1) voff[v + 1] = run;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nwords) cnt[i] = (uint32_t)__popc(words[i]);
+}
+
+// One thread per visibility word (32 Gaussians of one view): its set bits
+// become consecutive records from woff[w] on, in index order.
+__global__ void k_emit_vis_words(const uint32_t *words, const uint32_t *woff, uint32_t nv, uint32_t nw, uint32_t n,
+                                 const GeoRec *geo, int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA,
+                                 uint32_t *valA, uint32_t *voff)
+{
+    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nv * nw) return;
+    const uint32_t v = w / nw, wi = w - v * nw;
+    uint32_t bits = words[w], off = woff[w];
+    if (wi == 0) voff[v] = off;
+    if (w == nv * nw - 1) voff[nv] = off + (uint32_t)__popc(bits);
+    const uint32_t vkey = (v & vmask) << zb;
+    while (bits) {
+        const uint32_t b = (uint32_t)__ffs(bits) - 1u;
+        bits &= bits - 1u;
+        const uint32_t r = v * n + wi * 32u + b;
+        keyA[off] = vkey | (__float_as_uint(geo[r].b.z) - zmin);
+        valA[off] = r;
+        ++off;
     }
 }
 
@@ -390,26 +357,23 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, void
     return cudaGetLastError();
 }
 
-cudaError_t scan_flags_reduce(const uint32_t *counts, size_t total, void *tmp, cudaStream_t s)
+cudaError_t scan_vis_words(const uint32_t *words, size_t nwords, uint32_t *woff, void *tmp, cudaStream_t s)
 {
-    if (total == 0) return cudaSuccess;
-    const size_t nb = (total + kScanChunk - 1) / kScanChunk;
-    unsigned long long *partials = reinterpret_cast<unsigned long long *>(tmp);
-    k_scan_reduce<true><<<(unsigned)nb, kScanThreads, 0, s>>>(counts, total, partials, nullptr); count_launch();
-    k_scan_partials<<<1, kScanThreads, 0, s>>>(partials, (int)nb, nullptr); count_launch();
-    return cudaGetLastError();
+    if (nwords == 0) return cudaSuccess;
+    k_popc_words<<<(unsigned)((nwords + 255) / 256), 256, 0, s>>>(words, nwords, woff); count_launch();
+    return exclusive_scan_u32(woff, woff, nwords, tmp, nullptr, s);
 }
 
-cudaError_t scan_flags_emit(const uint32_t *counts, size_t total, const void *tmp, const GeoRec *geo, int64_t n,
-                            int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA, uint32_t *valA, uint32_t *voff,
-                            cudaStream_t s)
+cudaError_t emit_vis_words(const uint32_t *words, const uint32_t *woff, int nv, int64_t n, const GeoRec *geo,
+                           int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA, uint32_t *valA, uint32_t *voff,
+                           cudaStream_t s)
 {
-    if (total == 0) return cudaSuccess;
-    if (total >= ((size_t)1 << 32) || n <= 0 || zb < 0 || zb > 31) return cudaErrorInvalidValue;
-    const size_t nb = (total + kScanChunk - 1) / kScanChunk;
-    const unsigned long long *partials = reinterpret_cast<const unsigned long long *>(tmp);
-    k_scan_emit<<<(unsigned)nb, kScanThreads, 0, s>>>(counts, (uint32_t)total, partials, geo, (uint32_t)n, zb, zmin,
-                                                      vmask, keyA, valA, voff);
+    if (nv <= 0 || n <= 0) return cudaSuccess;
+    if ((size_t)nv * (size_t)n >= ((size_t)1 << 32) || zb < 0 || zb > 31) return cudaErrorInvalidValue;
+    const uint32_t nw = (uint32_t)((n + 31) / 32);
+    const size_t total = (size_t)nv * nw;
+    k_emit_vis_words<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(words, woff, (uint32_t)nv, nw, (uint32_t)n, geo,
+                                                                     zb, zmin, vmask, keyA, valA, voff);
     count_launch();
     return cudaGetLastError();
 }
