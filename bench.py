@@ -521,6 +521,27 @@ def run_gavis(args):
         dist.destroy_process_group()
 
 
+def kernel_source_sha(path, kernel):
+    """sha256 (16 hex digits) of a kernel's definition: from the line that
+    names it with '(CompositeArgs' or '(' up to its closing brace."""
+    import hashlib
+    text = open(path).read()
+    i = text.find(kernel + "(")
+    while i >= 0 and text.find("{", i) > text.find(";", i):   # skip declarations and calls
+        i = text.find(kernel + "(", i + 1)
+    if i < 0:
+        return None
+    start = text.rfind("\n", 0, text.rfind("template", 0, i)) + 1 if "template" in text[max(0, i - 200):i] else \
+        text.rfind("\n", 0, i) + 1
+    j = text.find("{", i)
+    depth = 0
+    for k in range(j, len(text)):
+        depth += {"{": 1, "}": -1}.get(text[k], 0)
+        if depth == 0:
+            return hashlib.sha256(text[start:k + 1].encode()).hexdigest()[:16]
+    return None
+
+
 def traffic_for(kernel):
     """DRAM bytes per launch from the committed ncu summary, when it was taken
     on the current source of the kernel (else null)."""
@@ -533,10 +554,8 @@ def traffic_for(kernel):
         e = d.get(kernel)
         if not e:
             return None
-        import hashlib
         src = os.path.join(ROOT, "paper_2605_30342_gb300", "csrc", e["source"])
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        return e["bytes_per_launch"] if h == e.get("source_sha") else None
+        return e["bytes_per_launch"] if kernel_source_sha(src, kernel) == e.get("kernel_sha") else None
     except Exception:
         return None
 
