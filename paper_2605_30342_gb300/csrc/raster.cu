@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
 {
     constexpr int NT = TILE * TILE / 2;
     constexpr int NW = NT / 32;
+    static_assert((TILE / 8) * (TILE / 8) == NW, "one warp per 8 x 8 pixel block");
     __shared__ float4 s_g0[NW][32];   // u, v, A, 2B
     __shared__ float2 s_g1[NW][32];   // C, opacity
     __shared__ float4 s_u0[NW][32];   // a1, a0, V, r
@@ -753,10 +754,11 @@ cudaError_t launch_composite_vis(const CompositeArgs &a, cudaStream_t s)
 {
     const unsigned blocks = (unsigned)(a.nv * a.TW * a.TH);
     if (blocks == 0) return cudaSuccess;
+    // one thread per two pixels of the tile, as the kernel is written for
     switch (a.tile) {
-    case 8: k_composite_vis<8><<<blocks, 32, 0, s>>>(a); count_launch(); break;
-    case 16: k_composite_vis<16><<<blocks, 128, 0, s>>>(a); count_launch(); break;
-    case 32: k_composite_vis<32><<<blocks, 512, 0, s>>>(a); count_launch(); break;
+    case 8: k_composite_vis<8><<<blocks, 8 * 8 / 2, 0, s>>>(a); count_launch(); break;
+    case 16: k_composite_vis<16><<<blocks, 16 * 16 / 2, 0, s>>>(a); count_launch(); break;
+    case 32: k_composite_vis<32><<<blocks, 32 * 32 / 2, 0, s>>>(a); count_launch(); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
