@@ -168,11 +168,16 @@ __global__ void k_ranges(const uint32_t *keys, size_t M, uint2 *ranges, const un
 {
     if (d_M && *d_M < M) M = (size_t)*d_M;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned lane = threadIdx.x & 31u;
+    // neighbours from the adjacent lanes; the warp's two edge lanes load theirs
+    const uint32_t t = i < M ? keys[i] : 0xffffffffu;
+    uint32_t prev = __shfl_up_sync(0xffffffffu, t, 1), next = __shfl_down_sync(0xffffffffu, t, 1);
     if (i >= M) return;
-    const uint32_t t = keys[i];
+    if (lane == 0 && i > 0) prev = keys[i - 1];
+    if (lane == 31 && i + 1 < M) next = keys[i + 1];
     const uint32_t ti = tile_index(t, tb, TT);
-    if (i == 0 || keys[i - 1] != t) ranges[ti].x = (uint32_t)i;
-    if (i == M - 1 || keys[i + 1] != t) ranges[ti].y = (uint32_t)(i + 1);
+    if (i == 0 || prev != t) ranges[ti].x = (uint32_t)i;
+    if (i == M - 1 || next != t) ranges[ti].y = (uint32_t)(i + 1);
 }
 
 __global__ void k_keys_export(const uint32_t *keyB, const uint32_t *valB, size_t M, const GeoRec *geo, int64_t n,
