@@ -138,29 +138,59 @@ __device__ __forceinline__ uint32_t tile_index(uint32_t key, int tb, uint32_t TT
     return tb < 0 ? key : (key >> tb) * TT + (key & ((1u << tb) - 1u));
 }
 
-// stage B: the tiles of each record, in stage-A order
+// stage B: the tiles of each record, in stage-A order.  A warp takes 32
+// consecutive records, whose entries are contiguous; its lanes write those
+// entries in order, lane j of a round finding its record by a binary search
+// over the warp's prefix counts, so the stores are coalesced.
 __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect, int64_t n,
                              int TW, int TH, uint32_t *keyB, uint32_t *valB, const unsigned long long *d_nrec,
                              size_t cap_M, uint32_t *overflow, int tb)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nrec || (d_nrec && i >= (size_t)*d_nrec)) return;
-    const uint32_t r = valA[i];
-    const uint32_t v = (uint32_t)(r / (uint64_t)n);
-    const uint32_t g = (uint32_t)(r - (uint64_t)v * (uint64_t)n);
-    const uint2 rc = rect[r];
-    const uint32_t x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu, y1 = rc.y >> 16;
-    const uint32_t vbase = tb < 0 ? v * (uint32_t)(TW * TH) : v << tb;
-    uint32_t off = off_sorted[i];
-    if ((size_t)off + (size_t)((x1 - x0 + 1) * (y1 - y0 + 1)) > cap_M && overflow) *overflow = 1u;
-    for (uint32_t ty = y0; ty <= y1; ++ty)
-        for (uint32_t tx = x0; tx <= x1; ++tx) {
-            if ((size_t)off < cap_M) {
-                keyB[off] = vbase + ty * (uint32_t)TW + tx;
-                valB[off] = g;
-            }
-            ++off;
+    const int lane = (int)(threadIdx.x & 31u);
+    size_t live = nrec;
+    if (d_nrec && (size_t)*d_nrec < live) live = (size_t)*d_nrec;
+    uint32_t g = 0, vbase = 0, x0 = 0, y0 = 0, w = 1, cnt = 0, off = 0;
+    if (i < live) {
+        const uint32_t r = valA[i];
+        const uint32_t v = (uint32_t)(r / (uint64_t)n);
+        g = (uint32_t)(r - (uint64_t)v * (uint64_t)n);
+        const uint2 rc = rect[r];
+        x0 = rc.x & 0xffffu;
+        y0 = rc.y & 0xffffu;
+        w = (rc.x >> 16) - x0 + 1u;
+        cnt = w * ((rc.y >> 16) - y0 + 1u);
+        vbase = tb < 0 ? v * (uint32_t)(TW * TH) : v << tb;
+        off = off_sorted[i];
+        if ((size_t)off + cnt > cap_M && overflow) *overflow = 1u;
+    }
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const uint32_t excl = inc - cnt;
+    const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+    const uint32_t base = __shfl_sync(0xffffffffu, off, 0);   // the valid lanes are a prefix of the warp
+    for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+        const uint32_t j = j0 + (uint32_t)lane;
+        int k = 0;   // last lane whose entries start at or before j
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t e = __shfl_sync(0xffffffffu, excl, k + step);
+            if (e <= j) k += step;
         }
+        const uint32_t ek = __shfl_sync(0xffffffffu, excl, k), wk = __shfl_sync(0xffffffffu, w, k);
+        const uint32_t xk = __shfl_sync(0xffffffffu, x0, k), yk = __shfl_sync(0xffffffffu, y0, k);
+        const uint32_t bk = __shfl_sync(0xffffffffu, vbase, k), gk = __shfl_sync(0xffffffffu, g, k);
+        const size_t pos = (size_t)base + j;
+        if (j < total && pos < cap_M) {
+            const uint32_t m = j - ek, ty = m / wk, tx = m - ty * wk;
+            keyB[pos] = bk + (yk + ty) * (uint32_t)TW + xk + tx;
+            valB[pos] = gk;
+        }
+    }
 }
 
 __global__ void k_ranges(const uint32_t *keys, size_t M, uint2 *ranges, const unsigned long long *d_M, int tb,
