@@ -141,26 +141,53 @@ __global__ void k_popc_words(const uint32_t *words, size_t nwords, uint32_t *cnt
     if (i < nwords) cnt[i] = (uint32_t)__popc(words[i]);
 }
 
-// One thread per visibility word (32 Gaussians of one view): its set bits
-// become consecutive records from woff[w] on, in index order.
+// One thread per visibility word (32 Gaussians of one view); a warp's words
+// are consecutive and so are their records, which the warp's lanes write in
+// order (coalesced): lane j of a round finds its word by a binary search over
+// the warp's prefix popcounts, then its set bit.
 __global__ void k_emit_vis_words(const uint32_t *words, const uint32_t *woff, uint32_t nv, uint32_t nw, uint32_t n,
                                  const GeoRec *geo, int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA,
                                  uint32_t *valA, uint32_t *voff)
 {
     const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= nv * nw) return;
-    const uint32_t v = w / nw, wi = w - v * nw;
-    uint32_t bits = words[w], off = woff[w];
-    if (wi == 0) voff[v] = off;
-    if (w == nv * nw - 1) voff[nv] = off + (uint32_t)__popc(bits);
-    const uint32_t vkey = (v & vmask) << zb;
-    while (bits) {
-        const uint32_t b = (uint32_t)__ffs(bits) - 1u;
-        bits &= bits - 1u;
-        const uint32_t r = v * n + wi * 32u + b;
-        keyA[off] = vkey | (__float_as_uint(geo[r].b.z) - zmin);
-        valA[off] = r;
-        ++off;
+    const int lane = (int)(threadIdx.x & 31u);
+    const uint32_t total_words = nv * nw;
+    uint32_t bits = 0, off = 0, v = 0, wi = 0;
+    if (w < total_words) {
+        v = w / nw;
+        wi = w - v * nw;
+        bits = words[w];
+        off = woff[w];
+        if (wi == 0) voff[v] = off;
+        if (w == total_words - 1) voff[nv] = off + (uint32_t)__popc(bits);
+    }
+    const uint32_t cnt = (uint32_t)__popc(bits);
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const uint32_t excl = inc - cnt;
+    const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+    const uint32_t base = __shfl_sync(0xffffffffu, off, 0);   // the valid lanes are a prefix of the warp
+    for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+        const uint32_t j = j0 + (uint32_t)lane;
+        int k = 0;   // last lane whose records start at or before j
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t e = __shfl_sync(0xffffffffu, excl, k + step);
+            if (e <= j) k += step;
+        }
+        const uint32_t ek = __shfl_sync(0xffffffffu, excl, k);
+        uint32_t bk = __shfl_sync(0xffffffffu, bits, k);
+        const uint32_t vk = __shfl_sync(0xffffffffu, v, k), wik = __shfl_sync(0xffffffffu, wi, k);
+        if (j < total) {
+            for (uint32_t m = j - ek; m > 0; --m) bk &= bk - 1u;   // drop the set bits before this record's
+            const uint32_t r = vk * n + wik * 32u + (uint32_t)(__ffs(bk) - 1);
+            keyA[base + j] = ((vk & vmask) << zb) | (__float_as_uint(geo[r].b.z) - zmin);
+            valA[base + j] = r;
+        }
     }
 }
 
