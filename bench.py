@@ -509,6 +509,9 @@ def run_gavis(args):
             "latency_ms": {"p50": percentile(step_ms, 50), "p99": percentile(step_ms, 99), "what": "one step"},
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in st.items()},
             "pairs_per_step": {"uncertainty": pairs_ua // args.steps, "visibility": pairs_vis // args.steps},
+            "pairs_per_s": {"uncertainty": pairs_ua / (st["composite_ua"][0] / 1e3) if st["composite_ua"][0] else None,
+                            "visibility": pairs_vis / (st["composite_vis"][0] / 1e3) if st["composite_vis"][0] else None,
+                            "what": "pixel-Gaussian pairs composited per second of the composite kernels"},
             "tile_keys_per_step": prof["keys"] // args.steps,
             "hbm": hbm,
             "plain_unbatched_f32": plain,
