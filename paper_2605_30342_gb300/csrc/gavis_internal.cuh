@@ -105,6 +105,10 @@ cudaError_t scan_vis_words(const uint32_t *words, size_t nwords, uint32_t *woff,
 cudaError_t emit_vis_words(const uint32_t *words, const uint32_t *woff, int nv, int64_t n, const GeoRec *geo,
                            int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA, uint32_t *valA, uint32_t *voff,
                            cudaStream_t s);
+// The same with 64-bit keys (view << 32) | depth bits, for chains that cannot
+// size the sort on the host; records past cap_R are dropped and set *overflow.
+cudaError_t emit_vis_words64(const uint32_t *words, const uint32_t *woff, int nv, int64_t n, const GeoRec *geo,
+                             uint64_t *keyA, uint32_t *valA, size_t cap_R, uint32_t *overflow, cudaStream_t s);
 
 // stable LSD radix sort of (keys, vals) on bits [0, end_bit); ping-pong
 // buffers; *result_in_alt tells which buffer holds the result.  KeyT is

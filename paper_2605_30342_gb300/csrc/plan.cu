@@ -130,7 +130,9 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     auto take = [&](size_t b) { size_t o = off; off += up256(b ? b : 1); return o; };
     const size_t o_cams = take((size_t)n_cams * sizeof(gavis_camera)), o_info = take(nb * sizeof(PlanInfo));
     const size_t o_geo = take(nvn * sizeof(GeoRec)), o_ua = take(nvn * sizeof(UaRec)), o_rect = take(nvn * 8);
-    const size_t o_cnt = take(nvn * 4), o_pos = take(nvn * 4), o_scan = take(scan_tmp_bytes(nvn) + 64);
+    const size_t nwords = (size_t)B * (size_t)((n + 31) / 32);
+    const size_t o_cnt = take(nvn * 4), o_words = take(nwords * 4), o_woff = take(nwords * 4);
+    const size_t o_scan = take(scan_tmp_bytes(nwords) + 64);
     const size_t o_ak0 = take(R * 8), o_ak1 = take(R * 8), o_av0 = take(R * 4), o_av1 = take(R * 4);
     const size_t o_acnt = take(R * 4), o_aoff = take(R * 4);
     const size_t o_bk0 = take(M * 4), o_bk1 = take(M * 4), o_bv0 = take(M * 4), o_bv1 = take(M * 4);
@@ -151,7 +153,8 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     GeoRec *geo = reinterpret_cast<GeoRec *>(b + o_geo);
     UaRec *ua = reinterpret_cast<UaRec *>(b + o_ua);
     uint2 *rect = reinterpret_cast<uint2 *>(b + o_rect);
-    uint32_t *counts = reinterpret_cast<uint32_t *>(b + o_cnt), *pos = reinterpret_cast<uint32_t *>(b + o_pos);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(b + o_cnt);
+    uint32_t *vis_words = reinterpret_cast<uint32_t *>(b + o_words), *woff = reinterpret_cast<uint32_t *>(b + o_woff);
     uint64_t *ak0 = reinterpret_cast<uint64_t *>(b + o_ak0), *ak1 = reinterpret_cast<uint64_t *>(b + o_ak1);
     uint32_t *av0 = reinterpret_cast<uint32_t *>(b + o_av0), *av1 = reinterpret_cast<uint32_t *>(b + o_av1);
     uint32_t *acnt = reinterpret_cast<uint32_t *>(b + o_acnt), *aoff = reinterpret_cast<uint32_t *>(b + o_aoff);
@@ -171,6 +174,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     pa.tile = p->tile; pa.TW = TW; pa.TH = TH;
     pa.n = n;
     pa.geo = geo; pa.ua = ua; pa.rect = rect; pa.counts = counts;
+    pa.vis_words = vis_words;
     CompositeArgs ca;
     std::memset(&ca, 0, sizeof(ca));
     ca.ranges = ranges; ca.geo = geo; ca.ua = ua;
@@ -192,7 +196,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     PK(cudaMemsetAsync(pl->d_info, 0, nb * sizeof(PlanInfo), cs));
     for (int bi = 0; bi < nb; ++bi) {
         const int v0 = bi * B, nv = n_cams - v0 < B ? n_cams - v0 : B;
-        const size_t nvn_b = (size_t)nv * (size_t)n, nvt_b = (size_t)nv * (size_t)TT;
+        const size_t nvt_b = (size_t)nv * (size_t)TT;
         PlanInfo *info = pl->d_info + bi;
         pa.cams = pl->d_cams + v0; pa.nv = nv;
         pa.zrange = info->b.zrange;
@@ -201,8 +205,9 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
         ca.nv = nv; ca.v0 = v0;
         PK(cudaMemsetAsync(&info->b.zrange[0], 0xff, sizeof(uint32_t), cs));
         PK(launch_project(pa, cs));
-        PK(exclusive_scan_u32(counts, pos, nvn_b, scan_tmp, nullptr, cs, true));
-        PK(launch_emit_records(counts, pos, geo, nv, n, 32, 0u, ak0, av0, cs, R, &info->records_over));
+        const size_t nwords_b = (size_t)nv * (size_t)((n + 31) / 32);
+        PK(scan_vis_words(vis_words, nwords_b, woff, scan_tmp, cs));
+        PK(emit_vis_words64(vis_words, woff, nv, n, geo, ak0, av0, R, &info->records_over, cs));
         bool alt_a = false, alt_b = false;
         PK(radix_sort_pairs<uint64_t>(ak0, av0, ak1, av1, R, bits_of((uint64_t)nv - 1) + 32, tmp, &alt_a, cs,
                                       &info->b.visible));

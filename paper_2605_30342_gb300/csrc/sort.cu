@@ -145,9 +145,12 @@ __global__ void k_popc_words(const uint32_t *words, size_t nwords, uint32_t *cnt
 // are consecutive and so are their records, which the warp's lanes write in
 // order (coalesced): lane j of a round finds its word by a binary search over
 // the warp's prefix popcounts, then its set bit.
+// KeyT = uint64_t writes (v << 32) | depth bits (zb = 32, zmin = 0, vmask all
+// ones).  Records at positions >= cap_R are dropped and set *overflow.
+template <typename KeyT>
 __global__ void k_emit_vis_words(const uint32_t *words, const uint32_t *woff, uint32_t nv, uint32_t nw, uint32_t n,
-                                 const GeoRec *geo, int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA,
-                                 uint32_t *valA, uint32_t *voff)
+                                 const GeoRec *geo, int zb, uint32_t zmin, uint32_t vmask, KeyT *keyA,
+                                 uint32_t *valA, uint32_t *voff, size_t cap_R, uint32_t *overflow)
 {
     const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = (int)(threadIdx.x & 31u);
@@ -158,8 +161,8 @@ __global__ void k_emit_vis_words(const uint32_t *words, const uint32_t *woff, ui
         wi = w - v * nw;
         bits = words[w];
         off = woff[w];
-        if (wi == 0) voff[v] = off;
-        if (w == total_words - 1) voff[nv] = off + (uint32_t)__popc(bits);
+        if (voff && wi == 0) voff[v] = off;
+        if (voff && w == total_words - 1) voff[nv] = off + (uint32_t)__popc(bits);
     }
     const uint32_t cnt = (uint32_t)__popc(bits);
     uint32_t inc = cnt;
@@ -183,9 +186,13 @@ __global__ void k_emit_vis_words(const uint32_t *words, const uint32_t *woff, ui
         uint32_t bk = __shfl_sync(0xffffffffu, bits, k);
         const uint32_t vk = __shfl_sync(0xffffffffu, v, k), wik = __shfl_sync(0xffffffffu, wi, k);
         if (j < total) {
+            if ((size_t)base + j >= cap_R) {
+                if (overflow) *overflow = 1u;
+                continue;
+            }
             for (uint32_t m = j - ek; m > 0; --m) bk &= bk - 1u;   // drop the set bits before this record's
             const uint32_t r = vk * n + wik * 32u + (uint32_t)(__ffs(bk) - 1);
-            keyA[base + j] = ((vk & vmask) << zb) | (__float_as_uint(geo[r].b.z) - zmin);
+            keyA[base + j] = ((KeyT)(vk & vmask) << zb) | (KeyT)(__float_as_uint(geo[r].b.z) - zmin);
             valA[base + j] = r;
         }
     }
@@ -399,8 +406,21 @@ cudaError_t emit_vis_words(const uint32_t *words, const uint32_t *woff, int nv, 
     if ((size_t)nv * (size_t)n >= ((size_t)1 << 32) || zb < 0 || zb > 31) return cudaErrorInvalidValue;
     const uint32_t nw = (uint32_t)((n + 31) / 32);
     const size_t total = (size_t)nv * nw;
-    k_emit_vis_words<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(words, woff, (uint32_t)nv, nw, (uint32_t)n, geo,
-                                                                     zb, zmin, vmask, keyA, valA, voff);
+    k_emit_vis_words<uint32_t><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        words, woff, (uint32_t)nv, nw, (uint32_t)n, geo, zb, zmin, vmask, keyA, valA, voff, ~(size_t)0, nullptr);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t emit_vis_words64(const uint32_t *words, const uint32_t *woff, int nv, int64_t n, const GeoRec *geo,
+                             uint64_t *keyA, uint32_t *valA, size_t cap_R, uint32_t *overflow, cudaStream_t s)
+{
+    if (nv <= 0 || n <= 0) return cudaSuccess;
+    if ((size_t)nv * (size_t)n >= ((size_t)1 << 32)) return cudaErrorInvalidValue;
+    const uint32_t nw = (uint32_t)((n + 31) / 32);
+    const size_t total = (size_t)nv * nw;
+    k_emit_vis_words<uint64_t><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        words, woff, (uint32_t)nv, nw, (uint32_t)n, geo, 32, 0u, 0xffffffffu, keyA, valA, nullptr, cap_R, overflow);
     count_launch();
     return cudaGetLastError();
 }
