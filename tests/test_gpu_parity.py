@@ -212,7 +212,7 @@ def test_score_views_parity(ctx, gv, name, tile):
 
 
 @pytest.mark.parametrize("name", ["tiny", "room_small"])
-@pytest.mark.parametrize("tile", [16, 8])
+@pytest.mark.parametrize("tile", [16, 8, 32])
 def test_expected_depth_parity(ctx, gv, name, tile):
     """Expected depth (colour weights x camera depth, background 0) against the
     oracle; it grows with the depths (up to ~10 here), so the gate is 1e-4

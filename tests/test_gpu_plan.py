@@ -179,3 +179,20 @@ def test_plan_in_view_batches(ctx, gv):
     assert torch.equal(tight.score, plan.score)
     plan.close()
     tight.close()
+
+
+def test_plan_with_colour_variances(ctx, gv):
+    """The captured chain also carries the per-Gaussian colour covariance
+    (FisherRF variant): replays equal gavis_score_views with sh_var."""
+    c = sg.config(2, n=20000, n_train=4, n_cand=5, train_wh=(160, 120), cand_wh=(160, 120))
+    sc = c["scene"]
+    var = np.random.default_rng(5).uniform(0.001, 0.05, sc.sh.shape).astype(np.float32)
+    gs = gv.Gaussians(*(torch.as_tensor(x).cuda().contiguous() for x in (sc.means, sc.scales, sc.rots, sc.opac, sc.sh)),
+                      sc.sh_degree, torch.as_tensor(var).cuda().contiguous())
+    vf = ctx.vf_build(gs, c["train"], degree=c["vf_degree"])
+    cand = c["cand"]
+    p = gv.Params(tile=16, vf_degree=c["vf_degree"])
+    plan = ctx.plan(gs, vf, len(cand), 160, 120, 1 << 22, params=p, want_unc=True)
+    plan.launch(cand)
+    assert_same(plan, ctx.score_views(gs, vf, cand, params=p, want_rgb=False))
+    plan.close()
