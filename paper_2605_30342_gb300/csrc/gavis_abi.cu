@@ -50,6 +50,8 @@ struct gavis_ctx {
     BatchInfo *h_info = nullptr;             // pinned
     uint32_t *h_voff = nullptr;              // pinned, per-view record offsets of a batch
     size_t h_voff_cap = 0;
+    RsBlock *h_blk = nullptr;                // pinned, block table of a segmented sort
+    size_t h_blk_cap = 0;
     int32_t *h_best = nullptr;               // pinned
     // instrumentation
     bool prof_on = false;
@@ -280,11 +282,13 @@ struct KeyLayout {
     uint64_t *a_k0, *a_k1;
     uint32_t *a_v0, *a_v1, *a_cnt, *a_off;
     uint32_t *b_k0, *b_k1, *b_v0, *b_v1;
+    RsBlock *blk_a, *blk_b;   // block tables of the segmented sorts
     void *tmp;
     size_t bytes;
 };
 
-KeyLayout key_layout(void *base, size_t nrec, size_t M)
+// nseg: the most segments (view groups) either sort splits into
+KeyLayout key_layout(void *base, size_t nrec, size_t M, size_t nseg)
 {
     KeyLayout L;
     char *p = reinterpret_cast<char *>(base);
@@ -300,7 +304,9 @@ KeyLayout key_layout(void *base, size_t nrec, size_t M)
     L.b_k1 = reinterpret_cast<uint32_t *>(take(M * 4));
     L.b_v0 = reinterpret_cast<uint32_t *>(take(M * 4));
     L.b_v1 = reinterpret_cast<uint32_t *>(take(M * 4));
-    const size_t big = nrec > M ? nrec : M;
+    L.blk_a = reinterpret_cast<RsBlock *>(take((nrec / 4096 + nseg + 1) * sizeof(RsBlock)));
+    L.blk_b = reinterpret_cast<RsBlock *>(take((M / 4096 + nseg + 1) * sizeof(RsBlock)));
+    const size_t big = (nrec > M ? nrec : M) + (nseg + 1) * 4096;   // a partial block per segment at most
     L.tmp = take(radix_tmp_bytes(big) + scan_tmp_bytes(big) + 64);
     L.bytes = off;
     return L;
@@ -442,9 +448,36 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
         ctx->prof_visible += nrec;
     }
 
-    KeyLayout KL = key_layout(nullptr, (size_t)nrec, (size_t)M);
+    const int vb = bits_of((uint64_t)nv - 1);
+    const int gb = vb + zb <= 32 ? vb : 32 - zb;
+    const int gsz_a = 1 << gb, nseg_a = (nv + gsz_a - 1) / gsz_a;
+    const int tbits = bits_of((uint64_t)G.TT - 1);
+    int tb = -1, gbb = 0;
+    if (tbits + vb > 16 && tbits <= 16 && ((nv - 1) >> (16 - tbits)) < 64) {
+        tb = tbits;
+        gbb = 16 - tbits;
+    }
+    const int nseg_b = tb < 0 ? 1 : (nv + (1 << gbb) - 1) >> gbb;
+    const size_t nseg = (size_t)(nseg_a > nseg_b ? nseg_a : nseg_b);
+    KeyLayout KL = key_layout(nullptr, (size_t)nrec, (size_t)M, nseg);
     if ((rc = ensure(ctx, ctx->keys, KL.bytes)) != GAVIS_OK) return rc;
-    KL = key_layout(ctx->keys.p, (size_t)nrec, (size_t)M);
+    KL = key_layout(ctx->keys.p, (size_t)nrec, (size_t)M, nseg);
+    // block table of a segmented sort over the segments [seg[s], seg[s+1]),
+    // staged through pinned memory (the previous table's copy has finished:
+    // a stream synchronisation lies between any two uses)
+    auto upload_blocks = [&](const std::vector<uint64_t> &seg, RsBlock *dst, size_t &nblk) -> int {
+        nblk = radix_segment_blocks(seg.data(), (int)seg.size() - 1, nullptr);
+        if (nblk > ctx->h_blk_cap) {
+            if (ctx->h_blk) cudaFreeHost(ctx->h_blk);
+            ctx->h_blk = nullptr;
+            ctx->h_blk_cap = 0;
+            CK(cudaMallocHost(&ctx->h_blk, nblk * sizeof(RsBlock)));
+            ctx->h_blk_cap = nblk;
+        }
+        radix_segment_blocks(seg.data(), (int)seg.size() - 1, ctx->h_blk);
+        if (nblk) CK(cudaMemcpyAsync(dst, ctx->h_blk, nblk * sizeof(RsBlock), cudaMemcpyHostToDevice, s));
+        return GAVIS_OK;
+    };
     bool alt_a = false, alt_b = false;
     // stage A: records sorted by (view, depth), ties in index order.  Keys
     // are 32 bits, ((view & (2^gb - 1)) << zb) | (depth bits - zmin) with
@@ -452,9 +485,6 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     // groups of 2^gb views are sorted one after another, each over its
     // contiguous range of records (records are emitted in view order).  The
     // keys are written from the visibility bits the projection leaves.
-    const int vb = bits_of((uint64_t)nv - 1);
-    const int gb = vb + zb <= 32 ? vb : 32 - zb;
-    const int gsz_a = 1 << gb;
     uint32_t *k0 = reinterpret_cast<uint32_t *>(KL.a_k0), *k1 = reinterpret_cast<uint32_t *>(KL.a_k1);
     {
         Stage st(ctx, GAVIS_STAGE_EMIT, s);
@@ -470,31 +500,17 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     }
     {
         Stage st(ctx, GAVIS_STAGE_SORT, s);
-        const int end_bit = gb + zb;
-        const bool want_alt = ((end_bit + 7) / 8) % 2 == 1;   // every group takes the same number of passes
-        for (int g0 = 0; g0 < nv; g0 += gsz_a) {
-            const uint32_t a = ctx->h_voff[g0], b = ctx->h_voff[g0 + gsz_a < nv ? g0 + gsz_a : nv];
-            if (b <= a) continue;
-            bool alt = false;
-            CK(radix_sort_pairs<uint32_t>(k0 + a, KL.a_v0 + a, k1 + a, KL.a_v1 + a, (size_t)(b - a), end_bit, KL.tmp,
-                                          &alt, s));
-            if (alt != want_alt)   // a group too small to sort stays where it was emitted
-                CK(cudaMemcpyAsync((want_alt ? KL.a_v1 : KL.a_v0) + a, (alt ? KL.a_v1 : KL.a_v0) + a,
-                                   (size_t)(b - a) * 4, cudaMemcpyDeviceToDevice, s));
-        }
-        alt_a = want_alt;
+        std::vector<uint64_t> seg((size_t)nseg_a + 1);
+        for (int g = 0; g <= nseg_a; ++g) seg[(size_t)g] = ctx->h_voff[g * gsz_a < nv ? g * gsz_a : nv];
+        size_t nblk = 0;
+        if ((rc = upload_blocks(seg, KL.blk_a, nblk)) != GAVIS_OK) return rc;
+        CK(radix_sort_segments<uint32_t>(k0, KL.a_v0, k1, KL.a_v1, KL.blk_a, nblk, gb + zb, KL.tmp, &alt_a, s));
     }
     const uint32_t *recs = alt_a ? KL.a_v1 : KL.a_v0;
     // stage B: tile entries in stage-A order, i.e. view by view.  When the
     // tile index fits in tb <= 16 bits the keys are (view << tb) | tile and
     // each group of 2^(16 - tb) views is sorted on 16 bits (two passes) over
     // its contiguous entries; otherwise keys are view * TT + tile, one sort.
-    const int tbits = bits_of((uint64_t)G.TT - 1);
-    int tb = -1, gbb = 0;
-    if (tbits + vb > 16 && tbits <= 16 && ((nv - 1) >> (16 - tbits)) < 64) {
-        tb = tbits;
-        gbb = 16 - tbits;
-    }
     {
         Stage st(ctx, GAVIS_STAGE_EMIT, s);
         CK(launch_gather_counts(recs, RL.counts, (size_t)nrec, KL.a_cnt, s));
@@ -514,20 +530,16 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
                                           KL.tmp, &alt_b, s));
         } else {
             const int gsz = 1 << gbb;
-            for (int g0 = 0; g0 < nv; g0 += gsz) {
-                const uint64_t e0 = h_eoff[g0], e1 = h_eoff[g0 + gsz < nv ? g0 + gsz : nv];
-                if (e1 < e0 || e1 > M) return fail(ctx, GAVIS_ERR_CUDA, "internal: inconsistent per-view entry offsets");
-                const uint64_t len = e1 - e0;
-                bool alt = false;
-                if (len > 0)
-                    CK(radix_sort_pairs<uint32_t>(KL.b_k0 + e0, KL.b_v0 + e0, KL.b_k1 + e0, KL.b_v1 + e0, (size_t)len, 16,
-                                                  KL.tmp, &alt, s));
-                if (alt) {   // two passes end in the first buffer; a group too small to sort already is there
-                    CK(cudaMemcpyAsync(KL.b_k0 + e0, KL.b_k1 + e0, (size_t)len * 4, cudaMemcpyDeviceToDevice, s));
-                    CK(cudaMemcpyAsync(KL.b_v0 + e0, KL.b_v1 + e0, (size_t)len * 4, cudaMemcpyDeviceToDevice, s));
-                }
+            std::vector<uint64_t> seg((size_t)nseg_b + 1);
+            for (int g = 0; g <= nseg_b; ++g) {
+                seg[(size_t)g] = h_eoff[g * gsz < nv ? g * gsz : nv];
+                if (seg[(size_t)g] > M || (g > 0 && seg[(size_t)g] < seg[(size_t)g - 1]))
+                    return fail(ctx, GAVIS_ERR_CUDA, "internal: inconsistent per-view entry offsets");
             }
-            alt_b = false;
+            size_t nblk = 0;
+            if ((rc = upload_blocks(seg, KL.blk_b, nblk)) != GAVIS_OK) return rc;
+            CK(radix_sort_segments<uint32_t>(KL.b_k0, KL.b_v0, KL.b_k1, KL.b_v1, KL.blk_b, nblk, 16, KL.tmp, &alt_b,
+                                             s));
         }
     }
     const uint32_t *keys = alt_b ? KL.b_k1 : KL.b_k0;
@@ -680,6 +692,7 @@ void gavis_ctx_destroy(gavis_ctx *ctx)
         if (b->p) cudaFree(b->p);
     if (ctx->h_info) cudaFreeHost(ctx->h_info);
     if (ctx->h_voff) cudaFreeHost(ctx->h_voff);
+    if (ctx->h_blk) cudaFreeHost(ctx->h_blk);
     if (ctx->h_best) cudaFreeHost(ctx->h_best);
     if (ctx->d_pairs) cudaFree(ctx->d_pairs);
     for (auto &r : ctx->pending) {

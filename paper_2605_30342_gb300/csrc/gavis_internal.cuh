@@ -123,6 +123,25 @@ cudaError_t radix_sort_pairs(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_
 // kernel attributes the sort sets on first use; call before stream capture
 void radix_prepare();
 
+// Segmented sort: several contiguous segments sorted independently on the
+// same bits in one sequence of passes.  Each thread block of a pass takes the
+// items [start, end) of one segment (at most 4096) and digit d's count of
+// that block lives at hist[h0 + d hs]; the histograms of consecutive
+// segments are concatenated (segment-major, then digit-major, then block),
+// so one exclusive scan of all of them gives every (segment, digit, block)
+// its global output position.
+struct RsBlock {
+    uint32_t start, end, h0, hs;
+};
+// Fills tbl (host; NULL to count) with the blocks of the segments
+// [seg[s], seg[s+1]), s < nseg; returns the number of blocks.
+size_t radix_segment_blocks(const uint64_t *seg, int nseg, RsBlock *tbl);
+// blk: device copy of the table (nblk blocks); tmp: radix_tmp_bytes of
+// nblk * 4096 items.
+template <typename KeyT>
+cudaError_t radix_sort_segments(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_t *vals_alt, const RsBlock *blk,
+                                size_t nblk, int end_bit, void *tmp, bool *result_in_alt, cudaStream_t s);
+
 // ---------------------------------------------------------------- raster.cu
 struct BatchInfo {                // device, read back once per batch
     unsigned long long total;     // number of tile entries

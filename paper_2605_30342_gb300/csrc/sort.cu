@@ -225,16 +225,42 @@ __device__ __forceinline__ unsigned digit_peers(int d)
 // Per-block digit histogram: warp-private counters with plain shared atomics
 // (rounds in which the whole warp holds one digit add 32 once).
 // d_n (optional): the actual item count in device memory, <= n (graph replays)
+// blk (optional): per-block item ranges and histogram columns of a
+// segmented sort (RsBlock); otherwise block b takes items [4096 b, 4096 b +
+// 4096) of [0, n) and histogram column b of nblocks.
+struct BlockRange {
+    size_t base, lim, h0, hs;   // items [base, lim); digit d's count at hist[h0 + d hs]
+};
+__device__ __forceinline__ BlockRange block_range(const RsBlock *blk, size_t n, int nblocks)
+{
+    BlockRange b;
+    if (blk) {
+        const RsBlock r = blk[blockIdx.x];
+        b.base = r.start;
+        b.lim = r.end;
+        b.h0 = r.h0;
+        b.hs = r.hs;
+    } else {
+        b.base = (size_t)blockIdx.x * kRsTile;
+        b.lim = b.base + kRsTile < n ? b.base + kRsTile : n;
+        b.h0 = blockIdx.x;
+        b.hs = (size_t)nblocks;
+    }
+    return b;
+}
+
 template <typename KeyT>
 __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const KeyT *keys, size_t n, int shift,
                                                            uint32_t *hist, int nblocks,
-                                                           const unsigned long long *d_n)
+                                                           const unsigned long long *d_n, const RsBlock *blk)
 {
     if (d_n && *d_n < n) n = (size_t)*d_n;
     __shared__ uint32_t s_h[kRsWarps][257];
-    const size_t base = (size_t)blockIdx.x * kRsTile;
+    const BlockRange br = block_range(blk, n, nblocks);
+    const size_t base = br.base;
+    n = br.lim;   // items of this block: [base, lim)
     if (base >= n) {   // whole block past the live items (graph replays)
-        hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = 0u;
+        hist[br.h0 + (size_t)threadIdx.x * br.hs] = 0u;
         return;
     }
     for (int i = threadIdx.x; i < kRsWarps * 257; i += kRsThreads) (&s_h[0][0])[i] = 0u;
@@ -255,7 +281,7 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const KeyT *keys, siz
     uint32_t c = 0;
 #pragma unroll
     for (int w = 0; w < kRsWarps; ++w) c += s_h[w][threadIdx.x];
-    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = c;
+    hist[br.h0 + (size_t)threadIdx.x * br.hs] = c;
 }
 
 // Stable scatter of one 4096-item tile.  Warp w owns the contiguous items
@@ -271,10 +297,13 @@ template <typename KeyT, bool BALLOT>
 __global__ void __launch_bounds__(kRsThreads, 2) k_radix_scatter(const KeyT *kin, const uint32_t *vin,
                                                               KeyT *kout, uint32_t *vout, size_t n, int shift,
                                                               const uint32_t *hist, const uint32_t *offs,
-                                                              int nblocks, const unsigned long long *d_n)
+                                                              int nblocks, const unsigned long long *d_n,
+                                                              const RsBlock *blk)
 {
     if (d_n && *d_n < n) n = (size_t)*d_n;
-    if ((size_t)blockIdx.x * kRsTile >= n) return;   // nothing of this block is live
+    const BlockRange br = block_range(blk, n, nblocks);
+    n = br.lim;   // items of this block: [base, lim)
+    if (br.base >= n) return;   // nothing of this block is live
     extern __shared__ __align__(16) unsigned char smem[];
     KeyT *s_key = reinterpret_cast<KeyT *>(smem);
     uint32_t *s_val = reinterpret_cast<uint32_t *>(smem + (size_t)kRsTile * sizeof(KeyT));
@@ -284,11 +313,11 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_radix_scatter(const KeyT *kin
     uint32_t *s_tmp = s_lstart + 256;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    const size_t base = (size_t)blockIdx.x * kRsTile;
+    const size_t base = br.base;
 
     // this block's digit counts -> block-local digit starts (exclusive scan)
-    const uint32_t mycnt = hist[(size_t)tid * nblocks + blockIdx.x];
-    s_goff[tid] = offs[(size_t)tid * nblocks + blockIdx.x];
+    const uint32_t mycnt = hist[br.h0 + (size_t)tid * br.hs];
+    s_goff[tid] = offs[br.h0 + (size_t)tid * br.hs];
     for (int w = 0; w < kRsWarps; ++w) s_wc[w * 256 + tid] = 0u;
     {
         uint32_t x = mycnt;
@@ -454,17 +483,17 @@ cudaError_t radix_sort_pairs(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_
     uint32_t *vin = vals, *vout = vals_alt;
     bool alt = false;
     for (int shift = 0; shift < end_bit; shift += 8) {
-        k_radix_hist<KeyT><<<nblocks, kRsThreads, 0, s>>>(kin, n, shift, hist, nblocks, d_n); count_launch();
+        k_radix_hist<KeyT><<<nblocks, kRsThreads, 0, s>>>(kin, n, shift, hist, nblocks, d_n, nullptr); count_launch();
         cudaError_t e = exclusive_scan_u32(hist, offs, h, stmp, nullptr, s);
         if (e != cudaSuccess) return e;
         // the lowest digit, and those below the top two passes, are close to
         // uniformly distributed
         if (shift == 0 || shift + 8 < end_bit - 8)
             k_radix_scatter<KeyT, true><<<nblocks, kRsThreads, smem, s>>>(kin, vin, kout, vout, n, shift, hist, offs,
-                                                                         nblocks, d_n);
+                                                                         nblocks, d_n, nullptr);
         else
             k_radix_scatter<KeyT, false><<<nblocks, kRsThreads, smem, s>>>(kin, vin, kout, vout, n, shift, hist,
-                                                                          offs, nblocks, d_n);
+                                                                          offs, nblocks, d_n, nullptr);
         count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -475,6 +504,70 @@ cudaError_t radix_sort_pairs(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_
     *result_in_alt = alt;
     return cudaSuccess;
 }
+
+size_t radix_segment_blocks(const uint64_t *seg, int nseg, RsBlock *tbl)
+{
+    size_t k = 0, hbase = 0;
+    for (int g = 0; g < nseg; ++g) {
+        const uint64_t len = seg[g + 1] - seg[g];
+        const uint64_t nb = (len + kRsTile - 1) / kRsTile;
+        if (tbl) {
+            for (uint64_t b = 0; b < nb; ++b) {
+                const uint64_t st = seg[g] + b * kRsTile;
+                tbl[k + b].start = (uint32_t)st;
+                tbl[k + b].end = (uint32_t)(st + kRsTile < seg[g + 1] ? st + kRsTile : seg[g + 1]);
+                tbl[k + b].h0 = (uint32_t)(hbase + b);
+                tbl[k + b].hs = (uint32_t)nb;
+            }
+        }
+        k += nb;
+        hbase += 256 * nb;
+    }
+    return k;
+}
+
+template <typename KeyT>
+cudaError_t radix_sort_segments(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_t *vals_alt, const RsBlock *blk,
+                                size_t nblk, int end_bit, void *tmp, bool *result_in_alt, cudaStream_t s)
+{
+    *result_in_alt = false;
+    if (nblk == 0 || end_bit <= 0) return cudaSuccess;
+    const size_t h = 256 * nblk;
+    const size_t a = (h * sizeof(uint32_t) + 255) & ~(size_t)255;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(tmp);
+    uint32_t *offs = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(tmp) + a);
+    void *stmp = reinterpret_cast<char *>(tmp) + 2 * a;
+    constexpr size_t smem = rs_smem<KeyT>();
+    cudaFuncSetAttribute(k_radix_scatter<KeyT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_radix_scatter<KeyT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    KeyT *kin = keys, *kout = keys_alt;
+    uint32_t *vin = vals, *vout = vals_alt;
+    bool alt = false;
+    const size_t nmax = ~(size_t)0;   // ranges come from blk
+    for (int shift = 0; shift < end_bit; shift += 8) {
+        k_radix_hist<KeyT><<<(unsigned)nblk, kRsThreads, 0, s>>>(kin, nmax, shift, hist, 0, nullptr, blk);
+        count_launch();
+        cudaError_t e = exclusive_scan_u32(hist, offs, h, stmp, nullptr, s);
+        if (e != cudaSuccess) return e;
+        if (shift == 0 || shift + 8 < end_bit - 8)
+            k_radix_scatter<KeyT, true><<<(unsigned)nblk, kRsThreads, smem, s>>>(kin, vin, kout, vout, nmax, shift,
+                                                                                hist, offs, 0, nullptr, blk);
+        else
+            k_radix_scatter<KeyT, false><<<(unsigned)nblk, kRsThreads, smem, s>>>(kin, vin, kout, vout, nmax, shift,
+                                                                                 hist, offs, 0, nullptr, blk);
+        count_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        KeyT *tk = kin; kin = kout; kout = tk;
+        uint32_t *tv = vin; vin = vout; vout = tv;
+        alt = !alt;
+    }
+    *result_in_alt = alt;
+    return cudaSuccess;
+}
+
+template cudaError_t radix_sort_segments<uint32_t>(uint32_t *, uint32_t *, uint32_t *, uint32_t *, const RsBlock *,
+                                                   size_t, int, void *, bool *, cudaStream_t);
 
 template cudaError_t radix_sort_pairs<uint64_t>(uint64_t *, uint32_t *, uint64_t *, uint32_t *, size_t, int, void *,
                                                 bool *, cudaStream_t, const unsigned long long *);
