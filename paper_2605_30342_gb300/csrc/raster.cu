@@ -284,6 +284,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
     const size_t vrow = (size_t)vb * (size_t)a.n;
     const RasterConsts rc = a.rc;
 
+    const bool colour = DEPTH || a.rgb != nullptr;   // colour path only when asked for
     float T[2], Tc[2], sl[2], swv[2], skc[2], cr[2], cg[2], cb[2], py[2], dz[2];
     bool ua_on[2], rgb_on[2], inside[2];
 #pragma unroll
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
         T[p] = 1.0f; Tc[p] = 1.0f; sl[p] = 0.0f; swv[p] = 0.0f; skc[p] = 0.0f; cr[p] = 0.0f; cg[p] = 0.0f; cb[p] = 0.0f;
         dz[p] = 0.0f;
         ua_on[p] = inside[p];
-        rgb_on[p] = inside[p] && (DEPTH || a.rgb != nullptr);   // colour path only when asked for
+        rgb_on[p] = inside[p] && colour;
     }
     uint32_t npairs = 0;
     float *kcs = s_kc[KC ? warp : 0];
@@ -337,37 +338,39 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a
             prefetch_l2(a.ua + vrow + nval);
         }
         const int nk = __popc(m);
+        // Straight-line body: a pixel that misses the entry, or whose
+        // accumulator has saturated, gets a zero opacity for it, which leaves
+        // every sum and transmittance exactly as it was.
         for (int k = 0; k < nk && (ua_on[0] || rgb_on[0] || ua_on[1] || rgb_on[1]); ++k) {
             const float4 g0 = g0s[k];
             const float2 g1 = g1s[k];
+            const float4 u0 = u0s[k];
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
-                if (!(ua_on[p] || rgb_on[p])) continue;
                 const float q = footprint_q(px, py[p], g0.x, g0.y, g0.z, g0.w, g1.x);
-                if (!(q <= rc.q_cut)) continue;
-                ++npairs;
+                const bool hit = q <= rc.q_cut;
+                const bool hc = hit && rgb_on[p], hu = hit && ua_on[p];
+                npairs += (uint32_t)(hc || hu);
                 const float alpha = g1.y * ex2_approx(q * kNegHalfLog2e);
-                const float4 u0 = u0s[k];
-                if (rgb_on[p]) {
+                if (colour) {   // the same for every thread of the launch
                     const float2 u1 = u1s[k];
-                    const float w = alpha * Tc[p];
-                    cr[p] = fmaf(w, u0.w, cr[p]);
-                    cg[p] = fmaf(w, u1.x, cg[p]);
-                    cb[p] = fmaf(w, u1.y, cb[p]);
-                    if (DEPTH) dz[p] = fmaf(w, zs[k], dz[p]);
-                    Tc[p] -= w;
+                    const float ac = hc ? alpha : 0.0f;
+                    const float wc = ac * Tc[p];
+                    cr[p] = fmaf(wc, u0.w, cr[p]);
+                    cg[p] = fmaf(wc, u1.x, cg[p]);
+                    cb[p] = fmaf(wc, u1.y, cb[p]);
+                    if (DEPTH) dz[p] = fmaf(wc, zs[k], dz[p]);
+                    Tc[p] -= wc;
                     rgb_on[p] = Tc[p] >= rc.eps_T;
                 }
-                if (ua_on[p]) {
-                    const float as = fmaf(alpha, u0.x, u0.y);   // eq:alpha_comp
-                    const float w = as * T[p];
-                    const float wv = w * u0.z;                   // weight of the visible component
-                    sl[p] = fmaf(wv, lg2_approx(fmaxf(wv, 1e-30f)), sl[p]);
-                    swv[p] += wv;
-                    if (KC) skc[p] = fmaf(wv, kcs[k], skc[p]);
-                    T[p] -= w;
-                    ua_on[p] = T[p] >= rc.eps_T;
-                }
+                const float as = hu ? fmaf(alpha, u0.x, u0.y) : 0.0f;   // eq:alpha_comp
+                const float w = as * T[p];
+                const float wv = w * u0.z;                               // weight of the visible component
+                sl[p] = fmaf(wv, lg2_approx(fmaxf(wv, 1e-30f)), sl[p]);
+                swv[p] += wv;
+                if (KC) skc[p] = fmaf(wv, kcs[k], skc[p]);
+                T[p] -= w;
+                ua_on[p] = T[p] >= rc.eps_T;
             }
         }
         __syncwarp();
