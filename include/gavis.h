@@ -108,7 +108,7 @@ typedef struct {
     float sigma_c2;              /* constant colour variance, Q_c = sigma_c2 I_3 (0.01) */
     float logdet_Q0;             /* log |Q_0| of the prior colour covariance, Q_0 = I_3 -> 0 */
     int32_t tile;                /* tile edge in pixels: 8, 16 or 32 (16) */
-    int32_t views_per_batch;     /* views per kernel chain: 0 = as many as the budget allows, 1 = plain */
+    int32_t views_per_batch;     /* views per kernel chain: 0 = as many as the budget allows (at most 256), 1 = plain; at most 1024 are used */
 } gavis_params;
 
 typedef struct gavis_ctx gavis_ctx;
@@ -228,7 +228,7 @@ int gavis_vf_query(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf
  * indices, sorted by key with ties in ascending index.  keys/vals: device
  * [cap]; *M_out (host) receives the number of keys (only min(M, cap) are
  * written); ranges: device [n_cams*TW*TH][2] uint32 [start, end) or NULL.
- * Synchronises `stream`. */
+ * n_cams <= 1024 (GAVIS_ERR_ARG beyond).  Synchronises `stream`. */
 int gavis_debug_bins(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_camera *cams, int n_cams,
                      const gavis_params *p, uint64_t *keys, uint32_t *vals, int64_t cap,
                      int64_t *M_out, uint32_t *ranges, void *stream);
@@ -279,7 +279,7 @@ typedef struct gavis_plan gavis_plan;
 
 /* Build a plan for n_cams (1..16384) candidate views of W x H pixels over
  * one scene and field.  The views go through the chain in batches of
- * p->views_per_batch (0: all in one batch), replayed one after another over
+ * p->views_per_batch (0: all in one batch; at most 1024), replayed one after another over
  * the same buffers.  The plan allocates all its device memory here, for one
  * batch: one projected record per (view, Gaussian), sort space for
  * record_capacity visible (view, Gaussian) records (0 = views x n, always

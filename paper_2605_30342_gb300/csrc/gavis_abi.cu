@@ -376,6 +376,7 @@ int auto_batch(gavis_ctx *ctx, int64_t n, int TT, int n_views, Mode m, int reque
         if (nv > 256) nv = 256;
         if (nv > n_views) nv = n_views;
     }
+    if (nv > kMaxBatchViews) nv = kMaxBatchViews;
     if (nv > idx_cap) nv = idx_cap;
     if (nv < 1) nv = 1;
     return (int)nv;
@@ -914,11 +915,13 @@ int gavis_vf_query(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf
     qa.vf_degree = vf->degree;
     qa.vf_dtype = vf->dtype;
     qa.n_train = vf->n_train_views;
-    qa.cams = reinterpret_cast<const gavis_camera *>(ctx->cams.p);
-    qa.nv = n_cams;
     qa.n = gs->n;
-    qa.V = V;
-    CK(launch_query(qa, s));
+    for (int v0 = 0; v0 < n_cams; v0 += kMaxBatchViews) {   // cameras of a launch sit in shared memory
+        qa.cams = reinterpret_cast<const gavis_camera *>(ctx->cams.p) + v0;
+        qa.nv = n_cams - v0 < kMaxBatchViews ? n_cams - v0 : kMaxBatchViews;
+        qa.V = V + (size_t)v0 * (size_t)gs->n;
+        CK(launch_query(qa, s));
+    }
     return GAVIS_OK;
 }
 
@@ -931,6 +934,7 @@ int gavis_debug_bins(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_came
     if ((rc = check_params(ctx, p)) || (rc = check_gaussians(ctx, gs, false)) || (rc = check_cams(ctx, cams, n_cams)))
         return rc;
     if (!M_out) return fail(ctx, GAVIS_ERR_ARG, "M_out is NULL");
+    if (n_cams > kMaxBatchViews) return fail(ctx, GAVIS_ERR_ARG, "gavis_debug_bins takes at most %d cameras", kMaxBatchViews);
     if (cap > 0 && (!keys || !vals)) return fail(ctx, GAVIS_ERR_ARG, "keys/vals NULL with cap > 0");
     cudaSetDevice(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

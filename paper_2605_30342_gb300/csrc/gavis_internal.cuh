@@ -48,6 +48,8 @@ struct RasterConsts {
 
 // fixed-point scale of the transmittance sums of the visibility pass
 constexpr float kTScale = 16777216.0f;   // 2^24
+// views one projection or query launch takes: their cameras sit in shared memory
+constexpr int kMaxBatchViews = 1024;
 
 // ---------------------------------------------------------------- project.cu
 struct ProjectArgs {

@@ -104,7 +104,8 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     const int64_t n = gs->n;
     const int TW = (W + p->tile - 1) / p->tile, TH = (H + p->tile - 1) / p->tile, TT = TW * TH;
     // views per batch: every batch reuses the same buffers, one after another
-    const int B = p->views_per_batch > 0 && p->views_per_batch < n_cams ? p->views_per_batch : n_cams;
+    int B = p->views_per_batch > 0 && p->views_per_batch < n_cams ? p->views_per_batch : n_cams;
+    if (B > kMaxBatchViews) B = kMaxBatchViews;   // one projection launch per batch
     const int nb = (n_cams + B - 1) / B;
     const size_t nvn = (size_t)B * (size_t)n, nvt = (size_t)B * (size_t)TT;
     const size_t M = (size_t)entry_capacity;

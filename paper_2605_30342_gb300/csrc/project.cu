@@ -297,6 +297,7 @@ cudaError_t launch_ua(const ProjectArgs &a, cudaStream_t s, int blocks, size_t s
 cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s)
 {
     if (a.n == 0 || a.nv == 0) return cudaSuccess;
+    if (a.nv > kMaxBatchViews) return cudaErrorInvalidValue;
     const int blocks = (int)((a.n + 127) / 128);
     const size_t smem = sizeof(gavis_camera) * (size_t)a.nv;
     if (smem > 48 * 1024) {
@@ -322,6 +323,7 @@ cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s)
 cudaError_t launch_query(const QueryArgs &a, cudaStream_t s)
 {
     if (a.n == 0 || a.nv == 0) return cudaSuccess;
+    if (a.nv > kMaxBatchViews) return cudaErrorInvalidValue;
     const int blocks = (int)((a.n + 127) / 128);
     const size_t smem = sizeof(gavis_camera) * (size_t)a.nv;
     switch (a.vf_degree) {

@@ -98,6 +98,70 @@ def test_bins_bit_exact_with_view_groups(ctx, gv):
         assert torch.equal(a[k], b[k]), k
 
 
+def _edge_scene(cams, n_per, seed):
+    """Gaussians whose centres project near the image borders of each camera:
+    up to 8 px inside to 40 px outside, at depths 0.25-8 and scales 1e-3-0.5,
+    so that many footprints reach into the image by a little and many miss
+    it by a little."""
+    rng = np.random.default_rng(seed)
+    means = []
+    for cam in cams:
+        side = rng.integers(0, 4, n_per)
+        d = rng.uniform(-8.0, 40.0, n_per)
+        along = rng.uniform(-20.0, max(cam.W, cam.H) + 20.0, n_per)
+        u = np.select([side == 0, side == 1], [-d, cam.W + d], along)
+        v = np.select([side == 2, side == 3], [-d, cam.H + d], along)
+        z = np.exp(rng.uniform(np.log(0.25), np.log(8.0), n_per))
+        xc = np.stack([(u - cam.cx) / cam.fx * z, (v - cam.cy) / cam.fy * z, z], 1)
+        R = cam.R.astype(np.float64)
+        means.append(np.linalg.solve(R, (xc - cam.t.astype(np.float64)).T).T)
+    means = np.concatenate(means)
+    n = len(means)
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    return sg.Scene(means=means.astype(np.float32),
+                    scales=np.exp(rng.uniform(np.log(1e-3), np.log(0.5), (n, 3))).astype(np.float32),
+                    rots=q.astype(np.float32), opac=rng.uniform(0.1, 1.0, n).astype(np.float32),
+                    sh=rng.normal(0, 0.3, (n, 1, 3)).astype(np.float32), sh_degree=0)
+
+
+@pytest.mark.parametrize("tile", [16, 8, 32])
+def test_bins_bit_exact_screen_edges(ctx, gv, tile):
+    """Footprints that just reach into, or just miss, the tile grid at every
+    border, for cameras with orthonormal, uniformly scaled and sheared
+    rotation matrices and wide and narrow fields of view: the bins stay
+    bit-exact (no Gaussian the exact projection keeps may be dropped early)."""
+    base = [sg.look_at_camera((0, 0, 0), (1.0, 0.2, 0.1), 160, 120, 90.0),
+            sg.look_at_camera((0.5, -1, 0.3), (0.0, 1.0, 0.0), 160, 120, 120.0),
+            sg.look_at_camera((0, 0, 1), (0.3, 0.1, -1.0), 160, 120, 30.0)]
+    cams = list(base)
+    for k, M in enumerate([np.eye(3) * 1.25, np.array([[1.0, 0.15, 0.0], [0.0, 1.0, 0.0], [0.1, 0.0, 1.0]])]):
+        c = sg.look_at_camera((0.2 * k, 0.1, 0.0), (-1.0, 0.4, 0.2), 160, 120, 75.0)
+        R = (M @ c.R.astype(np.float64)).astype(np.float32)
+        cams.append(sg.Camera(W=c.W, H=c.H, fx=c.fx, fy=c.fy, cx=c.cx, cy=c.cy, tan_half_fovx=c.tan_half_fovx,
+                              tan_half_fovy=c.tan_half_fovy, R=R,
+                              t=(-R.astype(np.float64) @ c.campos.astype(np.float64)).astype(np.float32),
+                              campos=c.campos, znear=c.znear))
+    sc = _edge_scene(cams, 3000, seed=11)
+    reach = miss = 0
+    for cam in cams:
+        out, st = oracle.project(cam, sc, tile=tile)
+        P = sc.means.astype(np.float64) @ cam.R.T.astype(np.float64) + cam.t
+        u = cam.fx * P[:, 0] / P[:, 2] + cam.cx
+        v = cam.fy * P[:, 1] / P[:, 2] + cam.cy
+        outside = (P[:, 2] > cam.znear) & ((u < 0) | (u > cam.W) | (v < 0) | (v > cam.H))
+        reach += int(np.sum(outside & (st == 1)))
+        miss += int(np.sum(outside & (st != 1)))
+    assert reach > 500 and miss > 500, (reach, miss)
+    gs = gpu_scene(gv, sc)
+    keys, vals, ranges = ctx.debug_bins(gs, cams, gv.Params(tile=tile))
+    rk, rv = oracle.bins(cams, sc, tile=tile)
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), rk)
+    assert np.array_equal(vals.cpu().numpy().view(np.uint32), rv)
+    TT = ((160 + tile - 1) // tile) * ((120 + tile - 1) // tile)
+    assert np.array_equal(ranges.cpu().numpy().view(np.uint32), oracle.ranges(rk, len(cams) * TT))
+
+
 # --------------------------------------------------------------------------- VF query
 
 @pytest.mark.parametrize("L,P,dtype", [(2, 8, torch.float32), (3, 100, torch.float32), (3, 200, torch.float16),
@@ -119,6 +183,26 @@ def test_vf_query_parity(ctx, gv, L, P, dtype):
         Vr, _ = oracle.vf_query(gq, L, P, cam, sc.means)
         assert np.abs(V[v] - Vr).max() <= TOL
         assert np.all(V[v][:50] == 0.0)
+
+
+def test_vf_query_more_views_than_one_launch(ctx, gv):
+    """2,100 views: the query runs in launches of at most 1,024 cameras; the
+    views of every launch (first, last, and either side of each boundary)
+    match the oracle, and debug bins refuse more cameras than one launch."""
+    sc = sg.tiny_scene(300, seed=5, sh_degree=0)
+    cams = sg.fibonacci_cameras(2100, 3.0, 32, 32, 60.0)
+    rng = np.random.default_rng(9)
+    gamma = np.abs(rng.normal(0, 1, (sc.n, 4))) * 2.0
+    g_dev = torch.as_tensor(gamma, dtype=torch.float32, device="cuda")
+    vf = gv.VisibilityField(g_dev.contiguous(), 1, 5, 1.0)
+    gs = gpu_scene(gv, sc)
+    V = ctx.vf_query(gs, vf, cams).cpu().numpy()
+    assert V.shape == (2100, sc.n)
+    for v in (0, 1, 1023, 1024, 1025, 2047, 2048, 2099):
+        Vr, _ = oracle.vf_query(gamma, 1, 5, cams[v], sc.means)
+        assert np.abs(V[v] - Vr).max() <= TOL, v
+    with pytest.raises(gv.GavisError, match="at most 1024 cameras"):
+        ctx.debug_bins(gs, cams[:1025], gv.Params(tile=16))
 
 
 # --------------------------------------------------------------------------- VF CONST
