@@ -478,7 +478,8 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
         const int nk = __popc(mk);
         // the warp's sums for the entry in slot k are kept by lane k and
         // added to the per-Gaussian totals once per chunk, all lanes at once
-        uint32_t my_sum = 0u, my_cnt = 0u;
+        uint32_t my_sum = 0u;
+        unsigned my_m0 = 0u, my_m1 = 0u;   // the slot's hit masks; counted once per chunk
         for (int k = 0; k < nk; ++k) {
             if (!__any_sync(0xffffffffu, on0 || on1)) break;   // warp-uniform
             const float4 g0 = g0s[k];
@@ -487,14 +488,12 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
             const float q1 = footprint_q(px, py1, g0.x, g0.y, g0.z, g0.w, g1.x);
             const bool h0 = on0 && (q0 <= qcut), h1 = on1 && (q1 <= qcut);
             const unsigned m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
-            if (m0 | m1) {
-                const uint32_t tq = (h0 ? __float2uint_rn(T0 * kTScale) : 0u) + (h1 ? __float2uint_rn(T1 * kTScale) : 0u);
-                const uint32_t sum = __reduce_add_sync(0xffffffffu, tq);
-                const uint32_t c = (uint32_t)(__popc(m0) + __popc(m1));
-                if (lane == k) {
-                    my_sum = sum;
-                    my_cnt = c;
-                }
+            const uint32_t tq = (h0 ? __float2uint_rn(T0 * kTScale) : 0u) + (h1 ? __float2uint_rn(T1 * kTScale) : 0u);
+            const uint32_t sum = __reduce_add_sync(0xffffffffu, tq);
+            if (lane == k) {
+                my_sum = sum;
+                my_m0 = m0;
+                my_m1 = m1;
             }
             if (h0) {
                 T0 = fmaf(-T0, g1.y * ex2_approx(q0 * kNegHalfLog2e), T0);
@@ -505,6 +504,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
                 on1 = T1 >= eps;
             }
         }
+        const uint32_t my_cnt = (uint32_t)(__popc(my_m0) + __popc(my_m1));
         if (my_cnt) {
             const size_t r = vrow + ids[lane];
             atomicAdd(&a.sumT[r], (unsigned long long)my_sum);
