@@ -314,8 +314,9 @@ KeyLayout key_layout(void *base, size_t nrec, size_t M, size_t nseg)
 
 struct SmallLayout {
     uint2 *ranges;
-    float *tile_sums;
-    uint32_t *pair_counts;
+    float *tile_sums;        // one per 8 x 8 pixel block
+    uint32_t *pair_counts;   // likewise
+    unsigned long long *work;
     BatchInfo *info;
     int32_t *best;
     uint32_t *voff;   // [nv + 1] visible records before each view, then [nv + 1] tile entries before each view
@@ -323,15 +324,17 @@ struct SmallLayout {
     size_t bytes;
 };
 
-SmallLayout small_layout(void *base, size_t nvt, size_t nv = 0)
+SmallLayout small_layout(void *base, size_t nvt, size_t nv = 0, int tile = 8)
 {
     SmallLayout L;
     char *p = reinterpret_cast<char *>(base);
     size_t off = 0;
     auto take = [&](size_t b) { char *q = p ? p + off : nullptr; off += align256(b); return q; };
     L.ranges = reinterpret_cast<uint2 *>(take(nvt * sizeof(uint2)));
-    L.tile_sums = reinterpret_cast<float *>(take(nvt * sizeof(float)));
-    L.pair_counts = reinterpret_cast<uint32_t *>(take(nvt * sizeof(uint32_t)));
+    const size_t nblk = nvt * (size_t)blocks_per_tile(tile);
+    L.tile_sums = reinterpret_cast<float *>(take(nblk * sizeof(float)));
+    L.pair_counts = reinterpret_cast<uint32_t *>(take(nblk * sizeof(uint32_t)));
+    L.work = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long)));
     L.info = reinterpret_cast<BatchInfo *>(take(sizeof(BatchInfo)));
     L.best = reinterpret_cast<int32_t *>(take(sizeof(int32_t)));
     L.voff = reinterpret_cast<uint32_t *>(take((2 * nv + 2) * sizeof(uint32_t)));
@@ -398,9 +401,9 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     RecLayout RL = rec_layout(nullptr, nvn, mode == MODE_SCORE, nwords);
     if ((rc = ensure(ctx, ctx->rec, RL.bytes)) != GAVIS_OK) return rc;
     RL = rec_layout(ctx->rec.p, nvn, mode == MODE_SCORE, nwords);
-    SmallLayout SL = small_layout(nullptr, nvt, (size_t)nv);
+    SmallLayout SL = small_layout(nullptr, nvt, (size_t)nv, p->tile);
     if ((rc = ensure(ctx, ctx->small, SL.bytes)) != GAVIS_OK) return rc;
-    SL = small_layout(ctx->small.p, nvt, (size_t)nv);
+    SL = small_layout(ctx->small.p, nvt, (size_t)nv, p->tile);
     if (ctx->h_voff_cap < 2 * (size_t)nv + 2) {
         if (ctx->h_voff) cudaFreeHost(ctx->h_voff);
         ctx->h_voff = nullptr;
@@ -572,6 +575,7 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     ca.n = n; ca.nv = nv; ca.v0 = v0; ca.W = G.W; ca.H = G.H; ca.tile = p->tile; ca.TW = G.TW; ca.TH = G.TH;
     ca.rc = raster_consts(p);
     ca.tile_sums = SL.tile_sums;
+    ca.work = SL.work;
     if (mode == MODE_SCORE) {
         ca.rgb = out.rgb; ca.unc = out.unc; ca.depth = out.depth;
         ca.per_entry_kc = gs->sh_var != nullptr;
@@ -580,9 +584,10 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
             Stage st(ctx, GAVIS_STAGE_COMPOSITE_UA, s);
             CK(launch_composite_ua(ca, s));
         }
-        if (ca.pair_counts) CK(launch_sum_counts(SL.pair_counts, nvt, ctx->d_pairs, s));
+        const int bpt = blocks_per_tile(p->tile);
+        if (ca.pair_counts) CK(launch_sum_counts(SL.pair_counts, nvt * (size_t)bpt, ctx->d_pairs, s));
         Stage st(ctx, GAVIS_STAGE_REDUCE, s);
-        CK(launch_view_reduce(SL.tile_sums, nv, G.TT, 1.0f / ((float)G.W * (float)G.H), out.score + v0, s));
+        CK(launch_view_reduce(SL.tile_sums, nv, G.TT * bpt, 1.0f / ((float)G.W * (float)G.H), out.score + v0, s));
     } else {
         if ((rc = ensure(ctx, ctx->vis, nvn * 12)) != GAVIS_OK) return rc;
         ca.sumT = reinterpret_cast<unsigned long long *>(ctx->vis.p);

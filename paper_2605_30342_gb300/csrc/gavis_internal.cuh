@@ -199,18 +199,23 @@ struct CompositeArgs {
     RasterConsts rc;
     float *rgb, *unc;      // may be NULL
     float *depth;          // expected depth (sum of colour weight x camera depth) or NULL
-    float *tile_sums;      // [nv * TW*TH]
+    float *tile_sums;      // [nv * TW*TH * blocks_per_tile(tile)]: entropy sum of each 8 x 8 pixel block
+    unsigned long long *work;  // uncertainty pass: its work counter (one word, reset by the launch)
     bool per_entry_kc;     // use the per-Gaussian kc of the UaRec (colour variances given)
     // visibility pass
     unsigned long long *sumT;  // [nv * n] fixed point 2^-24
     uint32_t *cnt;             // [nv * n]
     // optional instrumentation: (pixel, Gaussian) pairs composited; the
-    // uncertainty pass writes one count per tile (summed by launch_sum_counts),
+    // uncertainty pass writes one count per 8 x 8 block, like tile_sums (summed by launch_sum_counts),
     // the visibility pass adds per warp into *pairs
     uint32_t *pair_counts;
     unsigned long long *pairs;
 };
+// 8 x 8 pixel blocks per tile: the uncertainty pass's work items
+__host__ __device__ constexpr int blocks_per_tile(int tile) { return (tile / 8) * (tile / 8); }
 cudaError_t launch_composite_ua(const CompositeArgs &a, cudaStream_t s);
+// occupancy queries of the uncertainty pass for a tile size, ahead of a stream capture
+void composite_prepare(int tile);
 cudaError_t launch_composite_vis(const CompositeArgs &a, cudaStream_t s);
 cudaError_t launch_sum_counts(const uint32_t *c, size_t count, unsigned long long *out, cudaStream_t s);
 cudaError_t launch_view_reduce(const float *tile_sums, int nv, int sums_per_view, float inv_pixels,

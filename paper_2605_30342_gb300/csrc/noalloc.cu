@@ -139,7 +139,9 @@ extern "C" int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_v
     uint32_t *pos = reinterpret_cast<uint32_t *>(c.take(n * sizeof(uint32_t)));
     void *scan_tmp = c.take(scan_tmp_bytes(n));
     uint2 *ranges = reinterpret_cast<uint2 *>(c.take((size_t)TT * sizeof(uint2)));
-    float *tile_sums = reinterpret_cast<float *>(c.take((size_t)TT * sizeof(float)));
+    const int bpt = blocks_per_tile(p->tile);
+    float *tile_sums = reinterpret_cast<float *>(c.take((size_t)TT * (size_t)bpt * sizeof(float)));
+    unsigned long long *work = reinterpret_cast<unsigned long long *>(c.take(sizeof(unsigned long long)));
     if (c.off > kNoAllocScratchBytes)
         return report(err, err_len, GAVIS_ERR_BUDGET, "scratch layout exceeds %zu bytes", kNoAllocScratchBytes);
 
@@ -210,9 +212,9 @@ extern "C" int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_v
     const double l2pie = std::log(2.0 * M_PI) + 1.0;
     ca.rc.k_c = (float)(1.5 * std::log((double)p->sigma_c2) + 1.5 * l2pie);
     ca.rc.k_0 = (float)(0.5 * (double)p->logdet_Q0 + 1.5 * l2pie);
-    ca.rgb = rgb; ca.unc = unc; ca.tile_sums = tile_sums;
+    ca.rgb = rgb; ca.unc = unc; ca.tile_sums = tile_sums; ca.work = work;
     ca.per_entry_kc = gs->sh_var != nullptr;
     NA_CK(launch_composite_ua(ca, s));
-    NA_CK(launch_view_reduce(tile_sums, 1, TT, 1.0f / ((float)cam->W * (float)cam->H), score, s));
+    NA_CK(launch_view_reduce(tile_sums, 1, TT * bpt, 1.0f / ((float)cam->W * (float)cam->H), score, s));
     return GAVIS_OK;
 }

@@ -139,7 +139,9 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     const size_t o_bk0 = take(M * 4), o_bk1 = take(M * 4), o_bv0 = take(M * 4), o_bv1 = take(M * 4);
     const size_t big = R > M ? R : M;
     const size_t o_tmp = take(radix_tmp_bytes(big) + scan_tmp_bytes(big) + 64);
-    const size_t o_rng = take(nvt * sizeof(uint2)), o_ts = take(nvt * sizeof(float));
+    const int bpt = blocks_per_tile(p->tile);
+    const size_t o_rng = take(nvt * sizeof(uint2)), o_ts = take(nvt * (size_t)bpt * sizeof(float));
+    const size_t o_work = take(sizeof(unsigned long long));
     PK(cudaMalloc(&pl->buf, off));
     PK(cudaMallocHost(&pl->h_cams, (size_t)n_cams * sizeof(gavis_camera)));
     std::memset(pl->h_cams, 0, (size_t)n_cams * sizeof(gavis_camera));
@@ -164,6 +166,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     void *tmp = b + o_tmp, *scan_tmp = b + o_scan;
     uint2 *ranges = reinterpret_cast<uint2 *>(b + o_rng);
     float *tile_sums = reinterpret_cast<float *>(b + o_ts);
+    unsigned long long *work = reinterpret_cast<unsigned long long *>(b + o_work);
 
     ProjectArgs pa{};
     pa.means = gs->means; pa.scales = gs->scales; pa.rots = gs->rots; pa.opac = gs->opac;
@@ -184,11 +187,12 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     const double l2pie = std::log(2.0 * M_PI) + 1.0;
     ca.rc.k_c = pa.k_c;
     ca.rc.k_0 = (float)(0.5 * (double)p->logdet_Q0 + 1.5 * l2pie);
-    ca.rgb = rgb; ca.unc = unc; ca.tile_sums = tile_sums;
+    ca.rgb = rgb; ca.unc = unc; ca.tile_sums = tile_sums; ca.work = work;
     ca.per_entry_kc = gs->sh_var != nullptr;
 
     // the chain of every batch, captured on a private stream
     radix_prepare();
+    composite_prepare(p->tile);
     PK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     const long long k0 = g_launches.load();
     PK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -224,7 +228,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
         PK(cudaMemsetAsync(ranges, 0, nvt_b * sizeof(uint2), cs));
         PK(launch_ranges(keys, M, ranges, cs, &info->b.total));
         PK(launch_composite_ua(ca, cs));
-        PK(launch_view_reduce(tile_sums, nv, TT, 1.0f / ((float)W * (float)H), score + v0, cs));
+        PK(launch_view_reduce(tile_sums, nv, TT * bpt, 1.0f / ((float)W * (float)H), score + v0, cs));
     }
     if (best_dev) PK(launch_argmax(score, n_cams, best_dev, cs));
     PK(cudaStreamEndCapture(cs, &pl->graph));

@@ -25,6 +25,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <atomic>
+
 #include "gavis_internal.cuh"
 #include "sh_basis.cuh"
 
@@ -237,182 +239,184 @@ __device__ __forceinline__ float lg2_approx(float x)
 constexpr float kNegHalfLog2e = -0.72134752044448170368f;   // -log2(e) / 2
 constexpr float kLn2 = 0.69314718055994530942f;
 
-// Uncertainty + colour compositing.  Each warp owns an 8 x 8 pixel block of
-// the tile (each thread two pixels, (x, y) and (x, y + 4)) and walks the
+// Uncertainty + colour compositing.  The work items are the 8 x 8 pixel
+// blocks of every (view, tile), in view-major order; a persistent grid of
+// 4-warp CTAs runs them, each warp taking the next item from a global counter
+// as soon as it has finished the last, so that no warp waits for another
+// (the items' lengths differ a lot: list length and early saturation).  For
+// an item the warp (each thread two pixels, (x, y) and (x, y + 4)) walks the
 // tile's depth-sorted list on its own, 32 entries at a time: every lane loads
-// one entry's footprint, the entries whose box touches the block are
+// one entry's footprint, the entries whose footprint touches the block are
 // compacted (in list order) into the warp's shared-memory slots, and the warp
-// composites them.  A warp stops as soon as all its pixels are saturated;
-// warps never wait for each other until the final tile sum.
+// composites them.  It stops as soon as all its pixels are saturated.
 // Per pixel and overlapping entry: alpha = o 2^(-q log2(e)/2); colour
 // w = alpha Tc, Tc -= w; uncertainty alpha* = a1 alpha + a0 (eq:alpha_comp),
 // w = alpha* T, wv = w V, T -= w.  The entropy bound (eq:huber) is assembled
 // once per pixel from sum(wv), sum(wv log2 wv) and the prior mass
-// w0 = (1 - T) - sum(wv).
+// w0 = (1 - T) - sum(wv); each item writes its pixels' sum to
+// tile_sums[item] (summed per view in item order: deterministic).
 // KC: the visible components carry per-Gaussian kc (colour variances given);
 // otherwise the constant k_c is applied to sum(wv) once per pixel.
 // DEPTH: also accumulate the expected depth sum_i alpha_i T_c,i z_i along the
 // colour path (into a.depth).
+constexpr int kUaWarps = 4;   // warps per CTA of the uncertainty pass
+
 template <int TILE, bool KC, bool DEPTH>
-__global__ void __launch_bounds__(TILE *TILE / 2) k_composite_ua(CompositeArgs a)
+__global__ void __launch_bounds__(kUaWarps * 32) k_composite_ua(CompositeArgs a)
 {
-    constexpr int NT = TILE * TILE / 2;
-    constexpr int NW = NT / 32;
-    static_assert((TILE / 8) * (TILE / 8) == NW, "one warp per 8 x 8 pixel block");
+    constexpr int NW = kUaWarps;
+    constexpr int BPT = blocks_per_tile(TILE);
     __shared__ float4 s_g0[NW][32];   // u, v, A, 2B
     __shared__ float2 s_g1[NW][32];   // C, opacity
     __shared__ float4 s_u0[NW][32];   // a1, a0, V, r
     __shared__ float2 s_u1[NW][32];   // g, b
     __shared__ float s_kc[KC ? NW : 1][32];
     __shared__ float s_z[DEPTH ? NW : 1][32];
-    __shared__ float s_red[NW];
-    __shared__ uint32_t s_pairs[NW];
 
     const int tiles = a.TW * a.TH;
-    const int vb = blockIdx.x / tiles;
-    const int t = blockIdx.x - vb * tiles;
-    const int tx = t % a.TW, ty = t / a.TW;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned long long items = (unsigned long long)a.nv * (unsigned long long)tiles * BPT;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    const int wx = (warp % (TILE / 8)) * 8, wy = (warp / (TILE / 8)) * 8;
-    const int i = tx * TILE + wx + (lane & 7);
-    const int j0 = ty * TILE + wy + (lane >> 3);
-    const float bx0 = (float)(tx * TILE + wx) + 0.5f, bx1 = bx0 + 7.0f;
-    const float by0 = (float)(ty * TILE + wy) + 0.5f, by1 = by0 + 7.0f;
-    const float px = (float)i + 0.5f;
-    const uint2 rg = a.ranges[blockIdx.x];
-    const size_t vrow = (size_t)vb * (size_t)a.n;
     const RasterConsts rc = a.rc;
-
     const bool colour = DEPTH || a.rgb != nullptr;   // colour path only when asked for
-    float T[2], Tc[2], sl[2], swv[2], skc[2], cr[2], cg[2], cb[2], py[2], dz[2];
-    bool ua_on[2], rgb_on[2], inside[2];
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const int j = j0 + 4 * p;
-        inside[p] = i < a.W && j < a.H;
-        py[p] = (float)j + 0.5f;
-        T[p] = 1.0f; Tc[p] = 1.0f; sl[p] = 0.0f; swv[p] = 0.0f; skc[p] = 0.0f; cr[p] = 0.0f; cg[p] = 0.0f; cb[p] = 0.0f;
-        dz[p] = 0.0f;
-        ua_on[p] = inside[p];
-        rgb_on[p] = inside[p] && colour;
-    }
-    uint32_t npairs = 0;
     float *kcs = s_kc[KC ? warp : 0];
     float *zs = s_z[DEPTH ? warp : 0];
     float4 *g0s = s_g0[warp];
     float2 *g1s = s_g1[warp];
     float4 *u0s = s_u0[warp];
     float2 *u1s = s_u1[warp];
-
-    uint32_t nval = rg.x + lane < rg.y ? a.vals[rg.x + lane] : 0u;   // this lane's entry of the next chunk
-    for (uint32_t base = rg.x; base < rg.y; base += 32) {
-        if (!__any_sync(0xffffffffu, ua_on[0] || rgb_on[0] || ua_on[1] || rgb_on[1])) break;
-        const uint32_t e = base + lane;
-        const uint32_t val = nval;
-        const bool more = e + 32 < rg.y;
-        if (more) nval = a.vals[e + 32];
-        bool mine = false;
-        GeoRec gr;
-        size_t r = 0;
-        if (e < rg.y) {
-            r = vrow + val;
-            gr = a.geo[r];
-            mine = !box_misses(footprint_box(gr.a.x, gr.a.y, gr.b.w), bx0, bx1, by0, by1) &&
-                   !ellipse_misses(gr.a.x, gr.a.y, gr.a.z, gr.a.w, gr.b.x, bx0, bx1, by0, by1, rc.q_cut);
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, mine);
-        if (mine) {
-            const int slot = __popc(m & lt);
-            const UaRec ur = a.ua[r];
-            g0s[slot] = gr.a;
-            g1s[slot] = make_float2(gr.b.x, gr.b.y);
-            u0s[slot] = ur.a;
-            u1s[slot] = make_float2(ur.b.x, ur.b.y);
-            if (KC) kcs[slot] = ur.b.z;
-            if (DEPTH) zs[slot] = gr.b.z;
-        }
-        __syncwarp();
-        if (more) {
-            prefetch_l2(a.geo + vrow + nval);
-            prefetch_l2(a.ua + vrow + nval);
-        }
-        const int nk = __popc(m);
-        // Straight-line body: a pixel that misses the entry, or whose
-        // accumulator has saturated, gets a zero opacity for it, which leaves
-        // every sum and transmittance exactly as it was.
-        for (int k = 0; k < nk && (ua_on[0] || rgb_on[0] || ua_on[1] || rgb_on[1]); ++k) {
-            const float4 g0 = g0s[k];
-            const float2 g1 = g1s[k];
-            const float4 u0 = u0s[k];
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const float q = footprint_q(px, py[p], g0.x, g0.y, g0.z, g0.w, g1.x);
-                const bool hit = q <= rc.q_cut;
-                const bool hc = hit && rgb_on[p], hu = hit && ua_on[p];
-                npairs += (uint32_t)(hc || hu);
-                const float alpha = g1.y * ex2_approx(q * kNegHalfLog2e);
-                if (colour) {   // the same for every thread of the launch
-                    const float2 u1 = u1s[k];
-                    const float ac = hc ? alpha : 0.0f;
-                    const float wc = ac * Tc[p];
-                    cr[p] = fmaf(wc, u0.w, cr[p]);
-                    cg[p] = fmaf(wc, u1.x, cg[p]);
-                    cb[p] = fmaf(wc, u1.y, cb[p]);
-                    if (DEPTH) dz[p] = fmaf(wc, zs[k], dz[p]);
-                    Tc[p] -= wc;
-                    rgb_on[p] = Tc[p] >= rc.eps_T;
-                }
-                const float as = hu ? fmaf(alpha, u0.x, u0.y) : 0.0f;   // eq:alpha_comp
-                const float w = as * T[p];
-                const float wv = w * u0.z;                               // weight of the visible component
-                sl[p] = fmaf(wv, lg2_approx(fmaxf(wv, 1e-30f)), sl[p]);
-                swv[p] += wv;
-                if (KC) skc[p] = fmaf(wv, kcs[k], skc[p]);
-                T[p] -= w;
-                ua_on[p] = T[p] >= rc.eps_T;
-            }
-        }
-        __syncwarp();
-    }
-    float h = 0.0f;
-    const size_t vg = (size_t)(a.v0 + vb);
     const size_t plane = (size_t)a.W * a.H;
+
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(a.work, 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= items) break;
+        const unsigned long long bt = item / BPT;   // (view, tile)
+        const int blk = (int)(item - bt * BPT);
+        const int vb = (int)(bt / (unsigned long long)tiles);
+        const int t = (int)(bt - (unsigned long long)vb * tiles);
+        const int tx = t % a.TW, ty = t / a.TW;
+        const int wx = (blk % (TILE / 8)) * 8, wy = (blk / (TILE / 8)) * 8;
+        const int i = tx * TILE + wx + (lane & 7);
+        const int j0 = ty * TILE + wy + (lane >> 3);
+        const float bx0 = (float)(tx * TILE + wx) + 0.5f, bx1 = bx0 + 7.0f;
+        const float by0 = (float)(ty * TILE + wy) + 0.5f, by1 = by0 + 7.0f;
+        const float px = (float)i + 0.5f;
+        const uint2 rg = a.ranges[bt];
+        const size_t vrow = (size_t)vb * (size_t)a.n;
+
+        float T[2], Tc[2], sl[2], swv[2], skc[2], cr[2], cg[2], cb[2], py[2], dz[2];
+        bool ua_on[2], rgb_on[2], inside[2];
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        if (!inside[p]) continue;
-        // eq:huber: visible components sum wv (k_c - ln wv); prior w0 (k_0 - ln w0)
-        const float w0 = fmaxf((1.0f - T[p]) - swv[p], 0.0f);
-        float Hs = (KC ? skc[p] : rc.k_c * swv[p]) - kLn2 * sl[p];
-        if (w0 > 1e-30f) Hs = fmaf(w0, rc.k_0 - kLn2 * lg2_approx(w0), Hs);
-        const size_t pix = (size_t)(j0 + 4 * p) * a.W + i;
-        if (a.unc) a.unc[vg * plane + pix] = Hs;
-        if (DEPTH) a.depth[vg * plane + pix] = dz[p];
-        if (a.rgb) {
-            a.rgb[(vg * 3 + 0) * plane + pix] = cr[p];
-            a.rgb[(vg * 3 + 1) * plane + pix] = cg[p];
-            a.rgb[(vg * 3 + 2) * plane + pix] = cb[p];
+        for (int p = 0; p < 2; ++p) {
+            const int j = j0 + 4 * p;
+            inside[p] = i < a.W && j < a.H;
+            py[p] = (float)j + 0.5f;
+            T[p] = 1.0f; Tc[p] = 1.0f; sl[p] = 0.0f; swv[p] = 0.0f; skc[p] = 0.0f; cr[p] = 0.0f; cg[p] = 0.0f; cb[p] = 0.0f;
+            dz[p] = 0.0f;
+            ua_on[p] = inside[p];
+            rgb_on[p] = inside[p] && colour;
         }
-        h += Hs;
-    }
-    // tile partial sum of the per-pixel entropy (fixed order: deterministic)
+        uint32_t npairs = 0;
+
+        uint32_t nval = rg.x + lane < rg.y ? a.vals[rg.x + lane] : 0u;   // this lane's entry of the next chunk
+        for (uint32_t base = rg.x; base < rg.y; base += 32) {
+            if (!__any_sync(0xffffffffu, ua_on[0] || rgb_on[0] || ua_on[1] || rgb_on[1])) break;
+            const uint32_t e = base + lane;
+            const uint32_t val = nval;
+            const bool more = e + 32 < rg.y;
+            if (more) nval = a.vals[e + 32];
+            bool mine = false;
+            GeoRec gr;
+            size_t r = 0;
+            if (e < rg.y) {
+                r = vrow + val;
+                gr = a.geo[r];
+                mine = !box_misses(footprint_box(gr.a.x, gr.a.y, gr.b.w), bx0, bx1, by0, by1) &&
+                       !ellipse_misses(gr.a.x, gr.a.y, gr.a.z, gr.a.w, gr.b.x, bx0, bx1, by0, by1, rc.q_cut);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, mine);
+            if (mine) {
+                const int slot = __popc(m & lt);
+                const UaRec ur = a.ua[r];
+                g0s[slot] = gr.a;
+                g1s[slot] = make_float2(gr.b.x, gr.b.y);
+                u0s[slot] = ur.a;
+                u1s[slot] = make_float2(ur.b.x, ur.b.y);
+                if (KC) kcs[slot] = ur.b.z;
+                if (DEPTH) zs[slot] = gr.b.z;
+            }
+            __syncwarp();
+            if (more) {
+                prefetch_l2(a.geo + vrow + nval);
+                prefetch_l2(a.ua + vrow + nval);
+            }
+            const int nk = __popc(m);
+            // Straight-line body: a pixel that misses the entry, or whose
+            // accumulator has saturated, gets a zero opacity for it, which
+            // leaves every sum and transmittance exactly as it was.
+            for (int k = 0; k < nk && (ua_on[0] || rgb_on[0] || ua_on[1] || rgb_on[1]); ++k) {
+                const float4 g0 = g0s[k];
+                const float2 g1 = g1s[k];
+                const float4 u0 = u0s[k];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) h += __shfl_down_sync(0xffffffffu, h, o);
-    const uint32_t wp = __reduce_add_sync(0xffffffffu, npairs);
-    if (lane == 0) {
-        s_red[warp] = h;
-        s_pairs[warp] = wp;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        float sum = 0.0f;
-        uint32_t np = 0;
-        for (int w = 0; w < NW; ++w) {
-            sum += s_red[w];
-            np += s_pairs[w];
+                for (int p = 0; p < 2; ++p) {
+                    const float q = footprint_q(px, py[p], g0.x, g0.y, g0.z, g0.w, g1.x);
+                    const bool hit = q <= rc.q_cut;
+                    const bool hc = hit && rgb_on[p], hu = hit && ua_on[p];
+                    npairs += (uint32_t)(hc || hu);
+                    const float alpha = g1.y * ex2_approx(q * kNegHalfLog2e);
+                    if (colour) {   // the same for every thread of the launch
+                        const float2 u1 = u1s[k];
+                        const float ac = hc ? alpha : 0.0f;
+                        const float wc = ac * Tc[p];
+                        cr[p] = fmaf(wc, u0.w, cr[p]);
+                        cg[p] = fmaf(wc, u1.x, cg[p]);
+                        cb[p] = fmaf(wc, u1.y, cb[p]);
+                        if (DEPTH) dz[p] = fmaf(wc, zs[k], dz[p]);
+                        Tc[p] -= wc;
+                        rgb_on[p] = Tc[p] >= rc.eps_T;
+                    }
+                    const float as = hu ? fmaf(alpha, u0.x, u0.y) : 0.0f;   // eq:alpha_comp
+                    const float w = as * T[p];
+                    const float wv = w * u0.z;                               // weight of the visible component
+                    sl[p] = fmaf(wv, lg2_approx(fmaxf(wv, 1e-30f)), sl[p]);
+                    swv[p] += wv;
+                    if (KC) skc[p] = fmaf(wv, kcs[k], skc[p]);
+                    T[p] -= w;
+                    ua_on[p] = T[p] >= rc.eps_T;
+                }
+            }
+            __syncwarp();
         }
-        a.tile_sums[blockIdx.x] = sum;
-        if (a.pair_counts) a.pair_counts[blockIdx.x] = np;
+        float h = 0.0f;
+        const size_t vg = (size_t)(a.v0 + vb);
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            if (!inside[p]) continue;
+            // eq:huber: visible components sum wv (k_c - ln wv); prior w0 (k_0 - ln w0)
+            const float w0 = fmaxf((1.0f - T[p]) - swv[p], 0.0f);
+            float Hs = (KC ? skc[p] : rc.k_c * swv[p]) - kLn2 * sl[p];
+            if (w0 > 1e-30f) Hs = fmaf(w0, rc.k_0 - kLn2 * lg2_approx(w0), Hs);
+            const size_t pix = (size_t)(j0 + 4 * p) * a.W + i;
+            if (a.unc) a.unc[vg * plane + pix] = Hs;
+            if (DEPTH) a.depth[vg * plane + pix] = dz[p];
+            if (a.rgb) {
+                a.rgb[(vg * 3 + 0) * plane + pix] = cr[p];
+                a.rgb[(vg * 3 + 1) * plane + pix] = cg[p];
+                a.rgb[(vg * 3 + 2) * plane + pix] = cb[p];
+            }
+            h += Hs;
+        }
+        // the block's partial sum of the per-pixel entropy (fixed order: deterministic)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) h += __shfl_down_sync(0xffffffffu, h, o);
+        const uint32_t wp = __reduce_add_sync(0xffffffffu, npairs);
+        if (lane == 0) {
+            a.tile_sums[item] = h;
+            if (a.pair_counts) a.pair_counts[item] = wp;
+        }
     }
 }
 
@@ -760,32 +764,85 @@ cudaError_t launch_keys_export(const uint32_t *keyB, const uint32_t *valB, size_
     return cudaGetLastError();
 }
 
-template <int TILE>
-void launch_ua_tile(const CompositeArgs &a, unsigned blocks, cudaStream_t s)
+// Persistent grid of the uncertainty pass: as many CTAs as fit on the device
+// at once (cached per device and kernel instance), fewer for small batches.
+constexpr int kMaxDevices = 64;
+struct UaGrid {
+    std::atomic<int> ctas[kMaxDevices];
+};
+
+template <int TILE, bool KC, bool DEPTH>
+unsigned ua_resident_ctas()
 {
-    constexpr int NT = TILE * TILE / 2;
+    static UaGrid g;   // zero-initialised: computed on first use per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= kMaxDevices) dev = 0;
+    int c = g.ctas[dev].load(std::memory_order_relaxed);
+    if (c == 0) {
+        int per_sm = 0, nsm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite_ua<TILE, KC, DEPTH>, kUaWarps * 32, 0);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        c = (per_sm > 0 ? per_sm : 1) * (nsm > 0 ? nsm : 1);
+        g.ctas[dev].store(c, std::memory_order_relaxed);
+    }
+    return (unsigned)c;
+}
+
+template <int TILE, bool KC, bool DEPTH>
+void launch_ua_inst(const CompositeArgs &a, unsigned long long items, cudaStream_t s)
+{
+    const unsigned long long want = (items + kUaWarps - 1) / kUaWarps;
+    const unsigned cap = ua_resident_ctas<TILE, KC, DEPTH>();
+    const unsigned blocks = want < cap ? (unsigned)want : cap;
+    k_composite_ua<TILE, KC, DEPTH><<<blocks, kUaWarps * 32, 0, s>>>(a);
+}
+
+template <int TILE>
+void launch_ua_tile(const CompositeArgs &a, unsigned long long items, cudaStream_t s)
+{
     const bool d = a.depth != nullptr;
     if (a.per_entry_kc) {
-        if (d) k_composite_ua<TILE, true, true><<<blocks, NT, 0, s>>>(a);
-        else k_composite_ua<TILE, true, false><<<blocks, NT, 0, s>>>(a);
+        if (d) launch_ua_inst<TILE, true, true>(a, items, s);
+        else launch_ua_inst<TILE, true, false>(a, items, s);
     } else {
-        if (d) k_composite_ua<TILE, false, true><<<blocks, NT, 0, s>>>(a);
-        else k_composite_ua<TILE, false, false><<<blocks, NT, 0, s>>>(a);
+        if (d) launch_ua_inst<TILE, false, true>(a, items, s);
+        else launch_ua_inst<TILE, false, false>(a, items, s);
     }
     count_launch();
 }
 
+template <int TILE>
+void prepare_ua_tile()
+{
+    ua_resident_ctas<TILE, true, true>();
+    ua_resident_ctas<TILE, true, false>();
+    ua_resident_ctas<TILE, false, true>();
+    ua_resident_ctas<TILE, false, false>();
+}
+
 cudaError_t launch_composite_ua(const CompositeArgs &a, cudaStream_t s)
 {
-    const unsigned blocks = (unsigned)(a.nv * a.TW * a.TH);
-    if (blocks == 0) return cudaSuccess;
+    const unsigned long long items =
+        (unsigned long long)a.nv * (unsigned long long)(a.TW * a.TH) * (unsigned long long)blocks_per_tile(a.tile);
+    if (items == 0) return cudaSuccess;
+    if (!a.work) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s);   // the work counter
+    if (e != cudaSuccess) return e;
     switch (a.tile) {
-    case 8: launch_ua_tile<8>(a, blocks, s); break;
-    case 16: launch_ua_tile<16>(a, blocks, s); break;
-    case 32: launch_ua_tile<32>(a, blocks, s); break;
+    case 8: launch_ua_tile<8>(a, items, s); break;
+    case 16: launch_ua_tile<16>(a, items, s); break;
+    case 32: launch_ua_tile<32>(a, items, s); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+void composite_prepare(int tile)
+{
+    if (tile == 8) prepare_ua_tile<8>();
+    if (tile == 16) prepare_ua_tile<16>();
+    if (tile == 32) prepare_ua_tile<32>();
 }
 
 cudaError_t launch_composite_vis(const CompositeArgs &a, cudaStream_t s)
