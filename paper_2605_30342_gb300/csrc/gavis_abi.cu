@@ -304,9 +304,9 @@ KeyLayout key_layout(void *base, size_t nrec, size_t M, size_t nseg)
     L.b_k1 = reinterpret_cast<uint32_t *>(take(M * 4));
     L.b_v0 = reinterpret_cast<uint32_t *>(take(M * 4));
     L.b_v1 = reinterpret_cast<uint32_t *>(take(M * 4));
-    L.blk_a = reinterpret_cast<RsBlock *>(take((nrec / 4096 + nseg + 1) * sizeof(RsBlock)));
-    L.blk_b = reinterpret_cast<RsBlock *>(take((M / 4096 + nseg + 1) * sizeof(RsBlock)));
-    const size_t big = (nrec > M ? nrec : M) + (nseg + 1) * 4096;   // a partial block per segment at most
+    L.blk_a = reinterpret_cast<RsBlock *>(take((nrec / kRadixTile + nseg + 1) * sizeof(RsBlock)));
+    L.blk_b = reinterpret_cast<RsBlock *>(take((M / kRadixTile + nseg + 1) * sizeof(RsBlock)));
+    const size_t big = (nrec > M ? nrec : M) + (nseg + 1) * (size_t)kRadixTile;   // a partial block per segment at most
     L.tmp = take(radix_tmp_bytes(big) + scan_tmp_bytes(big) + 64);
     L.bytes = off;
     return L;

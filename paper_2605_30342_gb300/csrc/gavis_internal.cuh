@@ -50,6 +50,8 @@ struct RasterConsts {
 constexpr float kTScale = 16777216.0f;   // 2^24
 // views one projection or query launch takes: their cameras sit in shared memory
 constexpr int kMaxBatchViews = 1024;
+// keys per block of the radix sort passes (one histogram row per block)
+constexpr int kRadixTile = 4096;
 
 // ---------------------------------------------------------------- project.cu
 struct ProjectArgs {

@@ -199,8 +199,9 @@ __global__ void k_emit_vis_words(const uint32_t *words, const uint32_t *woff, ui
 }
 
 constexpr int kRsThreads = 256;
-constexpr int kRsRounds = 16;
-constexpr int kRsTile = kRsThreads * kRsRounds;   // 4096 keys per block
+constexpr int kRsTile = kRadixTile;
+constexpr int kRsRounds = kRsTile / kRsThreads;
+static_assert(kRsRounds * kRsThreads == kRsTile, "whole rounds of 256 keys per block");
 constexpr int kRsWarps = kRsThreads / 32;
 
 // Lanes of the warp holding the same digit d as this lane (d = 256 marks an
@@ -265,16 +266,26 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const KeyT *keys, siz
     }
     for (int i = threadIdx.x; i < kRsWarps * 257; i += kRsThreads) (&s_h[0][0])[i] = 0u;
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll 4
-    for (int r = 0; r < kRsRounds; ++r) {
-        const size_t i = base + (size_t)r * kRsThreads + threadIdx.x;
-        const int d = i < n ? (int)((keys[i] >> shift) & 255u) : 256;
-        const int d0 = __shfl_sync(0xffffffffu, d, 0);
-        if (__all_sync(0xffffffffu, d == d0)) {
-            if (lane == 0) atomicAdd(&s_h[warp][d0], 32u);
-        } else {
-            atomicAdd(&s_h[warp][d], 1u);
+    const int warp = threadIdx.x >> 5;
+    // The block's keys [base, n) are read as the 16-byte words that hold them
+    // (key buffers start 16-byte aligned and are padded to 256 bytes, so the
+    // word of the last key lies inside the buffer); keys outside are skipped.
+    constexpr int E = 16 / (int)sizeof(KeyT);
+    const size_t w0 = base / E, w1 = (n + E - 1) / E;
+    const uint4 *kw = reinterpret_cast<const uint4 *>(keys);
+    constexpr int WR = (kRsTile / E + kRsThreads - 1) / kRsThreads + 1;   // words per thread, at most
+#pragma unroll
+    for (int r = 0; r < WR; ++r) {
+        const size_t w = w0 + (size_t)r * kRsThreads + threadIdx.x;
+        if (w < w1) {
+            const uint4 q = kw[w];
+            KeyT kk[E];
+            memcpy(kk, &q, sizeof(q));
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                const size_t i = w * E + (size_t)j;
+                if (i >= base && i < n) atomicAdd(&s_h[warp][(int)((kk[j] >> shift) & 255u)], 1u);
+            }
         }
     }
     __syncthreads();
@@ -294,7 +305,7 @@ template <typename KeyT>
 constexpr size_t rs_smem() { return (size_t)kRsTile * (sizeof(KeyT) + 4) + (size_t)(kRsWarps + 3) * 256 * 4; }
 
 template <typename KeyT, bool BALLOT>
-__global__ void __launch_bounds__(kRsThreads, 2) k_radix_scatter(const KeyT *kin, const uint32_t *vin,
+__global__ void __launch_bounds__(kRsThreads, 8192 / kRsTile) k_radix_scatter(const KeyT *kin, const uint32_t *vin,
                                                               KeyT *kout, uint32_t *vout, size_t n, int shift,
                                                               const uint32_t *hist, const uint32_t *offs,
                                                               int nblocks, const unsigned long long *d_n,
@@ -334,7 +345,7 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_radix_scatter(const KeyT *kin
     }
 
     // phase A: warp-private stable ranks
-    constexpr int R = kRsTile / kRsThreads;   // 16 rounds of 32 items per warp
+    constexpr int R = kRsTile / kRsThreads;   // rounds of 32 items per warp
     KeyT k[R];
     uint32_t v[R], rk[R];
     int d[R];
