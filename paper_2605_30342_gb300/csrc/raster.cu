@@ -199,17 +199,28 @@ __global__ void k_ranges(const uint32_t *keys, size_t M, uint2 *ranges, const un
                          uint32_t TT)
 {
     if (d_M && *d_M < M) M = (size_t)*d_M;
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // one 16-byte word per thread: keys [4w, 4w + 4) (key buffers start 16-byte
+    // aligned and are padded, so the word of the last key lies inside them)
+    const size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t i0 = 4 * w;
     const unsigned lane = threadIdx.x & 31u;
-    // neighbours from the adjacent lanes; the warp's two edge lanes load theirs
-    const uint32_t t = i < M ? keys[i] : 0xffffffffu;
-    uint32_t prev = __shfl_up_sync(0xffffffffu, t, 1), next = __shfl_down_sync(0xffffffffu, t, 1);
-    if (i >= M) return;
-    if (lane == 0 && i > 0) prev = keys[i - 1];
-    if (lane == 31 && i + 1 < M) next = keys[i + 1];
-    const uint32_t ti = tile_index(t, tb, TT);
-    if (i == 0 || prev != t) ranges[ti].x = (uint32_t)i;
-    if (i == M - 1 || next != t) ranges[ti].y = (uint32_t)(i + 1);
+    uint4 q = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+    if (i0 < M) q = reinterpret_cast<const uint4 *>(keys)[w];
+    // the neighbours across words come from the adjacent lanes; the warp's two edge lanes load theirs
+    uint32_t prev = __shfl_up_sync(0xffffffffu, q.w, 1), next = __shfl_down_sync(0xffffffffu, q.x, 1);
+    if (i0 >= M) return;
+    if (lane == 0 && i0 > 0) prev = keys[i0 - 1];
+    if (lane == 31 && i0 + 4 < M) next = keys[i0 + 4];
+    const uint32_t k[6] = {prev, q.x, q.y, q.z, q.w, next};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const size_t i = i0 + (size_t)j;
+        if (i >= M) break;
+        const uint32_t t = k[j + 1];
+        const uint32_t ti = tile_index(t, tb, TT);
+        if (i == 0 || k[j] != t) ranges[ti].x = (uint32_t)i;
+        if (i == M - 1 || k[j + 2] != t) ranges[ti].y = (uint32_t)(i + 1);
+    }
 }
 
 __global__ void k_keys_export(const uint32_t *keyB, const uint32_t *valB, size_t M, const GeoRec *geo, int64_t n,
@@ -752,7 +763,7 @@ cudaError_t launch_ranges(const uint32_t *keys, size_t M, uint2 *ranges, cudaStr
                           int tb, uint32_t TT)
 {
     if (M == 0) return cudaSuccess;
-    k_ranges<<<nblk(M, 256), 256, 0, s>>>(keys, M, ranges, d_M, tb, TT); count_launch();
+    k_ranges<<<nblk((M + 3) / 4, 256), 256, 0, s>>>(keys, M, ranges, d_M, tb, TT); count_launch();
     return cudaGetLastError();
 }
 
