@@ -474,7 +474,8 @@ def run_gavis(args):
         ms, nl = st[dom]
         achieved = pairs * fpp / (ms / 1e3) / 1e12
         roof = {"kernel": "k_" + dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": traffic_for("k_" + dom),
+                "frac": achieved / fp32_peak,
+                "traffic": traffic_for("k_" + dom, prm_sc.tile if dom == "composite_ua" else prm_vf.tile),
                 "peak_source": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
                                f"(sm_max_mhz of {pk_kind} peaks file)",
                 "units_per_launch": pairs / max(nl, 1), "unit_name": "pixel-Gaussian pairs",
@@ -545,16 +546,16 @@ def kernel_source_sha(path, kernel):
     return None
 
 
-def traffic_for(kernel):
+def traffic_for(kernel, tile):
     """DRAM bytes per launch from the committed ncu summary, when it was taken
-    on the current source of the kernel (else null)."""
+    on the current source of the kernel at the same tile size (else null)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     try:
         with open(p) as f:
             d = json.load(f)
-        e = d.get(kernel)
+        e = d.get(f"{kernel}/tile{tile}")
         if not e:
             return None
         src = os.path.join(ROOT, "paper_2605_30342_gb300", "csrc", e["source"])
