@@ -203,6 +203,7 @@ struct CompositeArgs {
     float *depth;          // expected depth (sum of colour weight x camera depth) or NULL
     float *tile_sums;      // [nv * TW*TH * blocks_per_tile(tile)]: entropy sum of each 8 x 8 pixel block
     unsigned long long *work;  // uncertainty pass: its work counter (one word, reset by the launch)
+    const uint32_t *order;     // uncertainty pass: (view, tile) indices, longest lists first, or NULL (natural order)
     bool per_entry_kc;     // use the per-Gaussian kc of the UaRec (colour variances given)
     // visibility pass
     unsigned long long *sumT;  // [nv * n] fixed point 2^-24
@@ -218,6 +219,10 @@ __host__ __device__ constexpr int blocks_per_tile(int tile) { return (tile / 8) 
 cudaError_t launch_composite_ua(const CompositeArgs &a, cudaStream_t s);
 // occupancy queries of the uncertainty pass for a tile size, ahead of a stream capture
 void composite_prepare(int tile);
+// Order of the uncertainty pass's tiles: keys[t] = 255 - min(list length / 16, 255),
+// vals[t] = t for the nt (view, tile) ranges; sorted stably on the 8 key bits
+// (one radix pass) the values list the longest lists first.
+cudaError_t launch_order_keys(const uint2 *ranges, size_t nt, uint32_t *keys, uint32_t *vals, cudaStream_t s);
 cudaError_t launch_composite_vis(const CompositeArgs &a, cudaStream_t s);
 cudaError_t launch_sum_counts(const uint32_t *c, size_t count, unsigned long long *out, cudaStream_t s);
 cudaError_t launch_view_reduce(const float *tile_sums, int nv, int sums_per_view, float inv_pixels,

@@ -223,6 +223,17 @@ __global__ void k_ranges(const uint32_t *keys, size_t M, uint2 *ranges, const un
     }
 }
 
+__global__ void k_order_keys(const uint2 *ranges, size_t nt, uint32_t *keys, uint32_t *vals)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const uint2 rg = ranges[t];
+    const uint32_t len = rg.y > rg.x ? rg.y - rg.x : 0u;
+    const uint32_t q = len >> 4;
+    keys[t] = 255u - (q < 255u ? q : 255u);
+    vals[t] = (uint32_t)t;
+}
+
 __global__ void k_keys_export(const uint32_t *keyB, const uint32_t *valB, size_t M, const GeoRec *geo, int64_t n,
                               int tiles_per_view, uint64_t *out, int tb)
 {
@@ -303,8 +314,9 @@ __global__ void __launch_bounds__(kUaWarps * 32) k_composite_ua(CompositeArgs a)
         if (lane == 0) item = atomicAdd(a.work, 1ull);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= items) break;
-        const unsigned long long bt = item / BPT;   // (view, tile)
-        const int blk = (int)(item - bt * BPT);
+        const unsigned long long slot = item / BPT;
+        const int blk = (int)(item - slot * BPT);
+        const unsigned long long bt = a.order ? (unsigned long long)a.order[slot] : slot;   // (view, tile)
         const int vb = (int)(bt / (unsigned long long)tiles);
         const int t = (int)(bt - (unsigned long long)vb * tiles);
         const int tx = t % a.TW, ty = t / a.TW;
@@ -424,9 +436,9 @@ __global__ void __launch_bounds__(kUaWarps * 32) k_composite_ua(CompositeArgs a)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) h += __shfl_down_sync(0xffffffffu, h, o);
         const uint32_t wp = __reduce_add_sync(0xffffffffu, npairs);
-        if (lane == 0) {
-            a.tile_sums[item] = h;
-            if (a.pair_counts) a.pair_counts[item] = wp;
+        if (lane == 0) {   // at the block's natural index: summed per view in (tile, block) order
+            a.tile_sums[bt * BPT + blk] = h;
+            if (a.pair_counts) a.pair_counts[bt * BPT + blk] = wp;
         }
     }
 }
@@ -764,6 +776,13 @@ cudaError_t launch_ranges(const uint32_t *keys, size_t M, uint2 *ranges, cudaStr
 {
     if (M == 0) return cudaSuccess;
     k_ranges<<<nblk((M + 3) / 4, 256), 256, 0, s>>>(keys, M, ranges, d_M, tb, TT); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_order_keys(const uint2 *ranges, size_t nt, uint32_t *keys, uint32_t *vals, cudaStream_t s)
+{
+    if (nt == 0) return cudaSuccess;
+    k_order_keys<<<nblk(nt, 256), 256, 0, s>>>(ranges, nt, keys, vals); count_launch();
     return cudaGetLastError();
 }
 
