@@ -204,8 +204,7 @@ constexpr int kRsRounds = kRsTile / kRsThreads;
 static_assert(kRsRounds * kRsThreads == kRsTile, "whole rounds of 256 keys per block");
 constexpr int kRsWarps = kRsThreads / 32;
 
-// Lanes of the warp holding the same digit d as this lane (d = 256 marks an
-// invalid item and matches only other invalid items).  BALLOT builds the
+// Lanes of the warp holding the same digit d as this lane.  BALLOT builds the
 // mask from one ballot per digit bit, which is cheaper than __match_any_sync
 // when the 32 digits are mostly distinct (low digits of unsorted keys);
 // __match_any_sync wins when they are few (high digits).
@@ -215,7 +214,7 @@ __device__ __forceinline__ unsigned digit_peers(int d)
     if (!BALLOT) return __match_any_sync(0xffffffffu, d);
     unsigned p = 0xffffffffu;
 #pragma unroll
-    for (int b = 0; b < 9; ++b) {
+    for (int b = 0; b < 8; ++b) {
         const bool bit = (d >> b) & 1;
         const unsigned bal = __ballot_sync(0xffffffffu, bit);
         p &= bit ? bal : ~bal;
@@ -342,6 +341,7 @@ __global__ void __launch_bounds__(kRsThreads, 8192 / kRsTile) k_radix_scatter(co
         uint32_t wpre = 0;
         for (int w = 0; w < warp; ++w) wpre += s_tmp[w];
         s_lstart[tid] = wpre + x - mycnt;
+        s_goff[tid] -= wpre + x - mycnt;   // global start minus block-local start (mod 2^32)
     }
 
     // phase A: warp-private stable ranks
@@ -356,15 +356,17 @@ __global__ void __launch_bounds__(kRsThreads, 8192 / kRsTile) k_radix_scatter(co
         const bool valid = i < n;
         k[r] = valid ? kin[i] : (KeyT)0;
         v[r] = valid ? vin[i] : 0u;
-        d[r] = valid ? (int)((k[r] >> shift) & 255u) : 256;
+        // an item past the block's end ranks as digit 255: it follows every
+        // valid item of the block, so it lands past the valid ones and is not written
+        d[r] = valid ? (int)((k[r] >> shift) & 255u) : 255;
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const unsigned peers = digit_peers<BALLOT>(d[r]);
-        const uint32_t prior = d[r] < 256 ? wc[d[r]] : 0u;
+        const uint32_t prior = wc[d[r]];
         rk[r] = prior + (uint32_t)__popc(peers & lt);
         __syncwarp();
-        if (d[r] < 256 && lane == __ffs(peers) - 1) wc[d[r]] = prior + (uint32_t)__popc(peers);
+        if (lane == __ffs(peers) - 1) wc[d[r]] = prior + (uint32_t)__popc(peers);
         __syncwarp();
     }
     __syncthreads();
@@ -381,11 +383,9 @@ __global__ void __launch_bounds__(kRsThreads, 8192 / kRsTile) k_radix_scatter(co
     // phase B: place in shared memory in sorted order
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        if (d[r] < 256) {
-            const uint32_t lp = wc[d[r]] + rk[r];
-            s_key[lp] = k[r];
-            s_val[lp] = v[r];
-        }
+        const uint32_t lp = wc[d[r]] + rk[r];
+        s_key[lp] = k[r];
+        s_val[lp] = v[r];
     }
     __syncthreads();
     // phase C: coalesced write-out
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kRsThreads, 8192 / kRsTile) k_radix_scatter(co
     for (int i = tid; i < cnt; i += kRsThreads) {
         const KeyT kk = s_key[i];
         const int dd = (int)((kk >> shift) & 255u);
-        const uint32_t pos = s_goff[dd] + ((uint32_t)i - s_lstart[dd]);
+        const uint32_t pos = s_goff[dd] + (uint32_t)i;
         kout[pos] = kk;
         vout[pos] = s_val[i];
     }
