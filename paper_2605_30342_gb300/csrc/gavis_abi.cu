@@ -254,6 +254,7 @@ struct RecLayout {
     uint2 *rect;
     uint32_t *counts;
     uint32_t *vis_words, *woff;   // [nv][ceil(n/32)] visibility bits and their record offsets
+    float *zrec;                  // camera depth per visible record (what stage A's keys are made of)
     void *scan_tmp;
     size_t bytes;
 };
@@ -270,6 +271,7 @@ RecLayout rec_layout(void *base, size_t nvn, bool ua, size_t nwords)
     L.counts = reinterpret_cast<uint32_t *>(take(nvn * sizeof(uint32_t)));
     L.vis_words = reinterpret_cast<uint32_t *>(take(nwords * sizeof(uint32_t)));
     L.woff = reinterpret_cast<uint32_t *>(take(nwords * sizeof(uint32_t)));
+    L.zrec = reinterpret_cast<float *>(take(nvn * sizeof(float)));
     L.scan_tmp = take(scan_tmp_bytes(nwords) + 64);
     L.bytes = off;
     return L;
@@ -366,7 +368,7 @@ struct ChainOut {
 
 size_t per_view_bytes(int64_t n, int TT, Mode m)
 {
-    size_t rec = (size_t)n * (sizeof(GeoRec) + (m == MODE_SCORE ? sizeof(UaRec) : 0) + 8 + 4 + 4);
+    size_t rec = (size_t)n * (sizeof(GeoRec) + (m == MODE_SCORE ? sizeof(UaRec) : 0) + 8 + 4 + 4 + 4);
     size_t vis = m == MODE_VIS ? (size_t)n * 12 : 0;
     size_t keys = (size_t)n * 2 * 24;   // typical: ~2 tiles per Gaussian per view
     return rec + vis + keys + (size_t)TT * 12;
@@ -434,6 +436,7 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     pa.cams = d_cams + v0; pa.nv = nv; pa.n = n;
     pa.geo = RL.geo; pa.ua = RL.ua; pa.rect = RL.rect; pa.counts = RL.counts;
     pa.vis_words = RL.vis_words;
+    pa.zrec = RL.zrec;
     pa.zrange = SL.info->zrange;
     pa.visible = &SL.info->visible;
     pa.total = &SL.info->total;
@@ -499,7 +502,7 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     uint32_t *k0 = reinterpret_cast<uint32_t *>(KL.a_k0), *k1 = reinterpret_cast<uint32_t *>(KL.a_k1);
     {
         Stage st(ctx, GAVIS_STAGE_EMIT, s);
-        CK(emit_vis_words(RL.vis_words, RL.woff, nv, n, RL.geo, zb, zmin, (uint32_t)(gsz_a - 1), k0, KL.a_v0,
+        CK(emit_vis_words(RL.vis_words, RL.woff, nv, n, RL.geo, RL.zrec, zb, zmin, (uint32_t)(gsz_a - 1), k0, KL.a_v0,
                           SL.voff, s));
     }
     if (gsz_a < nv) {   // group boundaries: a second read-back

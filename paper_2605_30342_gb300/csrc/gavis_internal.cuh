@@ -72,6 +72,7 @@ struct ProjectArgs {
     uint2 *rect;
     uint32_t *counts;       // tile count of each visible record (and 0 for culled ones unless vis_words is given)
     uint32_t *vis_words;    // [nv][ceil(n/32)] visibility bits (bit g%32 of word g/32), or NULL
+    float *zrec;            // camera depth of each visible record (dense copy of GeoRec b.z), or NULL
     uint32_t *zrange;       // [2] min and max depth bits of visible records (atomic)
     unsigned long long *visible;   // count of visible records (atomic)
     unsigned long long *total;     // count of tile entries (atomic)
@@ -104,11 +105,12 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, void
 // scan_tmp_bytes(nv * nw)); emit_vis_words then writes, for every visible
 // record r = v n + g at its position p among the visible records,
 // keyA[p] = ((v & vmask) << zb) | (depth bits - zmin) and valA[p] = r, and
-// voff[v] = visible records before view v (v = 0..nv).
+// voff[v] = visible records before view v (v = 0..nv).  The depth is read
+// from zrec[r] when given (4 B per record), else from the GeoRec.
 cudaError_t scan_vis_words(const uint32_t *words, size_t nwords, uint32_t *woff, void *tmp, cudaStream_t s);
 cudaError_t emit_vis_words(const uint32_t *words, const uint32_t *woff, int nv, int64_t n, const GeoRec *geo,
-                           int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA, uint32_t *valA, uint32_t *voff,
-                           cudaStream_t s);
+                           const float *zrec, int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA, uint32_t *valA,
+                           uint32_t *voff, cudaStream_t s);
 // The same with 64-bit keys (view << 32) | depth bits, for chains that cannot
 // size the sort on the host; records past cap_R are dropped and set *overflow.
 cudaError_t emit_vis_words64(const uint32_t *words, const uint32_t *woff, int nv, int64_t n, const GeoRec *geo,

@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
                              ((uint32_t)__half_as_ushort(__float2half_ru(p.ey)) << 16);
         gr.b = make_float4(p.C, op, p.z, __uint_as_float(ext));
         a.geo[r] = gr;
+        if (a.zrec) a.zrec[r] = p.z;
         if (UA) {
             float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
             float rn = rsqrtf(dx * dx + dy * dy + dz * dz);

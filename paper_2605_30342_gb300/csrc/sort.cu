@@ -149,7 +149,7 @@ __global__ void k_popc_words(const uint32_t *words, size_t nwords, uint32_t *cnt
 // ones).  Records at positions >= cap_R are dropped and set *overflow.
 template <typename KeyT>
 __global__ void k_emit_vis_words(const uint32_t *words, const uint32_t *woff, uint32_t nv, uint32_t nw, uint32_t n,
-                                 const GeoRec *geo, int zb, uint32_t zmin, uint32_t vmask, KeyT *keyA,
+                                 const GeoRec *geo, const float *zrec, int zb, uint32_t zmin, uint32_t vmask, KeyT *keyA,
                                  uint32_t *valA, uint32_t *voff, size_t cap_R, uint32_t *overflow)
 {
     const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
@@ -190,9 +190,17 @@ __global__ void k_emit_vis_words(const uint32_t *words, const uint32_t *woff, ui
                 if (overflow) *overflow = 1u;
                 continue;
             }
-            for (uint32_t m = j - ek; m > 0; --m) bk &= bk - 1u;   // drop the set bits before this record's
-            const uint32_t r = vk * n + wik * 32u + (uint32_t)(__ffs(bk) - 1);
-            keyA[base + j] = ((KeyT)(vk & vmask) << zb) | (KeyT)(__float_as_uint(geo[r].b.z) - zmin);
+            // position of the (j - ek)-th set bit of the word: halve the
+            // search range five times by the set bits' counts
+            uint32_t m = j - ek, pos = 0;
+#pragma unroll
+            for (int h = 16; h > 0; h >>= 1) {
+                const uint32_t c = (uint32_t)__popc(bk & ((1u << h) - 1u));
+                if (m >= c) { m -= c; pos += (uint32_t)h; bk >>= h; }
+            }
+            const uint32_t r = vk * n + wik * 32u + pos;
+            const float z = zrec ? zrec[r] : geo[r].b.z;
+            keyA[base + j] = ((KeyT)(vk & vmask) << zb) | (KeyT)(__float_as_uint(z) - zmin);
             valA[base + j] = r;
         }
     }
@@ -439,15 +447,15 @@ cudaError_t scan_vis_words(const uint32_t *words, size_t nwords, uint32_t *woff,
 }
 
 cudaError_t emit_vis_words(const uint32_t *words, const uint32_t *woff, int nv, int64_t n, const GeoRec *geo,
-                           int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA, uint32_t *valA, uint32_t *voff,
-                           cudaStream_t s)
+                           const float *zrec, int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA, uint32_t *valA,
+                           uint32_t *voff, cudaStream_t s)
 {
     if (nv <= 0 || n <= 0) return cudaSuccess;
     if ((size_t)nv * (size_t)n >= ((size_t)1 << 32) || zb < 0 || zb > 31) return cudaErrorInvalidValue;
     const uint32_t nw = (uint32_t)((n + 31) / 32);
     const size_t total = (size_t)nv * nw;
     k_emit_vis_words<uint32_t><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-        words, woff, (uint32_t)nv, nw, (uint32_t)n, geo, zb, zmin, vmask, keyA, valA, voff, ~(size_t)0, nullptr);
+        words, woff, (uint32_t)nv, nw, (uint32_t)n, geo, zrec, zb, zmin, vmask, keyA, valA, voff, ~(size_t)0, nullptr);
     count_launch();
     return cudaGetLastError();
 }
@@ -460,7 +468,8 @@ cudaError_t emit_vis_words64(const uint32_t *words, const uint32_t *woff, int nv
     const uint32_t nw = (uint32_t)((n + 31) / 32);
     const size_t total = (size_t)nv * nw;
     k_emit_vis_words<uint64_t><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-        words, woff, (uint32_t)nv, nw, (uint32_t)n, geo, 32, 0u, 0xffffffffu, keyA, valA, nullptr, cap_R, overflow);
+        words, woff, (uint32_t)nv, nw, (uint32_t)n, geo, nullptr, 32, 0u, 0xffffffffu, keyA, valA, nullptr, cap_R,
+        overflow);
     count_launch();
     return cudaGetLastError();
 }
