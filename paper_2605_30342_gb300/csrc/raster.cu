@@ -616,20 +616,32 @@ __global__ void __launch_bounds__(128) k_vf_accumulate(AccumArgs a)
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = a.gamma32[(size_t)g * K + k];
     const float mx = a.means[3 * g], my = a.means[3 * g + 1], mz = a.means[3 * g + 2];
-    for (int v = 0; v < a.nv; ++v) {
-        const size_t r = (size_t)v * (size_t)a.n + (size_t)g;
-        const uint32_t c = a.cnt[r];
-        if (c == 0u) continue;   // Phi = 0: no pixel of this view reaches g
-        const float vis = (float)a.sumT[r] * (1.0f / kTScale) / (float)c;
-        const gavis_camera &cam = s_cams[v];
-        const float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
-        const float rn = rsqrtf(dx * dx + dy * dy + dz * dz);
-        float Y[K];
-        sh_basis<L>(dx * rn, dy * rn, dz * rn, Y);
+    // views in groups of VG: the group's counts, then its sums, are loaded
+    // before any is used (independent loads in flight); accumulation stays in
+    // view order
+    constexpr int VG = 8;
+    for (int v0 = 0; v0 < a.nv; v0 += VG) {
+        uint32_t c[VG];
+        unsigned long long st[VG];
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const int l = k >= 9 ? 3 : (k >= 4 ? 2 : (k >= 1 ? 1 : 0));
-            acc[k] = fmaf(vis * a.a_l[l], Y[k], acc[k]);
+        for (int u = 0; u < VG; ++u)
+            c[u] = v0 + u < a.nv ? a.cnt[(size_t)(v0 + u) * (size_t)a.n + (size_t)g] : 0u;
+#pragma unroll
+        for (int u = 0; u < VG; ++u) st[u] = c[u] ? a.sumT[(size_t)(v0 + u) * (size_t)a.n + (size_t)g] : 0ull;
+#pragma unroll
+        for (int u = 0; u < VG; ++u) {
+            if (c[u] == 0u) continue;   // Phi = 0: no pixel of this view reaches g
+            const float vis = (float)st[u] * (1.0f / kTScale) / (float)c[u];
+            const gavis_camera &cam = s_cams[v0 + u];
+            const float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
+            const float rn = rsqrtf(dx * dx + dy * dy + dz * dz);
+            float Y[K];
+            sh_basis<L>(dx * rn, dy * rn, dz * rn, Y);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int l = k >= 9 ? 3 : (k >= 4 ? 2 : (k >= 1 ? 1 : 0));
+                acc[k] = fmaf(vis * a.a_l[l], Y[k], acc[k]);
+            }
         }
     }
 #pragma unroll
