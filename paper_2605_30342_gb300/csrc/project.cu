@@ -163,73 +163,93 @@ __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
     uint32_t zlo = 0xffffffffu, zhi = 0u, nvis = 0u, ntiles = 0u;
     const unsigned am0 = __activemask();   // the warp's lanes with g < n; each runs every view iteration
 
-    for (int v = 0; v < a.nv; ++v) {
-        const gavis_camera &cam = s_cams[v];
-        const Proj p = project_one(cam, mx, my, mz, S, a.q_cut, rb, a.TW, a.TH);
-        const size_t r = (size_t)v * (size_t)a.n + (size_t)g;
-        if (a.vis_words) {   // one visibility word per warp (32 consecutive Gaussians) and view
-            const unsigned bal = __ballot_sync(am0, p.status == 1);
-            if ((threadIdx.x & 31) == (unsigned)(__ffs(am0) - 1))
-                a.vis_words[(size_t)v * (size_t)((a.n + 31) >> 5) + (size_t)(g >> 5)] = bal;
+    // Views in groups of VG (with appearance records): the geometry of each
+    // view first (visible lanes write their GeoRec), then the appearance of
+    // the group's visible records, each lane taking its next pending view per
+    // round, so that a round runs with every lane that still has one instead
+    // of the visible lanes of one view (about 4.5 rounds instead of 8 at a
+    // quarter of the records visible).
+    constexpr int VG = UA ? 8 : 1;
+    for (int v0 = 0; v0 < a.nv; v0 += VG) {
+        uint32_t pend = 0u;   // bit u: view v0 + u has this Gaussian visible, appearance pending
+        for (int u = 0; u < VG && v0 + u < a.nv; ++u) {
+            const int v = v0 + u;
+            const gavis_camera &cam = s_cams[v];
+            const Proj p = project_one(cam, mx, my, mz, S, a.q_cut, rb, a.TW, a.TH);
+            const size_t r = (size_t)v * (size_t)a.n + (size_t)g;
+            if (a.vis_words) {   // one visibility word per warp (32 consecutive Gaussians) and view
+                const unsigned bal = __ballot_sync(am0, p.status == 1);
+                if ((threadIdx.x & 31) == (unsigned)(__ffs(am0) - 1))
+                    a.vis_words[(size_t)v * (size_t)((a.n + 31) >> 5) + (size_t)(g >> 5)] = bal;
+            }
+            if (p.status != 1) {
+                if (!a.vis_words) a.counts[r] = 0u;
+                continue;
+            }
+            const uint32_t nt = (uint32_t)((p.x1 - p.x0 + 1) * (p.y1 - p.y0 + 1));
+            a.counts[r] = nt;
+            ntiles += nt;
+            a.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.x1 << 16), (uint32_t)p.y0 | ((uint32_t)p.y1 << 16));
+            zlo = min(zlo, __float_as_uint(p.z));
+            zhi = max(zhi, __float_as_uint(p.z));
+            ++nvis;
+            GeoRec gr;
+            gr.a = make_float4(p.u, p.v, p.A, fa(p.B, p.B));
+            // footprint half-extents, rounded up to half precision (conservative)
+            const uint32_t ext = (uint32_t)__half_as_ushort(__float2half_ru(p.ex)) |
+                                 ((uint32_t)__half_as_ushort(__float2half_ru(p.ey)) << 16);
+            gr.b = make_float4(p.C, op, p.z, __uint_as_float(ext));
+            a.geo[r] = gr;
+            if (a.zrec) a.zrec[r] = p.z;
+            if (UA) pend |= 1u << u;
         }
-        if (p.status != 1) {
-            if (!a.vis_words) a.counts[r] = 0u;
-            continue;
-        }
-        const uint32_t nt = (uint32_t)((p.x1 - p.x0 + 1) * (p.y1 - p.y0 + 1));
-        a.counts[r] = nt;
-        ntiles += nt;
-        a.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.x1 << 16), (uint32_t)p.y0 | ((uint32_t)p.y1 << 16));
-        zlo = min(zlo, __float_as_uint(p.z));
-        zhi = max(zhi, __float_as_uint(p.z));
-        ++nvis;
-        GeoRec gr;
-        gr.a = make_float4(p.u, p.v, p.A, fa(p.B, p.B));
-        // footprint half-extents, rounded up to half precision (conservative)
-        const uint32_t ext = (uint32_t)__half_as_ushort(__float2half_ru(p.ex)) |
-                             ((uint32_t)__half_as_ushort(__float2half_ru(p.ey)) << 16);
-        gr.b = make_float4(p.C, op, p.z, __uint_as_float(ext));
-        a.geo[r] = gr;
-        if (a.zrec) a.zrec[r] = p.z;
         if (UA) {
-            float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
-            float rn = rsqrtf(dx * dx + dy * dy + dz * dz);
-            float Y[KM];
-            sh_basis<LM>(dx * rn, dy * rn, dz * rn, Y);
-            float col[3] = {0.0f, 0.0f, 0.0f};
+            while (__any_sync(am0, pend != 0u)) {
+                if (pend) {
+                    const int v = v0 + __ffs(pend) - 1;
+                    pend &= pend - 1u;
+                    const gavis_camera &cam = s_cams[v];
+                    const size_t r = (size_t)v * (size_t)a.n + (size_t)g;
+                    float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
+                    float rn = rsqrtf(dx * dx + dy * dy + dz * dz);
+                    float Y[KM];
+                    sh_basis<LM>(dx * rn, dy * rn, dz * rn, Y);
+                    float col[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-            for (int j = 0; j < KC; ++j) {
-                col[0] = fmaf(th[3 * j], Y[j], col[0]);
-                col[1] = fmaf(th[3 * j + 1], Y[j], col[1]);
-                col[2] = fmaf(th[3 * j + 2], Y[j], col[2]);
-            }
-            float V = 0.0f;
-            if (a.n_train > 0) {
-                float vt = 0.0f;
+                    for (int j = 0; j < KC; ++j) {
+                        col[0] = fmaf(th[3 * j], Y[j], col[0]);
+                        col[1] = fmaf(th[3 * j + 1], Y[j], col[1]);
+                        col[2] = fmaf(th[3 * j + 2], Y[j], col[2]);
+                    }
+                    float V = 0.0f;
+                    if (a.n_train > 0) {
+                        float vt = 0.0f;
 #pragma unroll
-                for (int j = 0; j < KV; ++j) vt = fmaf(gm[j], Y[j], vt);
-                vt = fminf(fmaxf(vt, 0.0f), P);
-                V = -expm1f(P * log1pf(-vt / P));
-                V = fminf(fmaxf(V, 0.0f), 1.0f);
-            }
-            const float nv1 = 1.0f - V;
-            float kc = 0.0f;   // unused by the constant-covariance composite
-            if (VAR) {
-                // FisherRF variant: Q_k(d) = sum_j Y_j(d)^2 var_jk, diagonal
-                float lq = 0.0f;
+                        for (int j = 0; j < KV; ++j) vt = fmaf(gm[j], Y[j], vt);
+                        vt = fminf(fmaxf(vt, 0.0f), P);
+                        V = -expm1f(P * log1pf(-vt / P));
+                        V = fminf(fmaxf(V, 0.0f), 1.0f);
+                    }
+                    const float nv1 = 1.0f - V;
+                    float kc = 0.0f;   // unused by the constant-covariance composite
+                    if (VAR) {
+                        // FisherRF variant: Q_k(d) = sum_j Y_j(d)^2 var_jk, diagonal
+                        float lq = 0.0f;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    float q = 0.0f;
+                        for (int k = 0; k < 3; ++k) {
+                            float q = 0.0f;
 #pragma unroll
-                    for (int j = 0; j < KC; ++j) q = fmaf(Y[j] * Y[j], ld_coef(a.sh_var, ((size_t)g * KC + j) * 3 + k, a.sh_dtype), q);
-                    lq += logf(fmaxf(q, 1e-30f));
+                            for (int j = 0; j < KC; ++j) q = fmaf(Y[j] * Y[j], ld_coef(a.sh_var, ((size_t)g * KC + j) * 3 + k, a.sh_dtype), q);
+                            lq += logf(fmaxf(q, 1e-30f));
+                        }
+                        kc = fmaf(0.5f, lq, 4.256815599614018f);   // + 3/2 log(2 pi e)
+                    }
+                    UaRec ur;
+                    ur.a = make_float4(V + a.beta * nv1, a.o0 * (1.0f - a.beta) * nv1, V, col[0]);
+                    ur.b = make_float4(col[1], col[2], kc, 0.0f);
+                    a.ua[r] = ur;
                 }
-                kc = fmaf(0.5f, lq, 4.256815599614018f);   // + 3/2 log(2 pi e)
             }
-            UaRec ur;
-            ur.a = make_float4(V + a.beta * nv1, a.o0 * (1.0f - a.beta) * nv1, V, col[0]);
-            ur.b = make_float4(col[1], col[2], kc, 0.0f);
-            a.ua[r] = ur;
         }
     }
     // depth range of the batch, one atomic per warp
