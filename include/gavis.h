@@ -29,6 +29,9 @@
  *   stream).  Work is enqueued asynchronously on it; outputs are valid once the
  *   stream has reached the end of the call's work.  A call may synchronise the
  *   stream internally (to size the sort buffers); this is documented per call.
+ *   Calls on one context share its workspace; their GPU work runs in call
+ *   order even on different streams (a call's stream first waits for the
+ *   previous call's work when that ran on another stream).
  * Threads.  A context is used by one host thread at a time.
  * Errors.  Every function returns GAVIS_OK (0) or a negative status; the text
  *   of the last error is kept in the context (gavis_last_error).  Nothing

@@ -62,6 +62,29 @@ struct gavis_ctx {
     unsigned long long *d_pairs = nullptr;   // device [2]
     unsigned long long prof_keys = 0;        // tile keys sorted since gavis_prof_enable
     unsigned long long prof_visible = 0;     // visible (view, Gaussian) records since then
+    // end of the last call's GPU work, for ordering the next call after it
+    cudaEvent_t tail = nullptr;
+    cudaStream_t tail_stream = nullptr;
+    bool tail_set = false;
+};
+
+// Calls on one context share its workspace, so their GPU work must not
+// overlap: a call on another stream than the previous call's first makes its
+// stream wait for that call's end, and every call records its own end.
+struct CallOrder {
+    gavis_ctx *c;
+    cudaStream_t s;
+    CallOrder(gavis_ctx *ctx, cudaStream_t st) : c(ctx), s(st)
+    {
+        if (c->tail && c->tail_set && c->tail_stream != s) cudaStreamWaitEvent(s, c->tail, 0);
+    }
+    ~CallOrder()
+    {
+        if (c->tail && cudaEventRecord(c->tail, s) == cudaSuccess) {
+            c->tail_stream = s;
+            c->tail_set = true;
+        }
+    }
 };
 
 namespace {
@@ -702,8 +725,10 @@ int gavis_ctx_create(gavis_ctx **out, int device, size_t hbm_budget_bytes)
     }
     ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : fr / 10 * 6;
     if (cudaMallocHost(&ctx->h_info, sizeof(BatchInfo)) != cudaSuccess ||
-        cudaMallocHost(&ctx->h_best, sizeof(int32_t)) != cudaSuccess) {
+        cudaMallocHost(&ctx->h_best, sizeof(int32_t)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->tail, cudaEventDisableTiming) != cudaSuccess) {
         if (ctx->h_info) cudaFreeHost(ctx->h_info);
+        if (ctx->h_best) cudaFreeHost(ctx->h_best);
         delete ctx;
         return GAVIS_ERR_CUDA;
     }
@@ -728,6 +753,7 @@ void gavis_ctx_destroy(gavis_ctx *ctx)
         cudaEventDestroy(r.b);
     }
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+    if (ctx->tail) cudaEventDestroy(ctx->tail);
     delete ctx;
 }
 
@@ -829,6 +855,7 @@ int gavis_vf_build(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_camera
     if (accumulate && out->n_train_views < 0) return fail(ctx, GAVIS_ERR_ARG, "negative n_train_views");
     cudaSetDevice(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CallOrder order(ctx, s);
     const int L = out->degree;
     const size_t K = (size_t)(L + 1) * (L + 1);
     const size_t count = (size_t)gs->n * K;
@@ -891,6 +918,7 @@ int gavis_render_views(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf
     if (n_cand > 0 && !score) return fail(ctx, GAVIS_ERR_ARG, "score is NULL");
     cudaSetDevice(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CallOrder order(ctx, s);
     ChainOut co;
     co.rgb = rgb;
     co.unc = unc;
@@ -935,6 +963,7 @@ int gavis_vf_query(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf
     if (n_cams > 0 && gs->n > 0 && !V) return fail(ctx, GAVIS_ERR_ARG, "V is NULL");
     cudaSetDevice(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CallOrder order(ctx, s);
     if ((rc = upload_cams(ctx, cams, n_cams, s)) != GAVIS_OK) return rc;
     QueryArgs qa;
     qa.means = gs->means;
@@ -965,6 +994,7 @@ int gavis_debug_bins(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_came
     if (cap > 0 && (!keys || !vals)) return fail(ctx, GAVIS_ERR_ARG, "keys/vals NULL with cap > 0");
     cudaSetDevice(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CallOrder order(ctx, s);
     gavis_params q = *p;
     q.views_per_batch = n_cams;   // one batch: keys carry the view index within the call
     ChainOut co;
@@ -997,6 +1027,7 @@ int gavis_vf_density_control(gavis_ctx *ctx, const gavis_gaussians *gs, const fl
     if (!(rho > 0.0f) || !(eta > -1.0f)) return fail(ctx, GAVIS_ERR_ARG, "rho must be > 0 and eta > -1");
     cudaSetDevice(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CallOrder order(ctx, s);
     const double sd = std::cbrt(3.0 * (1.0 + (double)eta) / (4.0 * M_PI * (double)rho));
     if (scale_out) *scale_out = (float)sd;
     if (n_virt == 0) {
@@ -1100,6 +1131,7 @@ int gavis_autotune(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf
     if (n_cams < 1 || gs->n == 0) return GAVIS_OK;
     cudaSetDevice(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CallOrder order(ctx, s);
     const std::string key = tune_key(mode, gs, vf, cams, n_cams);
     const char *path = std::getenv("GAVIS_AUTOTUNE_CACHE");
     {
@@ -1172,6 +1204,7 @@ int gavis_debug_visibility(gavis_ctx *ctx, const gavis_gaussians *gs, const gavi
     if (n_cams > 0 && gs->n > 0 && (!sumT || !cnt)) return fail(ctx, GAVIS_ERR_ARG, "sumT/cnt is NULL");
     cudaSetDevice(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CallOrder order(ctx, s);
     ChainOut co;
     auto after = [&](int v0, int nv) -> int {
         const size_t nvn = (size_t)nv * (size_t)gs->n;

@@ -205,6 +205,30 @@ def test_vf_query_more_views_than_one_launch(ctx, gv):
         ctx.debug_bins(gs, cams[:1025], gv.Params(tile=16))
 
 
+def test_calls_on_two_streams_are_ordered(ctx, gv):
+    """Two scoring calls on one context, issued on different streams back to
+    back with no host synchronisation between them: they share the
+    context's workspace, so the context orders the second after the first,
+    and each equals the same call made alone."""
+    c = sg.config(2, n=200000, n_train=4, n_cand=8, train_wh=(320, 240), cand_wh=(800, 600))
+    gs = gpu_scene(gv, c["scene"])
+    p = gv.Params(vf_degree=2)
+    vf = ctx.vf_build(gs, c["train"], degree=2, params=p)
+    cam_a, cam_b = c["cand"][:4], c["cand"][4:]
+    ref_a = ctx.score_views(gs, vf, cam_a, params=p)
+    ref_b = ctx.score_views(gs, vf, cam_b, params=p)
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    with torch.cuda.stream(s1):
+        a = ctx.score_views(gs, vf, cam_a, params=p, sync_best=False)
+    with torch.cuda.stream(s2):
+        b = ctx.score_views(gs, vf, cam_b, params=p, sync_best=False)
+    torch.cuda.synchronize()
+    for k in ("unc", "rgb", "score"):
+        assert torch.equal(a[k], ref_a[k]), k
+        assert torch.equal(b[k], ref_b[k]), k
+
+
 # --------------------------------------------------------------------------- VF CONST
 
 @pytest.mark.parametrize("name", list(CASES))
