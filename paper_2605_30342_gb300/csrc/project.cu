@@ -71,6 +71,13 @@ __device__ __forceinline__ Sigma3 sigma3d(const float *sc, float qw, float qx, f
     return S;
 }
 
+// camera depth of a point, in the projection's operation order
+__device__ __forceinline__ float cam_depth(const gavis_camera &cam, float x, float y, float z)
+{
+    const float *R = cam.R, *t = cam.t;
+    return fa(fa(fa(fm(R[6], x), fm(R[7], y)), fm(R[8], z)), t[2]);
+}
+
 struct Proj {
     float z, u, v, A, B, C, ex, ey;
     int x0, x1, y0, y1;
@@ -87,7 +94,7 @@ __device__ __forceinline__ Proj project_one(const gavis_camera &cam, float x, fl
     const float *R = cam.R, *t = cam.t;
     float tx = fa(fa(fa(fm(R[0], x), fm(R[1], y)), fm(R[2], z)), t[0]);
     float ty = fa(fa(fa(fm(R[3], x), fm(R[4], y)), fm(R[5], z)), t[1]);
-    float tz = fa(fa(fa(fm(R[6], x), fm(R[7], y)), fm(R[8], z)), t[2]);
+    float tz = cam_depth(cam, x, y, z);
     o.z = tz;
     if (!(tz > cam.znear)) return o;
     float limx = fm(1.3f, cam.tan_half_fovx), limy = fm(1.3f, cam.tan_half_fovy);
@@ -163,46 +170,64 @@ __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
     uint32_t zlo = 0xffffffffu, zhi = 0u, nvis = 0u, ntiles = 0u;
     const unsigned am0 = __activemask();   // the warp's lanes with g < n; each runs every view iteration
 
-    // Views in groups of VG (with appearance records): the geometry of each
-    // view first (visible lanes write their GeoRec), then the appearance of
-    // the group's visible records, each lane taking its next pending view per
-    // round, so that a round runs with every lane that still has one instead
-    // of the visible lanes of one view (about 4.5 rounds instead of 8 at a
-    // quarter of the records visible).
-    constexpr int VG = UA ? 8 : 1;
+    // Views in groups of VG.  The camera depth of each view of the group
+    // first; then the projection of the views with the Gaussian in front of
+    // the near plane, and then (with appearance records) the appearance of
+    // the views where it has tiles, both in rounds in which every lane with a
+    // pending view takes its next one, so that a round runs with every such
+    // lane instead of the lanes of one view (the appearance takes about 4.5
+    // rounds instead of 8 at a quarter of the records visible).
+    constexpr int VG = 8;
+    const size_t nw = (size_t)((a.n + 31) >> 5);
     for (int v0 = 0; v0 < a.nv; v0 += VG) {
-        uint32_t pend = 0u;   // bit u: view v0 + u has this Gaussian visible, appearance pending
-        for (int u = 0; u < VG && v0 + u < a.nv; ++u) {
-            const int v = v0 + u;
-            const gavis_camera &cam = s_cams[v];
-            const Proj p = project_one(cam, mx, my, mz, S, a.q_cut, rb, a.TW, a.TH);
-            const size_t r = (size_t)v * (size_t)a.n + (size_t)g;
-            if (a.vis_words) {   // one visibility word per warp (32 consecutive Gaussians) and view
-                const unsigned bal = __ballot_sync(am0, p.status == 1);
-                if ((threadIdx.x & 31) == (unsigned)(__ffs(am0) - 1))
-                    a.vis_words[(size_t)v * (size_t)((a.n + 31) >> 5) + (size_t)(g >> 5)] = bal;
-            }
-            if (p.status != 1) {
-                if (!a.vis_words) a.counts[r] = 0u;
-                continue;
-            }
-            const uint32_t nt = (uint32_t)((p.x1 - p.x0 + 1) * (p.y1 - p.y0 + 1));
-            a.counts[r] = nt;
-            ntiles += nt;
-            a.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.x1 << 16), (uint32_t)p.y0 | ((uint32_t)p.y1 << 16));
-            zlo = min(zlo, __float_as_uint(p.z));
-            zhi = max(zhi, __float_as_uint(p.z));
-            ++nvis;
-            GeoRec gr;
-            gr.a = make_float4(p.u, p.v, p.A, fa(p.B, p.B));
-            // footprint half-extents, rounded up to half precision (conservative)
-            const uint32_t ext = (uint32_t)__half_as_ushort(__float2half_ru(p.ex)) |
-                                 ((uint32_t)__half_as_ushort(__float2half_ru(p.ey)) << 16);
-            gr.b = make_float4(p.C, op, p.z, __uint_as_float(ext));
-            a.geo[r] = gr;
-            if (a.zrec) a.zrec[r] = p.z;
-            if (UA) pend |= 1u << u;
+        const int nu = a.nv - v0 < VG ? a.nv - v0 : VG;
+        // views of the group in front of the camera's near plane (the rest are culled)
+        uint32_t front = 0u;
+        for (int u = 0; u < nu; ++u)
+            if (cam_depth(s_cams[v0 + u], mx, my, mz) > s_cams[v0 + u].znear) front |= 1u << u;
+        if (!a.vis_words) {
+            for (int u = 0; u < nu; ++u)
+                if (!((front >> u) & 1u)) a.counts[(size_t)(v0 + u) * (size_t)a.n + (size_t)g] = 0u;
         }
+        uint32_t vis = 0u;    // bit u: the Gaussian has tiles in view v0 + u
+        uint32_t pend = 0u;   // the same, appearance pending
+        while (__any_sync(am0, front != 0u)) {
+            if (front) {
+                const int u = __ffs(front) - 1;
+                front &= front - 1u;
+                const int v = v0 + u;
+                const Proj p = project_one(s_cams[v], mx, my, mz, S, a.q_cut, rb, a.TW, a.TH);
+                const size_t r = (size_t)v * (size_t)a.n + (size_t)g;
+                if (p.status != 1) {
+                    if (!a.vis_words) a.counts[r] = 0u;
+                } else {
+                    vis |= 1u << u;
+                    const uint32_t nt = (uint32_t)((p.x1 - p.x0 + 1) * (p.y1 - p.y0 + 1));
+                    a.counts[r] = nt;
+                    ntiles += nt;
+                    a.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.x1 << 16), (uint32_t)p.y0 | ((uint32_t)p.y1 << 16));
+                    zlo = min(zlo, __float_as_uint(p.z));
+                    zhi = max(zhi, __float_as_uint(p.z));
+                    ++nvis;
+                    GeoRec gr;
+                    gr.a = make_float4(p.u, p.v, p.A, fa(p.B, p.B));
+                    // footprint half-extents, rounded up to half precision (conservative)
+                    const uint32_t ext = (uint32_t)__half_as_ushort(__float2half_ru(p.ex)) |
+                                         ((uint32_t)__half_as_ushort(__float2half_ru(p.ey)) << 16);
+                    gr.b = make_float4(p.C, op, p.z, __uint_as_float(ext));
+                    a.geo[r] = gr;
+                    if (a.zrec) a.zrec[r] = p.z;
+                }
+            }
+        }
+        if (a.vis_words) {   // one visibility word per warp (32 consecutive Gaussians) and view
+            for (int u = 0; u < nu; ++u) {
+                const unsigned bal = __ballot_sync(am0, (vis >> u) & 1u);
+                if ((threadIdx.x & 31) == (unsigned)(__ffs(am0) - 1))
+                    a.vis_words[(size_t)(v0 + u) * nw + (size_t)(g >> 5)] = bal;
+            }
+        }
+        if (UA) pend = vis;
         if (UA) {
             while (__any_sync(am0, pend != 0u)) {
                 if (pend) {
