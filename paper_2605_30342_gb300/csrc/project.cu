@@ -175,9 +175,9 @@ __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
     // the near plane, and then (with appearance records) the appearance of
     // the views where it has tiles, both in rounds in which every lane with a
     // pending view takes its next one, so that a round runs with every such
-    // lane instead of the lanes of one view (the appearance takes about 4.5
-    // rounds instead of 8 at a quarter of the records visible).
-    constexpr int VG = 8;
+    // lane instead of the lanes of one view (the appearance takes about 8
+    // rounds instead of 16 at a quarter of the records visible).
+    constexpr int VG = 16;
     const size_t nw = (size_t)((a.n + 31) >> 5);
     for (int v0 = 0; v0 < a.nv; v0 += VG) {
         const int nu = a.nv - v0 < VG ? a.nv - v0 : VG;
