@@ -5,7 +5,9 @@
 // (centre, scale, rotation, opacity, colour SH, visibility-field SH) and loops
 // over every view of the batch, whose cameras sit in shared memory.  The
 // Gaussian record is therefore read from HBM once per batch rather than once
-// per view.
+// per view.  Views go in groups of 16, the work of a group in rounds over the
+// lanes that still have a view to project (or to colour), so that lanes whose
+// Gaussian is culled in one view do the work of another.
 //
 // Image-space geometry is evaluated with explicit round-to-nearest intrinsics
 // (no contraction) in a fixed operation order, so that depth keys, conics and
