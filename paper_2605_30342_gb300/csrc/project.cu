@@ -5,7 +5,7 @@
 // (centre, scale, rotation, opacity, colour SH, visibility-field SH) and loops
 // over every view of the batch, whose cameras sit in shared memory.  The
 // Gaussian record is therefore read from HBM once per batch rather than once
-// per view.  Views go in groups of 16, the work of a group in rounds over the
+// per view.  Views go in groups of 32, the work of a group in rounds over the
 // lanes that still have a view to project (or to colour), so that lanes whose
 // Gaussian is culled in one view do the work of another.
 //
@@ -177,9 +177,9 @@ __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
     // the near plane, and then (with appearance records) the appearance of
     // the views where it has tiles, both in rounds in which every lane with a
     // pending view takes its next one, so that a round runs with every such
-    // lane instead of the lanes of one view (the appearance takes about 8
-    // rounds instead of 16 at a quarter of the records visible).
-    constexpr int VG = 16;
+    // lane instead of the lanes of one view (the appearance takes about 14
+    // rounds instead of 32 at a quarter of the records visible).
+    constexpr int VG = 32;
     const size_t nw = (size_t)((a.n + 31) >> 5);
     for (int v0 = 0; v0 < a.nv; v0 += VG) {
         const int nu = a.nv - v0 < VG ? a.nv - v0 : VG;
