@@ -1,18 +1,22 @@
 // raster.cu -- tile binning, per-tile front-to-back compositing and the
 // reductions of the GAVIS hot path.
 //
-//   k_emit_records    stage A of binning: (view, depth) key per visible record
+//   k_emit_records    stage A of binning from per-record counts (the path
+//                     without visibility words; the batched path emits stage A
+//                     from the projection's visibility words, in sort.cu)
 //   k_emit_tiles      stage B: the record's tiles, in stage-A order
 //   k_ranges          [start, end) of every (view, tile) in the sorted entries
+//   k_order_keys      the scoring tiles' order, longest list first
 //   k_composite_ua    Alg. "3DGS Uncertainty Quantification with Visibility
-//                     Field" + plain colour (eq:orig_vr), one thread per pixel
-//   k_composite_vis   Alg. "Single-view Particle Visibility", one thread per
-//                     pixel, per-Gaussian sums reduced across the tile
+//                     Field" + plain colour (eq:orig_vr): a persistent grid
+//                     whose warps take (view, tile, 8x8 block) items
+//   k_composite_vis   Alg. "Single-view Particle Visibility": a block per
+//                     (view, tile), per-Gaussian sums reduced per warp
 //   k_view_reduce     per-view mean of the per-pixel entropy (eq:id)
 //   k_argmax          next-best view (eq:i_gain)
 //   k_vf_accumulate   gamma_lm += v a_l Y_lm(d_p) (eq:vis_gamma)
 //
-// Compositing: each warp owns an 8 x 8 pixel block of the tile (two pixels
+// Compositing: each warp owns an 8 x 8 pixel block of a tile (two pixels
 // per thread, rows j and j + 4) and walks the tile's list on its own, in
 // chunks of 32 entries: every lane gathers one entry's record (by Gaussian
 // index from the per-view records), drops it if the footprint box

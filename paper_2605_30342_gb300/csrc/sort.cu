@@ -1,14 +1,20 @@
-// sort.cu -- device-wide exclusive scan and stable LSD radix sort of
-// (uint64 key, uint32 value) pairs.
+// sort.cu -- device-wide exclusive scan, stable LSD radix sort of
+// (uint32 or uint64 key, uint32 value) pairs, and the stage-A key emission
+// from visibility words.
 //
 // Radix sort: 8-bit digits, one pass per digit over [0, end_bit).  Each pass
-// is (1) a per-block digit histogram over a tile of 4096 keys, (2) an
-// exclusive scan of the histograms in digit-major order, which gives every
-// (digit, block) its output offset, and (3) a stable scatter: items are
-// ranked within a warp (lanes with equal digits found by __match_any_sync or
-// by per-bit ballots), warps are ordered by a shared prefix, rounds of 256
-// items in input order, so equal digits keep their input order.  Starting
-// from index-ascending input this yields the canonical (key, index) order.
+// is (1) a per-block digit histogram over a tile of 4096 keys (read as
+// 16-byte words), (2) an exclusive scan of the histograms in digit-major
+// order, which gives every (digit, block) its output offset, and (3) a
+// stable scatter: items are ranked within a warp (lanes with equal digits
+// found by __match_any_sync or by per-bit ballots), warps are ordered by a
+// shared prefix, rounds of 256 items in input order, so equal digits keep
+// their input order; the block's items are placed in shared memory in sorted
+// order and written out in digit runs.  Items past a block's end rank as
+// digit 255 and are never written.  A segmented sort runs the passes over
+// several independent ranges at once (a table of blocks, each within one
+// range, and one scan over all their histograms).  Starting from
+// index-ascending input this yields the canonical (key, index) order.
 #include "gavis_internal.cuh"
 
 namespace gavis {
