@@ -137,11 +137,17 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     const size_t o_ak0 = take(R * 8), o_ak1 = take(R * 8), o_av0 = take(R * 4), o_av1 = take(R * 4);
     const size_t o_acnt = take(R * 4), o_aoff = take(R * 4);
     const size_t o_bk0 = take(M * 4), o_bk1 = take(M * 4), o_bv0 = take(M * 4), o_bv1 = take(M * 4);
-    const size_t big = R > M ? R : M;
+    size_t big = R > M ? R : M;
+    if (nvt > big) big = nvt;   // the tile-order sort shares the temporary space
     const size_t o_tmp = take(radix_tmp_bytes(big) + scan_tmp_bytes(big) + 64);
     const int bpt = blocks_per_tile(p->tile);
     const size_t o_rng = take(nvt * sizeof(uint2)), o_ts = take(nvt * (size_t)bpt * sizeof(float));
     const size_t o_work = take(sizeof(unsigned long long));
+    // tile order of the uncertainty pass (keys, values, double-buffered) and
+    // the device copy of the largest batch's tile count (sort size bound)
+    const bool ordered = p->tile <= 16;
+    const size_t o_ok0 = take(nvt * 4), o_ok1 = take(nvt * 4), o_ov0 = take(nvt * 4), o_ov1 = take(nvt * 4);
+    const size_t o_nt = take(sizeof(unsigned long long));
     PK(cudaMalloc(&pl->buf, off));
     PK(cudaMallocHost(&pl->h_cams, (size_t)n_cams * sizeof(gavis_camera)));
     std::memset(pl->h_cams, 0, (size_t)n_cams * sizeof(gavis_camera));
@@ -167,6 +173,13 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     uint2 *ranges = reinterpret_cast<uint2 *>(b + o_rng);
     float *tile_sums = reinterpret_cast<float *>(b + o_ts);
     unsigned long long *work = reinterpret_cast<unsigned long long *>(b + o_work);
+    uint32_t *ok0 = reinterpret_cast<uint32_t *>(b + o_ok0), *ok1 = reinterpret_cast<uint32_t *>(b + o_ok1);
+    uint32_t *ov0 = reinterpret_cast<uint32_t *>(b + o_ov0), *ov1 = reinterpret_cast<uint32_t *>(b + o_ov1);
+    unsigned long long *d_nt = reinterpret_cast<unsigned long long *>(b + o_nt);
+    {
+        const unsigned long long nt64 = (unsigned long long)nvt;
+        PK(cudaMemcpy(d_nt, &nt64, sizeof(nt64), cudaMemcpyHostToDevice));
+    }
 
     ProjectArgs pa{};
     pa.means = gs->means; pa.scales = gs->scales; pa.rots = gs->rots; pa.opac = gs->opac;
@@ -227,6 +240,13 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
         ca.vals = alt_b ? bv1 : bv0;
         PK(cudaMemsetAsync(ranges, 0, nvt_b * sizeof(uint2), cs));
         PK(launch_ranges(keys, M, ranges, cs, &info->b.total));
+        ca.order = nullptr;
+        if (ordered) {   // the batched call's longest-list-first tile order
+            PK(launch_order_keys(ranges, nvt_b, ok0, ov0, cs));
+            bool alt_o = false;
+            PK(radix_sort_pairs<uint32_t>(ok0, ov0, ok1, ov1, nvt_b, 8, tmp, &alt_o, cs, d_nt));
+            ca.order = alt_o ? ov1 : ov0;
+        }
         PK(launch_composite_ua(ca, cs));
         PK(launch_view_reduce(tile_sums, nv, TT * bpt, 1.0f / ((float)W * (float)H), score + v0, cs));
     }
