@@ -290,10 +290,10 @@ def run_gavis(args):
     prm_vf, prm_sc = prm, prm
     tuned = None
     if args.tile == 0:
-        # autotuner: tile edge per path, timed on 16 training / 32 candidate views (untimed here)
-        prm_vf, ms_vf = ctx.autotune(gs, train[:16], None, gv.Params(vf_degree=L, views_per_batch=args.views_per_batch))
+        # autotuner: tile edge per path, timed on 64 training / 64 candidate views (untimed here)
+        prm_vf, ms_vf = ctx.autotune(gs, train[:64], None, gv.Params(vf_degree=L, views_per_batch=args.views_per_batch))
         ctx.vf_build(gs, train, degree=L, params=prm_vf, out=vf)
-        prm_sc, ms_sc = ctx.autotune(gs, cand[:32], vf, gv.Params(vf_degree=L, views_per_batch=args.views_per_batch))
+        prm_sc, ms_sc = ctx.autotune(gs, cand[:64], vf, gv.Params(vf_degree=L, views_per_batch=args.views_per_batch))
         tuned = {"vf_build_tile": prm_vf.tile, "score_tile": prm_sc.tile}
     W, H = cand[0].W, cand[0].H
     outs = {"rgb": torch.empty((n_cand, 3, H, W), device=dev), "unc": torch.empty((n_cand, H, W), device=dev),
