@@ -27,7 +27,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # algorithmic float32 flops per (pixel, Gaussian) pair, counted from the
-# algorithms (see DESIGN.md): uncertainty + colour compositing, and the
+# algorithms: uncertainty + colour compositing, and the
 # single-view particle visibility pass
 FLOPS_PER_PAIR_UA = 32
 FLOPS_PER_PAIR_VIS = 14
