@@ -260,10 +260,13 @@ int gavis_debug_visibility(gavis_ctx *ctx, const gavis_gaussians *gs, const gavi
  *   tile 16), at most 2^19 tile keys; beyond them the call returns
  *   GAVIS_ERR_ARG (sizes) or GAVIS_ERR_BUDGET (keys) with a message and
  *   launches nothing further.
- * Set-up: the first call on each device looks up the array's device address
- *   (with that device current); make that first call before any stream
- *   capture.  The array is held by every GPU that loads this library until the
- *   process exits.
+ * Set-up: the first successful call on each device looks up the array's
+ *   device address (with that device current) and keeps it; a failed lookup
+ *   is retried by the next call.  Make that first call before any stream
+ *   capture.  The kept address belongs to the device's current context: after
+ *   cudaDeviceReset it is stale, so do not call this entry point again in
+ *   that process.  The array is held by every GPU that loads this library
+ *   until the process exits.
  * Sharing: every call on a device uses the same array, which keeps the last
  *   call's contents; calls whose GPU work overlaps (other streams or threads)
  *   race on it and must be serialised by the caller.

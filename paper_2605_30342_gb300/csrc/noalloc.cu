@@ -33,12 +33,10 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-struct DeviceScratch {
-    std::once_flag once;
-    unsigned char *ptr = nullptr;   // device address of g_noalloc_scratch on this device
-    cudaError_t err = cudaSuccess;
-};
-DeviceScratch g_dev[kMaxDevices];
+// device address of g_noalloc_scratch per device, cached once it was obtained
+// (a failed lookup is not cached: the next call tries again)
+std::mutex g_dev_mu;
+unsigned char *g_dev_ptr[kMaxDevices] = {};
 
 int report(char *err, size_t len, int code, const char *fmt, ...)
 {
@@ -109,15 +107,22 @@ extern "C" int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_v
     int dev = 0;
     NA_CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return report(err, err_len, GAVIS_ERR_ARG, "device index %d too large", dev);
-    DeviceScratch &ds = g_dev[dev];
-    // once per device, with that device current: the device address of the array
-    std::call_once(ds.once, [&ds]() {
-        void *q = nullptr;
-        ds.err = cudaGetSymbolAddress(&q, g_noalloc_scratch);
-        ds.ptr = reinterpret_cast<unsigned char *>(q);
-    });
-    if (ds.err != cudaSuccess || !ds.ptr)
-        return report(err, err_len, GAVIS_ERR_CUDA, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(ds.err));
+    // first successful call per device, with that device current: the device
+    // address of the array (host code cannot use the symbol itself)
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_dev_mu);
+        if (!g_dev_ptr[dev]) {
+            void *q = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&q, g_noalloc_scratch);
+            if (e != cudaSuccess || !q) {
+                cudaGetLastError();
+                return report(err, err_len, GAVIS_ERR_CUDA, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            }
+            g_dev_ptr[dev] = reinterpret_cast<unsigned char *>(q);
+        }
+        base = g_dev_ptr[dev];
+    }
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const size_t plane = (size_t)cam->W * (size_t)cam->H;
@@ -129,7 +134,7 @@ extern "C" int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_v
     }
 
     const size_t n = (size_t)gs->n;
-    Carver c{ds.ptr};
+    Carver c{base};
     gavis_camera *d_cam = reinterpret_cast<gavis_camera *>(c.take(sizeof(gavis_camera)));
     BatchInfo *d_info = reinterpret_cast<BatchInfo *>(c.take(sizeof(BatchInfo)));
     GeoRec *geo = reinterpret_cast<GeoRec *>(c.take(n * sizeof(GeoRec)));

@@ -119,16 +119,29 @@ struct Slot {   // one view of a batch
 
 void worker_main(gavis_server *s, size_t ws_budget)
 {
-    cudaSetDevice(s->device);
+    // a worker whose set-up failed stays up and fails every batch it takes
+    // with that status (no batch runs on a missing stream or buffer)
+    int rc0 = GAVIS_OK;
+    if (cudaSetDevice(s->device) != cudaSuccess) rc0 = GAVIS_ERR_CUDA;
     cudaStream_t stream = nullptr;
-    cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+    if (rc0 == GAVIS_OK && cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
+        stream = nullptr;
+        rc0 = GAVIS_ERR_CUDA;
+    }
     gavis_ctx *ctx = nullptr;
-    const int rc0 = gavis_ctx_create(&ctx, s->device, ws_budget);
+    if (rc0 == GAVIS_OK) rc0 = gavis_ctx_create(&ctx, s->device, ws_budget);
     float *score_stage = nullptr, *unc_stage = nullptr;
     size_t unc_cap = 0;
     int32_t *d_best = nullptr;
-    cudaMalloc(&score_stage, sizeof(float) * (size_t)s->max_batch);
-    cudaMalloc(&d_best, sizeof(int32_t));
+    if (rc0 == GAVIS_OK && cudaMalloc(&score_stage, sizeof(float) * (size_t)s->max_batch) != cudaSuccess) {
+        score_stage = nullptr;
+        rc0 = GAVIS_ERR_OOM;
+    }
+    if (rc0 == GAVIS_OK && cudaMalloc(&d_best, sizeof(int32_t)) != cudaSuccess) {
+        d_best = nullptr;
+        rc0 = GAVIS_ERR_OOM;
+    }
+    if (rc0 != GAVIS_OK) cudaGetLastError();
     std::vector<gavis_camera> cams;
     std::vector<Slot> slots;
     for (;;) {
@@ -174,8 +187,16 @@ void worker_main(gavis_server *s, size_t ws_budget)
         int rc = rc0;
         if (rc == GAVIS_OK && want_unc && unc_cap < (size_t)nb * plane) {
             if (unc_stage) cudaFree(unc_stage);
-            unc_cap = (size_t)s->max_batch * plane;
-            if (cudaMalloc(&unc_stage, unc_cap * sizeof(float)) != cudaSuccess) rc = GAVIS_ERR_OOM;
+            unc_stage = nullptr;
+            unc_cap = 0;
+            const size_t want = (size_t)s->max_batch * plane;
+            if (cudaMalloc(&unc_stage, want * sizeof(float)) == cudaSuccess) {
+                unc_cap = want;
+            } else {
+                unc_stage = nullptr;
+                cudaGetLastError();
+                rc = GAVIS_ERR_OOM;
+            }
         }
         if (rc == GAVIS_OK) {
             gavis_params p = lead.p;
@@ -194,7 +215,7 @@ void worker_main(gavis_server *s, size_t ws_budget)
                     rc = GAVIS_ERR_CUDA;
             }
         }
-        if (cudaStreamSynchronize(stream) != cudaSuccess && rc == GAVIS_OK) rc = GAVIS_ERR_CUDA;
+        if (stream && cudaStreamSynchronize(stream) != cudaSuccess && rc == GAVIS_OK) rc = GAVIS_ERR_CUDA;
         // completion: argmax of every request whose last view is in
         std::vector<std::shared_ptr<Request>> completed;
         {
