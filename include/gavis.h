@@ -208,6 +208,28 @@ int gavis_vf_density_control(gavis_ctx *ctx, const gavis_gaussians *gs, const fl
                              float eps_v, float *vis_out, uint8_t *keep, float *kept_means, int64_t *n_keep,
                              float *scale_out, void *stream);
 
+/* The scene that Alg. "Visibility Field Density Control" hands to the
+ * uncertainty step: the n trained Gaussians followed by the n_kept virtual
+ * particles kept by gavis_vf_density_control, each with the identity
+ * rotation, the isotropic `scale` (its scale_out), opacity 0, colour 0 and a
+ * zero visibility field, so that V = 0 and only the prior term of
+ * eq:alpha_comp remains for it.
+ *   gs, vf: the scene and its field (device, as for gavis_score_views).
+ *   kept_means: device [3 n_kept] float32.
+ *   means, scales (device [3(n + n_kept)]), rots (device [4(n + n_kept)],
+ *   16-byte aligned), opac (device [n + n_kept]): float32 outputs;
+ *   sh: device [(n + n_kept)][(Lc+1)^2][3] of gs->sh_dtype;
+ *   sh_var: same shape and dtype, required exactly when gs->sh_var is given
+ *   (the virtual particles get variance 1), else NULL;
+ *   coeffs: device [(n + n_kept)][(L+1)^2] of vf->dtype.
+ * Outputs are caller-allocated and must not overlap the inputs.  Only
+ * device-to-device copies and one fill kernel on `stream`; no
+ * synchronisation.  Errors: GAVIS_ERR_ARG for NULL or inconsistent
+ * arguments, GAVIS_ERR_CUDA if a copy or launch fails. */
+int gavis_augment(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf, const float *kept_means,
+                  int64_t n_kept, float scale, float *means, float *scales, float *rots, float *opac, void *sh,
+                  void *sh_var, void *coeffs, void *stream);
+
 /* Autotuner (no counterpart in the paper): times the chain on the sample
  * cameras with tile edges 8, 16 and 32 (one warm-up and two timed runs each,
  * CUDA events on `stream`) and writes the fastest into p->tile.  mode 0 tunes

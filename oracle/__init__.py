@@ -82,11 +82,11 @@ def _declare(L):
     L.oracle_composite.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
     L.oracle_vf_query.argtypes = [i64, vp, i32, i64, vp, vp, vp, vp]
     L.oracle_vf_exact.argtypes = [i64, i32, vp, vp, dbl, vp, vp]
-    L.oracle_visibility_view.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.oracle_visibility_view.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.oracle_visibility_view.restype = i64
-    L.oracle_vf_build.argtypes = [i32, vp, i64, vp, vp, vp, vp, i32, vp, vp, vp, vp]
-    L.oracle_render_view.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
-    L.oracle_density_control.argtypes = [i32, vp, i64, vp, vp, vp, vp, i64, vp, dbl, dbl, dbl, vp, vp, vp, vp]
+    L.oracle_vf_build.argtypes = [i32, vp, i64, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp]
+    L.oracle_render_view.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.oracle_density_control.argtypes = [i32, vp, i64, vp, vp, vp, vp, i64, vp, dbl, dbl, dbl, vp, vp, vp, vp, vp, vp]
     L.oracle_density_control.restype = i64
 
 
@@ -209,11 +209,13 @@ def composite(alpha, V, col, prm=None, kc=None, z=None):
     col = _f64(np.asarray(col).reshape(-1, 3))
     kc = None if kc is None else _f64(kc)
     z = None if z is None else _f64(z)
-    res = np.zeros(12)
+    res = np.zeros(24)
     lib().oracle_composite(len(alpha), _p(alpha), _p(V), _p(col), _p(z) if z is not None else None, _p(prm),
                            _p(kc) if kc is not None else None, _p(res))
     return dict(H=res[0], rgb=res[1:4].copy(), T=res[4], Tc=res[5], sum_w=res[6], sum_wc=res[7],
-                w0=res[8], used=int(res[9]), amb=bool(res[10]), depth=res[11])
+                w0=res[8], used=int(res[9]), amb=bool(res[10]), depth=res[11],
+                H_lo=res[12], H_hi=res[13], rgb_lo=res[14:17].copy(), rgb_hi=res[17:20].copy(),
+                depth_lo=res[20], depth_hi=res[21])
 
 
 def vf_query(gamma, L, P, cam, means):
@@ -236,29 +238,41 @@ def vf_exact(vis, dirs, kappa, d):
     return V
 
 
-def visibility_view(cam, scene, prm=None):
+def visibility_view(cam, scene, prm=None, want_bounds=False):
+    """Per-Gaussian sum of T and count of one view, the near-threshold mask and
+    the number of pairs; with want_bounds also a dict of the early sums and
+    the early and late counts (the run's range of possible stops)."""
     prm = params() if prm is None else prm
     n = scene.n
     sumT = np.zeros(n)
     cnt = np.zeros(n, np.int64)
     amb = np.zeros(n, np.uint8)
+    se, ce, cl = np.zeros(n), np.zeros(n, np.int64), np.zeros(n, np.int64)
+    bargs = [_p(se), _p(ce), _p(cl)] if want_bounds else [None, None, None]
     pairs = lib().oracle_visibility_view(_p(cam_record(cam)), n, _p(_f32(scene.means)), _p(_f32(scene.scales)),
                                          _p(_f32(scene.rots)), _p(_f32(scene.opac)), _p(prm),
-                                         _p(sumT), _p(cnt), _p(amb))
+                                         _p(sumT), _p(cnt), _p(amb), *bargs)
+    if want_bounds:
+        return sumT, cnt, amb.astype(bool), pairs, dict(sum_early=se, cnt_early=ce, cnt_late=cl)
     return sumT, cnt, amb.astype(bool), pairs
 
 
-def vf_build(cams, scene, L, prm=None, want_vis=False):
-    """gamma (n,(L+1)^2) float64, ambiguous mask (n,), per-view vis (P,n) or None."""
+def vf_build(cams, scene, L, prm=None, want_vis=False, want_rad=False):
+    """gamma (n,(L+1)^2) float64, ambiguous mask (n,), per-view vis (P,n) or
+    None; with want_rad also the per-coefficient radius (n,(L+1)^2) within
+    which a build with rounding-sensitive terminations stays."""
     prm = params() if prm is None else prm
     n = scene.n
     K = (L + 1) ** 2
     gamma = np.zeros((n, K))
     amb = np.zeros(n, np.uint8)
     vis = np.zeros((len(cams), n)) if want_vis else None
+    rad = np.zeros((n, K)) if want_rad else None
     lib().oracle_vf_build(len(cams), _p(cam_records(cams)), n, _p(_f32(scene.means)), _p(_f32(scene.scales)),
                           _p(_f32(scene.rots)), _p(_f32(scene.opac)), int(L), _p(prm), _p(gamma),
-                          _p(vis) if want_vis else None, _p(amb))
+                          _p(vis) if want_vis else None, _p(amb), _p(rad) if want_rad else None)
+    if want_rad:
+        return gamma, amb.astype(bool), vis, rad
     return gamma, amb.astype(bool), vis
 
 
@@ -267,25 +281,33 @@ def virtual_scale(rho, eta):
     return (3.0 * (1.0 + eta) / (4.0 * np.pi * rho)) ** (1.0 / 3.0)
 
 
-def density_control(cams, scene, vmeans, rho=100.0, eta=0.5, eps_v=0.95, prm=None):
+def density_control(cams, scene, vmeans, rho=100.0, eta=0.5, eps_v=0.95, prm=None, want_bounds=False):
     """Multi-view visibility of the virtual particles (float64), keep mask
-    (visibility <= eps_v) and the rounding-ambiguity mask."""
+    (visibility <= eps_v) and the rounding-ambiguity mask; with want_bounds
+    also the range (lo, hi) of the visibility under rounding-sensitive
+    terminations."""
     prm = params() if prm is None else prm
     vm = _f32(vmeans).reshape(-1, 3)
     nv = vm.shape[0]
     vis = np.zeros(nv)
     keep = np.zeros(nv, np.uint8)
     amb = np.zeros(nv, np.uint8)
+    lo, hi = np.zeros(nv), np.zeros(nv)
     lib().oracle_density_control(len(cams), _p(cam_records(cams)), scene.n, _p(_f32(scene.means)),
                                  _p(_f32(scene.scales)), _p(_f32(scene.rots)), _p(_f32(scene.opac)), nv, _p(vm),
-                                 float(rho), float(eta), float(eps_v), _p(prm), _p(vis), _p(keep), _p(amb))
+                                 float(rho), float(eta), float(eps_v), _p(prm), _p(vis), _p(keep), _p(amb),
+                                 _p(lo), _p(hi))
+    if want_bounds:
+        return vis, keep.astype(bool), amb.astype(bool), lo, hi
     return vis, keep.astype(bool), amb.astype(bool)
 
 
-def render_view(cam, scene, V, prm=None, sh=None, sh_var=None, want_depth=False):
+def render_view(cam, scene, V, prm=None, sh=None, sh_var=None, want_depth=False, want_bounds=False):
     """rgb (3,H,W), unc (H,W), amb (H,W) bool, used (H,W) [, depth (H,W) if
-    want_depth].  sh_var: optional per-coefficient colour variances (FisherRF
-    variant of Q_c)."""
+    want_depth] [, bounds dict if want_bounds: the least and greatest value
+    of unc, rgb and depth per pixel when the transmittance tests near eps_T
+    go either way].  sh_var: optional per-coefficient colour variances
+    (FisherRF variant of Q_c)."""
     prm = params() if prm is None else prm
     n = scene.n
     sh = _f64(scene.sh if sh is None else sh)
@@ -296,31 +318,44 @@ def render_view(cam, scene, V, prm=None, sh=None, sh_var=None, want_depth=False)
     amb = np.zeros((cam.H, cam.W), np.uint8)
     used = np.zeros((cam.H, cam.W), np.int32)
     depth = np.zeros((cam.H, cam.W)) if want_depth else None
+    bnd = np.zeros((10, cam.H, cam.W)) if want_bounds else None
     lib().oracle_render_view(_p(cam_record(cam)), n, _p(_f32(scene.means)), _p(_f32(scene.scales)),
                              _p(_f32(scene.rots)), _p(_f32(scene.opac)), _p(sh), _p(var) if var is not None else None,
                              Lc, _p(_f64(V)), _p(prm),
-                             _p(rgb), _p(unc), _p(depth) if want_depth else None, _p(amb), _p(used))
+                             _p(rgb), _p(unc), _p(depth) if want_depth else None, _p(amb), _p(used),
+                             _p(bnd) if want_bounds else None)
+    out = [rgb, unc, amb.astype(bool), used]
     if want_depth:
-        return rgb, unc, amb.astype(bool), used, depth
-    return rgb, unc, amb.astype(bool), used
+        out.append(depth)
+    if want_bounds:
+        out.append(dict(unc_lo=bnd[0], unc_hi=bnd[1], rgb_lo=bnd[2:5], rgb_hi=bnd[5:8],
+                        depth_lo=bnd[8], depth_hi=bnd[9]))
+    return tuple(out)
 
 
 def score_views(scene, gamma, L, P, cams, prm=None, sh=None, keep_images=True, sh_var=None, want_depth=False):
     """Per-view mean entropy score S_v (eq:id with f_corr = 0) and the argmax
-    of eq:i_gain (ties to the lowest index)."""
+    of eq:i_gain (ties to the lowest index).  Also the per-pixel bounds of
+    render_view ("bnd") and the range of each score under rounding-sensitive
+    terminations ("score_lo", "score_hi")."""
     prm = params() if prm is None else prm
-    out = dict(rgb=[], unc=[], amb=[], used=[], depth=[], score=np.zeros(len(cams)))
+    out = dict(rgb=[], unc=[], amb=[], used=[], depth=[], bnd=[], score=np.zeros(len(cams)),
+               score_lo=np.zeros(len(cams)), score_hi=np.zeros(len(cams)))
     for v, cam in enumerate(cams):
         V, _ = vf_query(gamma, L, P, cam, scene.means)
-        r = render_view(cam, scene, V, prm, sh, sh_var, want_depth=want_depth)
+        r = render_view(cam, scene, V, prm, sh, sh_var, want_depth=want_depth, want_bounds=True)
         rgb, unc, amb, used = r[:4]
+        bnd = r[-1]
         if want_depth and keep_images:
             out["depth"].append(r[4])
         out["score"][v] = unc.mean()
+        out["score_lo"][v] = bnd["unc_lo"].mean()
+        out["score_hi"][v] = bnd["unc_hi"].mean()
         if keep_images:
             out["rgb"].append(rgb)
             out["unc"].append(unc)
             out["amb"].append(amb)
             out["used"].append(used)
+            out["bnd"].append(bnd)
     out["best"] = int(np.argmax(out["score"])) if len(cams) else -1
     return out

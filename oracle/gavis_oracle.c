@@ -497,7 +497,17 @@ static int near_thresh(double T, double eps, double margin)
  * out: res[0] = H, res[1..3] = rgb, res[4] = T_end, res[5] = Tc_end,
  *      res[6] = sum of w*, res[7] = sum of colour weights, res[8] = w0bar,
  *      res[9] = entries consumed, res[10] = 1 if a transmittance test landed
- *      within margin*eps of eps. */
+ *      within margin*eps of eps, res[11] = expected depth.
+ *      res[12], res[13]: the least and greatest H, res[14..16], res[17..19]:
+ *      the least and greatest rgb, res[20], res[21]: the least and greatest
+ *      expected depth over every place where the run could have stopped had
+ *      each transmittance test inside [eps(1-margin), eps(1+margin)] gone
+ *      either way: each accumulator stops no earlier than its first test
+ *      below eps(1+margin) and no later than its first test below
+ *      eps(1-margin) (or the end of the list).  A transmittance computed with
+ *      a relative error below margin stops inside that range, so these are
+ *      bounds on its outputs; where no test falls in the band, lo = hi = the
+ *      value above. */
 void oracle_composite(int64_t n, const double *alpha, const double *V, const double *col, const double *z,
                       const double *prm, const double *kc_each, double *res)
 {
@@ -505,40 +515,85 @@ void oracle_composite(int64_t n, const double *alpha, const double *V, const dou
     const double kc_const = 0.5 * 3.0 * log(prm[P_SIGMA_C2]) + 1.5 * (log(2.0 * M_PI) + 1.0);
     const double k0 = 0.5 * prm[P_LOGDET_Q0] + 1.5 * (log(2.0 * M_PI) + 1.0);
     const double margin = prm[P_MARGIN];
-    double T = 1.0, Tc = 1.0, H = 0.0, w0 = 0.0, sw = 0.0, swc = 0.0, D = 0.0;
+    const double band_hi = eps * (1.0 + margin), band_lo = eps * (1.0 - margin);
+    double T = 1.0, Tc = 1.0, Hv = 0.0, w0 = 0.0, sw = 0.0, swc = 0.0, D = 0.0;
     double C[3] = {0, 0, 0};
-    int ua = 1, rgb = 1, amb = 0;
+    /* the oracle's own decisions (test after the update, as printed) */
+    int ua_on = 1, rgb_on = 1, amb = 0;
     int64_t used = 0;
-    for (int64_t i = 0; i < n && (ua || rgb); ++i) {
+    double oH = 0.0, oT = 1.0, osw = 0.0, ow0 = 0.0, oC[3] = {0, 0, 0}, oD = 0.0, oTc = 1.0, oswc = 0.0;
+    /* bounds: 2 = before the earliest possible stop, 1 = inside the range of
+     * possible stops, 0 = past the latest */
+    int ua_b = 2, rgb_b = 2;
+    double Hlo = 0.0, Hhi = 0.0, Clo[3] = {0, 0, 0}, Chi[3] = {0, 0, 0}, Dlo = 0.0, Dhi = 0.0;
+    for (int64_t i = 0; i < n && (ua_b || rgb_b); ++i) {
         double a = alpha[i];
-        used = i + 1;
-        if (rgb) {
+        if (ua_on || rgb_on) used = i + 1;
+        if (rgb_b) {
             double w = a * Tc;
             C[0] += w * col[3 * i]; C[1] += w * col[3 * i + 1]; C[2] += w * col[3 * i + 2];
             if (z) D += w * z[i];            /* expected depth, background at 0 */
             swc += w;
             Tc = Tc * (1.0 - a);
-            if (near_thresh(Tc, eps, margin)) amb = 1;
-            if (Tc < eps) rgb = 0;
+            if (rgb_on) {
+                if (near_thresh(Tc, eps, margin)) amb = 1;
+                if (Tc < eps) {
+                    rgb_on = 0;
+                    oC[0] = C[0]; oC[1] = C[1]; oC[2] = C[2]; oD = D; oTc = Tc; oswc = swc;
+                }
+            }
+            if (rgb_b == 2 && Tc < band_hi) {
+                rgb_b = 1;
+                for (int k = 0; k < 3; ++k) Clo[k] = Chi[k] = C[k];
+                Dlo = Dhi = D;
+            } else if (rgb_b == 1) {
+                for (int k = 0; k < 3; ++k) { Clo[k] = fmin(Clo[k], C[k]); Chi[k] = fmax(Chi[k], C[k]); }
+                Dlo = fmin(Dlo, D); Dhi = fmax(Dhi, D);
+            }
+            if (rgb_b == 1 && Tc < band_lo) rgb_b = 0;
         }
-        if (ua) {
+        if (ua_b) {
             double v = V[i];
             double as = (v + beta * (1.0 - v)) * a + o0 * (1.0 - beta) * (1.0 - v);  /* eq:alpha_comp */
             double w = as * T;
             double wv = w * v;
             double kc = kc_each ? kc_each[i] : kc_const;   /* 1/2 log((2 pi e)^3 |Q_c|) */
-            if (wv > 0.0) H += phi(wv) + wv * kc;          /* visible component of eq:huber */
+            if (wv > 0.0) Hv += phi(wv) + wv * kc;         /* visible component of eq:huber */
             w0 += w * (1.0 - v);             /* mass of the prior component */
             sw += w;
             T = T * (1.0 - as);
-            if (near_thresh(T, eps, margin)) amb = 1;
-            if (T < eps) ua = 0;
+            double Hstop = Hv + (phi(w0) + w0 * k0);   /* H if the run stops here */
+            if (ua_on) {
+                if (near_thresh(T, eps, margin)) amb = 1;
+                if (T < eps) {
+                    ua_on = 0;
+                    oH = Hstop; oT = T; osw = sw; ow0 = w0;
+                }
+            }
+            if (ua_b == 2 && T < band_hi) {
+                ua_b = 1;
+                Hlo = Hhi = Hstop;
+            } else if (ua_b == 1) {
+                Hlo = fmin(Hlo, Hstop); Hhi = fmax(Hhi, Hstop);
+            }
+            if (ua_b == 1 && T < band_lo) ua_b = 0;
         }
     }
-    H += phi(w0) + w0 * k0;                  /* invisible component */
-    res[0] = H; res[1] = C[0]; res[2] = C[1]; res[3] = C[2];
-    res[4] = T; res[5] = Tc; res[6] = sw; res[7] = swc; res[8] = w0;
-    res[9] = (double)used; res[10] = (double)amb; res[11] = D;
+    /* runs still going stop at the end of the list */
+    if (rgb_on) { oC[0] = C[0]; oC[1] = C[1]; oC[2] = C[2]; oD = D; oTc = Tc; oswc = swc; }
+    if (rgb_b == 2) { for (int k = 0; k < 3; ++k) Clo[k] = Chi[k] = C[k]; Dlo = Dhi = D; }
+    {
+        double Hend = Hv + (phi(w0) + w0 * k0);   /* invisible component added at the stop */
+        if (ua_on) { oH = Hend; oT = T; osw = sw; ow0 = w0; }
+        if (ua_b == 2) Hlo = Hhi = Hend;
+    }
+    res[0] = oH; res[1] = oC[0]; res[2] = oC[1]; res[3] = oC[2];
+    res[4] = oT; res[5] = oTc; res[6] = osw; res[7] = oswc; res[8] = ow0;
+    res[9] = (double)used; res[10] = (double)amb; res[11] = oD;
+    res[12] = Hlo; res[13] = Hhi;
+    res[14] = Clo[0]; res[15] = Clo[1]; res[16] = Clo[2];
+    res[17] = Chi[0]; res[18] = Chi[1]; res[19] = Chi[2];
+    res[20] = Dlo; res[21] = Dhi;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -610,12 +665,23 @@ void oracle_vf_exact(int64_t n, int nview, const double *vis, const double *dirs
 
 /* sumT, cnt: per Gaussian (float64, int64), overwritten.  amb (optional):
  * set to 1 for Gaussians that follow a near-threshold transmittance test in
- * some pixel's list (their inclusion depends on rounding).  Returns pairs. */
-int64_t oracle_visibility_view(const float *cam, int64_t n, const float *means, const float *scales,
-                               const float *rots, const float *opac, const double *prm,
-                               double *sumT, int64_t *cnt, uint8_t *amb)
+ * some pixel's list (their inclusion depends on rounding).
+ * bnd (optional): per Gaussian, the sums a run could take when each test
+ * inside [eps(1-margin), eps(1+margin)] may go either way: every pixel stops
+ * no earlier than its first test below eps(1+margin) and no later than its
+ * first test below eps(1-margin).  sum_early / cnt_early: T summed and
+ * entries counted up to the earliest stops; cnt_late: entries counted up to
+ * the latest stops.  The entries between the two stops (cnt_late -
+ * cnt_early of them) each carry a transmittance in
+ * [eps(1-margin), eps(1+margin)].  Returns pairs. */
+typedef struct { double *sum_early; int64_t *cnt_early, *cnt_late; } vis_bounds;
+
+int64_t oracle_visibility_view_b(const float *cam, int64_t n, const float *means, const float *scales,
+                                 const float *rots, const float *opac, const double *prm,
+                                 double *sumT, int64_t *cnt, uint8_t *amb, const vis_bounds *bnd)
 {
     const double eps = prm[P_EPS_T], qcut = prm[P_QCUT], margin = prm[P_MARGIN];
+    const double band_hi = eps * (1.0 + margin), band_lo = eps * (1.0 - margin);
     const int tile = (int)prm[P_TILE];
     oproj *P = (oproj *)malloc(sizeof(oproj) * (size_t)(n > 0 ? n : 1));
     #pragma omp parallel for schedule(static)
@@ -625,27 +691,48 @@ int64_t oracle_visibility_view(const float *cam, int64_t n, const float *means, 
     build_lists(cam, n, P, qcut, 0, &Lst);
     memset(sumT, 0, sizeof(double) * (size_t)n);
     memset(cnt, 0, sizeof(int64_t) * (size_t)n);
+    if (bnd) {
+        memset(bnd->sum_early, 0, sizeof(double) * (size_t)n);
+        memset(bnd->cnt_early, 0, sizeof(int64_t) * (size_t)n);
+        memset(bnd->cnt_late, 0, sizeof(int64_t) * (size_t)n);
+    }
     int W = (int)cam[C_W], H = (int)cam[C_H];
     int64_t npix = (int64_t)W * H, pairs = 0;
     #pragma omp parallel for schedule(dynamic, 64) reduction(+ : pairs)
     for (int64_t p = 0; p < npix; ++p) {
         int i = (int)(p % W), j = (int)(p / W);
         double T = 1.0;
+        int on = 1, early = 1;       /* the oracle's own run; before the earliest stop */
         int64_t s = Lst.start[p], e = Lst.start[p + 1];
         for (int64_t k = s; k < e; ++k) {
             uint32_t g = (uint32_t)(Lst.ent[k] & 0xffffffffu);
             double q = (double)footprint_q(&P[g], i, j);
             double a = (double)opac[g] * exp(-0.5 * q);
-            #pragma omp atomic
-            sumT[g] += T;
-            #pragma omp atomic
-            cnt[g] += 1;
-            ++pairs;
+            if (on) {
+                #pragma omp atomic
+                sumT[g] += T;
+                #pragma omp atomic
+                cnt[g] += 1;
+                ++pairs;
+            }
+            if (bnd) {
+                if (early) {
+                    #pragma omp atomic
+                    bnd->sum_early[g] += T;
+                    #pragma omp atomic
+                    bnd->cnt_early[g] += 1;
+                }
+                #pragma omp atomic
+                bnd->cnt_late[g] += 1;
+            }
             T = T * (1.0 - a);
-            if (amb && near_thresh(T, eps, margin)) {
+            if (on && amb && near_thresh(T, eps, margin)) {
                 for (int64_t r = k + 1; r < e; ++r) amb[(uint32_t)(Lst.ent[r] & 0xffffffffu)] = 1;
             }
-            if (T < eps) break;
+            if (T < eps) on = 0;
+            if (T < band_hi) early = 0;
+            if (!bnd && !on) break;
+            if (T < band_lo) break;
         }
     }
     free_lists(&Lst);
@@ -653,31 +740,79 @@ int64_t oracle_visibility_view(const float *cam, int64_t n, const float *means, 
     return pairs;
 }
 
+int64_t oracle_visibility_view(const float *cam, int64_t n, const float *means, const float *scales,
+                               const float *rots, const float *opac, const double *prm,
+                               double *sumT, int64_t *cnt, uint8_t *amb, double *sum_early,
+                               int64_t *cnt_early, int64_t *cnt_late)
+{
+    vis_bounds b = {sum_early, cnt_early, cnt_late};
+    return oracle_visibility_view_b(cam, n, means, scales, rots, opac, prm, sumT, cnt, amb,
+                                    sum_early ? &b : NULL);
+}
+
+/* Range [v_lo, v_hi] of v = sumT / cnt over the runs vis_bounds allows, for
+ * one Gaussian: k of its late entries beyond the early ones (0 <= k <= K)
+ * each add a transmittance t; the other pass's own float32 transmittance may
+ * differ by a further factor (1 +- margin), so t lies in
+ * [eps (1-margin)^2, eps (1+margin)^2].  (S + k t) / (C + k) is monotone in k
+ * and in t, so its extremes sit at k in {0, K} and the ends of t's range. */
+static void visibility_range(double S, int64_t C, int64_t Cl, double eps, double margin, double *vlo, double *vhi)
+{
+    const double tlo = eps * (1.0 - margin) * (1.0 - margin), thi = eps * (1.0 + margin) * (1.0 + margin);
+    const int64_t K = Cl - C;
+    const double v0 = C > 0 ? S / (double)C : 0.0;
+    *vlo = *vhi = v0;
+    if (K > 0) {
+        double a = (S + (double)K * tlo) / (double)(C + K), b = (S + (double)K * thi) / (double)(C + K);
+        *vlo = fmin(v0, a);
+        *vhi = fmax(v0, b);
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Alg. Anisotropic Visibility Field Construction                           */
 /* ------------------------------------------------------------------------ */
 
 /* gamma: n x (L+1)^2 float64, overwritten.  vis_out (optional): nview x n
- * per-view visibilities v_p[g].  amb (optional, n): union over views. */
+ * per-view visibilities v_p[g].  amb (optional, n): union over views.
+ * gamma_rad (optional, n x (L+1)^2): sum over views of
+ * r_p |a_l Y_j(d_p)|, where r_p is the largest distance from v_p to the ends
+ * of its range under rounding-sensitive terminations (visibility_range):
+ * a bound on how far a field built with such terminations can lie from
+ * gamma, coefficient by coefficient. */
 void oracle_vf_build(int nview, const float *cams, int64_t n, const float *means, const float *scales,
                      const float *rots, const float *opac, int L, const double *prm,
-                     double *gamma, double *vis_out, uint8_t *amb)
+                     double *gamma, double *vis_out, uint8_t *amb, double *gamma_rad)
 {
     int K = (L + 1) * (L + 1);
-    double a[32];
+    double a[64];
     vmf_coeffs(L, prm[P_KAPPA], a);
     memset(gamma, 0, sizeof(double) * (size_t)n * K);
+    if (gamma_rad) memset(gamma_rad, 0, sizeof(double) * (size_t)n * K);
     if (amb) memset(amb, 0, (size_t)n);
-    double *sumT = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-    int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    double *sumT = (double *)malloc(sizeof(double) * nn);
+    int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * nn);
+    vis_bounds b = {NULL, NULL, NULL};
+    if (gamma_rad) {
+        b.sum_early = (double *)malloc(sizeof(double) * nn);
+        b.cnt_early = (int64_t *)malloc(sizeof(int64_t) * nn);
+        b.cnt_late = (int64_t *)malloc(sizeof(int64_t) * nn);
+    }
     for (int p = 0; p < nview; ++p) {
         const float *cam = cams + (size_t)C_LEN * p;
-        oracle_visibility_view(cam, n, means, scales, rots, opac, prm, sumT, cnt, amb);
+        oracle_visibility_view_b(cam, n, means, scales, rots, opac, prm, sumT, cnt, amb, gamma_rad ? &b : NULL);
         #pragma omp parallel for schedule(static)
         for (int64_t g = 0; g < n; ++g) {
             double v = cnt[g] > 0 ? sumT[g] / (double)cnt[g] : 0.0;
             if (vis_out) vis_out[(size_t)p * n + g] = v;
-            if (v == 0.0) continue;
+            double r = 0.0;
+            if (gamma_rad) {
+                double vlo, vhi;
+                visibility_range(b.sum_early[g], b.cnt_early[g], b.cnt_late[g], prm[P_EPS_T], prm[P_MARGIN], &vlo, &vhi);
+                r = fmax(vhi - v, v - vlo);
+            }
+            if (v == 0.0 && r == 0.0) continue;
             double d[3], Y[64];
             unit_dir(means + 3 * g, cam + C_POS, d);
             oracle_sh_real(L, d, Y);
@@ -685,11 +820,15 @@ void oracle_vf_build(int nview, const float *cams, int64_t n, const float *means
                 for (int m = -l; m <= l; ++m) {
                     int j = l * l + l + m;
                     gamma[(size_t)g * K + j] += v * a[l] * Y[j];
+                    if (gamma_rad) gamma_rad[(size_t)g * K + j] += r * fabs(a[l] * Y[j]);
                 }
         }
     }
     free(sumT);
     free(cnt);
+    free(b.sum_early);
+    free(b.cnt_early);
+    free(b.cnt_late);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -698,11 +837,14 @@ void oracle_vf_build(int nview, const float *cams, int64_t n, const float *means
 
 /* rgb: 3 x H x W planar; unc: H x W; amb: H x W (0/1); used: H x W entries
  * consumed.  V: per-Gaussian visibility for this view (from oracle_vf_query).
- * sh: n x (Lc+1)^2 x 3 colour coefficients. */
+ * sh: n x (Lc+1)^2 x 3 colour coefficients.  bounds (optional): 10 planes of
+ * H x W, the least and greatest value each output can take when the
+ * transmittance tests near eps_T go either way (see oracle_composite):
+ * unc_lo, unc_hi, r_lo, g_lo, b_lo, r_hi, g_hi, b_hi, depth_lo, depth_hi. */
 void oracle_render_view(const float *cam, int64_t n, const float *means, const float *scales,
                         const float *rots, const float *opac, const double *sh, const double *sh_var, int Lc,
                         const double *V, const double *prm, double *rgb, double *unc, double *depth,
-                        uint8_t *amb, int32_t *used)
+                        uint8_t *amb, int32_t *used, double *bounds)
 {
     const double qcut = prm[P_QCUT];
     const int tile = (int)prm[P_TILE];
@@ -761,8 +903,15 @@ void oracle_render_view(const float *cam, int64_t n, const float *means, const f
                 if (kcg) kk[k] = kcg[g];
                 zz[k] = (double)P[g].z;
             }
-            double res[12];
+            double res[24];
             oracle_composite(m, al, vv, cc, zz, prm, kcg ? kk : NULL, res);
+            if (bounds) {
+                bounds[p] = res[12];
+                bounds[npix + p] = res[13];
+                for (int k = 0; k < 6; ++k) bounds[(2 + k) * npix + p] = res[14 + k];
+                bounds[8 * npix + p] = res[20];
+                bounds[9 * npix + p] = res[21];
+            }
             unc[p] = res[0];
             rgb[p] = res[1];
             rgb[npix + p] = res[2];
@@ -790,12 +939,15 @@ void oracle_render_view(const float *cam, int64_t n, const float *means, const f
  * scene and the virtual particles; a particle is kept (under-explored) iff
  * that visibility is <= eps_v.
  *   vis_out: n_virt (float64); keep: n_virt (0/1); amb (optional): n_virt,
- *   set when a rounding-sensitive transmittance test touched the particle.
+ *   set when a rounding-sensitive transmittance test touched the particle;
+ *   vis_lo, vis_hi (optional): n_virt, the range of the multi-view
+ *   visibility when those tests go either way (per-view ranges from
+ *   visibility_range; 1 - prod(1 - v) is increasing in every v).
  * Returns the number kept. */
 int64_t oracle_density_control(int nview, const float *cams, int64_t n, const float *means, const float *scales,
                                const float *rots, const float *opac, int64_t n_virt, const float *vmeans,
                                double rho, double eta, double eps_v, const double *prm, double *vis_out,
-                               uint8_t *keep, uint8_t *amb)
+                               uint8_t *keep, uint8_t *amb, double *vis_lo, double *vis_hi)
 {
     const int64_t na = n + n_virt;
     const double s = cbrt(3.0 * (1.0 + eta) / (4.0 * M_PI * rho));
@@ -816,26 +968,39 @@ int64_t oracle_density_control(int nview, const float *cams, int64_t n, const fl
         ar[4 * (n + j) + 1] = ar[4 * (n + j) + 2] = ar[4 * (n + j) + 3] = 0.0f;
         ao[n + j] = 0.0f;
     }
-    double *prod = (double *)malloc(sizeof(double) * (size_t)(n_virt > 0 ? n_virt : 1));
-    for (int64_t j = 0; j < n_virt; ++j) prod[j] = 1.0;
-    double *sumT = (double *)malloc(sizeof(double) * (size_t)(na > 0 ? na : 1));
-    int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(na > 0 ? na : 1));
-    uint8_t *ab = (uint8_t *)calloc((size_t)(na > 0 ? na : 1), 1);
+    const size_t nv1 = (size_t)(n_virt > 0 ? n_virt : 1), na1 = (size_t)(na > 0 ? na : 1);
+    double *prod = (double *)malloc(sizeof(double) * nv1);
+    double *plo = (double *)malloc(sizeof(double) * nv1);   /* product with every v at its low end */
+    double *phi_ = (double *)malloc(sizeof(double) * nv1);  /* ... at its high end */
+    for (int64_t j = 0; j < n_virt; ++j) prod[j] = plo[j] = phi_[j] = 1.0;
+    double *sumT = (double *)malloc(sizeof(double) * na1);
+    int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * na1);
+    uint8_t *ab = (uint8_t *)calloc(na1, 1);
+    vis_bounds b = {(double *)malloc(sizeof(double) * na1), (int64_t *)malloc(sizeof(int64_t) * na1),
+                    (int64_t *)malloc(sizeof(int64_t) * na1)};
     for (int p = 0; p < nview; ++p) {
-        oracle_visibility_view(cams + (size_t)C_LEN * p, na, am, as, ar, ao, prm, sumT, cnt, ab);
+        oracle_visibility_view_b(cams + (size_t)C_LEN * p, na, am, as, ar, ao, prm, sumT, cnt, ab, &b);
         for (int64_t j = 0; j < n_virt; ++j) {
             double v = cnt[n + j] > 0 ? sumT[n + j] / (double)cnt[n + j] : 0.0;
+            double vlo, vhi;
+            visibility_range(b.sum_early[n + j], b.cnt_early[n + j], b.cnt_late[n + j], prm[P_EPS_T],
+                             prm[P_MARGIN], &vlo, &vhi);
             prod[j] *= 1.0 - v;
+            plo[j] *= 1.0 - vlo;
+            phi_[j] *= 1.0 - vhi;
         }
     }
     int64_t kept = 0;
     for (int64_t j = 0; j < n_virt; ++j) {
         double vt = 1.0 - prod[j];
         if (vis_out) vis_out[j] = vt;
+        if (vis_lo) vis_lo[j] = 1.0 - plo[j];
+        if (vis_hi) vis_hi[j] = 1.0 - phi_[j];
         keep[j] = (uint8_t)(vt <= eps_v);
         kept += keep[j];
         if (amb) amb[j] = ab[n + j];
     }
-    free(am); free(as); free(ar); free(ao); free(prod); free(sumT); free(cnt); free(ab);
+    free(am); free(as); free(ar); free(ao); free(prod); free(plo); free(phi_); free(sumT); free(cnt); free(ab);
+    free(b.sum_early); free(b.cnt_early); free(b.cnt_late);
     return kept;
 }

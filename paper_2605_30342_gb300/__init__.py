@@ -74,7 +74,7 @@ EXPORTS = ["gavis_ctx_create", "gavis_ctx_destroy", "gavis_last_error", "gavis_p
            "gavis_server_create", "gavis_server_destroy", "gavis_server_last_error", "gavis_server_add_scene",
            "gavis_server_submit", "gavis_server_wait", "gavis_server_stats", "gavis_autotune",
            "gavis_plan_create", "gavis_plan_launch", "gavis_plan_overflowed", "gavis_plan_kernels",
-           "gavis_plan_destroy", "gavis_render_views"]
+           "gavis_plan_destroy", "gavis_render_views", "gavis_augment"]
 
 STAGES = ["project", "scan", "emit", "sort", "ranges", "composite_ua", "composite_vis", "reduce", "vf_accum"]
 
@@ -116,6 +116,8 @@ def load(path: str | None = None):
         lib.gavis_vf_density_control.argtypes = [vp, C.POINTER(gavis_gaussians), vp, i64, C.POINTER(gavis_camera), i32,
                                                  C.POINTER(gavis_params), C.c_float, C.c_float, C.c_float, vp, vp, vp,
                                                  C.POINTER(C.c_int64), C.POINTER(C.c_float), vp]
+        lib.gavis_augment.argtypes = [vp, C.POINTER(gavis_gaussians), C.POINTER(gavis_vf), vp, i64, C.c_float,
+                                      vp, vp, vp, vp, vp, vp, vp, vp]
         lib.gavis_server_create.argtypes = [C.POINTER(vp), i32, C.c_size_t, i32, i32]
         lib.gavis_server_destroy.argtypes = [vp]
         lib.gavis_server_destroy.restype = None
@@ -372,26 +374,31 @@ class Context:
         n_keep = int(nk.value)
         return dict(vis=vis, keep=keep.bool(), kept_means=kept[:n_keep], n_keep=n_keep, scale=float(scale.value))
 
-    @staticmethod
-    def augment(gs: Gaussians, vf: VisibilityField, kept_means: torch.Tensor, scale: float):
-        """The scene used for uncertainty scoring after density control: the
-        trained Gaussians plus the kept virtual particles (identity rotation,
-        isotropic `scale`, zero opacity, zero colour, gamma = 0 so V = 0)."""
+    def augment(self, gs: Gaussians, vf: VisibilityField, kept_means: torch.Tensor, scale: float, stream=None):
+        """The scene used for uncertainty scoring after density control
+        (gavis_augment): the trained Gaussians plus the kept virtual
+        particles (identity rotation, isotropic `scale`, zero opacity, zero
+        colour, gamma = 0 so V = 0).  Allocates the outputs only."""
         k = int(kept_means.shape[0])
+        n = int(gs.means.shape[0])
         dev = gs.means.device
-        means = torch.cat([gs.means, kept_means.to(dev, torch.float32)])
-        scales = torch.cat([gs.scales, torch.full((k, 3), float(scale), device=dev)])
-        rots = torch.cat([gs.rots, torch.tensor([1.0, 0.0, 0.0, 0.0], device=dev).repeat(k, 1)])
-        opac = torch.cat([gs.opac, torch.zeros(k, device=dev)])
-        sh = torch.cat([gs.sh, torch.zeros((k,) + tuple(gs.sh.shape[1:]), dtype=gs.sh.dtype, device=dev)])
-        coeffs = torch.cat([vf.coeffs, torch.zeros((k, vf.coeffs.shape[1]), dtype=vf.coeffs.dtype, device=dev)])
-        var = None
-        if gs.sh_var is not None:   # any positive variance: virtual particles have V = 0
-            var = torch.cat([gs.sh_var, torch.ones((k,) + tuple(gs.sh_var.shape[1:]), dtype=gs.sh_var.dtype,
-                                                   device=dev)]).contiguous()
-        return (Gaussians(means.contiguous(), scales.contiguous(), rots.contiguous(), opac.contiguous(),
-                          sh.contiguous(), gs.sh_degree, var),
-                VisibilityField(coeffs.contiguous(), vf.degree, vf.n_train_views, vf.kappa))
+        km = kept_means.contiguous()
+        means = torch.empty((n + k, 3), device=dev)
+        scales = torch.empty((n + k, 3), device=dev)
+        rots = torch.empty((n + k, 4), device=dev)
+        opac = torch.empty(n + k, device=dev)
+        sh = torch.empty((n + k,) + tuple(gs.sh.shape[1:]), dtype=gs.sh.dtype, device=dev)
+        var = None if gs.sh_var is None else torch.empty_like(sh)
+        coeffs = torch.empty((n + k, vf.coeffs.shape[1]), dtype=vf.coeffs.dtype, device=dev)
+        self._check(self._lib.gavis_augment(
+            self._h, C.byref(gs.struct), C.byref(vf.struct()),
+            C.c_void_p(_dev(km, "kept_means", torch.float32) if k else None), k, float(scale),
+            C.c_void_p(means.data_ptr()), C.c_void_p(scales.data_ptr()), C.c_void_p(rots.data_ptr()),
+            C.c_void_p(opac.data_ptr()), C.c_void_p(sh.data_ptr()),
+            C.c_void_p(var.data_ptr() if var is not None else None), C.c_void_p(coeffs.data_ptr()),
+            _stream_ptr(stream)))
+        return (Gaussians(means, scales, rots, opac, sh, gs.sh_degree, var),
+                VisibilityField(coeffs, vf.degree, vf.n_train_views, vf.kappa))
 
     # -------------------------------------------------------------- instrumentation
     def prof_enable(self, on: bool = True):

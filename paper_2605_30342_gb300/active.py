@@ -47,7 +47,7 @@ class ActiveMapper:
             dc = self.ctx.density_control(self.gs, self.virtual_means, self.views, rho=self.rho, eta=self.eta,
                                           eps_v=self.eps_v, params=self.params)
             kept = dc["n_keep"]
-            gs, vf = Context.augment(self.gs, self.vf, dc["kept_means"], dc["scale"])
+            gs, vf = self.ctx.augment(self.gs, self.vf, dc["kept_means"], dc["scale"])
         out = self.ctx.score_views(gs, vf, candidates, params=self.params, want_rgb=False)
         best = int(out["best"])
         self.views.append(candidates[best])                   # the pose whose image is taken next

@@ -1084,6 +1084,56 @@ int gavis_vf_density_control(gavis_ctx *ctx, const gavis_gaussians *gs, const fl
     return GAVIS_OK;
 }
 
+int gavis_augment(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf, const float *kept_means,
+                  int64_t n_kept, float scale, float *means, float *scales, float *rots, float *opac, void *sh,
+                  void *sh_var, void *coeffs, void *stream)
+{
+    if (!ctx) return GAVIS_ERR_ARG;
+    int rc;
+    if ((rc = check_gaussians(ctx, gs, true)) || (rc = check_vf(ctx, gs, vf))) return rc;
+    if (n_kept < 0 || gs->n + n_kept >= ((int64_t)1 << 31)) return fail(ctx, GAVIS_ERR_ARG, "n_kept out of range");
+    if (n_kept > 0 && !kept_means) return fail(ctx, GAVIS_ERR_ARG, "kept_means is NULL");
+    if (!(scale > 0.0f)) return fail(ctx, GAVIS_ERR_ARG, "scale must be > 0");
+    if (!means || !scales || !rots || !opac || !sh || !coeffs)
+        return fail(ctx, GAVIS_ERR_ARG, "NULL output array");
+    if ((gs->sh_var != nullptr) != (sh_var != nullptr))
+        return fail(ctx, GAVIS_ERR_ARG, "sh_var output must be given exactly when the scene has colour variances");
+    if ((uintptr_t)rots & 15u) return fail(ctx, GAVIS_ERR_ARG, "rots must be 16-byte aligned");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CallOrder order(ctx, s);
+    const size_t n = (size_t)gs->n, k = (size_t)n_kept;
+    const size_t esh = gs->sh_dtype == GAVIS_F32 ? 4 : 2, evf = vf->dtype == GAVIS_F32 ? 4 : 2;
+    const size_t Kc = (size_t)(gs->sh_degree + 1) * (gs->sh_degree + 1) * 3;
+    const size_t Kv = (size_t)(vf->degree + 1) * (vf->degree + 1);
+    // the trained Gaussians, unchanged, then the kept virtual particles
+    if (n) {
+        CK(cudaMemcpyAsync(means, gs->means, n * 12, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(scales, gs->scales, n * 12, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(rots, gs->rots, n * 16, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(opac, gs->opac, n * 4, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(sh, gs->sh, n * Kc * esh, cudaMemcpyDeviceToDevice, s));
+        if (sh_var) CK(cudaMemcpyAsync(sh_var, gs->sh_var, n * Kc * esh, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(coeffs, vf->coeffs, n * Kv * evf, cudaMemcpyDeviceToDevice, s));
+    }
+    if (k) {
+        // identity rotation, isotropic scale, zero opacity; zero colour and
+        // zero field (V = 0: only the prior component of eq:alpha_comp)
+        CK(launch_virtual_fill(kept_means, n_kept, scale, means + 3 * n, scales + 3 * n, rots + 4 * n, opac + n, s));
+        CK(cudaMemsetAsync(static_cast<char *>(sh) + n * Kc * esh, 0, k * Kc * esh, s));
+        CK(cudaMemsetAsync(static_cast<char *>(coeffs) + n * Kv * evf, 0, k * Kv * evf, s));
+        if (sh_var) {   // any positive variance will do: a Gaussian with V = 0 has no visible component
+            char *dst = static_cast<char *>(sh_var) + n * Kc * esh;
+            if (gs->sh_dtype == GAVIS_F32)
+                CK(launch_fill_f32(reinterpret_cast<float *>(dst), k * Kc, 1.0f, s));
+            else
+                CK(launch_fill_u16(reinterpret_cast<uint16_t *>(dst), k * Kc,
+                                   gs->sh_dtype == GAVIS_F16 ? (uint16_t)0x3c00u : (uint16_t)0x3f80u, s));
+        }
+    }
+    return GAVIS_OK;
+}
+
 // ---------------------------------------------------------------- autotuner
 namespace {
 

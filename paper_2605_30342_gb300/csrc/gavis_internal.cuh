@@ -250,6 +250,7 @@ cudaError_t launch_vf_load(const void *in, int dtype, size_t count, float *gamma
 cudaError_t launch_virtual_fill(const float *vmeans, int64_t n_virt, float scale, float *means, float *scales,
                                 float *rots, float *opac, cudaStream_t s);
 cudaError_t launch_fill_f32(float *x, size_t count, float value, cudaStream_t s);
+cudaError_t launch_fill_u16(uint16_t *x, size_t count, uint16_t bits, cudaStream_t s);
 cudaError_t launch_vf_product(const unsigned long long *sumT, const uint32_t *cnt, int nv, int64_t n_all,
                               int64_t first, int64_t n_virt, float *prod, cudaStream_t s);
 cudaError_t launch_density_finalize(const float *prod, int64_t n_virt, float eps_v, float *vis, uint8_t *keep,

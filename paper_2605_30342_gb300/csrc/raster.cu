@@ -710,6 +710,13 @@ __global__ void k_fill_f32(float *x, size_t count, float value)
     if (i < count) x[i] = value;
 }
 
+// count 16-bit elements set to one bit pattern (1.0 in f16 or bf16)
+__global__ void k_fill_u16(uint16_t *x, size_t count, uint16_t bits)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) x[i] = bits;
+}
+
 // prod[j] *= 1 - v_p[first + j] for every view p of the batch
 __global__ void k_vf_product(const unsigned long long *sumT, const uint32_t *cnt, int nv, int64_t n_all, int64_t first,
                              int64_t n_virt, float *prod)
@@ -973,6 +980,13 @@ cudaError_t launch_fill_f32(float *x, size_t count, float value, cudaStream_t s)
 {
     if (count == 0) return cudaSuccess;
     k_fill_f32<<<nblk(count, 256), 256, 0, s>>>(x, count, value); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_u16(uint16_t *x, size_t count, uint16_t bits, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    k_fill_u16<<<nblk(count, 256), 256, 0, s>>>(x, count, bits); count_launch();
     return cudaGetLastError();
 }
 

@@ -33,7 +33,7 @@ def test_active_mapping_loop():
     assert torch.allclose(fresh.coeffs, am.vf.coeffs, atol=1e-5)
     # the last step's scores equal a direct scoring of the same augmented scene
     dc = ctx.density_control(gs, vm, am.views[:4], rho=100.0)
-    gs2, vf2 = gv.Context.augment(gs, am.vf, dc["kept_means"], dc["scale"])
+    gs2, vf2 = am.ctx.augment(gs, am.vf, dc["kept_means"], dc["scale"])
     direct = ctx.score_views(gs2, vf2, sg.fibonacci_cameras(8, 2.6 + 0.3 * 2, 96, 96))
     assert torch.equal(direct["score"], am.history[-1]["scores"])
     ctx.close()

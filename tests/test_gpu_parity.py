@@ -3,9 +3,11 @@
 Tile bins and sort keys must match bit for bit; per-pixel uncertainty, colour,
 visibility-field coefficients (as gamma/|P|), queried visibilities and view
 scores within 1e-4 absolute; the selected view must match whenever the
-oracle's top-2 gap exceeds 2e-4.  Pixels whose transmittance test lands within
-0.1% of eps_T in the float64 oracle are counted and left out of the value
-gate: float32 rounding may legitimately flip them.
+oracle's top-2 gap exceeds 2e-4.  Where a transmittance test lands within
+0.1% of eps_T in the float64 oracle, float32 rounding may stop the run one or
+more entries earlier or later: there the oracle gives the range of values
+every such stop produces, and the GPU value must lie in that range (within
+the same 1e-4).  No pixel and no Gaussian is left out.
 """
 import numpy as np
 import pytest
@@ -13,7 +15,7 @@ import torch
 
 import oracle
 import scenegen as sg
-from _util import GAP, TOL, compare_views, sorted_gap
+from _util import GAP, TOL, compare_views, excess, score_excess, sorted_gap, visibility_check
 
 pytestmark = pytest.mark.gpu
 
@@ -239,12 +241,12 @@ def test_single_view_visibility_parity(ctx, gv, name):
     sumT, cnt = ctx.debug_visibility(gs, cams)
     sumT, cnt = sumT.cpu().numpy(), cnt.cpu().numpy()
     for v, cam in enumerate(cams):
-        rs, rc, amb, _ = oracle.visibility_view(cam, sc)
-        ok = ~amb
-        assert np.array_equal(cnt[v][ok], rc[ok])                    # pixel counts are integers: exact
-        vis_g = np.where(cnt[v] > 0, sumT[v] / np.maximum(cnt[v], 1), 0.0)
-        vis_r = np.where(rc > 0, rs / np.maximum(rc, 1), 0.0)
-        assert np.abs(vis_g[ok] - vis_r[ok]).max() <= TOL
+        rs, rc, amb, _, b = oracle.visibility_view(cam, sc, want_bounds=True)
+        bad, err, moved = visibility_check(sumT[v], cnt[v], b)
+        n_band = int((b["cnt_late"] > b["cnt_early"]).sum())
+        msg = f"view {v}: {n_band} Gaussians reachable by a band stop, GPU count off the early one for {moved}"
+        assert bad == 0, msg                 # pixel counts are integers: inside [early, late] exactly
+        assert err <= TOL, (err, msg)
         assert (cnt[v] > 0).sum() > 10
 
 
@@ -258,15 +260,16 @@ def test_vf_build_parity(ctx, gv, name, dtype):
     vf = ctx.vf_build(gs, train, degree=L, dtype=dtype)
     assert vf.n_train_views == len(train)
     g = vf.coeffs.double().cpu().numpy()
-    ref, amb, _ = oracle.vf_build(train, sc, L)
-    ok = ~amb
+    ref, _, _, rad = oracle.vf_build(train, sc, L, want_rad=True)
     P = len(train)
     # half-precision storage rounds gamma to 2^-11 (f16) or 2^-8 (bf16) relative: state it and gate on it
     rel = {torch.float32: 0.0, torch.float16: 2.0 ** -11, torch.bfloat16: 2.0 ** -8}[dtype]
-    tol = TOL + rel * np.abs(ref[ok]).max() / P
-    err = np.abs(g[ok] - ref[ok]).max() / P
-    assert err <= tol, (err, tol)
-    assert ok.mean() > 0.8   # at least 80% of Gaussians are clear of the eps_T rounding margin
+    # every coefficient of every Gaussian: within 1e-4 |P| of the oracle, plus
+    # the radius that rounding-sensitive stops allow (0 for most Gaussians),
+    # plus the storage rounding
+    err = (np.abs(g - ref) - rad - rel * (np.abs(ref) + rad)) / P
+    n_rad = int((rad.max(1) > 0).sum())
+    assert err.max() <= TOL, (err.max(), f"{n_rad} of {sc.n} Gaussians have a nonzero radius")
 
 
 def test_vf_build_batched_equals_plain(ctx, gv):
@@ -308,13 +311,10 @@ def test_score_views_parity(ctx, gv, name, tile):
     out = ctx.score_views(gs, vf, cand, params=gv.Params(tile=tile, vf_degree=L))
     unc, rgb, score = out["unc"].cpu().numpy(), out["rgb"].cpu().numpy(), out["score"].cpu().numpy()
     ref = oracle.score_views(sc, g32.astype(np.float64), L, len(c["train"]), cand)
-    err, n_amb = compare_views(unc, rgb, ref)
+    err, n_band = compare_views(unc, rgb, ref)
     npix = len(cand) * cand[0].W * cand[0].H
-    assert err <= TOL, err
-    assert n_amb <= 0.01 * npix
-    # view scores: the ambiguous pixels' actual differences are allowed for
-    amb_slack = np.array([np.abs(unc[v] - ref["unc"][v])[ref["amb"][v]].sum() / unc[v].size for v in range(len(cand))])
-    assert np.all(np.abs(score - ref["score"]) <= TOL + amb_slack)
+    assert err <= TOL, (err, f"{n_band} of {npix} pixels have a stop inside the band")
+    assert score_excess(score, ref).max() <= TOL
     if sorted_gap(ref["score"]) > GAP:
         assert out["best"] == ref["best"]
 
@@ -339,13 +339,10 @@ def test_expected_depth_parity(ctx, gv, name, tile):
         assert torch.equal(a[k], b[k]), k
     ref = oracle.score_views(sc, g32.astype(np.float64), L, len(c["train"]), cand, want_depth=True)
     d = a["depth"].cpu().numpy()
-    n_amb = 0
     for v in range(len(cand)):
-        ok = ~ref["amb"][v]
-        n_amb += int((~ok).sum())
-        err = np.abs(d[v] - ref["depth"][v]) / np.maximum(1.0, np.abs(ref["depth"][v]))
-        assert err[ok].max() <= TOL, (v, err[ok].max())
-    assert n_amb <= 0.01 * d.size
+        b = ref["bnd"][v]
+        err = excess(d[v], b["depth_lo"], b["depth_hi"]) / np.maximum(1.0, np.abs(ref["depth"][v]))
+        assert err.max() <= TOL, (v, err.max())
     assert np.abs(d).max() > 1.0   # the case exercises depths well above 1
 
 
@@ -363,16 +360,26 @@ def test_score_batched_equals_plain(ctx, gv):
 
 def test_end_to_end_tiny(ctx, gv):
     """VF CONST on the GPU feeding scoring on the GPU, against the oracle run
-    end to end on the same inputs."""
+    end to end on the same inputs: the field within its radius, every pixel
+    and every view score within 1e-4 of the oracle's range.  (The ranges of
+    the scoring pass cover its own rounding-sensitive stops; that the GPU's
+    field build takes the oracle's stops on this case is part of what the
+    test checks: a different stop moves a Gaussian's field by up to its
+    radius, and the scores with it.)"""
     c = case("tiny")
     sc = c["scene"]
     gs = gpu_scene(gv, sc)
     vf = ctx.vf_build(gs, c["train"], degree=2)
     out = ctx.score_views(gs, vf, c["cand"])
-    g, amb_g, _ = oracle.vf_build(c["train"], sc, 2)
-    ref = oracle.score_views(sc, g, 2, len(c["train"]), c["cand"])
-    # Gaussians whose field is ambiguous shift V slightly: compare the scores
-    assert np.abs(out["score"].cpu().numpy() - ref["score"]).max() <= 1e-3
+    g, _, _, rad = oracle.vf_build(c["train"], sc, 2, want_rad=True)
+    P = len(c["train"])
+    gg = vf.coeffs.double().cpu().numpy()
+    assert ((np.abs(gg - g) - rad) / P).max() <= TOL
+    ref = oracle.score_views(sc, g, 2, P, c["cand"])
+    err, n_band = compare_views(out["unc"].cpu().numpy(), out["rgb"].cpu().numpy(), ref)
+    moved = int((np.abs(gg - g) / P > TOL).any(1).sum())
+    assert err <= TOL, (err, f"{moved} Gaussians' fields moved by a band stop; {n_band} pixels in the band")
+    assert score_excess(out["score"].cpu().numpy(), ref).max() <= TOL
     if sorted_gap(ref["score"]) > GAP:
         assert out["best"] == ref["best"]
 
@@ -451,9 +458,9 @@ def test_invalid_arguments_raise(ctx, gv):
 @pytest.mark.parametrize("name", ["tiny", "room_small"])
 def test_density_control_parity(ctx, gv, name):
     """Alg. Visibility Field Density Control against the oracle: multi-view
-    visibility of the virtual particles within 1e-4, same kept set except
-    particles whose visibility lies within 1e-4 of eps_v or that a
-    rounding-sensitive transmittance test touched."""
+    visibility of every virtual particle within 1e-4 of the oracle's range,
+    and the same keep decision wherever that range (widened by 1e-4) lies
+    on one side of eps_v."""
     c = case(name)
     sc = c["scene"]
     lo, hi = sc.bbox_min.astype(np.float64), sc.bbox_max.astype(np.float64)
@@ -462,11 +469,12 @@ def test_density_control_parity(ctx, gv, name):
     vm = np.random.default_rng(11).uniform(lo, hi, (nvirt, 3)).astype(np.float32)
     gs = gpu_scene(gv, sc)
     out = ctx.density_control(gs, torch.as_tensor(vm).cuda(), c["train"], rho=rho, eta=0.5, eps_v=0.95)
-    vis_r, keep_r, amb = oracle.density_control(c["train"], sc, vm, rho=rho, eta=0.5, eps_v=0.95)
+    vis_r, keep_r, _, vlo, vhi = oracle.density_control(c["train"], sc, vm, rho=rho, eta=0.5, eps_v=0.95,
+                                                        want_bounds=True)
     vis_g = out["vis"].cpu().numpy()
-    ok = ~amb
-    assert np.abs(vis_g[ok] - vis_r[ok]).max() <= TOL
-    clear = ok & (np.abs(vis_r - 0.95) > TOL)
+    assert excess(vis_g, vlo, vhi).max() <= TOL
+    clear = (vhi < 0.95 - TOL) | (vlo > 0.95 + TOL)
+    assert clear.mean() > 0.98, clear.mean()
     assert np.array_equal(out["keep"].cpu().numpy()[clear], keep_r[clear])
     assert out["n_keep"] == int(out["keep"].sum().item())
     np.testing.assert_array_equal(out["kept_means"].cpu().numpy(), vm[out["keep"].cpu().numpy()])
@@ -475,26 +483,47 @@ def test_density_control_parity(ctx, gv, name):
 
 
 def test_density_control_feeds_scoring(ctx, gv):
-    """Kept virtual particles join scoring with V = 0: the augmented scene's
-    scores match the oracle run on the same augmented scene."""
+    """Kept virtual particles join scoring with V = 0 (zero field, zero
+    opacity, zero colour): the scene augmented with the oracle's kept set,
+    scored on the GPU, against the oracle run on the same augmented scene;
+    and the GPU's own augmentation of its kept set holds exactly those
+    records."""
     c = case("tiny")
     sc = c["scene"]
     vm = np.random.default_rng(12).uniform(-1.5, 1.5, (500, 3)).astype(np.float32)
-    gs = gpu_scene(gv, sc)
-    vf = ctx.vf_build(gs, c["train"][:3], degree=2)
-    dc = ctx.density_control(gs, torch.as_tensor(vm).cuda(), c["train"][:3], rho=100.0)
-    gs2, vf2 = gv.Context.augment(gs, vf, dc["kept_means"], dc["scale"])
-    out = ctx.score_views(gs2, vf2, c["cand"][:4])
-    k = dc["n_keep"]
-    aug = sg.Scene(np.concatenate([sc.means, dc["kept_means"].cpu().numpy()]),
-                   np.concatenate([sc.scales, np.full((k, 3), dc["scale"], np.float32)]),
+    train = c["train"][:3]
+    g, _, _ = oracle.vf_build(train, sc, 2)
+    _, keep_r, _ = oracle.density_control(train, sc, vm, rho=100.0)
+    k = int(keep_r.sum())
+    assert k > 0
+    s = np.float32(oracle.virtual_scale(100.0, 0.5))
+    aug = sg.Scene(np.concatenate([sc.means, vm[keep_r]]),
+                   np.concatenate([sc.scales, np.full((k, 3), s, np.float32)]),
                    np.concatenate([sc.rots, np.tile(np.array([[1, 0, 0, 0]], np.float32), (k, 1))]),
                    np.concatenate([sc.opac, np.zeros(k, np.float32)]),
                    np.concatenate([sc.sh, np.zeros((k,) + sc.sh.shape[1:], np.float32)]), sc.sh_degree)
-    ref = oracle.score_views(aug, vf2.coeffs.double().cpu().numpy(), 2, 3, c["cand"][:4])
+    g_aug = np.concatenate([g, np.zeros((k, g.shape[1]))]).astype(np.float32)
+    vf_aug = gv.VisibilityField(torch.as_tensor(g_aug).cuda(), 2, 3, 1.0)
+    out = ctx.score_views(gpu_scene(gv, aug), vf_aug, c["cand"][:4])
+    ref = oracle.score_views(aug, g_aug.astype(np.float64), 2, 3, c["cand"][:4])
     err, _ = compare_views(out["unc"].cpu().numpy(), out["rgb"].cpu().numpy(), ref)
     assert err <= TOL
-    assert k > 0
+    assert score_excess(out["score"].cpu().numpy(), ref).max() <= TOL
+    # the GPU's augmentation of its own kept set: the scene's records, then
+    # the kept particles as zero-opacity isotropic Gaussians with a zero field
+    gs = gpu_scene(gv, sc)
+    vf = ctx.vf_build(gs, train, degree=2)
+    dc = ctx.density_control(gs, torch.as_tensor(vm).cuda(), train, rho=100.0)
+    gs2, vf2 = ctx.augment(gs, vf, dc["kept_means"], dc["scale"])
+    kg = dc["n_keep"]
+    km = dc["kept_means"].cpu().numpy()
+    assert torch.equal(gs2.means.cpu(), torch.as_tensor(np.concatenate([sc.means, km])))
+    assert torch.equal(gs2.scales[sc.n:].cpu(), torch.full((kg, 3), dc["scale"], dtype=torch.float32))
+    assert torch.equal(gs2.rots[sc.n:].cpu(), torch.tensor([[1.0, 0.0, 0.0, 0.0]]).repeat(kg, 1))
+    assert torch.all(gs2.opac[sc.n:] == 0) and torch.all(gs2.sh[sc.n:] == 0)
+    assert torch.equal(gs2.opac[:sc.n].cpu(), torch.as_tensor(sc.opac))
+    assert torch.equal(vf2.coeffs[:sc.n], vf.coeffs) and torch.all(vf2.coeffs[sc.n:] == 0)
+    assert vf2.n_train_views == vf.n_train_views
 
 
 def test_autotune_picks_a_tile_and_caches(ctx, gv):

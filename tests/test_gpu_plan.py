@@ -7,7 +7,7 @@ import torch
 
 import oracle
 import scenegen as sg
-from _util import GAP, TOL, compare_views, sorted_gap
+from _util import GAP, TOL, compare_views, score_excess, sorted_gap
 
 pytestmark = pytest.mark.gpu
 
@@ -80,13 +80,9 @@ def test_plan_matches_oracle(ctx, gv):
     plan.launch(cand)
     torch.cuda.synchronize()
     ref = oracle.score_views(sc, g32.astype(np.float64), L, len(c["train"]), cand)
-    err, n_amb = compare_views(plan.unc.cpu().numpy(), plan.rgb.cpu().numpy(), ref)
-    assert err <= TOL, err
-    assert n_amb <= 0.01 * len(cand) * cand[0].W * cand[0].H
-    score = plan.score.cpu().numpy()
-    unc = plan.unc.cpu().numpy()
-    amb_slack = np.array([np.abs(unc[v] - ref["unc"][v])[ref["amb"][v]].sum() / unc[v].size for v in range(len(cand))])
-    assert np.all(np.abs(score - ref["score"]) <= TOL + amb_slack)
+    err, n_band = compare_views(plan.unc.cpu().numpy(), plan.rgb.cpu().numpy(), ref)
+    assert err <= TOL, (err, n_band)
+    assert score_excess(plan.score.cpu().numpy(), ref).max() <= TOL
     if sorted_gap(ref["score"]) > GAP:
         assert int(plan.best_dev.item()) == ref["best"]
 

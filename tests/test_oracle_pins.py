@@ -583,3 +583,106 @@ def test_expected_depth_partition_of_unity():
         r = oracle.composite(al, rng.uniform(0, 1, n), rng.normal(size=(n, 3)), z=np.full(n, 4.25))
         assert r["depth"] == pytest.approx(4.25 * (1.0 - r["Tc"]), rel=1e-12, abs=1e-12)
         assert r["depth"] == pytest.approx(4.25 * r["sum_wc"], rel=1e-12)
+
+
+# --------------------------------------------------------------------------- bounds under rounding-sensitive stops
+
+def _band_list(seed):
+    """A list whose transmittance lingers inside the band around eps_T for
+    several entries: a few opaque entries bring T near eps, then faint ones."""
+    rng = np.random.default_rng(seed)
+    eps = 1e-4
+    a = list(rng.uniform(0.5, 0.9, 3))
+    T = float(np.prod(1 - np.array(a)))
+    a.append(1 - eps * 1.0004 / T)              # T lands at eps (1 + 4e-4)
+    a += list(rng.uniform(1e-4, 4e-4, 6))       # T creeps down through the band
+    a += list(rng.uniform(0.2, 0.6, 4))
+    n = len(a)
+    V = rng.uniform(0, 1, n)
+    V[:10] = 1.0                                # alpha* = alpha there: both accumulators cross the band
+    col = rng.normal(0, 1, (n, 3))
+    z = rng.uniform(1, 5, n)
+    return np.array(a), V, col, z
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_composite_bounds_are_runs_at_thresholds_in_the_band(seed):
+    """[H_lo, H_hi] (and the rgb, depth ranges) equal the least and greatest
+    outputs of plain runs (margin 0) whose threshold sweeps the band
+    [eps (1 - m), eps (1 + m)]: every possible stop is some threshold's stop."""
+    a, V, col, z = _band_list(seed)
+    eps, m = 1e-4, 1e-3
+    r = oracle.composite(a, V, col, oracle.params(eps_T=eps, margin=m), z=z)
+    outs = []
+    for thr in np.linspace(eps * (1 - m), eps * (1 + m), 801):
+        outs.append(oracle.composite(a, V, col, oracle.params(eps_T=float(thr), margin=0.0), z=z))
+    H = np.array([o["H"] for o in outs])
+    rgb = np.array([o["rgb"] for o in outs])
+    d = np.array([o["depth"] for o in outs])
+    assert H.max() > H.min()        # the band holds more than one stop here
+    assert r["H_lo"] == pytest.approx(H.min(), abs=1e-15) and r["H_hi"] == pytest.approx(H.max(), abs=1e-15)
+    np.testing.assert_allclose(r["rgb_lo"], rgb.min(0), atol=1e-15)
+    np.testing.assert_allclose(r["rgb_hi"], rgb.max(0), atol=1e-15)
+    assert r["depth_lo"] == pytest.approx(d.min(), abs=1e-14) and r["depth_hi"] == pytest.approx(d.max(), abs=1e-14)
+    assert r["H_lo"] <= r["H"] <= r["H_hi"]
+
+
+def test_composite_bounds_collapse_away_from_the_band():
+    rng = np.random.default_rng(3)
+    a = rng.uniform(0.1, 0.5, 12)
+    V = rng.uniform(0, 1, 12)
+    col = rng.normal(0, 1, (12, 3))
+    r = oracle.composite(a, V, col, oracle.params(eps_T=1e-4, margin=1e-3))
+    assert not r["amb"]
+    assert r["H_lo"] == r["H"] == r["H_hi"]
+    assert np.array_equal(r["rgb_lo"], r["rgb"]) and np.array_equal(r["rgb_hi"], r["rgb"])
+
+
+def test_visibility_bounds_are_runs_at_band_edges():
+    """The early sums and counts are exactly the plain run stopping at
+    eps (1 + m); the late counts the plain run stopping at eps (1 - m)."""
+    c = sg.config(1, n=800, n_train=2, train_wh=(96, 80))
+    sc = c["scene"]
+    eps, m = 1e-4, 1e-2   # a wide band, so that small cases exercise it
+    in_band = 0
+    for cam in c["train"]:
+        s, cn, _, _, b = oracle.visibility_view(cam, sc, oracle.params(eps_T=eps, margin=m), want_bounds=True)
+        s_hi, c_hi, _, _ = oracle.visibility_view(cam, sc, oracle.params(eps_T=eps * (1 + m), margin=0.0))
+        s_lo, c_lo, _, _ = oracle.visibility_view(cam, sc, oracle.params(eps_T=eps * (1 - m), margin=0.0))
+        assert np.array_equal(b["cnt_early"], c_hi) and np.array_equal(b["cnt_late"], c_lo)
+        np.testing.assert_allclose(b["sum_early"], s_hi, rtol=1e-12, atol=1e-15)
+        assert np.all(b["cnt_early"] <= cn) and np.all(cn <= b["cnt_late"])
+        in_band += int((b["cnt_late"] > b["cnt_early"]).sum())
+    assert in_band > 0     # the case exercises the band
+
+
+def test_field_radius_contains_builds_at_band_edges():
+    """A field built with the thresholds at either edge of the band (two of
+    the builds a rounding-sensitive pass could produce) lies within gamma +-
+    the radius, coefficient by coefficient."""
+    c = sg.config(1, n=800, n_train=3, train_wh=(96, 80))
+    sc, L = c["scene"], 2
+    eps, m = 1e-4, 1e-2   # a wide band, so that small cases exercise it
+    g, _, _, rad = oracle.vf_build(c["train"], sc, L, oracle.params(eps_T=eps, margin=m), want_rad=True)
+    assert rad.max() > 0
+    for thr in (eps * (1 - m), eps * (1 + m)):
+        g2, _, _ = oracle.vf_build(c["train"], sc, L, oracle.params(eps_T=thr, margin=0.0))
+        assert np.all(np.abs(g2 - g) <= rad + 1e-12)
+    # Gaussians untouched by the band have radius 0 and the same field
+    g0, _, _, rad0 = oracle.vf_build(c["train"], sc, L, oracle.params(eps_T=eps, margin=0.0), want_rad=True)
+    np.testing.assert_allclose(g0, g, rtol=1e-12, atol=1e-14)   # (sums over pixels run in parallel)
+    assert np.all(rad0 <= 1e-12)
+
+
+def test_density_control_range_contains_band_edges():
+    c = sg.config(1, n=600, n_train=3, train_wh=(64, 64))
+    sc = c["scene"]
+    rng = np.random.default_rng(9)
+    vm = rng.uniform(-1, 1, (300, 3)).astype(np.float32)
+    eps, m = 1e-4, 1e-2   # a wide band, so that small cases exercise it
+    vis, _, _, lo, hi = oracle.density_control(c["train"], sc, vm, prm=oracle.params(eps_T=eps, margin=m),
+                                               want_bounds=True)
+    assert np.all(lo <= vis + 1e-15) and np.all(vis <= hi + 1e-15)
+    for thr in (eps * (1 - m), eps * (1 + m)):
+        v2, _, _ = oracle.density_control(c["train"], sc, vm, prm=oracle.params(eps_T=thr, margin=0.0))
+        assert np.all(lo - 1e-12 <= v2) and np.all(v2 <= hi + 1e-12)
