@@ -26,13 +26,26 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# algorithmic float32 flops per (pixel, Gaussian) pair, counted from the
-# algorithms: uncertainty + colour compositing, and the
-# single-view particle visibility pass
-FLOPS_PER_PAIR_UA = 32
-FLOPS_PER_PAIR_VIS = 14
+# Algorithmic float32 operations per (pixel, Gaussian) pair, counted
+# operation by operation from the algorithms (an FMA counts 2, any other
+# float32 add, multiply or compare 1; exp and log go to the special-function
+# unit and are listed apart):
+#   footprint q = A dx^2 + 2B dx dy + C dy^2 from dx, dy:        9
+#   overlap test q <= q_cut:                                      1
+#   alpha = o exp(-q/2): scale + multiply (+ 1 exp):              2
+# single-view particle visibility (Alg. visibility):
+#   sum_T += T, T *= 1 - alpha (FMA), T < eps_T:                  4   -> 16 + 1 exp
+# uncertainty + colour (Alg. UQ with eq:alpha_comp, eq:huber, eq:orig_vr):
+#   alpha* = a1 alpha + a0 (FMA), w = alpha* T, wv = w V:         4
+#   H += -wv ln wv + wv k_c (multiply, add, FMA; + 1 log):        4
+#   w0 += w (1 - V) (FMA), T *= 1 - alpha* (FMA), T < eps_T:      5
+#   colour: wc = alpha Tc, rgb += wc c (3 FMA), Tc *= 1 - alpha
+#   (FMA), Tc < eps_T:                                            10  -> 35 + 1 exp + 1 log
+FLOPS_PER_PAIR_UA = 35
+FLOPS_PER_PAIR_VIS = 16
 FP32_LANES_PER_SM = 128
-N_SM = 152
+# warp instructions a Blackwell SM issues per clock (4 schedulers x 1)
+ISSUE_PER_SM_CLK = 4
 
 
 def parse():
@@ -53,6 +66,9 @@ def parse():
                     help="cpu_baseline: training and candidate views of the oracle sample (about 10 s of CPU work)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain unbatched f32 comparison step")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph scoring comparison")
+    ap.add_argument("--no-precision", action="store_true", help="skip the storage-precision errors vs the oracle")
+    ap.add_argument("--precision-views", type=int, default=8,
+                    help="precision_err: sampled training and candidate views (about 30 s of CPU work)")
     ap.add_argument("--serving", action="store_true", help="serving workload: Poisson requests over 4 resident scenes")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean request rate (req/s)")
     ap.add_argument("--requests", type=int, default=300, help="serving: number of requests")
@@ -465,7 +481,8 @@ def run_gavis(args):
     pk, pk_kind = peaks()
     dom = max(st, key=lambda k: st[k][0])
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    fp32_peak = 2.0 * N_SM * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12   # TFLOP/s, FMA = 2 flops
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = 2.0 * n_sm * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12   # TFLOP/s, FMA = 2 flops
     pairs_ua, pairs_vis = prof["pairs"]
     roof = None
     if dom in ("composite_ua", "composite_vis"):
@@ -473,17 +490,33 @@ def run_gavis(args):
         fpp = FLOPS_PER_PAIR_UA if dom == "composite_ua" else FLOPS_PER_PAIR_VIS
         ms, nl = st[dom]
         achieved = pairs * fpp / (ms / 1e3) / 1e12
+        tile = prm_sc.tile if dom == "composite_ua" else prm_vf.tile
+        prof_k = profile_for("k_" + dom, tile)
         roof = {"kernel": "k_" + dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
-                "traffic": traffic_for("k_" + dom, prm_sc.tile if dom == "composite_ua" else prm_vf.tile),
-                "peak_source": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
+                "traffic": prof_k.get("bytes_per_launch") if prof_k else None,
+                "peak_source": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
                                f"(sm_max_mhz of {pk_kind} peaks file)",
                 "units_per_launch": pairs / max(nl, 1), "unit_name": "pixel-Gaussian pairs",
                 "flops_per_unit": fpp, "avg_launch_ms": ms / max(nl, 1), "launches": nl}
+        ipp = prof_k.get("warp_inst_per_pair") if prof_k else None
+        if ipp:
+            # the kernel is issue-bound: its ceiling is the SMs' warp-instruction
+            # issue rate divided by the instructions it issues per pair
+            peak_pairs = n_sm * ISSUE_PER_SM_CLK * sm_mhz * 1e6 / ipp
+            roof["issue"] = {"warp_inst_per_pair": ipp, "peak_pairs_per_s": peak_pairs,
+                             "achieved_pairs_per_s": pairs / (ms / 1e3),
+                             "frac": pairs / (ms / 1e3) / peak_pairs,
+                             "source": "warp instructions per pair from the ncu capture in profiles/"}
     else:
         ms, nl = st[dom]
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                 "frac": None, "traffic": None, "avg_launch_ms": ms / max(nl, 1), "launches": nl}
+
+    # ---------------- storage precision against the float64 oracle ----------------
+    prec = None
+    if rank == 0 and world == 1 and not args.no_precision and cdt != torch.float32:
+        prec = precision_errors(gv, ctx, c, gs, cdt, prm_vf, prm_sc, args.precision_views)
 
     # ---------------- CPU baseline (rank 0, N = 1) ----------------
     cpu = None
@@ -517,12 +550,58 @@ def run_gavis(args):
             "hbm": hbm,
             "plain_unbatched_f32": plain,
             "graph_scoring": graph,
+            "precision_err": prec,
             "best_view": best,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def precision_errors(gv, ctx, c, gs, cdt, prm_vf, prm_sc, k):
+    """Error of every output of the stored-precision path against the oracle
+    fed the float32 inputs (float64 field, float32 colour) on k sampled
+    views: the field of k training views (gamma/|P|), and k candidate views
+    scored with that oracle field rounded to the storage type (rgb, unc,
+    score, V).  Max-abs and 99th percentile per output."""
+    import numpy as np
+    import torch
+    import oracle
+    oracle.build()
+    sc = c["scene"]
+    L = c["vf_degree"]
+    spread = lambda n: [int(round(i * (n - 1) / (k - 1))) for i in range(k)]
+    train = [c["train"][i] for i in spread(len(c["train"]))]
+    cands = [c["cand"][i] for i in spread(len(c["cand"]))]
+    t0 = time.perf_counter()
+    g_o, _, _ = oracle.vf_build(train, sc, L)
+    P = len(train)
+    g_dev = ctx.vf_build(gs, train, degree=L, params=prm_vf, dtype=cdt).coeffs.double().cpu().numpy()
+
+    def st(e):
+        e = np.abs(np.asarray(e, np.float64)).ravel()
+        return {"max_abs": float(e.max(initial=0.0)), "p99": float(np.percentile(e, 99)) if e.size else 0.0}
+
+    res = {"gamma_over_P": st((g_dev - g_o) / P)}
+    vf = gv.VisibilityField(torch.as_tensor(g_o.astype(np.float32)).to("cuda", cdt).contiguous(), L, P, 1.0)
+    out = ctx.score_views(gs, vf, cands, params=prm_sc)
+    Vg = ctx.vf_query(gs, vf, cands).double().cpu().numpy()
+    unc, rgb, score = out["unc"].cpu().numpy(), out["rgb"].cpu().numpy(), out["score"].cpu().numpy()
+    e_rgb, e_unc, e_V, e_s = [], [], [], []
+    for v, cam in enumerate(cands):
+        V64, _ = oracle.vf_query(g_o, L, P, cam, sc.means)
+        r = oracle.render_view(cam, sc, V64)
+        e_rgb.append((rgb[v] - r[0]).ravel())
+        e_unc.append((unc[v] - r[1]).ravel())
+        e_V.append(Vg[v] - V64)
+        e_s.append(score[v] - r[1].mean())
+    res.update(rgb=st(np.concatenate(e_rgb)), unc=st(np.concatenate(e_unc)), V=st(np.concatenate(e_V)),
+               score=st(e_s))
+    res["what"] = (f"stored {str(cdt).split('.')[-1]} coefficients vs the float64 oracle on float32 inputs: field "
+                   f"of {P} sampled training views, {len(cands)} sampled candidate views scored with that field")
+    res["oracle_s"] = time.perf_counter() - t0
+    return res
 
 
 def kernel_source_sha(path, kernel):
@@ -546,9 +625,10 @@ def kernel_source_sha(path, kernel):
     return None
 
 
-def traffic_for(kernel, tile):
-    """DRAM bytes per launch from the committed ncu summary, when it was taken
-    on the current source of the kernel at the same tile size (else null)."""
+def profile_for(kernel, tile):
+    """The committed ncu figures of a kernel (DRAM bytes per launch, warp
+    instructions per pair), when they were taken on the current source of
+    the kernel at the same tile size (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -559,9 +639,15 @@ def traffic_for(kernel, tile):
         if not e:
             return None
         src = os.path.join(ROOT, "paper_2605_30342_gb300", "csrc", e["source"])
-        return e["bytes_per_launch"] if kernel_source_sha(src, kernel) == e.get("kernel_sha") else None
+        return e if kernel_source_sha(src, kernel) == e.get("kernel_sha") else None
     except Exception:
         return None
+
+
+def traffic_for(kernel, tile):
+    """DRAM bytes per launch from the committed ncu summary (see profile_for)."""
+    e = profile_for(kernel, tile)
+    return e["bytes_per_launch"] if e else None
 
 
 def run_serving(args):

@@ -1,9 +1,10 @@
 // gavis_internal.cuh -- shared declarations of the CUDA translation units.
 //
 // Record layouts (HBM, one entry per (view-in-batch, Gaussian), index v*N + g):
-//   GeoRec  32 B  a = (u, v, A, 2B)  b = (C, opacity, depth z, ext)
-//           image-space centre and conic of the projected Gaussian; ext packs
-//           the footprint half-extents (ex, ey) as two halves rounded up.
+//   GeoRec  32 B  a = (u, v, A, 2B)  b = (C, log2(opacity), depth z, ext)
+//           image-space centre and conic of the projected Gaussian (log2 of
+//           the opacity, -inf for opacity 0); ext packs the footprint
+//           half-extents (ex, ey) as two halves rounded up.
 //   UaRec   32 B  a = (a1, a0, V, r)  b = (g, b, kc, 0)
 //           alpha* = a1 * alpha + a0 (eq:alpha_comp, a1 = V + beta(1-V),
 //           a0 = o0(1-beta)(1-V)), the queried visibility V (eq:vis_bound) and
@@ -46,8 +47,11 @@ struct RasterConsts {
     float k_0;   // 1/2 log|Q_0| + 3/2 log(2 pi e)
 };
 
-// fixed-point scale of the transmittance sums of the visibility pass
-constexpr float kTScale = 16777216.0f;   // 2^24
+// fixed-point scale of the transmittance sums of the visibility pass: 2^18,
+// so that a warp's per-entry sum of 64 pixels' round(T 2^18) shifted left by
+// kCntBits, plus their hit count in the low kCntBits bits, fits 32 bits
+constexpr float kTScale = 262144.0f;   // 2^18
+constexpr int kCntBits = 7;
 // views one projection or query launch takes: their cameras sit in shared memory
 constexpr int kMaxBatchViews = 1024;
 // keys per block of the radix sort passes (one histogram row per block)

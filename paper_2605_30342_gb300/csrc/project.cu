@@ -153,6 +153,8 @@ __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
     const float sc[3] = {a.scales[3 * g], a.scales[3 * g + 1], a.scales[3 * g + 2]};
     const float4 q = reinterpret_cast<const float4 *>(a.rots)[g];
     const float op = a.opac[g];
+    // the records carry log2(opacity): the composites take alpha = 2^(log2(o) - q log2(e)/2)
+    const float lop = op > 0.0f ? log2f(op) : -INFINITY;
     const Sigma3 S = sigma3d(sc, q.x, q.y, q.z, q.w);
     const float rb = 1.0f / (float)a.tile;
 
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
                     // footprint half-extents, rounded up to half precision (conservative)
                     const uint32_t ext = (uint32_t)__half_as_ushort(__float2half_ru(p.ex)) |
                                          ((uint32_t)__half_as_ushort(__float2half_ru(p.ey)) << 16);
-                    gr.b = make_float4(p.C, op, p.z, __uint_as_float(ext));
+                    gr.b = make_float4(p.C, lop, p.z, __uint_as_float(ext));
                     a.geo[r] = gr;
                     if (a.zrec) a.zrec[r] = p.z;
                 }

@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kUaWarps * 32) k_composite_ua(CompositeArgs a)
                     const bool hit = q <= rc.q_cut;
                     const bool hc = hit && rgb_on[p], hu = hit && ua_on[p];
                     npairs += (uint32_t)(hc || hu);
-                    const float alpha = g1.y * ex2_approx(q * kNegHalfLog2e);
+                    const float alpha = ex2_approx(fmaf(q, kNegHalfLog2e, g1.y));   // o exp(-q/2)
                     if (colour) {   // the same for every thread of the launch
                         const float2 u1 = u1s[k];
                         const float ac = hc ? alpha : 0.0f;
@@ -451,9 +451,12 @@ __global__ void __launch_bounds__(kUaWarps * 32) k_composite_ua(CompositeArgs a)
 // the tile (each thread two pixels) and walks the tile's depth-sorted list on
 // its own, 32 entries at a time, compacting the entries whose footprint box
 // touches the block.  Per overlapping entry a pixel contributes its current T
-// (fixed point, 2^-24) and a count of one to the Gaussian's sums; the warp adds
-// its 64 pixels with one redux and lane 0 adds them to the Gaussian's
-// accumulators with one atomic each.  A warp stops when its pixels saturate.
+// (fixed point, 2^-18) and a count of one to the Gaussian's sums: the pixel's
+// word is (round(T 2^18) << kCntBits) + 1, the warp adds its 64 pixels' words
+// with one redux, and the chunk's per-entry sums are flushed to the
+// Gaussians' accumulators once per chunk, one atomic pair per entry.  The
+// transmittance is kept scaled by 2^18 (exact: a power of two), and alpha is
+// 2^(log2(o) - q log2(e)/2).  A warp stops when its pixels saturate.
 template <int TILE>
 __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs a)
 {
@@ -462,6 +465,7 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
     __shared__ float4 s_g0[NW][32];
     __shared__ float2 s_g1[NW][32];
     __shared__ uint32_t s_idx[NW][32];
+    __shared__ uint32_t s_sum[NW][32];
 
     const int tiles = a.TW * a.TH;
     const int vb = blockIdx.x / tiles;
@@ -477,14 +481,16 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
     const float px = (float)i + 0.5f, py0 = (float)j0 + 0.5f, py1 = py0 + 4.0f;
     const uint2 rg = a.ranges[blockIdx.x];
     const size_t vrow = (size_t)vb * (size_t)a.n;
-    const float eps = a.rc.eps_T, qcut = a.rc.q_cut;
+    const float eps = a.rc.eps_T * kTScale, qcut = a.rc.q_cut;
 
-    float T0 = 1.0f, T1 = 1.0f;
+    float T0 = kTScale, T1 = kTScale;   // transmittance x 2^18
     bool on0 = i < a.W && j0 < a.H, on1 = i < a.W && j0 + 4 < a.H;
     uint32_t wpairs = 0;
     float4 *g0s = s_g0[warp];
     float2 *g1s = s_g1[warp];
     uint32_t *ids = s_idx[warp];
+    uint32_t *sums = s_sum[warp];
+    constexpr uint32_t kCntMul = 1u << kCntBits;
 
     for (uint32_t base = rg.x; base < rg.y; base += 32) {
         if (!__any_sync(0xffffffffu, on0 || on1)) break;
@@ -505,12 +511,9 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
             g1s[slot] = make_float2(gr.b.x, gr.b.y);
             ids[slot] = g;
         }
+        sums[lane] = 0u;   // entries the warp does not reach (it saturated) add nothing
         __syncwarp();
         const int nk = __popc(mk);
-        // the warp's sums for the entry in slot k are kept by lane k and
-        // added to the per-Gaussian totals once per chunk, all lanes at once
-        uint32_t my_sum = 0u;
-        unsigned my_m0 = 0u, my_m1 = 0u;   // the slot's hit masks; counted once per chunk
         for (int k = 0; k < nk; ++k) {
             if (!__any_sync(0xffffffffu, on0 || on1)) break;   // warp-uniform
             const float4 g0 = g0s[k];
@@ -518,27 +521,26 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
             const float q0 = footprint_q(px, py0, g0.x, g0.y, g0.z, g0.w, g1.x);
             const float q1 = footprint_q(px, py1, g0.x, g0.y, g0.z, g0.w, g1.x);
             const bool h0 = on0 && (q0 <= qcut), h1 = on1 && (q1 <= qcut);
-            const unsigned m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
-            const uint32_t tq = (h0 ? __float2uint_rn(T0 * kTScale) : 0u) + (h1 ? __float2uint_rn(T1 * kTScale) : 0u);
-            const uint32_t sum = __reduce_add_sync(0xffffffffu, tq);
-            if (lane == k) {
-                my_sum = sum;
-                my_m0 = m0;
-                my_m1 = m1;
-            }
+            const uint32_t w0 = h0 ? __float2uint_rn(T0) * kCntMul + 1u : 0u;
+            const uint32_t w1 = h1 ? __float2uint_rn(T1) * kCntMul + 1u : 0u;
+            const uint32_t sum = __reduce_add_sync(0xffffffffu, w0 + w1);
+            if (lane == 0) sums[k] = sum;   // the same in every lane
             if (h0) {
-                T0 = fmaf(-T0, g1.y * ex2_approx(q0 * kNegHalfLog2e), T0);
+                T0 = fmaf(-T0, ex2_approx(fmaf(q0, kNegHalfLog2e, g1.y)), T0);
                 on0 = T0 >= eps;
             }
             if (h1) {
-                T1 = fmaf(-T1, g1.y * ex2_approx(q1 * kNegHalfLog2e), T1);
+                T1 = fmaf(-T1, ex2_approx(fmaf(q1, kNegHalfLog2e, g1.y)), T1);
                 on1 = T1 >= eps;
             }
         }
-        const uint32_t my_cnt = (uint32_t)(__popc(my_m0) + __popc(my_m1));
+        __syncwarp();
+        // lane k adds slot k's sums to its Gaussian's accumulators
+        const uint32_t my = sums[lane];
+        const uint32_t my_cnt = my & (kCntMul - 1u);
         if (my_cnt) {
             const size_t r = vrow + ids[lane];
-            atomicAdd(&a.sumT[r], (unsigned long long)my_sum);
+            atomicAdd(&a.sumT[r], (unsigned long long)(my >> kCntBits));
             atomicAdd(&a.cnt[r], my_cnt);
             wpairs += my_cnt;
         }
