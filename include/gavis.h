@@ -95,7 +95,7 @@ typedef struct {
 typedef struct {
     int64_t n;                   /* must equal the Gaussians' n */
     void *coeffs;                /* device [n][(degree+1)^2] of dtype (gamma of eq:vis_gamma) */
-    int32_t degree;              /* L, 0..3 */
+    int32_t degree;              /* L, 0..5 */
     int32_t dtype;               /* gavis_dtype of coeffs */
     int32_t n_train_views;       /* |P| of eq:vis_bound; 0 means "never seen": V = 0 everywhere */
     float kappa;                 /* concentration used to build it */
@@ -134,7 +134,7 @@ int gavis_params_default(gavis_params *p);
 
 /* a_l = 4 pi e^{-kappa} i_l(kappa), l = 0..L (the per-degree factor of
  * eq:vis_gamma; i_l the modified spherical Bessel function of the first kind).
- * a: host [L+1].  L in 0..3, kappa >= 0. */
+ * a: host [L+1].  L in 0..5, kappa >= 0. */
 int gavis_vmf_coeffs(int L, double kappa, double *a);
 
 /* Visibility-field construction (Alg. "Anisotropic Visibility Field

@@ -115,10 +115,6 @@ cudaError_t scan_vis_words(const uint32_t *words, size_t nwords, uint32_t *woff,
 cudaError_t emit_vis_words(const uint32_t *words, const uint32_t *woff, int nv, int64_t n, const GeoRec *geo,
                            const float *zrec, int zb, uint32_t zmin, uint32_t vmask, uint32_t *keyA, uint32_t *valA,
                            uint32_t *voff, cudaStream_t s);
-// The same with 64-bit keys (view << 32) | depth bits, for chains that cannot
-// size the sort on the host; records past cap_R are dropped and set *overflow.
-cudaError_t emit_vis_words64(const uint32_t *words, const uint32_t *woff, int nv, int64_t n, const GeoRec *geo,
-                             uint64_t *keyA, uint32_t *valA, size_t cap_R, uint32_t *overflow, cudaStream_t s);
 
 // stable LSD radix sort of (keys, vals) on bits [0, end_bit); ping-pong
 // buffers; *result_in_alt tells which buffer holds the result.  KeyT is
@@ -148,9 +144,12 @@ struct RsBlock {
 size_t radix_segment_blocks(const uint64_t *seg, int nseg, RsBlock *tbl);
 // blk: device copy of the table (nblk blocks); tmp: radix_tmp_bytes of
 // nblk * 4096 items.
+// prepared: the kernel attributes were set beforehand (radix_prepare; needed
+// while a stream is being captured).
 template <typename KeyT>
 cudaError_t radix_sort_segments(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_t *vals_alt, const RsBlock *blk,
-                                size_t nblk, int end_bit, void *tmp, bool *result_in_alt, cudaStream_t s);
+                                size_t nblk, int end_bit, void *tmp, bool *result_in_alt, cudaStream_t s,
+                                bool prepared = false);
 
 // ---------------------------------------------------------------- raster.cu
 struct BatchInfo {                // device, read back once per batch
@@ -159,14 +158,45 @@ struct BatchInfo {                // device, read back once per batch
     unsigned long long visible;   // (view, Gaussian) records with tiles
 };
 // bits needed to represent x
-inline int bits_of(uint64_t x)
+__host__ __device__ inline int bits_of(uint64_t x)
 {
     int b = 0;
     while (b < 64 && (x >> b) != 0) ++b;
     return b;
 }
 // bits of the depth part of the record keys of a batch
-inline int depth_bits(uint32_t zmin, uint32_t zmax) { return bits_of(zmax > zmin ? zmax - zmin : 0u); }
+__host__ __device__ inline int depth_bits(uint32_t zmin, uint32_t zmax)
+{
+    return bits_of(zmax > zmin ? zmax - zmin : 0u);
+}
+
+// Stage-A key parameters of a batch computed on the device from its
+// BatchInfo, for chains captured in a CUDA graph (the batched call computes
+// the same on the host): zmin, zb = depth_bits, and view groups of
+// gsz = 2^gb views, gb = min(bits(nv - 1), 32 - zb), vmask = gsz - 1.
+struct KeyParams {
+    uint32_t zmin, vmask;
+    int32_t zb, gsz;
+};
+cudaError_t launch_key_params(const BatchInfo *info, int nv, KeyParams *kp, cudaStream_t s);
+// emit_vis_words with the key parameters read from kp (device); records at
+// positions >= cap_R are dropped and set *overflow.
+cudaError_t emit_vis_words_dev(const uint32_t *words, const uint32_t *woff, int nv, int64_t n, const GeoRec *geo,
+                               const KeyParams *kp, uint32_t *keyA, uint32_t *valA, uint32_t *voff, size_t cap_R,
+                               uint32_t *overflow, cudaStream_t s);
+// The block table of a segmented sort built on the device (nv <= 1024):
+// segment s covers [off[min(s g, nv)], off[min((s + 1) g, nv)]) clamped to
+// cap, for groups of g views (g = kp->gsz when kp is given, else gsz),
+// s < ceil(nv / g).  All nblk_max entries are written: the live blocks as
+// radix_segment_blocks lays them out, then empty blocks whose histogram
+// columns follow the live ones.  nblk_max >= radix_segment_blocks_max.
+cudaError_t launch_segment_blocks(const uint32_t *off, int nv, const KeyParams *kp, int gsz, size_t cap,
+                                  RsBlock *blk, size_t nblk_max, cudaStream_t s);
+size_t radix_segment_blocks_max(size_t cap, int nv);
+// eoff[v] (v = 0..nv) as launch_entry_offsets, from device counts: records
+// past min(visible, cap_R) and entries past min(total, cap_M) are cut off.
+cudaError_t launch_entry_offsets_dev(const uint32_t *off_sorted, const uint32_t *voff, int nv, const BatchInfo *info,
+                                     size_t cap_R, size_t cap_M, uint32_t *eoff, cudaStream_t s);
 // Two-level binning.  Stage A: one key per visible (view, Gaussian) record,
 // ((view << zb) | (depth bits - zmin)), value the record index, sorted.
 // Stage B: in that order, one entry per tile of the record's rectangle with
@@ -212,7 +242,7 @@ struct CompositeArgs {
     const uint32_t *order;     // uncertainty pass: (view, tile) indices, longest lists first, or NULL (natural order)
     bool per_entry_kc;     // use the per-Gaussian kc of the UaRec (colour variances given)
     // visibility pass
-    unsigned long long *sumT;  // [nv * n] fixed point 2^-24
+    unsigned long long *sumT;  // [nv * n] fixed point 2^-18 (kTScale)
     uint32_t *cnt;             // [nv * n]
     // optional instrumentation: (pixel, Gaussian) pairs composited; the
     // uncertainty pass writes one count per 8 x 8 block, like tile_sums (summed by launch_sum_counts),
@@ -242,7 +272,7 @@ struct AccumArgs {
     int64_t n;
     const unsigned long long *sumT;
     const uint32_t *cnt;
-    float a_l[4];
+    float a_l[6];               // a_l for l = 0..L (L <= 5)
     int L;
     float *gamma32;             // [n * K], accumulated in place
 };

@@ -90,7 +90,7 @@ extern "C" int gavis_score_view_noalloc(const gavis_gaussians *gs, const gavis_v
     if (gs->n > 0 && ((uintptr_t)gs->rots & 15u)) return report(err, err_len, GAVIS_ERR_ARG, "rots must be 16-byte aligned");
     if (gs->sh_degree < 0 || gs->sh_degree > 3 || gs->sh_dtype < 0 || gs->sh_dtype > 2)
         return report(err, err_len, GAVIS_ERR_ARG, "bad colour SH degree or dtype");
-    if (vf->n != gs->n || vf->degree < 0 || vf->degree > 3 || vf->dtype < 0 || vf->dtype > 2 ||
+    if (vf->n != gs->n || vf->degree < 0 || vf->degree > 5 || vf->dtype < 0 || vf->dtype > 2 ||
         vf->n_train_views < 0 || (vf->n > 0 && !vf->coeffs))
         return report(err, err_len, GAVIS_ERR_ARG, "bad visibility field");
     if (!(p->tile == 8 || p->tile == 16 || p->tile == 32) || !(p->eps_T > 0.0f && p->eps_T < 1.0f) ||

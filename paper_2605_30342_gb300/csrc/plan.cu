@@ -14,9 +14,14 @@
 // capacity, the excess is dropped, a device flag is set, and
 // gavis_plan_overflowed reports it (the caller then rebuilds the plan with
 // larger capacities).
-// The stage-A keys keep all 32 depth bits (the per-batch path subtracts the
-// batch's minimum and keeps only the bits that vary), so the record sort may
-// take one more 8-bit pass; the resulting order is the same.
+// The sorts are sized on the device as the batched call sizes them on the
+// host: after the projection a kernel derives the depth bits and the view
+// groups of the stage-A keys from the batch's depth range, the record and
+// tile-entry offsets of every view give the segments of the two segmented
+// sorts, and kernels build their block tables (as many blocks as the
+// capacities can need; the unused ones are empty).  So a replay runs the
+// same passes over the same keys as gavis_score_views, and its outputs are
+// the same bits.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -134,12 +139,19 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     const size_t nwords = (size_t)B * (size_t)((n + 31) / 32);
     const size_t o_cnt = take(nvn * 4), o_words = take(nwords * 4), o_woff = take(nwords * 4);
     const size_t o_scan = take(scan_tmp_bytes(nwords) + 64);
-    const size_t o_ak0 = take(R * 8), o_ak1 = take(R * 8), o_av0 = take(R * 4), o_av1 = take(R * 4);
+    const size_t o_ak0 = take(R * 4), o_ak1 = take(R * 4), o_av0 = take(R * 4), o_av1 = take(R * 4);
     const size_t o_acnt = take(R * 4), o_aoff = take(R * 4);
     const size_t o_bk0 = take(M * 4), o_bk1 = take(M * 4), o_bv0 = take(M * 4), o_bv1 = take(M * 4);
+    // segmented sorts: block tables for the largest batch, key parameters,
+    // per-view record and entry offsets
+    const size_t nblk_a = radix_segment_blocks_max(R, B), nblk_b = radix_segment_blocks_max(M, B);
+    const size_t o_blka = take(nblk_a * sizeof(RsBlock)), o_blkb = take(nblk_b * sizeof(RsBlock));
+    const size_t o_kp = take(sizeof(KeyParams));
+    const size_t o_voff = take(((size_t)B + 1) * 4), o_eoff = take(((size_t)B + 1) * 4);
     size_t big = R > M ? R : M;
     if (nvt > big) big = nvt;   // the tile-order sort shares the temporary space
-    const size_t o_tmp = take(radix_tmp_bytes(big) + scan_tmp_bytes(big) + 64);
+    const size_t seg_items = (nblk_a > nblk_b ? nblk_a : nblk_b) * (size_t)kRadixTile;
+    const size_t o_tmp = take(radix_tmp_bytes(big > seg_items ? big : seg_items) + scan_tmp_bytes(big) + 64);
     const int bpt = blocks_per_tile(p->tile);
     const size_t o_rng = take(nvt * sizeof(uint2)), o_ts = take(nvt * (size_t)bpt * sizeof(float));
     const size_t o_work = take(sizeof(unsigned long long));
@@ -164,7 +176,10 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     uint2 *rect = reinterpret_cast<uint2 *>(b + o_rect);
     uint32_t *counts = reinterpret_cast<uint32_t *>(b + o_cnt);
     uint32_t *vis_words = reinterpret_cast<uint32_t *>(b + o_words), *woff = reinterpret_cast<uint32_t *>(b + o_woff);
-    uint64_t *ak0 = reinterpret_cast<uint64_t *>(b + o_ak0), *ak1 = reinterpret_cast<uint64_t *>(b + o_ak1);
+    uint32_t *ak0 = reinterpret_cast<uint32_t *>(b + o_ak0), *ak1 = reinterpret_cast<uint32_t *>(b + o_ak1);
+    RsBlock *blk_a = reinterpret_cast<RsBlock *>(b + o_blka), *blk_b = reinterpret_cast<RsBlock *>(b + o_blkb);
+    KeyParams *kp = reinterpret_cast<KeyParams *>(b + o_kp);
+    uint32_t *voff = reinterpret_cast<uint32_t *>(b + o_voff), *eoff = reinterpret_cast<uint32_t *>(b + o_eoff);
     uint32_t *av0 = reinterpret_cast<uint32_t *>(b + o_av0), *av1 = reinterpret_cast<uint32_t *>(b + o_av1);
     uint32_t *acnt = reinterpret_cast<uint32_t *>(b + o_acnt), *aoff = reinterpret_cast<uint32_t *>(b + o_aoff);
     uint32_t *bk0 = reinterpret_cast<uint32_t *>(b + o_bk0), *bk1 = reinterpret_cast<uint32_t *>(b + o_bk1);
@@ -225,21 +240,35 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
         PK(launch_project(pa, cs));
         const size_t nwords_b = (size_t)nv * (size_t)((n + 31) / 32);
         PK(scan_vis_words(vis_words, nwords_b, woff, scan_tmp, cs));
-        PK(emit_vis_words64(vis_words, woff, nv, n, geo, ak0, av0, R, &info->records_over, cs));
+        // stage A: 32-bit (view in group, depth) keys, groups of views sorted
+        // as segments (one sequence of four 8-bit passes)
+        PK(launch_key_params(&info->b, nv, kp, cs));
+        PK(emit_vis_words_dev(vis_words, woff, nv, n, geo, kp, ak0, av0, voff, R, &info->records_over, cs));
+        PK(launch_segment_blocks(voff, nv, kp, 0, R, blk_a, nblk_a, cs));
         bool alt_a = false, alt_b = false;
-        PK(radix_sort_pairs<uint64_t>(ak0, av0, ak1, av1, R, bits_of((uint64_t)nv - 1) + 32, tmp, &alt_a, cs,
-                                      &info->b.visible));
+        PK(radix_sort_segments<uint32_t>(ak0, av0, ak1, av1, blk_a, nblk_a, 32, tmp, &alt_a, cs, true));
         const uint32_t *recs = alt_a ? av1 : av0;
         PK(launch_gather_counts(recs, counts, R, acnt, cs, &info->b.visible));
         PK(exclusive_scan_u32(acnt, aoff, R, tmp, nullptr, cs, false, &info->b.visible));
+        // stage B: tile keys (view << tb) | tile sorted on 16 bits per group
+        // of 2^(16 - tb) views when the tile index fits tb <= 16 bits and the
+        // batch's views do not (as the batched call), else view * TT + tile
+        const int vb = bits_of((uint64_t)nv - 1), tbits = bits_of((uint64_t)TT - 1);
+        const int tb = tbits + vb > 16 && tbits <= 16 && ((nv - 1) >> (16 - tbits)) < 64 ? tbits : -1;
         PK(launch_emit_tiles(recs, aoff, R, rect, n, TW, TH, bk0, bv0, cs, &info->b.visible, M,
-                             &info->entries_over));
-        PK(radix_sort_pairs<uint32_t>(bk0, bv0, bk1, bv1, M, bits_of((uint64_t)nvt_b - 1), tmp, &alt_b, cs,
-                                      &info->b.total));
+                             &info->entries_over, tb));
+        if (tb >= 0) {
+            PK(launch_entry_offsets_dev(aoff, voff, nv, &info->b, R, M, eoff, cs));
+            PK(launch_segment_blocks(eoff, nv, nullptr, 1 << (16 - tb), M, blk_b, nblk_b, cs));
+            PK(radix_sort_segments<uint32_t>(bk0, bv0, bk1, bv1, blk_b, nblk_b, 16, tmp, &alt_b, cs, true));
+        } else {
+            PK(radix_sort_pairs<uint32_t>(bk0, bv0, bk1, bv1, M, bits_of((uint64_t)nvt_b - 1), tmp, &alt_b, cs,
+                                          &info->b.total));
+        }
         const uint32_t *keys = alt_b ? bk1 : bk0;
         ca.vals = alt_b ? bv1 : bv0;
         PK(cudaMemsetAsync(ranges, 0, nvt_b * sizeof(uint2), cs));
-        PK(launch_ranges(keys, M, ranges, cs, &info->b.total));
+        PK(launch_ranges(keys, M, ranges, cs, &info->b.total, tb, (uint32_t)TT));
         ca.order = nullptr;
         if (ordered) {   // the batched call's longest-list-first tile order
             PK(launch_order_keys(ranges, nvt_b, ok0, ov0, cs));

@@ -366,6 +366,8 @@ cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s)
     GAVIS_UA_CASE(1, 0) GAVIS_UA_CASE(1, 1) GAVIS_UA_CASE(1, 2) GAVIS_UA_CASE(1, 3)
     GAVIS_UA_CASE(2, 0) GAVIS_UA_CASE(2, 1) GAVIS_UA_CASE(2, 2) GAVIS_UA_CASE(2, 3)
     GAVIS_UA_CASE(3, 0) GAVIS_UA_CASE(3, 1) GAVIS_UA_CASE(3, 2) GAVIS_UA_CASE(3, 3)
+    GAVIS_UA_CASE(0, 4) GAVIS_UA_CASE(1, 4) GAVIS_UA_CASE(2, 4) GAVIS_UA_CASE(3, 4)
+    GAVIS_UA_CASE(0, 5) GAVIS_UA_CASE(1, 5) GAVIS_UA_CASE(2, 5) GAVIS_UA_CASE(3, 5)
 #undef GAVIS_UA_CASE
     return cudaErrorInvalidValue;
 }
@@ -377,14 +379,12 @@ cudaError_t launch_query(const QueryArgs &a, cudaStream_t s)
     const int blocks = (int)((a.n + 127) / 128);
     const size_t smem = sizeof(gavis_camera) * (size_t)a.nv;
     switch (a.vf_degree) {
-    case 0: if (smem > 48 * 1024) cudaFuncSetAttribute(k_query<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_query<0><<<blocks, 128, smem, s>>>(a); count_launch(); break;
-    case 1: if (smem > 48 * 1024) cudaFuncSetAttribute(k_query<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_query<1><<<blocks, 128, smem, s>>>(a); count_launch(); break;
-    case 2: if (smem > 48 * 1024) cudaFuncSetAttribute(k_query<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_query<2><<<blocks, 128, smem, s>>>(a); count_launch(); break;
-    case 3: if (smem > 48 * 1024) cudaFuncSetAttribute(k_query<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_query<3><<<blocks, 128, smem, s>>>(a); count_launch(); break;
+#define GAVIS_Q_CASE(L)                                                                                      \
+    case L:                                                                                                  \
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k_query<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        k_query<L><<<blocks, 128, smem, s>>>(a); count_launch(); break;
+        GAVIS_Q_CASE(0) GAVIS_Q_CASE(1) GAVIS_Q_CASE(2) GAVIS_Q_CASE(3) GAVIS_Q_CASE(4) GAVIS_Q_CASE(5)
+#undef GAVIS_Q_CASE
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -512,26 +512,38 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
             ids[slot] = g;
         }
         sums[lane] = 0u;   // entries the warp does not reach (it saturated) add nothing
-        __syncwarp();
+        // pad the survivors to a multiple of four with entries that overlap no
+        // pixel (q = +inf), so the loop below takes four at a time and tests
+        // for saturation once per four
         const int nk = __popc(mk);
-        for (int k = 0; k < nk; ++k) {
+        const int nk4 = (nk + 3) & ~3;
+        if (lane >= nk && lane < nk4) {
+            g0s[lane] = make_float4(1e30f, 1e30f, 1.0f, 0.0f);
+            g1s[lane] = make_float2(1.0f, -INFINITY);
+        }
+        __syncwarp();
+        for (int k = 0; k < nk4; k += 4) {
             if (!__any_sync(0xffffffffu, on0 || on1)) break;   // warp-uniform
-            const float4 g0 = g0s[k];
-            const float2 g1 = g1s[k];
-            const float q0 = footprint_q(px, py0, g0.x, g0.y, g0.z, g0.w, g1.x);
-            const float q1 = footprint_q(px, py1, g0.x, g0.y, g0.z, g0.w, g1.x);
-            const bool h0 = on0 && (q0 <= qcut), h1 = on1 && (q1 <= qcut);
-            const uint32_t w0 = h0 ? __float2uint_rn(T0) * kCntMul + 1u : 0u;
-            const uint32_t w1 = h1 ? __float2uint_rn(T1) * kCntMul + 1u : 0u;
-            const uint32_t sum = __reduce_add_sync(0xffffffffu, w0 + w1);
-            if (lane == 0) sums[k] = sum;   // the same in every lane
-            if (h0) {
-                T0 = fmaf(-T0, ex2_approx(fmaf(q0, kNegHalfLog2e, g1.y)), T0);
-                on0 = T0 >= eps;
-            }
-            if (h1) {
-                T1 = fmaf(-T1, ex2_approx(fmaf(q1, kNegHalfLog2e, g1.y)), T1);
-                on1 = T1 >= eps;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 g0 = g0s[k + u];
+                const float2 g1 = g1s[k + u];
+                const float q0 = footprint_q(px, py0, g0.x, g0.y, g0.z, g0.w, g1.x);
+                const float q1 = footprint_q(px, py1, g0.x, g0.y, g0.z, g0.w, g1.x);
+                const bool h0 = on0 && (q0 <= qcut), h1 = on1 && (q1 <= qcut);
+                uint32_t w = 0u;
+                if (h0) w = __float2uint_rn(T0) * kCntMul + 1u;
+                if (h1) w += __float2uint_rn(T1) * kCntMul + 1u;
+                const uint32_t sum = __reduce_add_sync(0xffffffffu, w);
+                if (lane == 0) sums[k + u] = sum;   // the same in every lane
+                if (h0) {
+                    T0 = fmaf(-T0, ex2_approx(fmaf(q0, kNegHalfLog2e, g1.y)), T0);
+                    on0 = T0 >= eps;
+                }
+                if (h1) {
+                    T1 = fmaf(-T1, ex2_approx(fmaf(q1, kNegHalfLog2e, g1.y)), T1);
+                    on1 = T1 >= eps;
+                }
             }
         }
         __syncwarp();
@@ -645,7 +657,7 @@ __global__ void __launch_bounds__(128) k_vf_accumulate(AccumArgs a)
             sh_basis<L>(dx * rn, dy * rn, dz * rn, Y);
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const int l = k >= 9 ? 3 : (k >= 4 ? 2 : (k >= 1 ? 1 : 0));
+                const int l = k >= 25 ? 5 : (k >= 16 ? 4 : (k >= 9 ? 3 : (k >= 4 ? 2 : (k >= 1 ? 1 : 0))));   // k in [l^2, (l+1)^2)
                 acc[k] = fmaf(vis * a.a_l[l], Y[k], acc[k]);
             }
         }
@@ -949,7 +961,7 @@ cudaError_t launch_vf_accumulate(const AccumArgs &a, cudaStream_t s)
             cudaFuncSetAttribute(k_vf_accumulate<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         k_vf_accumulate<L><<<blocks, 128, smem, s>>>(a); count_launch();                                                    \
         break;
-        GAVIS_ACC_CASE(0) GAVIS_ACC_CASE(1) GAVIS_ACC_CASE(2) GAVIS_ACC_CASE(3)
+        GAVIS_ACC_CASE(0) GAVIS_ACC_CASE(1) GAVIS_ACC_CASE(2) GAVIS_ACC_CASE(3) GAVIS_ACC_CASE(4) GAVIS_ACC_CASE(5)
 #undef GAVIS_ACC_CASE
     default: return cudaErrorInvalidValue;
     }

@@ -151,13 +151,18 @@ __global__ void k_popc_words(const uint32_t *words, size_t nwords, uint32_t *cnt
 // are consecutive and so are their records, which the warp's lanes write in
 // order (coalesced): lane j of a round finds its word by a binary search over
 // the warp's prefix popcounts, then its set bit.
-// KeyT = uint64_t writes (v << 32) | depth bits (zb = 32, zmin = 0, vmask all
-// ones).  Records at positions >= cap_R are dropped and set *overflow.
+// Records at positions >= cap_R are dropped and set *overflow.
 template <typename KeyT>
 __global__ void k_emit_vis_words(const uint32_t *words, const uint32_t *woff, uint32_t nv, uint32_t nw, uint32_t n,
                                  const GeoRec *geo, const float *zrec, int zb, uint32_t zmin, uint32_t vmask, KeyT *keyA,
-                                 uint32_t *valA, uint32_t *voff, size_t cap_R, uint32_t *overflow)
+                                 uint32_t *valA, uint32_t *voff, size_t cap_R, uint32_t *overflow,
+                                 const KeyParams *kp)
 {
+    if (kp) {   // key parameters computed on the device (graph replays)
+        zb = kp->zb;
+        zmin = kp->zmin;
+        vmask = kp->vmask;
+    }
     const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = (int)(threadIdx.x & 31u);
     const uint32_t total_words = nv * nw;
@@ -209,6 +214,105 @@ __global__ void k_emit_vis_words(const uint32_t *words, const uint32_t *woff, ui
             keyA[base + j] = ((KeyT)(vk & vmask) << zb) | (KeyT)(__float_as_uint(z) - zmin);
             valA[base + j] = r;
         }
+    }
+}
+
+__global__ void k_key_params(const BatchInfo *info, int nv, KeyParams *kp)
+{
+    if (threadIdx.x != 0) return;
+    const unsigned long long vis = info->visible;
+    const uint32_t zmin = info->zrange[0];
+    const int zb = vis ? depth_bits(zmin, info->zrange[1]) : 0;
+    const int vb = bits_of((uint64_t)nv - 1);
+    const int gb = vb + zb <= 32 ? vb : 32 - zb;
+    KeyParams k;
+    k.zmin = vis ? zmin : 0u;
+    k.zb = zb;
+    k.gsz = 1 << gb;
+    k.vmask = (uint32_t)(k.gsz - 1);
+    *kp = k;
+}
+
+// One block of 1024 threads: the segments' starts and their first blocks in
+// shared memory, then every table entry by a binary search over those.
+__global__ void __launch_bounds__(1024) k_segment_blocks(const uint32_t *off, int nv, const KeyParams *kp, int gsz,
+                                                         uint32_t cap, RsBlock *blk, uint32_t nblk_max)
+{
+    __shared__ uint32_t s_seg[1025];   // segment starts (clamped to cap); s_seg[nseg] = end of the last
+    __shared__ uint32_t s_bst[1025];   // first table block of each segment; s_bst[nseg] = live blocks
+    __shared__ uint32_t s_warp[32];
+    const int g = kp ? kp->gsz : gsz;
+    const int nseg = (nv + g - 1) / g;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int sg = t; sg <= nseg; sg += blockDim.x) {
+        const int v = sg * g < nv ? sg * g : nv;
+        const uint32_t o = off[v];
+        s_seg[sg] = o < cap ? o : cap;
+    }
+    __syncthreads();
+    uint32_t nb = 0;
+    if (t < nseg) {
+        const uint32_t a = s_seg[t], b = s_seg[t + 1];
+        nb = b > a ? (b - a + (uint32_t)kRadixTile - 1) / (uint32_t)kRadixTile : 0u;
+    }
+    uint32_t x = nb;   // inclusive scan over the block (nseg <= 1024)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t incl = x + (warp ? s_warp[warp - 1] : 0u);
+    if (t < nseg) s_bst[t] = incl - nb;
+    if (t == (nseg > 0 ? nseg - 1 : 0)) s_bst[nseg] = nseg > 0 ? incl : 0u;
+    __syncthreads();
+    const uint32_t live = s_bst[nseg];
+    for (uint32_t k = (uint32_t)t; k < nblk_max; k += blockDim.x) {
+        RsBlock b;
+        if (k < live) {
+            int lo = 0, hi = nseg - 1;   // the last segment whose first block is <= k
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_bst[mid] <= k) lo = mid;
+                else hi = mid - 1;
+            }
+            const uint32_t j = k - s_bst[lo];
+            const uint32_t st = s_seg[lo] + j * (uint32_t)kRadixTile;
+            const uint32_t en = s_seg[lo + 1];
+            b.start = st;
+            b.end = st + (uint32_t)kRadixTile < en ? st + (uint32_t)kRadixTile : en;
+            b.h0 = 256u * s_bst[lo] + j;
+            b.hs = s_bst[lo + 1] - s_bst[lo];
+        } else {   // empty: its zero histogram follows the live ones
+            b.start = 0u;
+            b.end = 0u;
+            b.h0 = 256u * k;
+            b.hs = 1u;
+        }
+        blk[k] = b;
+    }
+}
+
+__global__ void k_entry_offsets_dev(const uint32_t *off_sorted, const uint32_t *voff, int nv, const BatchInfo *info,
+                                    unsigned long long cap_R, unsigned long long cap_M, uint32_t *eoff)
+{
+    const unsigned long long nrec = info->visible < cap_R ? info->visible : cap_R;
+    const unsigned long long M = info->total < cap_M ? info->total : cap_M;
+    for (int v = threadIdx.x; v <= nv; v += blockDim.x) {
+        const uint32_t r = voff[v];
+        unsigned long long e = v < nv && (unsigned long long)r < nrec ? (unsigned long long)off_sorted[r] : M;
+        eoff[v] = (uint32_t)(e < M ? e : M);
     }
 }
 
@@ -461,22 +565,48 @@ cudaError_t emit_vis_words(const uint32_t *words, const uint32_t *woff, int nv, 
     const uint32_t nw = (uint32_t)((n + 31) / 32);
     const size_t total = (size_t)nv * nw;
     k_emit_vis_words<uint32_t><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-        words, woff, (uint32_t)nv, nw, (uint32_t)n, geo, zrec, zb, zmin, vmask, keyA, valA, voff, ~(size_t)0, nullptr);
+        words, woff, (uint32_t)nv, nw, (uint32_t)n, geo, zrec, zb, zmin, vmask, keyA, valA, voff, ~(size_t)0, nullptr,
+        nullptr);
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t emit_vis_words64(const uint32_t *words, const uint32_t *woff, int nv, int64_t n, const GeoRec *geo,
-                             uint64_t *keyA, uint32_t *valA, size_t cap_R, uint32_t *overflow, cudaStream_t s)
+cudaError_t launch_key_params(const BatchInfo *info, int nv, KeyParams *kp, cudaStream_t s)
+{
+    k_key_params<<<1, 32, 0, s>>>(info, nv, kp); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t emit_vis_words_dev(const uint32_t *words, const uint32_t *woff, int nv, int64_t n, const GeoRec *geo,
+                               const KeyParams *kp, uint32_t *keyA, uint32_t *valA, uint32_t *voff, size_t cap_R,
+                               uint32_t *overflow, cudaStream_t s)
 {
     if (nv <= 0 || n <= 0) return cudaSuccess;
     if ((size_t)nv * (size_t)n >= ((size_t)1 << 32)) return cudaErrorInvalidValue;
     const uint32_t nw = (uint32_t)((n + 31) / 32);
     const size_t total = (size_t)nv * nw;
-    k_emit_vis_words<uint64_t><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-        words, woff, (uint32_t)nv, nw, (uint32_t)n, geo, nullptr, 32, 0u, 0xffffffffu, keyA, valA, nullptr, cap_R,
-        overflow);
+    k_emit_vis_words<uint32_t><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        words, woff, (uint32_t)nv, nw, (uint32_t)n, geo, nullptr, 0, 0u, 0u, keyA, valA, voff, cap_R, overflow, kp);
     count_launch();
+    return cudaGetLastError();
+}
+
+size_t radix_segment_blocks_max(size_t cap, int nv) { return (cap + kRsTile - 1) / kRsTile + (size_t)(nv > 0 ? nv : 1); }
+
+cudaError_t launch_segment_blocks(const uint32_t *off, int nv, const KeyParams *kp, int gsz, size_t cap,
+                                  RsBlock *blk, size_t nblk_max, cudaStream_t s)
+{
+    if (nv < 1 || nv > 1024 || (!kp && gsz < 1) || nblk_max >= ((size_t)1 << 24) || cap >= ((size_t)1 << 32))
+        return cudaErrorInvalidValue;
+    k_segment_blocks<<<1, 1024, 0, s>>>(off, nv, kp, gsz, (uint32_t)cap, blk, (uint32_t)nblk_max); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_entry_offsets_dev(const uint32_t *off_sorted, const uint32_t *voff, int nv, const BatchInfo *info,
+                                     size_t cap_R, size_t cap_M, uint32_t *eoff, cudaStream_t s)
+{
+    if (nv <= 0) return cudaSuccess;
+    k_entry_offsets_dev<<<1, 256, 0, s>>>(off_sorted, voff, nv, info, cap_R, cap_M, eoff); count_launch();
     return cudaGetLastError();
 }
 
@@ -554,7 +684,8 @@ size_t radix_segment_blocks(const uint64_t *seg, int nseg, RsBlock *tbl)
 
 template <typename KeyT>
 cudaError_t radix_sort_segments(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint32_t *vals_alt, const RsBlock *blk,
-                                size_t nblk, int end_bit, void *tmp, bool *result_in_alt, cudaStream_t s)
+                                size_t nblk, int end_bit, void *tmp, bool *result_in_alt, cudaStream_t s,
+                                bool prepared)
 {
     *result_in_alt = false;
     if (nblk == 0 || end_bit <= 0) return cudaSuccess;
@@ -564,8 +695,10 @@ cudaError_t radix_sort_segments(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint
     uint32_t *offs = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(tmp) + a);
     void *stmp = reinterpret_cast<char *>(tmp) + 2 * a;
     constexpr size_t smem = rs_smem<KeyT>();
-    cudaFuncSetAttribute(k_radix_scatter<KeyT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_radix_scatter<KeyT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!prepared) {
+        cudaFuncSetAttribute(k_radix_scatter<KeyT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_radix_scatter<KeyT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
     KeyT *kin = keys, *kout = keys_alt;
     uint32_t *vin = vals, *vout = vals_alt;
     bool alt = false;
@@ -593,7 +726,7 @@ cudaError_t radix_sort_segments(KeyT *keys, uint32_t *vals, KeyT *keys_alt, uint
 }
 
 template cudaError_t radix_sort_segments<uint32_t>(uint32_t *, uint32_t *, uint32_t *, uint32_t *, const RsBlock *,
-                                                   size_t, int, void *, bool *, cudaStream_t);
+                                                   size_t, int, void *, bool *, cudaStream_t, bool);
 
 template cudaError_t radix_sort_pairs<uint64_t>(uint64_t *, uint32_t *, uint64_t *, uint32_t *, size_t, int, void *,
                                                 bool *, cudaStream_t, const unsigned long long *);

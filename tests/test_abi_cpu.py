@@ -48,17 +48,18 @@ def test_params_default_are_the_paper_defaults(lib):
 def test_host_vmf_coefficients_match_oracle(lib):
     import oracle
     import paper_2605_30342_gb300 as gv
-    for kappa in (0.0, 0.1, 0.5, 1.0, 3.0, 10.0):
-        a = gv.Context.vmf_coeffs(3, kappa)
-        b = oracle.vmf_coeffs(3, kappa)
-        for l in range(4):
-            assert a[l] == pytest.approx(b[l], rel=1e-9, abs=1e-15)
+    for L in (3, 5):
+        for kappa in (0.0, 0.1, 0.3, 0.5, 1.0, 3.0, 4.5, 10.0):
+            a = gv.Context.vmf_coeffs(L, kappa)
+            b = oracle.vmf_coeffs(L, kappa)
+            for l in range(L + 1):
+                assert a[l] == pytest.approx(b[l], rel=1e-9, abs=1e-15), (L, kappa, l)
     assert gv.Context.vmf_coeffs(0, 0.0)[0] == pytest.approx(4 * math.pi)
 
 
 def test_bad_arguments_rejected_without_gpu(lib):
     import paper_2605_30342_gb300 as gv
-    assert lib.gavis_vmf_coeffs(4, 1.0, (C.c_double * 5)()) == gv.ERR_ARG
+    assert lib.gavis_vmf_coeffs(6, 1.0, (C.c_double * 7)()) == gv.ERR_ARG
     assert lib.gavis_vmf_coeffs(2, -1.0, (C.c_double * 3)()) == gv.ERR_ARG
     assert lib.gavis_params_default(None) == gv.ERR_ARG
 

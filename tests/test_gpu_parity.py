@@ -167,7 +167,8 @@ def test_bins_bit_exact_screen_edges(ctx, gv, tile):
 # --------------------------------------------------------------------------- VF query
 
 @pytest.mark.parametrize("L,P,dtype", [(2, 8, torch.float32), (3, 100, torch.float32), (3, 200, torch.float16),
-                                       (1, 1, torch.float32), (0, 0, torch.float32)])
+                                       (1, 1, torch.float32), (0, 0, torch.float32), (4, 50, torch.float32),
+                                       (5, 30, torch.float32), (5, 200, torch.float16)])
 def test_vf_query_parity(ctx, gv, L, P, dtype):
     c = case("tiny")
     sc = c["scene"]
@@ -270,6 +271,37 @@ def test_vf_build_parity(ctx, gv, name, dtype):
     err = (np.abs(g - ref) - rad - rel * (np.abs(ref) + rad)) / P
     n_rad = int((rad.max(1) > 0).sum())
     assert err.max() <= TOL, (err.max(), f"{n_rad} of {sc.n} Gaussians have a nonzero radius")
+
+
+@pytest.mark.parametrize("L", [4, 5])
+@pytest.mark.parametrize("kappa", [0.0, 0.3, 3.0, 10.0])
+def test_vf_build_high_degree(ctx, gv, L, kappa):
+    """Field degrees 4 and 5 over the concentrations of the paper's ablation
+    (Tab. ablation: L in 1..5, kappa in 0, 0.1, 0.3, 3, 10): every
+    coefficient within 1e-4 |P| of the oracle beyond its radius; then the
+    queried V and the scores of candidate views from the oracle's field."""
+    c = case("tiny")
+    sc, train = c["scene"], c["train"]
+    gs = gpu_scene(gv, sc)
+    p = gv.Params(vf_degree=L, kappa=kappa)
+    vf = ctx.vf_build(gs, train, degree=L, params=p)
+    P = len(train)
+    prm = oracle.params(kappa=kappa)
+    ref, _, _, rad = oracle.vf_build(train, sc, L, prm, want_rad=True)
+    err = ((np.abs(vf.coeffs.double().cpu().numpy() - ref) - rad) / P).max()
+    assert err <= TOL, err
+    g32 = ref.astype(np.float32)
+    vfo = gv.VisibilityField(torch.as_tensor(g32).cuda(), L, P, kappa)
+    cand = c["cand"][:4]
+    V = ctx.vf_query(gs, vfo, cand, params=p).cpu().numpy()
+    for v, cam in enumerate(cand):
+        Vr, _ = oracle.vf_query(g32.astype(np.float64), L, P, cam, sc.means)
+        assert np.abs(V[v] - Vr).max() <= TOL
+    out = ctx.score_views(gs, vfo, cand, params=p)
+    r = oracle.score_views(sc, g32.astype(np.float64), L, P, cand, prm)
+    e, _ = compare_views(out["unc"].cpu().numpy(), out["rgb"].cpu().numpy(), r)
+    assert e <= TOL
+    assert score_excess(out["score"].cpu().numpy(), r).max() <= TOL
 
 
 def test_vf_build_batched_equals_plain(ctx, gv):
