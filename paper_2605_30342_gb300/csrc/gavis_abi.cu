@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "gavis_internal.cuh"
+#include "sh_basis.cuh"
 
 using namespace gavis;
 
@@ -46,6 +47,9 @@ struct gavis_ctx {
     size_t budget = 0;
     size_t used = 0;
     std::string err;
+    // the workspace comes from this context's own stream-ordered pool, so that
+    // growing a buffer never waits for the device (nor for other contexts)
+    cudaMemPool_t mem = nullptr;
     Buf rec, vis, keys, small, gamma, cams, aug, tune;
     BatchInfo *h_info = nullptr;             // pinned
     uint32_t *h_voff = nullptr;              // pinned, per-view record offsets of a batch
@@ -109,8 +113,12 @@ int fail(gavis_ctx *c, int code, const char *fmt, ...)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// grow-only device buffer within the context budget
-int ensure(gavis_ctx *ctx, Buf &b, size_t bytes)
+// Grow-only device buffer within the context budget, in stream order on s:
+// the old buffer is released once the work queued on s before this point
+// has run, and the new one is ready for the work queued after it (every call
+// on a context runs after the previous one, see CallOrder).  No device-wide
+// synchronisation.
+int ensure(gavis_ctx *ctx, Buf &b, size_t bytes, cudaStream_t s)
 {
     bytes = align256(bytes ? bytes : 256);
     if (b.cap >= bytes) return GAVIS_OK;
@@ -119,16 +127,16 @@ int ensure(gavis_ctx *ctx, Buf &b, size_t bytes)
         return fail(ctx, GAVIS_ERR_BUDGET, "workspace of %zu bytes exceeds the budget (%zu used of %zu)", bytes,
                     other, ctx->budget);
     if (b.p) {
-        CK(cudaDeviceSynchronize());
-        CK(cudaFree(b.p));
+        CK(cudaFreeAsync(b.p, s));
         b.p = nullptr;
         ctx->used -= b.cap;
         b.cap = 0;
     }
-    cudaError_t e = cudaMalloc(&b.p, bytes);
+    cudaError_t e = cudaMallocFromPoolAsync(&b.p, bytes, ctx->mem, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(ctx, GAVIS_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        b.p = nullptr;
+        return fail(ctx, GAVIS_ERR_OOM, "cudaMallocFromPoolAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
     }
     b.cap = bytes;
     ctx->used += bytes;
@@ -236,7 +244,8 @@ RasterConsts raster_consts(const gavis_params *p)
 // series (kappa < 1).
 void bessel_i(int L, double x, double *out)
 {
-    if (x < 1.0) {
+    // power series where the upward recurrence would lose digits (x < L)
+    if (x < 1.0 || x < (double)L) {
         for (int l = 0; l <= L; ++l) {
             double df = 1.0;
             for (int k = 3; k <= 2 * l + 1; k += 2) df *= (double)k;
@@ -431,17 +440,19 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
 
     const size_t nwords = (size_t)nv * (size_t)((n + 31) / 32);
     RecLayout RL = rec_layout(nullptr, nvn, mode == MODE_SCORE, nwords);
-    if ((rc = ensure(ctx, ctx->rec, RL.bytes)) != GAVIS_OK) return rc;
+    if ((rc = ensure(ctx, ctx->rec, RL.bytes, s)) != GAVIS_OK) return rc;
     RL = rec_layout(ctx->rec.p, nvn, mode == MODE_SCORE, nwords);
     SmallLayout SL = small_layout(nullptr, nvt, (size_t)nv, p->tile);
-    if ((rc = ensure(ctx, ctx->small, SL.bytes)) != GAVIS_OK) return rc;
+    if ((rc = ensure(ctx, ctx->small, SL.bytes, s)) != GAVIS_OK) return rc;
     SL = small_layout(ctx->small.p, nvt, (size_t)nv, p->tile);
     if (ctx->h_voff_cap < 2 * (size_t)nv + 2) {
         if (ctx->h_voff) cudaFreeHost(ctx->h_voff);
         ctx->h_voff = nullptr;
         ctx->h_voff_cap = 0;
-        CK(cudaMallocHost(&ctx->h_voff, (2 * (size_t)nv + 2) * sizeof(uint32_t)));
-        ctx->h_voff_cap = 2 * (size_t)nv + 2;
+        // sized once for the largest batch (a batch has at most kMaxBatchViews views)
+        const size_t cap = 2 * (size_t)(nv > kMaxBatchViews ? nv : kMaxBatchViews) + 2;
+        CK(cudaMallocHost(&ctx->h_voff, cap * sizeof(uint32_t)));
+        ctx->h_voff_cap = cap;
     }
     uint32_t *h_eoff = ctx->h_voff + nv + 1;
 
@@ -497,7 +508,7 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     const int nseg_b = tb < 0 ? 1 : (nv + (1 << gbb) - 1) >> gbb;
     const size_t nseg = (size_t)(nseg_a > nseg_b ? nseg_a : nseg_b);
     KeyLayout KL = key_layout(nullptr, (size_t)nrec, (size_t)M, nseg);
-    if ((rc = ensure(ctx, ctx->keys, KL.bytes)) != GAVIS_OK) return rc;
+    if ((rc = ensure(ctx, ctx->keys, KL.bytes, s)) != GAVIS_OK) return rc;
     KL = key_layout(ctx->keys.p, (size_t)nrec, (size_t)M, nseg);
     // block table of a segmented sort over the segments [seg[s], seg[s+1]),
     // staged through pinned memory (the previous table's copy has finished:
@@ -508,8 +519,12 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
             if (ctx->h_blk) cudaFreeHost(ctx->h_blk);
             ctx->h_blk = nullptr;
             ctx->h_blk_cap = 0;
-            CK(cudaMallocHost(&ctx->h_blk, nblk * sizeof(RsBlock)));
-            ctx->h_blk_cap = nblk;
+            // geometric growth: the rare regrowth (a pinned free waits for the
+            // device) stays out of the steady state
+            size_t cap = ctx->h_blk_cap ? 2 * ctx->h_blk_cap : ((size_t)1 << 16);
+            while (cap < nblk) cap *= 2;
+            CK(cudaMallocHost(&ctx->h_blk, cap * sizeof(RsBlock)));
+            ctx->h_blk_cap = cap;
         }
         radix_segment_blocks(seg.data(), (int)seg.size() - 1, ctx->h_blk);
         if (nblk) CK(cudaMemcpyAsync(dst, ctx->h_blk, nblk * sizeof(RsBlock), cudaMemcpyHostToDevice, s));
@@ -634,7 +649,7 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
         Stage st(ctx, GAVIS_STAGE_REDUCE, s);
         CK(launch_view_reduce(SL.tile_sums, nv, G.TT * bpt, 1.0f / ((float)G.W * (float)G.H), out.score + v0, s));
     } else {
-        if ((rc = ensure(ctx, ctx->vis, nvn * 12)) != GAVIS_OK) return rc;
+        if ((rc = ensure(ctx, ctx->vis, nvn * 12, s)) != GAVIS_OK) return rc;
         ca.sumT = reinterpret_cast<unsigned long long *>(ctx->vis.p);
         ca.cnt = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(ctx->vis.p) + nvn * 8);
         ca.pairs = ctx->prof_on ? ctx->d_pairs + 1 : nullptr;
@@ -648,7 +663,7 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
 
 int upload_cams(gavis_ctx *ctx, const gavis_camera *cams, int n, cudaStream_t s)
 {
-    int rc = ensure(ctx, ctx->cams, sizeof(gavis_camera) * (size_t)(n > 0 ? n : 1));
+    int rc = ensure(ctx, ctx->cams, sizeof(gavis_camera) * (size_t)(n > 0 ? n : 1), s);
     if (rc != GAVIS_OK) return rc;
     if (n > 0)
         CK(cudaMemcpyAsync(ctx->cams.p, cams, sizeof(gavis_camera) * (size_t)n, cudaMemcpyHostToDevice, s));
@@ -688,7 +703,7 @@ int check_vf(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf)
     if (!vf) return fail(ctx, GAVIS_ERR_ARG, "vf is NULL");
     if (vf->n != gs->n) return fail(ctx, GAVIS_ERR_ARG, "vf->n (%lld) != gaussians n (%lld)", (long long)vf->n,
                                     (long long)gs->n);
-    if (vf->degree < 0 || vf->degree > 3) return fail(ctx, GAVIS_ERR_ARG, "vf degree must be 0..3");
+    if (vf->degree < 0 || vf->degree > kMaxVfDegree) return fail(ctx, GAVIS_ERR_ARG, "vf degree must be 0..5");
     if (vf->dtype < 0 || vf->dtype > 2) return fail(ctx, GAVIS_ERR_ARG, "bad vf dtype");
     if (vf->n_train_views < 0) return fail(ctx, GAVIS_ERR_ARG, "negative n_train_views");
     if (vf->n > 0 && !vf->coeffs) return fail(ctx, GAVIS_ERR_ARG, "vf coeffs is NULL");
@@ -724,11 +739,25 @@ int gavis_ctx_create(gavis_ctx **out, int device, size_t hbm_budget_bytes)
         return GAVIS_ERR_CUDA;
     }
     ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : fr / 10 * 6;
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&ctx->mem, &props) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return GAVIS_ERR_CUDA;
+    }
+    // keep released blocks in the pool (up to the budget) for the next growth
+    uint64_t keep = (uint64_t)ctx->budget;
+    cudaMemPoolSetAttribute(ctx->mem, cudaMemPoolAttrReleaseThreshold, &keep);
     if (cudaMallocHost(&ctx->h_info, sizeof(BatchInfo)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_best, sizeof(int32_t)) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->tail, cudaEventDisableTiming) != cudaSuccess) {
         if (ctx->h_info) cudaFreeHost(ctx->h_info);
         if (ctx->h_best) cudaFreeHost(ctx->h_best);
+        cudaMemPoolDestroy(ctx->mem);
         delete ctx;
         return GAVIS_ERR_CUDA;
     }
@@ -743,6 +772,7 @@ void gavis_ctx_destroy(gavis_ctx *ctx)
     cudaDeviceSynchronize();
     for (Buf *b : {&ctx->rec, &ctx->vis, &ctx->keys, &ctx->small, &ctx->gamma, &ctx->cams, &ctx->aug, &ctx->tune})
         if (b->p) cudaFree(b->p);
+    if (ctx->mem) cudaMemPoolDestroy(ctx->mem);
     if (ctx->h_info) cudaFreeHost(ctx->h_info);
     if (ctx->h_voff) cudaFreeHost(ctx->h_voff);
     if (ctx->h_blk) cudaFreeHost(ctx->h_blk);
@@ -828,8 +858,8 @@ int gavis_params_default(gavis_params *p)
 
 int gavis_vmf_coeffs(int L, double kappa, double *a)
 {
-    if (!a || L < 0 || L > 3 || !(kappa >= 0.0)) return GAVIS_ERR_ARG;
-    double i[4] = {0, 0, 0, 0};
+    if (!a || L < 0 || L > kMaxVfDegree || !(kappa >= 0.0)) return GAVIS_ERR_ARG;
+    double i[kMaxVfDegree + 1] = {};
     if (kappa == 0.0) {
         i[0] = 1.0;
     } else {
@@ -849,7 +879,7 @@ int gavis_vf_build(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_camera
         return rc;
     if (!out) return fail(ctx, GAVIS_ERR_ARG, "out is NULL");
     if (out->n != gs->n) return fail(ctx, GAVIS_ERR_ARG, "out->n != gaussians n");
-    if (out->degree < 0 || out->degree > 3) return fail(ctx, GAVIS_ERR_ARG, "out degree must be 0..3");
+    if (out->degree < 0 || out->degree > kMaxVfDegree) return fail(ctx, GAVIS_ERR_ARG, "out degree must be 0..5");
     if (out->dtype < 0 || out->dtype > 2) return fail(ctx, GAVIS_ERR_ARG, "bad out dtype");
     if (out->n > 0 && !out->coeffs) return fail(ctx, GAVIS_ERR_ARG, "out coeffs is NULL");
     if (accumulate && out->n_train_views < 0) return fail(ctx, GAVIS_ERR_ARG, "negative n_train_views");
@@ -859,11 +889,11 @@ int gavis_vf_build(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_camera
     const int L = out->degree;
     const size_t K = (size_t)(L + 1) * (L + 1);
     const size_t count = (size_t)gs->n * K;
-    if ((rc = ensure(ctx, ctx->gamma, count * sizeof(float))) != GAVIS_OK) return rc;
+    if ((rc = ensure(ctx, ctx->gamma, count * sizeof(float), s)) != GAVIS_OK) return rc;
     float *g32 = reinterpret_cast<float *>(ctx->gamma.p);
     if (accumulate) CK(launch_vf_load(out->coeffs, out->dtype, count, g32, s));
     else CK(cudaMemsetAsync(g32, 0, count * sizeof(float), s));
-    double ad[4] = {0, 0, 0, 0};
+    double ad[kMaxVfDegree + 1] = {};
     gavis_vmf_coeffs(L, (double)p->kappa, ad);
     ChainOut co;
     auto after = [&](int v0, int nv) -> int {
@@ -875,7 +905,7 @@ int gavis_vf_build(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_camera
         const size_t nvn = (size_t)nv * (size_t)gs->n;
         aa.sumT = reinterpret_cast<const unsigned long long *>(ctx->vis.p);
         aa.cnt = reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(ctx->vis.p) + nvn * 8);
-        for (int l = 0; l < 4; ++l) aa.a_l[l] = (float)ad[l];
+        for (int l = 0; l <= kMaxVfDegree; ++l) aa.a_l[l] = (float)ad[l];
         aa.L = L;
         aa.gamma32 = g32;
         Stage st(ctx, GAVIS_STAGE_VF_ACCUM, s);
@@ -937,7 +967,7 @@ int gavis_render_views(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf
     }
     if (best_dev || best_host) {
         SmallLayout SL = small_layout(nullptr, 1);
-        if ((rc = ensure(ctx, ctx->small, SL.bytes)) != GAVIS_OK) return rc;
+        if ((rc = ensure(ctx, ctx->small, SL.bytes, s)) != GAVIS_OK) return rc;
         SL = small_layout(ctx->small.p, 1);
         int32_t *dbest = best_dev ? best_dev : SL.best;
         Stage st(ctx, GAVIS_STAGE_REDUCE, s);
@@ -1043,7 +1073,7 @@ int gavis_vf_density_control(gavis_ctx *ctx, const gavis_gaussians *gs, const fl
                  o_o = take((size_t)na * 4), o_p = take((size_t)n_virt * 4), o_k = take((size_t)n_virt * 4),
                  o_q = take((size_t)n_virt * 4), o_t = take(scan_tmp_bytes((size_t)n_virt) + 64),
                  o_n = take(sizeof(unsigned long long));
-    if ((rc = ensure(ctx, ctx->aug, off)) != GAVIS_OK) return rc;
+    if ((rc = ensure(ctx, ctx->aug, off, s)) != GAVIS_OK) return rc;
     char *base = reinterpret_cast<char *>(ctx->aug.p);
     float *am = reinterpret_cast<float *>(base + o_m), *as = reinterpret_cast<float *>(base + o_s);
     float *ar = reinterpret_cast<float *>(base + o_r), *ao = reinterpret_cast<float *>(base + o_o);
@@ -1204,7 +1234,7 @@ int gavis_autotune(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf
     const size_t K = (size_t)(L + 1) * (L + 1);
     const size_t bytes = mode == 0 ? align256((size_t)n_cams * 4) + (size_t)n_cams * plane * 4
                                    : (size_t)gs->n * K * 4;
-    if ((rc = ensure(ctx, ctx->tune, bytes)) != GAVIS_OK) return rc;
+    if ((rc = ensure(ctx, ctx->tune, bytes, s)) != GAVIS_OK) return rc;
     float *score = reinterpret_cast<float *>(ctx->tune.p);
     float *unc = reinterpret_cast<float *>(reinterpret_cast<char *>(ctx->tune.p) + align256((size_t)n_cams * 4));
     gavis_vf tv;

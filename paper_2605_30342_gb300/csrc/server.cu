@@ -186,11 +186,12 @@ void worker_main(gavis_server *s, size_t ws_budget)
         }
         int rc = rc0;
         if (rc == GAVIS_OK && want_unc && unc_cap < (size_t)nb * plane) {
-            if (unc_stage) cudaFree(unc_stage);
+            // stream-ordered on the worker's stream: other workers' streams never wait for it
+            if (unc_stage) cudaFreeAsync(unc_stage, stream);
             unc_stage = nullptr;
             unc_cap = 0;
             const size_t want = (size_t)s->max_batch * plane;
-            if (cudaMalloc(&unc_stage, want * sizeof(float)) == cudaSuccess) {
+            if (cudaMallocAsync(reinterpret_cast<void **>(&unc_stage), want * sizeof(float), stream) == cudaSuccess) {
                 unc_cap = want;
             } else {
                 unc_stage = nullptr;
@@ -255,7 +256,8 @@ void worker_main(gavis_server *s, size_t ws_budget)
     }
     if (ctx) gavis_ctx_destroy(ctx);
     if (score_stage) cudaFree(score_stage);
-    if (unc_stage) cudaFree(unc_stage);
+    if (unc_stage) cudaFreeAsync(unc_stage, stream);
+    if (stream) cudaStreamSynchronize(stream);
     if (d_best) cudaFree(d_best);
     if (stream) cudaStreamDestroy(stream);
 }
