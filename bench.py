@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--n-cand", type=int, default=None)
     ap.add_argument("--views-per-batch", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0, help="tile edge 8/16/32; 0 = autotune per path")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-views", type=int, default=16,
                     help="cpu_baseline: training and candidate views of the oracle sample (about 10 s of CPU work)")
@@ -71,6 +71,8 @@ def parse():
                     help="precision_err: sampled training and candidate views (about 30 s of CPU work)")
     ap.add_argument("--serving", action="store_true", help="serving workload: Poisson requests over 4 resident scenes")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean request rate (req/s)")
+    ap.add_argument("--rates", default="", help="serving: comma-separated request rates, one line each")
+    ap.add_argument("--serving-budget-gb", type=float, default=120.0, help="serving: HBM admission budget (GB)")
     ap.add_argument("--requests", type=int, default=300, help="serving: number of requests")
     ap.add_argument("--workers", type=int, default=4, help="serving: worker streams")
     ap.add_argument("--batch-views", type=int, default=128, help="serving: views per batch")
@@ -463,18 +465,30 @@ def run_gavis(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier(device_ids=[local])
+    # events between the parts of each step (device time of the copies and of the step)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(e2e_steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_host0 = time.perf_counter()
     e0.record(stream)
-    for _ in range(e2e_steps):
+    for k_ in range(e2e_steps):
+        ev[k_][0].record(stream)
         for k in host:
             devt[k].copy_(host[k], non_blocking=True)
+        ev[k_][1].record(stream)
         step()
+        ev[k_][2].record(stream)
         score_h.copy_(outs["score"], non_blocking=True)
         best_h.copy_(outs["best_dev"], non_blocking=True)
+        ev[k_][3].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
+    t_host = (time.perf_counter() - t_host0) * 1e3 / e2e_steps
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dev)
     e2e_value = job_throughput(n_cand, world, e2e_ms)
+    e2e_parts = {"h2d_ms": sum(e[0].elapsed_time(e[1]) for e in ev) / e2e_steps,
+                 "step_ms": sum(e[1].elapsed_time(e[2]) for e in ev) / e2e_steps,
+                 "d2h_ms": sum(e[2].elapsed_time(e[3]) for e in ev) / e2e_steps,
+                 "host_wall_ms": t_host}
 
     # ---------------- roofline of the dominant kernel ----------------
     st = prof["stages"]
@@ -533,9 +547,11 @@ def run_gavis(args):
             "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": config_json(c, args, {"autotuned": tuned} if tuned else None),
+            "config": config_json(c, args, dict({"autotuned": tuned} if tuned else {}, scoring_path=(
+                "gavis_score_views (the chain sized on the host); the same chain captured as one CUDA graph is "
+                "timed in graph_scoring"))),
             "e2e": {"value": e2e_value, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "steps": e2e_steps, "parts": e2e_parts},
             "gpu_launches": int(launches),
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -651,70 +667,84 @@ def traffic_for(kernel, tile):
 
 
 def run_serving(args):
-    """Serving workload: 4 resident scenes (100k, 500k, 1M, 2M Gaussians, one
-    room each as in the room workload, fields from 50 training views), Poisson
-    arrivals, 8-512 candidate views per request (log-uniform) at one of four
-    resolutions, f16 coefficients, f32 compositing."""
+    """Serving workload: 4 resident scenes of 100k, 500k, 1M and 2M Gaussians
+    built as in the room workload (one room, fields from 100 training views at
+    800x800 along a walk), Poisson arrivals, 8-512 candidate views per request
+    (log-uniform) at one of four resolutions, f16 coefficients, f32
+    compositing, a 120 GB admission budget.  One line per request rate."""
     import numpy as np
     import torch
     import scenegen as sg
     import __graft_entry__ as ge
     ge.build()
     import paper_2605_30342_gb300 as gv
-    dev = torch.device("cuda", 0)
     ctx = gv.Context(0)
     scenes = []
+    t_build = time.perf_counter()
     for k, n in enumerate((100_000, 500_000, 1_000_000, 2_000_000)):
         sc = sg.multi_room_scene(n, 1, 1, seed=k, sh_degree=3)
         gs = gv.Gaussians.from_numpy(sc, sh_dtype=torch.float16)
-        train = sg.walk_cameras(50, sc, 640, 480, seed=k + 1, x_frac=(0.0, 0.5))
+        train = sg.walk_cameras(100, sc, 800, 800, seed=k + 1, x_frac=(0.0, 0.5))
         vf = ctx.vf_build(gs, train, degree=3, dtype=torch.float16)
         scenes.append((sc, gs, vf))
     torch.cuda.synchronize()
-    rng = np.random.default_rng(7)
-    res = [(160, 120), (320, 240), (640, 480), (800, 600)]
-    reqs = []
-    t = 0.0
-    for r in range(args.requests):
-        t += rng.exponential(1.0 / args.rate)
-        sid = int(rng.integers(4))
-        nv = int(round(np.exp(rng.uniform(np.log(8), np.log(512)))))
-        W, H = res[int(rng.integers(4))]
-        cams = sg.se2_cameras(nv, scenes[sid][0], W, H, seed=1000 + r)
-        reqs.append((t, sid, cams))
-    srv = gv.Server(0, n_workers=args.workers, max_views_per_batch=args.batch_views)
-    ids = [srv.add_scene(gs, vf) for _, gs, vf in scenes]
-    prm = gv.Params(vf_degree=3)
-    sampler = ClockSampler(0)
-    sampler.start()
-    t0 = time.perf_counter()
-    rids = []
-    for (ta, sid, cams) in reqs:
-        now = time.perf_counter() - t0
-        if ta > now:
-            time.sleep(ta - now)
-        rids.append(srv.submit(ids[sid], cams, params=prm))
-    out = [srv.wait(r) for r in rids]
-    wall = time.perf_counter() - t0
-    clocks = sampler.stop()
-    lat = [o["latency_ms"] for o in out]
-    views = sum(len(c) for _, _, c in reqs)
-    st = srv.stats()
-    srv.close()
-    line = {
-        "metric": "serving: views/s and p50/p99 request latency (4 resident scenes 100k-2M Gaussians)",
-        "value": views / wall, "unit": "views/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": "serving: Poisson arrivals over 4 resident room scenes (100k, 500k, 1M, 2M)",
-                   "rate_req_s": args.rate, "requests": args.requests, "views": views,
-                   "views_per_request": "log-uniform 8..512", "resolutions": res, "coeff_storage": "f16",
-                   "workers": args.workers, "batch_views": args.batch_views},
-        "latency_ms": {"p50": percentile(lat, 50), "p99": percentile(lat, 99), "max": max(lat)},
-        "offered_views_per_s": views / reqs[-1][0],
-        "wall_s": wall, "server": st, "clocks": clocks,
-    }
-    print(json.dumps(line), flush=True)
+    t_build = time.perf_counter() - t_build
     ctx.close()
+    res = [(160, 120), (320, 240), (640, 480), (800, 600)]
+    budget = int(args.serving_budget_gb * 1e9)
+    rates = [float(r) for r in args.rates.split(",")] if args.rates else [args.rate]
+    for rate in rates:
+        rng = np.random.default_rng(7)
+        reqs = []
+        t = 0.0
+        for r in range(args.requests):
+            t += rng.exponential(1.0 / rate)
+            sid = int(rng.integers(4))
+            nv = int(round(np.exp(rng.uniform(np.log(8), np.log(512)))))
+            W, H = res[int(rng.integers(4))]
+            cams = sg.se2_cameras(nv, scenes[sid][0], W, H, seed=1000 + r)
+            reqs.append((t, sid, cams))
+        srv = gv.Server(0, budget_bytes=budget, n_workers=args.workers, max_views_per_batch=args.batch_views)
+        ids = [srv.add_scene(gs, vf) for _, gs, vf in scenes]
+        prm = gv.Params(vf_degree=3)
+        # warm-up: one request per (scene, resolution), untimed
+        for sid in range(4):
+            for (W, H) in res:
+                srv.wait(srv.submit(ids[sid], sg.se2_cameras(8, scenes[sid][0], W, H, seed=99), params=prm))
+        st0 = srv.stats()
+        sampler = ClockSampler(0)
+        sampler.start()
+        t0 = time.perf_counter()
+        rids = []
+        for (ta, sid, cams) in reqs:
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            rids.append(srv.submit(ids[sid], cams, params=prm))
+        out = [srv.wait(r) for r in rids]
+        wall = time.perf_counter() - t0
+        clocks = sampler.stop()
+        lat = [o["latency_ms"] for o in out]
+        views = sum(len(c) for _, _, c in reqs)
+        st = srv.stats()
+        st["views_scored"] -= st0["views_scored"]
+        st["batches"] -= st0["batches"]
+        srv.close()
+        offered = views / reqs[-1][0]
+        line = {
+            "metric": "serving: views/s and p50/p99 request latency (4 resident scenes 100k-2M Gaussians)",
+            "value": views / wall, "unit": "views/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "serving: Poisson arrivals over 4 resident room scenes (100k, 500k, 1M, 2M "
+                                   "Gaussians; fields from 100 training views at 800x800)",
+                       "rate_req_s": rate, "requests": args.requests, "views": views,
+                       "views_per_request": "log-uniform 8..512", "resolutions": res, "coeff_storage": "f16",
+                       "workers": args.workers, "batch_views": args.batch_views, "budget_bytes": budget},
+            "latency_ms": {"p50": percentile(lat, 50), "p99": percentile(lat, 99), "max": max(lat)},
+            "offered_views_per_s": offered, "achieved_over_offered": (views / wall) / offered,
+            "wall_s": wall, "scene_build_s": t_build, "server": st, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
 
 
 def main():

@@ -390,6 +390,12 @@ int gavis_server_submit(gavis_server *s, int scene_id, const gavis_camera *cams,
  * (request kept) if it is not finished in time. */
 int gavis_server_wait(gavis_server *s, int64_t request_id, int timeout_ms, int32_t *best, double *latency_ms);
 
+/* Pause (paused = 1) or resume (0) the workers: while paused they finish the
+ * batch in flight and start no new one; submissions and admission go on, and
+ * gavis_server_wait keeps its timeout (for draining a device, and for
+ * testing the timeout path). */
+int gavis_server_pause(gavis_server *s, int paused);
+
 /* Counters: views scored, batches run, the most requests one batch served,
  * the peak of the admitted workspace estimates and the budget. */
 int gavis_server_stats(gavis_server *s, int64_t *views_scored, int64_t *batches, int64_t *max_requests_in_batch,

@@ -74,7 +74,7 @@ EXPORTS = ["gavis_ctx_create", "gavis_ctx_destroy", "gavis_last_error", "gavis_p
            "gavis_server_create", "gavis_server_destroy", "gavis_server_last_error", "gavis_server_add_scene",
            "gavis_server_submit", "gavis_server_wait", "gavis_server_stats", "gavis_autotune",
            "gavis_plan_create", "gavis_plan_launch", "gavis_plan_overflowed", "gavis_plan_kernels",
-           "gavis_plan_destroy", "gavis_render_views", "gavis_augment"]
+           "gavis_plan_destroy", "gavis_render_views", "gavis_augment", "gavis_server_pause"]
 
 STAGES = ["project", "scan", "emit", "sort", "ranges", "composite_ua", "composite_vis", "reduce", "vf_accum"]
 
@@ -127,6 +127,7 @@ def load(path: str | None = None):
         lib.gavis_server_submit.argtypes = [vp, i32, C.POINTER(gavis_camera), i32, C.POINTER(gavis_params), vp, vp,
                                             C.POINTER(C.c_int64)]
         lib.gavis_server_wait.argtypes = [vp, i64, i32, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+        lib.gavis_server_pause.argtypes = [vp, i32]
         lib.gavis_server_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                            C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
         lib.gavis_autotune.argtypes = [vp, C.POINTER(gavis_gaussians), C.POINTER(gavis_vf), C.POINTER(gavis_camera), i32,
@@ -551,6 +552,10 @@ class Server:
                                                   C.byref(rid)))
         self._keep[int(rid.value)] = (score, unc)
         return int(rid.value)
+
+    def pause(self, paused: bool = True):
+        """Stop (or restart) the workers from taking new batches."""
+        self._check(self._lib.gavis_server_pause(self._h, int(bool(paused))))
 
     def wait(self, request_id: int, timeout_ms: int = 600000):
         """dict(score, unc, best, latency_ms); raises GavisError (code

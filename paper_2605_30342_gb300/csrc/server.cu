@@ -69,6 +69,7 @@ struct gavis_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     bool stop = false;
+    bool paused = false;   // workers take no new batch while set
     std::vector<Scene> scenes;
     std::deque<std::shared_ptr<Request>> waiting;            // not yet admitted, arrival order
     std::vector<std::shared_ptr<Request>> active;            // admitted, arrival order
@@ -88,13 +89,22 @@ int sfail(gavis_server *s, int code, const char *msg)
     return code;
 }
 
-// workspace estimate of one request's views on one scene (records, keys,
-// outputs of the batch staging), used for admission
-size_t estimate_bytes(const Scene &sc, const Request &r)
+// Workspace estimate of one admitted request on one scene: the views of it
+// that can be in flight at once (at most one batch), each with the projected
+// records of every Gaussian, stage-A keys for every Gaussian (an upper
+// bound), stage-B tile entries for a quarter of the Gaussians visible at four
+// tiles each (the measured scale of the room workloads at tile 16; the true
+// count depends on the poses), and the staging of its uncertainty map.  An
+// estimate: what the workers allocate is bounded by their contexts' budgets
+// (budget / workers each), and a batch whose keys do not fit one context is
+// halved.
+size_t estimate_bytes(const Scene &sc, const Request &r, int max_batch)
 {
-    const size_t n = (size_t)sc.gs.n, v = r.cams.size();
+    const size_t n = (size_t)sc.gs.n;
+    const size_t v = r.cams.size() < (size_t)max_batch ? r.cams.size() : (size_t)max_batch;
     const size_t plane = (size_t)r.cams[0].W * r.cams[0].H;
-    return v * (n * (sizeof(gavis::GeoRec) + sizeof(gavis::UaRec) + 16) + n * 2 * 24 + plane * 4 + 64);
+    return v * (n * (sizeof(gavis::GeoRec) + sizeof(gavis::UaRec) + 16) + n * 2 * 24 + n / 4 * 4 * 16 + plane * 4 +
+                64);
 }
 
 // admit waiting requests in arrival order while they fit the budget (a
@@ -151,6 +161,7 @@ void worker_main(gavis_server *s, size_t ws_budget)
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv_work.wait(lk, [&] {
                 if (s->stop) return true;
+                if (s->paused) return false;
                 for (auto &r : s->active)
                     if (r->next < (int)r->cams.size()) return true;
                 return false;
@@ -302,6 +313,17 @@ void gavis_server_destroy(gavis_server *s)
 
 const char *gavis_server_last_error(const gavis_server *s) { return s ? s->err.c_str() : "no server"; }
 
+int gavis_server_pause(gavis_server *s, int paused)
+{
+    if (!s) return GAVIS_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->paused = paused != 0;
+    }
+    s->cv_work.notify_all();
+    return GAVIS_OK;
+}
+
 int gavis_server_add_scene(gavis_server *s, const gavis_gaussians *gs, const gavis_vf *vf, int *scene_id)
 {
     if (!s || !gs || !vf || !scene_id) return sfail(s, GAVIS_ERR_ARG, "NULL argument");
@@ -331,7 +353,7 @@ int gavis_server_submit(gavis_server *s, int scene_id, const gavis_camera *cams,
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (scene_id < 0 || scene_id >= (int)s->scenes.size()) return sfail(s, GAVIS_ERR_ARG, "unknown scene");
-        r->reserve = estimate_bytes(s->scenes[scene_id], *r);
+        r->reserve = estimate_bytes(s->scenes[scene_id], *r, s->max_batch);
         r->id = s->next_id++;
         s->all[r->id] = r;
         s->waiting.push_back(r);

@@ -77,10 +77,10 @@ def test_alone_equals_mix(gv, scenes):
 def test_admission_respects_budget(gv, scenes):
     ctx, sc = scenes
     c0, gs0, vf0 = sc[0]
-    # the server's per-request workspace estimate; a budget between one and two
-    # requests' worth admits them one at a time (and still holds one worker's
-    # workspace)
-    one = 6 * (2000 * (32 + 32 + 16) + 2000 * 2 * 24 + 128 * 128 * 4 + 64)
+    # the server's per-request workspace estimate (6 views, all in one batch
+    # of at most 8); a budget between one and two requests' worth admits them
+    # one at a time (and still holds one worker's workspace)
+    one = 6 * (2000 * (32 + 32 + 16) + 2000 * 2 * 24 + 2000 // 4 * 4 * 16 + 128 * 128 * 4 + 64)
     srv = gv.Server(0, budget_bytes=int(1.5 * one), n_workers=1, max_views_per_batch=8)
     sid = srv.add_scene(gs0, vf0)
     rids = [srv.submit(sid, cams_for(c0, 6, (128, 128), s), params=gv.Params(vf_degree=2)) for s in range(5)]
@@ -105,10 +105,18 @@ def test_errors_are_status_codes(gv, scenes):
     with pytest.raises(gv.GavisError) as e:
         srv.wait(12345, timeout_ms=0)
     assert e.value.code == gv.ERR_ARG
-    rid = srv.submit(sid, cams_for(c0, 64, (128, 128), 1), params=gv.Params(vf_degree=2))
-    try:
-        srv.wait(rid, timeout_ms=0)                  # usually still running
-    except gv.GavisError as ex:
-        assert ex.code == gv.ERR_TIMEOUT
-        srv.wait(rid)
+    # a request held behind paused workers cannot finish: a zero timeout
+    # returns GAVIS_ERR_TIMEOUT, and after resuming the request completes
+    srv.pause(True)
+    rid = srv.submit(sid, cams_for(c0, 8, (128, 128), 1), params=gv.Params(vf_degree=2))
+    with pytest.raises(gv.GavisError) as e:
+        srv.wait(rid, timeout_ms=0)
+    assert e.value.code == gv.ERR_TIMEOUT
+    with pytest.raises(gv.GavisError) as e:
+        srv.wait(rid, timeout_ms=50)
+    assert e.value.code == gv.ERR_TIMEOUT
+    assert srv.stats()["views_scored"] == 0
+    srv.pause(False)
+    r = srv.wait(rid)
+    assert 0 <= r["best"] < 8 and srv.stats()["views_scored"] == 8
     srv.close()
