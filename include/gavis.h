@@ -419,8 +419,10 @@ enum {
     GAVIS_STAGE_COUNT = 9
 };
 
-/* on != 0 starts recording stage events on later calls; every call resets
- * the accumulators.  Recording adds two events per stage and batch. */
+/* on = 1 starts recording stage events on later calls (two events per stage
+ * and batch); on = 2 also counts the composited pixel-Gaussian pairs on the
+ * device (counters in the composite kernels: slower); 0 stops.  Every call
+ * resets the accumulators. */
 int gavis_prof_enable(gavis_ctx *ctx, int on);
 
 /* Synchronises the device, then returns per stage the summed device time

@@ -402,8 +402,10 @@ class Context:
                 VisibilityField(coeffs, vf.degree, vf.n_train_views, vf.kappa))
 
     # -------------------------------------------------------------- instrumentation
-    def prof_enable(self, on: bool = True):
-        self._check(self._lib.gavis_prof_enable(self._h, int(bool(on))))
+    def prof_enable(self, on: bool = True, pairs: bool = False):
+        """Stage timing on later calls; with pairs, also count the composited
+        pixel-Gaussian pairs (device counters: slower)."""
+        self._check(self._lib.gavis_prof_enable(self._h, (2 if pairs else 1) if on else 0))
 
     def prof_read(self):
         """dict(stage -> (ms, launches)), total kernel launches, pairs (ua, vis)."""

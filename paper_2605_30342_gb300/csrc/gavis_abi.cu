@@ -58,7 +58,8 @@ struct gavis_ctx {
     size_t h_blk_cap = 0;
     int32_t *h_best = nullptr;               // pinned
     // instrumentation
-    bool prof_on = false;
+    bool prof_on = false;     // stage events
+    bool prof_pairs = false;  // and the composited pairs (device counters in the composites)
     std::vector<ProfRec> pending;
     std::vector<cudaEvent_t> pool;
     double prof_ms[GAVIS_STAGE_COUNT] = {};
@@ -639,7 +640,7 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     if (mode == MODE_SCORE) {
         ca.rgb = out.rgb; ca.unc = out.unc; ca.depth = out.depth;
         ca.per_entry_kc = gs->sh_var != nullptr;
-        ca.pair_counts = ctx->prof_on ? SL.pair_counts : nullptr;
+        ca.pair_counts = ctx->prof_pairs ? SL.pair_counts : nullptr;
         {
             Stage st(ctx, GAVIS_STAGE_COMPOSITE_UA, s);
             CK(launch_composite_ua(ca, s));
@@ -652,7 +653,7 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
         if ((rc = ensure(ctx, ctx->vis, nvn * 12, s)) != GAVIS_OK) return rc;
         ca.sumT = reinterpret_cast<unsigned long long *>(ctx->vis.p);
         ca.cnt = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(ctx->vis.p) + nvn * 8);
-        ca.pairs = ctx->prof_on ? ctx->d_pairs + 1 : nullptr;
+        ca.pairs = ctx->prof_pairs ? ctx->d_pairs + 1 : nullptr;
         Stage st(ctx, GAVIS_STAGE_COMPOSITE_VIS, s);
         CK(cudaMemsetAsync(ctx->vis.p, 0, nvn * 12, s));
         CK(launch_composite_vis(ca, s));
@@ -806,6 +807,7 @@ int gavis_prof_enable(gavis_ctx *ctx, int on)
     ctx->prof_keys = 0;
     ctx->prof_visible = 0;
     ctx->prof_on = on != 0;
+    ctx->prof_pairs = on >= 2;
     return GAVIS_OK;
 }
 
