@@ -5,9 +5,13 @@
 // (centre, scale, rotation, opacity, colour SH, visibility-field SH) and loops
 // over every view of the batch, whose cameras sit in shared memory.  The
 // Gaussian record is therefore read from HBM once per batch rather than once
-// per view.  Views go in groups of 32, the work of a group in rounds over the
-// lanes that still have a view to project (or to colour), so that lanes whose
-// Gaussian is culled in one view do the work of another.
+// per view.  Views go in groups of 32.  In the geometry-only launches (field
+// construction) the warp deals its (view, Gaussian) projections out to its
+// lanes, 32 per round, so that no lane idles while another has views left;
+// in the launches with appearance records each lane projects (and then
+// colours) its own Gaussian's views in rounds over the lanes with a view
+// left, because its 64 colour and field coefficients stay in its registers
+// (dealing there spilled and measured no faster).
 //
 // Image-space geometry is evaluated with explicit round-to-nearest intrinsics
 // (no contraction) in a fixed operation order, so that depth keys, conics and
@@ -140,15 +144,24 @@ __device__ __forceinline__ Proj project_one(const gavis_camera &cam, float x, fl
     return o;
 }
 
+constexpr bool kDealWithAppearance = false;   // see the file header
+
 // VAR: per-Gaussian colour covariance from coefficient variances
 template <int LC, int LV, bool UA, bool VAR>
 __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
 {
     extern __shared__ gavis_camera s_cams[];
+    __shared__ uint32_t s_vis[4][32];   // per warp: visibility bits of each lane's Gaussian in the group's views
     for (int i = threadIdx.x; i < a.nv; i += blockDim.x) s_cams[i] = a.cams[i];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    s_vis[wib][lane] = 0u;
     __syncthreads();
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= a.n) return;
+    // every lane of a warp stays to the end (the warp redistributes its
+    // projections over its lanes); a lane past the last Gaussian has none in front
+    const int64_t g_raw = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = g_raw < a.n;
+    const int64_t g = live ? g_raw : a.n - 1;   // loads stay in bounds; nothing is written for it
+    const int64_t gw0 = g_raw - lane;           // the warp's first Gaussian
     const float mx = a.means[3 * g], my = a.means[3 * g + 1], mz = a.means[3 * g + 2];
     const float sc[3] = {a.scales[3 * g], a.scales[3 * g + 1], a.scales[3 * g + 2]};
     const float4 q = reinterpret_cast<const float4 *>(a.rots)[g];
@@ -172,63 +185,148 @@ __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
     }
     const float P = (float)a.n_train;
     uint32_t zlo = 0xffffffffu, zhi = 0u, nvis = 0u, ntiles = 0u;
-    const unsigned am0 = __activemask();   // the warp's lanes with g < n; each runs every view iteration
+    constexpr unsigned am0 = 0xffffffffu;   // every lane of the warp runs every view iteration
+    // deal the projections out over the warp's lanes (geometry-only launches;
+    // the appearance launches keep 64 coefficient registers per lane live)
+    constexpr bool kDeal = !UA || kDealWithAppearance;
 
     // Views in groups of VG.  The camera depth of each view of the group
-    // first; then the projection of the views with the Gaussian in front of
-    // the near plane, and then (with appearance records) the appearance of
-    // the views where it has tiles, both in rounds in which every lane with a
-    // pending view takes its next one, so that a round runs with every such
-    // lane instead of the lanes of one view (the appearance takes about 14
-    // rounds instead of 32 at a quarter of the records visible).
+    // first.  Then the projections: the warp's (view, Gaussian) pairs with
+    // the Gaussian in front of the near plane are dealt out to its lanes view
+    // by view, 32 per round (a lane takes the owner's centre and covariance
+    // by shuffle), so every lane works in every round however unevenly the
+    // warp's Gaussians face the cameras, and consecutive lanes write
+    // consecutive Gaussians of a view.  Then (with appearance records) the
+    // appearance of the views where the Gaussian has tiles, in rounds in
+    // which every lane with a pending view takes its next one (the appearance
+    // needs the Gaussian's colour and field coefficients, which stay in its
+    // own lane's registers).
     constexpr int VG = 32;
     const size_t nw = (size_t)((a.n + 31) >> 5);
     for (int v0 = 0; v0 < a.nv; v0 += VG) {
         const int nu = a.nv - v0 < VG ? a.nv - v0 : VG;
         // views of the group in front of the camera's near plane (the rest are culled)
         uint32_t front = 0u;
-        for (int u = 0; u < nu; ++u)
-            if (cam_depth(s_cams[v0 + u], mx, my, mz) > s_cams[v0 + u].znear) front |= 1u << u;
-        if (!a.vis_words) {
+        if (live)
+            for (int u = 0; u < nu; ++u)
+                if (cam_depth(s_cams[v0 + u], mx, my, mz) > s_cams[v0 + u].znear) front |= 1u << u;
+        if (!a.vis_words && live) {
             for (int u = 0; u < nu; ++u)
                 if (!((front >> u) & 1u)) a.counts[(size_t)(v0 + u) * (size_t)a.n + (size_t)g] = 0u;
         }
-        uint32_t vis = 0u;    // bit u: the Gaussian has tiles in view v0 + u
+        uint32_t vis = 0u;    // bit u: the lane's Gaussian has tiles in view v0 + u
         uint32_t pend = 0u;   // the same, appearance pending
-        while (__any_sync(am0, front != 0u)) {
-            if (front) {
-                const int u = __ffs(front) - 1;
-                front &= front - 1u;
-                const int v = v0 + u;
-                const Proj p = project_one(s_cams[v], mx, my, mz, S, a.q_cut, rb, a.TW, a.TH);
-                const size_t r = (size_t)v * (size_t)a.n + (size_t)g;
-                if (p.status != 1) {
-                    if (!a.vis_words) a.counts[r] = 0u;
-                } else {
-                    vis |= 1u << u;
-                    const uint32_t nt = (uint32_t)((p.x1 - p.x0 + 1) * (p.y1 - p.y0 + 1));
-                    a.counts[r] = nt;
-                    ntiles += nt;
-                    a.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.x1 << 16), (uint32_t)p.y0 | ((uint32_t)p.y1 << 16));
-                    zlo = min(zlo, __float_as_uint(p.z));
-                    zhi = max(zhi, __float_as_uint(p.z));
-                    ++nvis;
-                    GeoRec gr;
-                    gr.a = make_float4(p.u, p.v, p.A, fa(p.B, p.B));
-                    // footprint half-extents, rounded up to half precision (conservative)
-                    const uint32_t ext = (uint32_t)__half_as_ushort(__float2half_ru(p.ex)) |
-                                         ((uint32_t)__half_as_ushort(__float2half_ru(p.ey)) << 16);
-                    gr.b = make_float4(p.C, lop, p.z, __uint_as_float(ext));
-                    a.geo[r] = gr;
-                    if (a.zrec) a.zrec[r] = p.z;
+        if (kDeal) {
+            // lane u (< nu) holds the lanes whose Gaussian is in front of view v0 + u
+            uint32_t own = 0u;
+            for (int u = 0; u < nu; ++u) {
+                const unsigned b = __ballot_sync(am0, (front >> u) & 1u);
+                if (lane == u) own = b;
+            }
+            const uint32_t cv = (uint32_t)__popc(own);
+            uint32_t iv = cv;   // pairs up to and including view u (scan over the lanes)
+    #pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(am0, iv, o);
+                if (lane >= o) iv += y;
+            }
+            const uint32_t total = __shfl_sync(am0, iv, 31);
+            const uint32_t ev = iv - cv;   // pairs before view u
+            for (uint32_t base = 0; base < total; base += 32) {
+                const uint32_t j = base + (uint32_t)lane;
+                int u = 0;   // the last view whose pairs start at or before j
+    #pragma unroll
+                for (int st = 16; st > 0; st >>= 1) {
+                    const uint32_t e = __shfl_sync(am0, ev, u + st);
+                    if (e <= j) u += st;
+                }
+                uint32_t ow = __shfl_sync(am0, own, u);
+                uint32_t m = j - __shfl_sync(am0, ev, u);   // rank of the pair among view u's
+                int o = 0;   // its owner lane: the m-th set bit of ow (halving by the set bits' counts)
+    #pragma unroll
+                for (int h = 16; h > 0; h >>= 1) {
+                    const uint32_t c = (uint32_t)__popc(ow & ((1u << h) - 1u));
+                    if (m >= c) {
+                        m -= c;
+                        o += h;
+                        ow >>= h;
+                    }
+                }
+                o &= 31;
+                const float gx = __shfl_sync(am0, mx, o), gy = __shfl_sync(am0, my, o), gz = __shfl_sync(am0, mz, o);
+                Sigma3 So;
+                So.s00 = __shfl_sync(am0, S.s00, o); So.s01 = __shfl_sync(am0, S.s01, o);
+                So.s02 = __shfl_sync(am0, S.s02, o); So.s11 = __shfl_sync(am0, S.s11, o);
+                So.s12 = __shfl_sync(am0, S.s12, o); So.s22 = __shfl_sync(am0, S.s22, o);
+                const float glop = __shfl_sync(am0, lop, o);
+                if (j < total) {
+                    const int v = v0 + u;
+                    const Proj p = project_one(s_cams[v], gx, gy, gz, So, a.q_cut, rb, a.TW, a.TH);
+                    const size_t r = (size_t)v * (size_t)a.n + (size_t)(gw0 + o);
+                    if (p.status != 1) {
+                        if (!a.vis_words) a.counts[r] = 0u;
+                    } else {
+                        atomicOr(&s_vis[wib][o], 1u << u);
+                        const uint32_t nt = (uint32_t)((p.x1 - p.x0 + 1) * (p.y1 - p.y0 + 1));
+                        a.counts[r] = nt;
+                        ntiles += nt;
+                        a.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.x1 << 16), (uint32_t)p.y0 | ((uint32_t)p.y1 << 16));
+                        zlo = min(zlo, __float_as_uint(p.z));
+                        zhi = max(zhi, __float_as_uint(p.z));
+                        ++nvis;
+                        GeoRec gr;
+                        gr.a = make_float4(p.u, p.v, p.A, fa(p.B, p.B));
+                        // footprint half-extents, rounded up to half precision (conservative)
+                        const uint32_t ext = (uint32_t)__half_as_ushort(__float2half_ru(p.ex)) |
+                                             ((uint32_t)__half_as_ushort(__float2half_ru(p.ey)) << 16);
+                        gr.b = make_float4(p.C, glop, p.z, __uint_as_float(ext));
+                        a.geo[r] = gr;
+                        if (a.zrec) a.zrec[r] = p.z;
+                    }
+                }
+            }
+            __syncwarp();
+            vis = s_vis[wib][lane];
+            __syncwarp();
+            s_vis[wib][lane] = 0u;   // for the next group
+            __syncwarp();
+        } else {
+            // per-lane rounds: every lane with a pending view takes its next one
+            while (__any_sync(am0, front != 0u)) {
+                if (front) {
+                    const int u = __ffs(front) - 1;
+                    front &= front - 1u;
+                    const int v = v0 + u;
+                    const Proj p = project_one(s_cams[v], mx, my, mz, S, a.q_cut, rb, a.TW, a.TH);
+                    const size_t r = (size_t)v * (size_t)a.n + (size_t)g;
+                    if (p.status != 1) {
+                        if (!a.vis_words) a.counts[r] = 0u;
+                    } else {
+                        vis |= 1u << u;
+                        const uint32_t nt = (uint32_t)((p.x1 - p.x0 + 1) * (p.y1 - p.y0 + 1));
+                        a.counts[r] = nt;
+                        ntiles += nt;
+                        a.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.x1 << 16),
+                                               (uint32_t)p.y0 | ((uint32_t)p.y1 << 16));
+                        zlo = min(zlo, __float_as_uint(p.z));
+                        zhi = max(zhi, __float_as_uint(p.z));
+                        ++nvis;
+                        GeoRec gr;
+                        gr.a = make_float4(p.u, p.v, p.A, fa(p.B, p.B));
+                        const uint32_t ext = (uint32_t)__half_as_ushort(__float2half_ru(p.ex)) |
+                                             ((uint32_t)__half_as_ushort(__float2half_ru(p.ey)) << 16);
+                        gr.b = make_float4(p.C, lop, p.z, __uint_as_float(ext));
+                        a.geo[r] = gr;
+                        if (a.zrec) a.zrec[r] = p.z;
+                    }
                 }
             }
         }
         if (a.vis_words) {   // one visibility word per warp (32 consecutive Gaussians) and view
             for (int u = 0; u < nu; ++u) {
                 const unsigned bal = __ballot_sync(am0, (vis >> u) & 1u);
-                if ((threadIdx.x & 31) == (unsigned)(__ffs(am0) - 1))
-                    a.vis_words[(size_t)(v0 + u) * nw + (size_t)(g >> 5)] = bal;
+                if (lane == 0 && gw0 < a.n)   // a warp wholly past the last Gaussian owns no word
+                    a.vis_words[(size_t)(v0 + u) * nw + (size_t)(gw0 >> 5)] = bal;
             }
         }
         if (UA) pend = vis;
