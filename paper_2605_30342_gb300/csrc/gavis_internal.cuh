@@ -180,10 +180,11 @@ struct KeyParams {
 };
 cudaError_t launch_key_params(const BatchInfo *info, int nv, KeyParams *kp, cudaStream_t s);
 // emit_vis_words with the key parameters read from kp (device); records at
-// positions >= cap_R are dropped and set *overflow.
+// positions >= cap_R are dropped and set *overflow; depths from zrec when
+// given (dense, 4 B a record), else from the GeoRec.
 cudaError_t emit_vis_words_dev(const uint32_t *words, const uint32_t *woff, int nv, int64_t n, const GeoRec *geo,
-                               const KeyParams *kp, uint32_t *keyA, uint32_t *valA, uint32_t *voff, size_t cap_R,
-                               uint32_t *overflow, cudaStream_t s);
+                               const float *zrec, const KeyParams *kp, uint32_t *keyA, uint32_t *valA, uint32_t *voff,
+                               size_t cap_R, uint32_t *overflow, cudaStream_t s);
 // The block table of a segmented sort built on the device (nv <= 1024):
 // segment s covers [off[min(s g, nv)], off[min((s + 1) g, nv)]) clamped to
 // cap, for groups of g views (g = kp->gsz when kp is given, else gsz),

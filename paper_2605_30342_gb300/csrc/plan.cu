@@ -138,6 +138,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     const size_t o_geo = take(nvn * sizeof(GeoRec)), o_ua = take(nvn * sizeof(UaRec)), o_rect = take(nvn * 8);
     const size_t nwords = (size_t)B * (size_t)((n + 31) / 32);
     const size_t o_cnt = take(nvn * 4), o_words = take(nwords * 4), o_woff = take(nwords * 4);
+    const size_t o_zrec = take(nvn * 4);   // dense depth copy of the visible records (stage-A keys)
     const size_t o_scan = take(scan_tmp_bytes(nwords) + 64);
     const size_t o_ak0 = take(R * 4), o_ak1 = take(R * 4), o_av0 = take(R * 4), o_av1 = take(R * 4);
     const size_t o_acnt = take(R * 4), o_aoff = take(R * 4);
@@ -176,6 +177,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     uint2 *rect = reinterpret_cast<uint2 *>(b + o_rect);
     uint32_t *counts = reinterpret_cast<uint32_t *>(b + o_cnt);
     uint32_t *vis_words = reinterpret_cast<uint32_t *>(b + o_words), *woff = reinterpret_cast<uint32_t *>(b + o_woff);
+    float *zrec = reinterpret_cast<float *>(b + o_zrec);
     uint32_t *ak0 = reinterpret_cast<uint32_t *>(b + o_ak0), *ak1 = reinterpret_cast<uint32_t *>(b + o_ak1);
     RsBlock *blk_a = reinterpret_cast<RsBlock *>(b + o_blka), *blk_b = reinterpret_cast<RsBlock *>(b + o_blkb);
     KeyParams *kp = reinterpret_cast<KeyParams *>(b + o_kp);
@@ -207,6 +209,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     pa.n = n;
     pa.geo = geo; pa.ua = ua; pa.rect = rect; pa.counts = counts;
     pa.vis_words = vis_words;
+    pa.zrec = zrec;
     CompositeArgs ca;
     std::memset(&ca, 0, sizeof(ca));
     ca.ranges = ranges; ca.geo = geo; ca.ua = ua;
@@ -243,7 +246,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
         // stage A: 32-bit (view in group, depth) keys, groups of views sorted
         // as segments (one sequence of four 8-bit passes)
         PK(launch_key_params(&info->b, nv, kp, cs));
-        PK(emit_vis_words_dev(vis_words, woff, nv, n, geo, kp, ak0, av0, voff, R, &info->records_over, cs));
+        PK(emit_vis_words_dev(vis_words, woff, nv, n, geo, zrec, kp, ak0, av0, voff, R, &info->records_over, cs));
         PK(launch_segment_blocks(voff, nv, kp, 0, R, blk_a, nblk_a, cs));
         bool alt_a = false, alt_b = false;
         PK(radix_sort_segments<uint32_t>(ak0, av0, ak1, av1, blk_a, nblk_a, 32, tmp, &alt_a, cs, true));

@@ -578,15 +578,15 @@ cudaError_t launch_key_params(const BatchInfo *info, int nv, KeyParams *kp, cuda
 }
 
 cudaError_t emit_vis_words_dev(const uint32_t *words, const uint32_t *woff, int nv, int64_t n, const GeoRec *geo,
-                               const KeyParams *kp, uint32_t *keyA, uint32_t *valA, uint32_t *voff, size_t cap_R,
-                               uint32_t *overflow, cudaStream_t s)
+                               const float *zrec, const KeyParams *kp, uint32_t *keyA, uint32_t *valA, uint32_t *voff,
+                               size_t cap_R, uint32_t *overflow, cudaStream_t s)
 {
     if (nv <= 0 || n <= 0) return cudaSuccess;
     if ((size_t)nv * (size_t)n >= ((size_t)1 << 32)) return cudaErrorInvalidValue;
     const uint32_t nw = (uint32_t)((n + 31) / 32);
     const size_t total = (size_t)nv * nw;
     k_emit_vis_words<uint32_t><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-        words, woff, (uint32_t)nv, nw, (uint32_t)n, geo, nullptr, 0, 0u, 0u, keyA, valA, voff, cap_R, overflow, kp);
+        words, woff, (uint32_t)nv, nw, (uint32_t)n, geo, zrec, 0, 0u, 0u, keyA, valA, voff, cap_R, overflow, kp);
     count_launch();
     return cudaGetLastError();
 }

@@ -209,3 +209,41 @@ def test_selected_view_is_the_argmax(batched):
     assert e.value.code == gv.ERR_ARG
     with pytest.raises(gv.GavisError):
         ctx.score_views(gs, vf, c["cand"][:1], params=gv.Params(tile=12))
+
+
+# --------------------------------------------------------------------------- room workload (f32 path)
+
+@pytest.fixture(scope="module")
+def room():
+    gv, c = _build(2)
+    ctx = gv.Context(0)
+    gs = gv.Gaussians.from_numpy(c["scene"])
+    yield gv, ctx, c, gs
+    ctx.close()
+
+
+def test_room_full_size_f32(room):
+    """The room workload at full size (200k Gaussians, 100 training and 64
+    candidate views at 800x800, f32 coefficients, tile 16): the field of 4
+    sampled training views within 1e-4 |P| of the oracle beyond its radius;
+    all 64 candidates scored from the oracle's field, 4 sampled views within
+    1e-4 of the oracle's ranges pixel by pixel and in their scores."""
+    gv, ctx, c, gs = room
+    sc = c["scene"]
+    p = gv.Params(vf_degree=3, tile=16)
+    train = [c["train"][i] for i in _spread(len(c["train"]), 4)]
+    P = len(train)
+    g_o, _, _, rad = oracle.vf_build(train, sc, 3, want_rad=True)
+    g_gpu = ctx.vf_build(gs, train, degree=3, params=p).coeffs.double().cpu().numpy()
+    assert ((np.abs(g_gpu - g_o) - rad) / P).max() <= TOL
+    g32 = g_o.astype(np.float32)
+    vf = gv.VisibilityField(torch.as_tensor(g32).cuda(), 3, P, 1.0)
+    out = ctx.score_views(gs, vf, c["cand"], params=p)
+    unc, rgb, score = out["unc"].cpu().numpy(), out["rgb"].cpu().numpy(), out["score"].cpu().numpy()
+    for v in _spread(len(c["cand"]), 4):
+        ref = oracle.score_views(sc, g32.astype(np.float64), 3, P, [c["cand"][v]])
+        err, n_band = compare_views(unc[v:v + 1], rgb[v:v + 1], ref)
+        assert err <= TOL, (v, err, n_band)
+        assert score_excess(score[v:v + 1], ref).max() <= TOL
+        assert ref["used"][0].mean() > 2
+    assert out["best"] == int(np.argmax(score))
