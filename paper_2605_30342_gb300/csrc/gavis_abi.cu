@@ -280,12 +280,11 @@ Geometry geometry_of(const gavis_camera *cams, int tile)
 }
 
 
-// per-batch workspace: records, tile counts, flag-scan partials
+// per-batch workspace: records, tile rectangles, flag-scan partials
 struct RecLayout {
     GeoRec *geo;
     UaRec *ua;
     uint2 *rect;
-    uint32_t *counts;
     uint32_t *vis_words, *woff;   // [nv][ceil(n/32)] visibility bits and their record offsets
     float *zrec;                  // camera depth per visible record (what stage A's keys are made of)
     void *scan_tmp;
@@ -301,7 +300,6 @@ RecLayout rec_layout(void *base, size_t nvn, bool ua, size_t nwords)
     L.geo = reinterpret_cast<GeoRec *>(take(nvn * sizeof(GeoRec)));
     L.ua = ua ? reinterpret_cast<UaRec *>(take(nvn * sizeof(UaRec))) : nullptr;
     L.rect = reinterpret_cast<uint2 *>(take(nvn * sizeof(uint2)));
-    L.counts = reinterpret_cast<uint32_t *>(take(nvn * sizeof(uint32_t)));
     L.vis_words = reinterpret_cast<uint32_t *>(take(nwords * sizeof(uint32_t)));
     L.woff = reinterpret_cast<uint32_t *>(take(nwords * sizeof(uint32_t)));
     L.zrec = reinterpret_cast<float *>(take(nvn * sizeof(float)));
@@ -311,8 +309,9 @@ RecLayout rec_layout(void *base, size_t nvn, bool ua, size_t nwords)
 }
 
 // per-batch workspace of the two-level binning: stage A over the nrec visible
-// records (64-bit keys, record indices, their tile counts and offsets), stage
-// B over the M tile entries (32-bit tile ids, Gaussian indices)
+// records (32-bit keys in 8-byte slots, which hold the records' tile
+// rectangles once the keys are sorted; record indices, their tile counts and
+// offsets), stage B over the M tile entries (tile ids, Gaussian indices)
 struct KeyLayout {
     uint64_t *a_k0, *a_k1;
     uint32_t *a_v0, *a_v1, *a_cnt, *a_off;
@@ -469,7 +468,7 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     pa.q_cut = p->q_cut; pa.beta = p->beta; pa.o0 = p->o0;
     pa.tile = p->tile; pa.TW = G.TW; pa.TH = G.TH;
     pa.cams = d_cams + v0; pa.nv = nv; pa.n = n;
-    pa.geo = RL.geo; pa.ua = RL.ua; pa.rect = RL.rect; pa.counts = RL.counts;
+    pa.geo = RL.geo; pa.ua = RL.ua; pa.rect = RL.rect; pa.counts = nullptr;   // the rectangles give the counts
     pa.vis_words = RL.vis_words;
     pa.zrec = RL.zrec;
     pa.zrange = SL.info->zrange;
@@ -566,10 +565,12 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     // its contiguous entries; otherwise keys are view * TT + tile, one sort.
     {
         Stage st(ctx, GAVIS_STAGE_EMIT, s);
-        CK(launch_gather_counts(recs, RL.counts, (size_t)nrec, KL.a_cnt, s));
+        // the stage-A keys are spent: their buffer holds the rectangles in stage-A order
+        uint2 *rect_sorted = reinterpret_cast<uint2 *>(KL.a_k0);
+        CK(launch_gather_rects(recs, RL.rect, (size_t)nrec, KL.a_cnt, rect_sorted, s));
         CK(exclusive_scan_u32(KL.a_cnt, KL.a_off, (size_t)nrec, KL.tmp, nullptr, s));
         CK(launch_emit_tiles(recs, KL.a_off, (size_t)nrec, RL.rect, n, G.TW, G.TH, KL.b_k0, KL.b_v0, s, nullptr,
-                             ~(size_t)0, nullptr, tb));
+                             ~(size_t)0, nullptr, tb, rect_sorted));
         if (tb >= 0) {   // tile entries before each view: a second read-back
             CK(launch_entry_offsets(KL.a_off, SL.voff, nv, (uint32_t)M, SL.eoff, s));
             CK(cudaMemcpyAsync(h_eoff, SL.eoff, ((size_t)nv + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));

@@ -74,7 +74,7 @@ struct ProjectArgs {
     GeoRec *geo;
     UaRec *ua;              // NULL for the visibility pass
     uint2 *rect;
-    uint32_t *counts;       // tile count of each visible record (and 0 for culled ones unless vis_words is given)
+    uint32_t *counts;       // optional: tile count of each visible record (and 0 for culled ones unless vis_words is given)
     uint32_t *vis_words;    // [nv][ceil(n/32)] visibility bits (bit g%32 of word g/32), or NULL
     float *zrec;            // camera depth of each visible record (dense copy of GeoRec b.z), or NULL
     uint32_t *zrange;       // [2] min and max depth bits of visible records (atomic)
@@ -215,12 +215,18 @@ cudaError_t launch_entry_offsets(const uint32_t *off_sorted, const uint32_t *vof
 // entries past cap_M are not written and set *overflow (when given).
 cudaError_t launch_gather_counts(const uint32_t *valA, const uint32_t *counts, size_t nrec, uint32_t *cnt_sorted,
                                  cudaStream_t s, const unsigned long long *d_nrec = nullptr);
+// rect_sorted[i] = rect[valA[i]] and cnt_sorted[i] = its tile count (one
+// gather of the rectangle, in stage-A order).
+cudaError_t launch_gather_rects(const uint32_t *valA, const uint2 *rect, size_t nrec, uint32_t *cnt_sorted,
+                                uint2 *rect_sorted, cudaStream_t s, const unsigned long long *d_nrec = nullptr);
 // tb: tile keys are v * TT + tile (tb < 0) or (v << tb) | tile (2^tb >= TT),
 // which lets a group of 2^g views be sorted on its low tb + g bits.
+// rect_sorted (optional): the rectangles in stage-A order (read in order
+// instead of gathered from rect).
 cudaError_t launch_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect,
                               int64_t n, int TW, int TH, uint32_t *keyB, uint32_t *valB, cudaStream_t s,
                               const unsigned long long *d_nrec = nullptr, size_t cap_M = ~(size_t)0,
-                              uint32_t *overflow = nullptr, int tb = -1);
+                              uint32_t *overflow = nullptr, int tb = -1, const uint2 *rect_sorted = nullptr);
 cudaError_t launch_ranges(const uint32_t *keys, size_t M, uint2 *ranges, cudaStream_t s,
                           const unsigned long long *d_M = nullptr, int tb = -1, uint32_t TT = 0);
 // canonical keys ((view*tiles + tile) << 32) | depth bits, for verification

@@ -137,11 +137,11 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     const size_t o_cams = take((size_t)n_cams * sizeof(gavis_camera)), o_info = take(nb * sizeof(PlanInfo));
     const size_t o_geo = take(nvn * sizeof(GeoRec)), o_ua = take(nvn * sizeof(UaRec)), o_rect = take(nvn * 8);
     const size_t nwords = (size_t)B * (size_t)((n + 31) / 32);
-    const size_t o_cnt = take(nvn * 4), o_words = take(nwords * 4), o_woff = take(nwords * 4);
+    const size_t o_words = take(nwords * 4), o_woff = take(nwords * 4);
     const size_t o_zrec = take(nvn * 4);   // dense depth copy of the visible records (stage-A keys)
     const size_t o_scan = take(scan_tmp_bytes(nwords) + 64);
     const size_t o_ak0 = take(R * 4), o_ak1 = take(R * 4), o_av0 = take(R * 4), o_av1 = take(R * 4);
-    const size_t o_acnt = take(R * 4), o_aoff = take(R * 4);
+    const size_t o_acnt = take(R * 4), o_aoff = take(R * 4), o_rs = take(R * 8);
     const size_t o_bk0 = take(M * 4), o_bk1 = take(M * 4), o_bv0 = take(M * 4), o_bv1 = take(M * 4);
     // segmented sorts: block tables for the largest batch, key parameters,
     // per-view record and entry offsets
@@ -175,7 +175,6 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     GeoRec *geo = reinterpret_cast<GeoRec *>(b + o_geo);
     UaRec *ua = reinterpret_cast<UaRec *>(b + o_ua);
     uint2 *rect = reinterpret_cast<uint2 *>(b + o_rect);
-    uint32_t *counts = reinterpret_cast<uint32_t *>(b + o_cnt);
     uint32_t *vis_words = reinterpret_cast<uint32_t *>(b + o_words), *woff = reinterpret_cast<uint32_t *>(b + o_woff);
     float *zrec = reinterpret_cast<float *>(b + o_zrec);
     uint32_t *ak0 = reinterpret_cast<uint32_t *>(b + o_ak0), *ak1 = reinterpret_cast<uint32_t *>(b + o_ak1);
@@ -184,6 +183,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     uint32_t *voff = reinterpret_cast<uint32_t *>(b + o_voff), *eoff = reinterpret_cast<uint32_t *>(b + o_eoff);
     uint32_t *av0 = reinterpret_cast<uint32_t *>(b + o_av0), *av1 = reinterpret_cast<uint32_t *>(b + o_av1);
     uint32_t *acnt = reinterpret_cast<uint32_t *>(b + o_acnt), *aoff = reinterpret_cast<uint32_t *>(b + o_aoff);
+    uint2 *rect_sorted = reinterpret_cast<uint2 *>(b + o_rs);
     uint32_t *bk0 = reinterpret_cast<uint32_t *>(b + o_bk0), *bk1 = reinterpret_cast<uint32_t *>(b + o_bk1);
     uint32_t *bv0 = reinterpret_cast<uint32_t *>(b + o_bv0), *bv1 = reinterpret_cast<uint32_t *>(b + o_bv1);
     void *tmp = b + o_tmp, *scan_tmp = b + o_scan;
@@ -207,7 +207,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     pa.q_cut = p->q_cut; pa.beta = p->beta; pa.o0 = p->o0;
     pa.tile = p->tile; pa.TW = TW; pa.TH = TH;
     pa.n = n;
-    pa.geo = geo; pa.ua = ua; pa.rect = rect; pa.counts = counts;
+    pa.geo = geo; pa.ua = ua; pa.rect = rect; pa.counts = nullptr;   // the rectangles give the counts
     pa.vis_words = vis_words;
     pa.zrec = zrec;
     CompositeArgs ca;
@@ -251,7 +251,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
         bool alt_a = false, alt_b = false;
         PK(radix_sort_segments<uint32_t>(ak0, av0, ak1, av1, blk_a, nblk_a, 32, tmp, &alt_a, cs, true));
         const uint32_t *recs = alt_a ? av1 : av0;
-        PK(launch_gather_counts(recs, counts, R, acnt, cs, &info->b.visible));
+        PK(launch_gather_rects(recs, rect, R, acnt, rect_sorted, cs, &info->b.visible));
         PK(exclusive_scan_u32(acnt, aoff, R, tmp, nullptr, cs, false, &info->b.visible));
         // stage B: tile keys (view << tb) | tile sorted on 16 bits per group
         // of 2^(16 - tb) views when the tile index fits tb <= 16 bits and the
@@ -259,7 +259,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
         const int vb = bits_of((uint64_t)nv - 1), tbits = bits_of((uint64_t)TT - 1);
         const int tb = tbits + vb > 16 && tbits <= 16 && ((nv - 1) >> (16 - tbits)) < 64 ? tbits : -1;
         PK(launch_emit_tiles(recs, aoff, R, rect, n, TW, TH, bk0, bv0, cs, &info->b.visible, M,
-                             &info->entries_over, tb));
+                             &info->entries_over, tb, rect_sorted));
         if (tb >= 0) {
             PK(launch_entry_offsets_dev(aoff, voff, nv, &info->b, R, M, eoff, cs));
             PK(launch_segment_blocks(eoff, nv, nullptr, 1 << (16 - tb), M, blk_b, nblk_b, cs));

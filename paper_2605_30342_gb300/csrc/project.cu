@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
                 if (cam_depth(s_cams[v0 + u], mx, my, mz) > s_cams[v0 + u].znear) front |= 1u << u;
         if (!a.vis_words && live) {
             for (int u = 0; u < nu; ++u)
-                if (!((front >> u) & 1u)) a.counts[(size_t)(v0 + u) * (size_t)a.n + (size_t)g] = 0u;
+                if (a.counts && !((front >> u) & 1u)) a.counts[(size_t)(v0 + u) * (size_t)a.n + (size_t)g] = 0u;
         }
         uint32_t vis = 0u;    // bit u: the lane's Gaussian has tiles in view v0 + u
         uint32_t pend = 0u;   // the same, appearance pending
@@ -264,11 +264,11 @@ __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
                     const Proj p = project_one(s_cams[v], gx, gy, gz, So, a.q_cut, rb, a.TW, a.TH);
                     const size_t r = (size_t)v * (size_t)a.n + (size_t)(gw0 + o);
                     if (p.status != 1) {
-                        if (!a.vis_words) a.counts[r] = 0u;
+                        if (!a.vis_words && a.counts) a.counts[r] = 0u;
                     } else {
                         atomicOr(&s_vis[wib][o], 1u << u);
                         const uint32_t nt = (uint32_t)((p.x1 - p.x0 + 1) * (p.y1 - p.y0 + 1));
-                        a.counts[r] = nt;
+                        if (a.counts) a.counts[r] = nt;
                         ntiles += nt;
                         a.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.x1 << 16), (uint32_t)p.y0 | ((uint32_t)p.y1 << 16));
                         zlo = min(zlo, __float_as_uint(p.z));
@@ -300,11 +300,11 @@ __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
                     const Proj p = project_one(s_cams[v], mx, my, mz, S, a.q_cut, rb, a.TW, a.TH);
                     const size_t r = (size_t)v * (size_t)a.n + (size_t)g;
                     if (p.status != 1) {
-                        if (!a.vis_words) a.counts[r] = 0u;
+                        if (!a.vis_words && a.counts) a.counts[r] = 0u;
                     } else {
                         vis |= 1u << u;
                         const uint32_t nt = (uint32_t)((p.x1 - p.x0 + 1) * (p.y1 - p.y0 + 1));
-                        a.counts[r] = nt;
+                        if (a.counts) a.counts[r] = nt;
                         ntiles += nt;
                         a.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.x1 << 16),
                                                (uint32_t)p.y0 | ((uint32_t)p.y1 << 16));

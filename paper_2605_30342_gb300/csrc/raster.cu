@@ -137,6 +137,18 @@ __global__ void k_gather_counts(const uint32_t *valA, const uint32_t *counts, si
     cnt_sorted[i] = counts[valA[i]];
 }
 
+// the tile rectangle of each record in stage-A order (one gather), and its
+// tile count, which the rectangle gives
+__global__ void k_gather_rects(const uint32_t *valA, const uint2 *rect, size_t nrec, uint32_t *cnt_sorted,
+                               uint2 *rect_sorted, const unsigned long long *d_nrec)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrec || (d_nrec && i >= (size_t)*d_nrec)) return;
+    const uint2 rc = rect[valA[i]];
+    rect_sorted[i] = rc;
+    cnt_sorted[i] = ((rc.x >> 16) - (rc.x & 0xffffu) + 1u) * ((rc.y >> 16) - (rc.y & 0xffffu) + 1u);
+}
+
 // Tile keys: v * TT + tile (tb < 0), or (v << tb) | tile with 2^tb >= TT, so
 // that the keys of a group of 2^g views differ only in their low tb + g bits.
 __device__ __forceinline__ uint32_t tile_index(uint32_t key, int tb, uint32_t TT)
@@ -150,7 +162,7 @@ __device__ __forceinline__ uint32_t tile_index(uint32_t key, int tb, uint32_t TT
 // over the warp's prefix counts, so the stores are coalesced.
 __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect, int64_t n,
                              int TW, int TH, uint32_t *keyB, uint32_t *valB, const unsigned long long *d_nrec,
-                             size_t cap_M, uint32_t *overflow, int tb)
+                             size_t cap_M, uint32_t *overflow, int tb, const uint2 *rect_sorted)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = (int)(threadIdx.x & 31u);
@@ -161,7 +173,7 @@ __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, s
         const uint32_t r = valA[i];
         const uint32_t v = (uint32_t)(r / (uint64_t)n);
         g = (uint32_t)(r - (uint64_t)v * (uint64_t)n);
-        const uint2 rc = rect[r];
+        const uint2 rc = rect_sorted ? rect_sorted[i] : rect[r];
         x0 = rc.x & 0xffffu;
         y0 = rc.y & 0xffffu;
         w = (rc.x >> 16) - x0 + 1u;
@@ -798,13 +810,22 @@ cudaError_t launch_gather_counts(const uint32_t *valA, const uint32_t *counts, s
     return cudaGetLastError();
 }
 
+cudaError_t launch_gather_rects(const uint32_t *valA, const uint2 *rect, size_t nrec, uint32_t *cnt_sorted,
+                                uint2 *rect_sorted, cudaStream_t s, const unsigned long long *d_nrec)
+{
+    if (nrec == 0) return cudaSuccess;
+    k_gather_rects<<<nblk(nrec, 256), 256, 0, s>>>(valA, rect, nrec, cnt_sorted, rect_sorted, d_nrec); count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect,
                               int64_t n, int TW, int TH, uint32_t *keyB, uint32_t *valB, cudaStream_t s,
-                              const unsigned long long *d_nrec, size_t cap_M, uint32_t *overflow, int tb)
+                              const unsigned long long *d_nrec, size_t cap_M, uint32_t *overflow, int tb,
+                              const uint2 *rect_sorted)
 {
     if (nrec == 0) return cudaSuccess;
     k_emit_tiles<<<nblk(nrec, 256), 256, 0, s>>>(valA, off_sorted, nrec, rect, n, TW, TH, keyB, valB, d_nrec, cap_M,
-                                                 overflow, tb); count_launch();
+                                                 overflow, tb, rect_sorted); count_launch();
     return cudaGetLastError();
 }
 
