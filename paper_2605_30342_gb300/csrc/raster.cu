@@ -168,20 +168,22 @@ __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, s
     const int lane = (int)(threadIdx.x & 31u);
     size_t live = nrec;
     if (d_nrec && (size_t)*d_nrec < live) live = (size_t)*d_nrec;
-    uint32_t g = 0, vbase = 0, x0 = 0, y0 = 0, w = 1, cnt = 0, off = 0;
+    // per record: its Gaussian, the key of its first tile, the rectangle's
+    // width and its reciprocal, its tile count and first entry
+    uint32_t g = 0, kfirst = 0, w = 1, cnt = 0, off = 0;
     if (i < live) {
-        const uint32_t r = valA[i];
-        const uint32_t v = (uint32_t)(r / (uint64_t)n);
-        g = (uint32_t)(r - (uint64_t)v * (uint64_t)n);
+        const uint32_t r = valA[i];   // record indices are 32-bit: v = r / n in 32-bit arithmetic
+        const uint32_t v = r / (uint32_t)n;
+        g = r - v * (uint32_t)n;
         const uint2 rc = rect_sorted ? rect_sorted[i] : rect[r];
-        x0 = rc.x & 0xffffu;
-        y0 = rc.y & 0xffffu;
+        const uint32_t x0 = rc.x & 0xffffu, y0 = rc.y & 0xffffu;
         w = (rc.x >> 16) - x0 + 1u;
         cnt = w * ((rc.y >> 16) - y0 + 1u);
-        vbase = tb < 0 ? v * (uint32_t)(TW * TH) : v << tb;
+        kfirst = (tb < 0 ? v * (uint32_t)(TW * TH) : v << tb) + y0 * (uint32_t)TW + x0;
         off = off_sorted[i];
         if ((size_t)off + cnt > cap_M && overflow) *overflow = 1u;
     }
+    const float rw = 1.0f / (float)w;
     uint32_t inc = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -191,6 +193,7 @@ __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, s
     const uint32_t excl = inc - cnt;
     const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
     const uint32_t base = __shfl_sync(0xffffffffu, off, 0);   // the valid lanes are a prefix of the warp
+    const uint32_t room = cap_M > (size_t)base ? (uint32_t)min(cap_M - (size_t)base, (size_t)0xffffffffu) : 0u;
     for (uint32_t j0 = 0; j0 < total; j0 += 32) {
         const uint32_t j = j0 + (uint32_t)lane;
         int k = 0;   // last lane whose entries start at or before j
@@ -200,12 +203,26 @@ __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, s
             if (e <= j) k += step;
         }
         const uint32_t ek = __shfl_sync(0xffffffffu, excl, k), wk = __shfl_sync(0xffffffffu, w, k);
-        const uint32_t xk = __shfl_sync(0xffffffffu, x0, k), yk = __shfl_sync(0xffffffffu, y0, k);
-        const uint32_t bk = __shfl_sync(0xffffffffu, vbase, k), gk = __shfl_sync(0xffffffffu, g, k);
-        const size_t pos = (size_t)base + j;
-        if (j < total && pos < cap_M) {
-            const uint32_t m = j - ek, ty = m / wk, tx = m - ty * wk;
-            keyB[pos] = bk + (yk + ty) * (uint32_t)TW + xk + tx;
+        const uint32_t fk = __shfl_sync(0xffffffffu, kfirst, k), gk = __shfl_sync(0xffffffffu, g, k);
+        const float rk = __shfl_sync(0xffffffffu, rw, k);
+        if (j < total && j < room) {
+            // row and column of entry m of the rectangle: the float quotient
+            // is within one of m / wk for m < 2^22 (relative error < 2^-22),
+            // and one correction step each way makes it exact
+            const uint32_t m = j - ek;
+            uint32_t ty, tx;
+            if (m < (1u << 22)) {
+                ty = (uint32_t)((float)m * rk);
+                int d = (int)(m - ty * wk);
+                if (d < 0) { --ty; d += (int)wk; }
+                else if (d >= (int)wk) { ++ty; d -= (int)wk; }
+                tx = (uint32_t)d;
+            } else {
+                ty = m / wk;
+                tx = m - ty * wk;
+            }
+            const size_t pos = (size_t)base + j;
+            keyB[pos] = fk + ty * (uint32_t)TW + tx;
             valB[pos] = gk;
         }
     }
