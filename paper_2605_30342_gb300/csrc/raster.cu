@@ -316,7 +316,9 @@ constexpr float kLn2 = 0.69314718055994530942f;
 // colour path (into a.depth).
 constexpr int kUaWarps = 4;   // warps per CTA of the uncertainty pass
 
-template <int TILE, bool KC, bool DEPTH>
+// PAIRS: count the pixel-Gaussian pairs composited (instrumentation; into
+// a.pair_counts, one count per 8 x 8 block).
+template <int TILE, bool KC, bool DEPTH, bool PAIRS>
 __global__ void __launch_bounds__(kUaWarps * 32) k_composite_ua(CompositeArgs a)
 {
     constexpr int NW = kUaWarps;
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(kUaWarps * 32) k_composite_ua(CompositeArgs a)
                     const float q = footprint_q(px, py[p], g0.x, g0.y, g0.z, g0.w, g1.x);
                     const bool hit = q <= rc.q_cut;
                     const bool hc = hit && rgb_on[p], hu = hit && ua_on[p];
-                    npairs += (uint32_t)(hc || hu);
+                    if (PAIRS) npairs += (uint32_t)(hc || hu);
                     const float alpha = ex2_approx(fmaf(q, kNegHalfLog2e, g1.y));   // o exp(-q/2)
                     if (colour) {   // the same for every thread of the launch
                         const float2 u1 = u1s[k];
@@ -468,10 +470,10 @@ __global__ void __launch_bounds__(kUaWarps * 32) k_composite_ua(CompositeArgs a)
         // the block's partial sum of the per-pixel entropy (fixed order: deterministic)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) h += __shfl_down_sync(0xffffffffu, h, o);
-        const uint32_t wp = __reduce_add_sync(0xffffffffu, npairs);
+        const uint32_t wp = PAIRS ? __reduce_add_sync(0xffffffffu, npairs) : 0u;
         if (lane == 0) {   // at the block's natural index: summed per view in (tile, block) order
             a.tile_sums[bt * BPT + blk] = h;
-            if (a.pair_counts) a.pair_counts[bt * BPT + blk] = wp;
+            if (PAIRS) a.pair_counts[bt * BPT + blk] = wp;
         }
     }
 }
@@ -486,6 +488,15 @@ __global__ void __launch_bounds__(kUaWarps * 32) k_composite_ua(CompositeArgs a)
 // Gaussians' accumulators once per chunk, one atomic pair per entry.  The
 // transmittance is kept scaled by 2^18 (exact: a power of two), and alpha is
 // 2^(log2(o) - q log2(e)/2).  A warp stops when its pixels saturate.
+// round(T) * 2^kCntBits + 1 (one hit carrying its scaled transmittance), for
+// 0 <= T < 2^23: adding 2^23 leaves T rounded to the nearest integer (ties to
+// even, as __float2uint_rn) in the low bits of the sum, without a conversion
+__device__ __forceinline__ uint32_t hit_word(float T)
+{
+    constexpr uint32_t kMul = 1u << kCntBits;
+    return __float_as_uint(T + 8388608.0f) * kMul + (1u - 0x4B000000u * kMul);
+}
+
 template <int TILE>
 __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs a)
 {
@@ -561,8 +572,8 @@ __global__ void __launch_bounds__(TILE *TILE / 2) k_composite_vis(CompositeArgs 
                 const float q1 = footprint_q(px, py1, g0.x, g0.y, g0.z, g0.w, g1.x);
                 const bool h0 = on0 && (q0 <= qcut), h1 = on1 && (q1 <= qcut);
                 uint32_t w = 0u;
-                if (h0) w = __float2uint_rn(T0) * kCntMul + 1u;
-                if (h1) w += __float2uint_rn(T1) * kCntMul + 1u;
+                if (h0) w = hit_word(T0);
+                if (h1) w += hit_word(T1);
                 const uint32_t sum = __reduce_add_sync(0xffffffffu, w);
                 if (lane == 0) sums[k + u] = sum;   // the same in every lane
                 if (h0) {
@@ -876,7 +887,7 @@ struct UaGrid {
     std::atomic<int> ctas[kMaxDevices];
 };
 
-template <int TILE, bool KC, bool DEPTH>
+template <int TILE, bool KC, bool DEPTH, bool PAIRS>
 unsigned ua_resident_ctas()
 {
     static UaGrid g;   // zero-initialised: computed on first use per device
@@ -886,7 +897,8 @@ unsigned ua_resident_ctas()
     int c = g.ctas[dev].load(std::memory_order_relaxed);
     if (c == 0) {
         int per_sm = 0, nsm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite_ua<TILE, KC, DEPTH>, kUaWarps * 32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite_ua<TILE, KC, DEPTH, PAIRS>, kUaWarps * 32,
+                                                      0);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         c = (per_sm > 0 ? per_sm : 1) * (nsm > 0 ? nsm : 1);
         g.ctas[dev].store(c, std::memory_order_relaxed);
@@ -894,13 +906,20 @@ unsigned ua_resident_ctas()
     return (unsigned)c;
 }
 
-template <int TILE, bool KC, bool DEPTH>
+template <int TILE, bool KC, bool DEPTH, bool PAIRS>
 void launch_ua_inst(const CompositeArgs &a, unsigned long long items, cudaStream_t s)
 {
     const unsigned long long want = (items + kUaWarps - 1) / kUaWarps;
-    const unsigned cap = ua_resident_ctas<TILE, KC, DEPTH>();
+    const unsigned cap = ua_resident_ctas<TILE, KC, DEPTH, PAIRS>();
     const unsigned blocks = want < cap ? (unsigned)want : cap;
-    k_composite_ua<TILE, KC, DEPTH><<<blocks, kUaWarps * 32, 0, s>>>(a);
+    k_composite_ua<TILE, KC, DEPTH, PAIRS><<<blocks, kUaWarps * 32, 0, s>>>(a);
+}
+
+template <int TILE, bool KC, bool DEPTH>
+void launch_ua_pairs(const CompositeArgs &a, unsigned long long items, cudaStream_t s)
+{
+    if (a.pair_counts) launch_ua_inst<TILE, KC, DEPTH, true>(a, items, s);
+    else launch_ua_inst<TILE, KC, DEPTH, false>(a, items, s);
 }
 
 template <int TILE>
@@ -908,11 +927,11 @@ void launch_ua_tile(const CompositeArgs &a, unsigned long long items, cudaStream
 {
     const bool d = a.depth != nullptr;
     if (a.per_entry_kc) {
-        if (d) launch_ua_inst<TILE, true, true>(a, items, s);
-        else launch_ua_inst<TILE, true, false>(a, items, s);
+        if (d) launch_ua_pairs<TILE, true, true>(a, items, s);
+        else launch_ua_pairs<TILE, true, false>(a, items, s);
     } else {
-        if (d) launch_ua_inst<TILE, false, true>(a, items, s);
-        else launch_ua_inst<TILE, false, false>(a, items, s);
+        if (d) launch_ua_pairs<TILE, false, true>(a, items, s);
+        else launch_ua_pairs<TILE, false, false>(a, items, s);
     }
     count_launch();
 }
@@ -920,10 +939,14 @@ void launch_ua_tile(const CompositeArgs &a, unsigned long long items, cudaStream
 template <int TILE>
 void prepare_ua_tile()
 {
-    ua_resident_ctas<TILE, true, true>();
-    ua_resident_ctas<TILE, true, false>();
-    ua_resident_ctas<TILE, false, true>();
-    ua_resident_ctas<TILE, false, false>();
+    ua_resident_ctas<TILE, true, true, false>();
+    ua_resident_ctas<TILE, true, false, false>();
+    ua_resident_ctas<TILE, false, true, false>();
+    ua_resident_ctas<TILE, false, false, false>();
+    ua_resident_ctas<TILE, true, true, true>();
+    ua_resident_ctas<TILE, true, false, true>();
+    ua_resident_ctas<TILE, false, true, true>();
+    ua_resident_ctas<TILE, false, false, true>();
 }
 
 cudaError_t launch_composite_ua(const CompositeArgs &a, cudaStream_t s)

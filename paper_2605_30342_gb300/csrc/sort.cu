@@ -418,13 +418,10 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const KeyT *keys, siz
 // turned into block-local digit offsets, items are placed in shared memory in
 // sorted order, and written out so that consecutive threads write consecutive
 // addresses of each digit run.
-// Each warp ranks its items as kRsStreams independent streams (consecutive
-// sub-ranges, each with its own digit counters), interleaved round by round,
-// so that the dependent counter updates of one stream overlap the others'.
-constexpr int kRsStreams = 2;
-constexpr int kRsRows = kRsWarps * kRsStreams;   // counter rows, in input order
+// Each item's digit and rank share one register, so that 32-bit passes fit
+// three CTAs per SM (80 registers).
 template <typename KeyT>
-constexpr size_t rs_smem() { return (size_t)kRsTile * (sizeof(KeyT) + 4) + (size_t)(kRsRows + 3) * 256 * 4; }
+constexpr size_t rs_smem() { return (size_t)kRsTile * (sizeof(KeyT) + 4) + (size_t)(kRsWarps + 3) * 256 * 4; }
 
 template <typename KeyT, bool BALLOT>
 __global__ void __launch_bounds__(kRsThreads, sizeof(KeyT) == 4 ? 3 : 2) k_radix_scatter(const KeyT *kin, const uint32_t *vin,
@@ -440,8 +437,8 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(KeyT) == 4 ? 3 : 2) k_radix
     extern __shared__ __align__(16) unsigned char smem[];
     KeyT *s_key = reinterpret_cast<KeyT *>(smem);
     uint32_t *s_val = reinterpret_cast<uint32_t *>(smem + (size_t)kRsTile * sizeof(KeyT));
-    uint32_t *s_wc = reinterpret_cast<uint32_t *>(smem + (size_t)kRsTile * (sizeof(KeyT) + 4));   // [rows][256]
-    uint32_t *s_goff = s_wc + kRsRows * 256;
+    uint32_t *s_wc = reinterpret_cast<uint32_t *>(smem + (size_t)kRsTile * (sizeof(KeyT) + 4));   // [warps][256]
+    uint32_t *s_goff = s_wc + kRsWarps * 256;
     uint32_t *s_lstart = s_goff + 256;
     uint32_t *s_tmp = s_lstart + 256;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -451,7 +448,7 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(KeyT) == 4 ? 3 : 2) k_radix
     // this block's digit counts -> block-local digit starts (exclusive scan)
     const uint32_t mycnt = hist[br.h0 + (size_t)tid * br.hs];
     s_goff[tid] = offs[br.h0 + (size_t)tid * br.hs];
-    for (int w = 0; w < kRsRows; ++w) s_wc[w * 256 + tid] = 0u;
+    for (int w = 0; w < kRsWarps; ++w) s_wc[w * 256 + tid] = 0u;
     {
         uint32_t x = mycnt;
 #pragma unroll
@@ -469,12 +466,10 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(KeyT) == 4 ? 3 : 2) k_radix
 
     // phase A: warp-private stable ranks
     constexpr int R = kRsTile / kRsThreads;   // rounds of 32 items per warp
-    constexpr int RS = R / kRsStreams;        // rounds per stream
-    static_assert(RS * kRsStreams == R, "whole rounds per stream");
     KeyT k[R];
     uint32_t v[R];
-    uint32_t dr[R];   // (digit << 16) | rank in the stream's digit run (ranks < 4096)
-    uint32_t *wc = s_wc + warp * kRsStreams * 256;   // stream j's counters at wc + 256 j
+    uint32_t dr[R];   // (digit << 16) | rank in the warp's digit run (ranks < 4096)
+    uint32_t *wc = s_wc + warp * 256;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const size_t i = base + (size_t)warp * (32 * R) + (size_t)r * 32 + lane;
@@ -485,32 +480,21 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(KeyT) == 4 ? 3 : 2) k_radix
         // valid item of the block, so it lands past the valid ones and is not written
         dr[r] = (valid ? (uint32_t)((k[r] >> shift) & 255u) : 255u) << 16;
     }
-    // round q of every stream at once: stream j takes round j RS + q
 #pragma unroll
-    for (int q = 0; q < RS; ++q) {
-        unsigned peers[kRsStreams];
-        uint32_t prior[kRsStreams];
-#pragma unroll
-        for (int j = 0; j < kRsStreams; ++j) {
-            const int r = j * RS + q;
-            const int d = (int)(dr[r] >> 16);
-            peers[j] = digit_peers<BALLOT>(d);
-            prior[j] = wc[j * 256 + d];
-            dr[r] |= prior[j] + (uint32_t)__popc(peers[j] & lt);
-        }
+    for (int r = 0; r < R; ++r) {
+        const int d = (int)(dr[r] >> 16);
+        const unsigned peers = digit_peers<BALLOT>(d);
+        const uint32_t prior = wc[d];
+        dr[r] |= prior + (uint32_t)__popc(peers & lt);
         __syncwarp();
-#pragma unroll
-        for (int j = 0; j < kRsStreams; ++j) {
-            const int r = j * RS + q;
-            if (lane == __ffs(peers[j]) - 1) wc[j * 256 + (dr[r] >> 16)] = prior[j] + (uint32_t)__popc(peers[j]);
-        }
+        if (lane == __ffs(peers) - 1) wc[d] = prior + (uint32_t)__popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    // per digit: offsets of the streams' runs inside the block's digit run
+    // per digit: offsets of the warps' runs inside the block's digit run
     {
         uint32_t run = s_lstart[tid];
-        for (int w = 0; w < kRsRows; ++w) {
+        for (int w = 0; w < kRsWarps; ++w) {
             const uint32_t c = s_wc[w * 256 + tid];
             s_wc[w * 256 + tid] = run;
             run += c;
@@ -520,7 +504,7 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(KeyT) == 4 ? 3 : 2) k_radix
     // phase B: place in shared memory in sorted order
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const uint32_t lp = wc[(r / RS) * 256 + (dr[r] >> 16)] + (dr[r] & 0xffffu);
+        const uint32_t lp = wc[dr[r] >> 16] + (dr[r] & 0xffffu);
         s_key[lp] = k[r];
         s_val[lp] = v[r];
     }
