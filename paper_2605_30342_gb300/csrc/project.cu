@@ -146,13 +146,69 @@ __device__ __forceinline__ Proj project_one(const gavis_camera &cam, float x, fl
 
 constexpr bool kDealWithAppearance = false;   // see the file header
 
+// A cheap screen test ahead of project_one, conservative by construction:
+// it returns false only where project_one returns no tiles.  The centre's
+// camera coordinates are computed with project_one's operations (same bits);
+// the pixel centre uses an approximate reciprocal, and the footprint
+// half-width is bounded from above: the first row of J W is J00 R0 + J02 R2
+// with J00 = fx/tz and |J02| <= fx limx / tz (|ctx| <= limx tz), so the
+// screen-space variance a <= smax2 (fx/tz)^2 (|R0|^2 + 2 limx |R0.R2| +
+// limx^2 |R2|^2) + 0.3 (smax2: the covariance's largest eigenvalue, the
+// largest squared scale; any R, orthonormal or not).  kx, ky = those
+// factors' square roots times fx, fy with 2% margin, rg = sqrt(q_cut smax2)
+// with 1% margin, c0 = sqrt(0.31 q_cut) + 1 pixel; the approximate centre
+// adds 1e-5 (|u| + |cx|) of slack.
+struct ScreenBound {
+    float kx, ky;   // fx, fy times the bound on |J W| rows per unit 1/tz (see may_have_tiles), 2% margin
+    float c0;       // sqrt(0.31 q_cut) + 1
+    float Wt, Ht;   // extent of the tile grid in pixels
+    float pad;
+};
+static_assert(sizeof(gavis_camera) % 8 == 0, "the bound factors follow the cameras 8-byte aligned");
+
+__device__ __forceinline__ ScreenBound screen_bound(const gavis_camera &c, float q_cut, int TW, int TH, int tile)
+{
+    const float lx = 1.3f * c.tan_half_fovx, ly = 1.3f * c.tan_half_fovy;
+    const float *R = c.R;
+    const float n0 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2], n1 = R[3] * R[3] + R[4] * R[4] + R[5] * R[5];
+    const float n2 = R[6] * R[6] + R[7] * R[7] + R[8] * R[8];
+    const float d02 = fabsf(R[0] * R[6] + R[1] * R[7] + R[2] * R[8]), d12 = fabsf(R[3] * R[6] + R[4] * R[7] + R[5] * R[8]);
+    ScreenBound b;
+    b.kx = c.fx * sqrtf(n0 + 2.0f * lx * d02 + lx * lx * n2) * 1.02f;
+    b.ky = c.fy * sqrtf(n1 + 2.0f * ly * d12 + ly * ly * n2) * 1.02f;
+    b.c0 = sqrtf(0.31f * q_cut) + 1.0f;
+    b.Wt = (float)(TW * tile);
+    b.Ht = (float)(TH * tile);
+    b.pad = 0.0f;
+    return b;
+}
+
+__device__ __forceinline__ bool may_have_tiles(const gavis_camera &cam, const ScreenBound &sb, float x, float y,
+                                               float z, float rg)
+{
+    const float tz = cam_depth(cam, x, y, z);
+    if (!(tz > cam.znear)) return false;
+    const float *R = cam.R, *t = cam.t;
+    const float tx = fa(fa(fa(fm(R[0], x), fm(R[1], y)), fm(R[2], z)), t[0]);
+    const float ty = fa(fa(fa(fm(R[3], x), fm(R[4], y)), fm(R[5], z)), t[1]);
+    const float iz = __fdividef(1.0f, tz);
+    const float u = fmaf(cam.fx, tx * iz, cam.cx), v = fmaf(cam.fy, ty * iz, cam.cy);
+    const float ex = fmaf(rg * sb.kx, iz, sb.c0) + (fabsf(u) + fabsf(cam.cx)) * 1e-5f;
+    const float ey = fmaf(rg * sb.ky, iz, sb.c0) + (fabsf(v) + fabsf(cam.cy)) * 1e-5f;
+    return u + ex > 0.5f && u - ex - 0.5f < sb.Wt && v + ey > 0.5f && v - ey - 0.5f < sb.Ht;
+}
+
 // VAR: per-Gaussian colour covariance from coefficient variances
 template <int LC, int LV, bool UA, bool VAR>
 __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
 {
-    extern __shared__ gavis_camera s_cams[];
+    extern __shared__ gavis_camera s_cams[];   // nv cameras, then their screen-bound factors
+    ScreenBound *s_sb = reinterpret_cast<ScreenBound *>(s_cams + a.nv);
     __shared__ uint32_t s_vis[4][32];   // per warp: visibility bits of each lane's Gaussian in the group's views
-    for (int i = threadIdx.x; i < a.nv; i += blockDim.x) s_cams[i] = a.cams[i];
+    for (int i = threadIdx.x; i < a.nv; i += blockDim.x) {
+        s_cams[i] = a.cams[i];
+        s_sb[i] = screen_bound(a.cams[i], a.q_cut, a.TW, a.TH, a.tile);
+    }
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     s_vis[wib][lane] = 0u;
     __syncthreads();
@@ -170,6 +226,8 @@ __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
     const float lop = op > 0.0f ? log2f(op) : -INFINITY;
     const Sigma3 S = sigma3d(sc, q.x, q.y, q.z, q.w);
     const float rb = 1.0f / (float)a.tile;
+    const float smax2 = fmaxf(fmaxf(sc[0] * sc[0], sc[1] * sc[1]), sc[2] * sc[2]);
+    const float rg = sqrtf(a.q_cut * smax2) * 1.01f;
 
     constexpr int KC = (LC + 1) * (LC + 1);
     constexpr int KV = (LV + 1) * (LV + 1);
@@ -192,7 +250,7 @@ __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
 
     // Views in groups of VG.  The camera depth of each view of the group
     // first.  Then the projections: the warp's (view, Gaussian) pairs with
-    // the Gaussian in front of the near plane are dealt out to its lanes view
+    // the Gaussian possibly on screen (may_have_tiles) are dealt out to its lanes view
     // by view, 32 per round (a lane takes the owner's centre and covariance
     // by shuffle), so every lane works in every round however unevenly the
     // warp's Gaussians face the cameras, and consecutive lanes write
@@ -205,11 +263,12 @@ __global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
     const size_t nw = (size_t)((a.n + 31) >> 5);
     for (int v0 = 0; v0 < a.nv; v0 += VG) {
         const int nu = a.nv - v0 < VG ? a.nv - v0 : VG;
-        // views of the group in front of the camera's near plane (the rest are culled)
+        // views of the group where the Gaussian may have tiles (in front of the
+        // near plane and not surely off-screen; the rest are culled)
         uint32_t front = 0u;
         if (live)
             for (int u = 0; u < nu; ++u)
-                if (cam_depth(s_cams[v0 + u], mx, my, mz) > s_cams[v0 + u].znear) front |= 1u << u;
+                if (may_have_tiles(s_cams[v0 + u], s_sb[v0 + u], mx, my, mz, rg)) front |= 1u << u;
         if (!a.vis_words && live) {
             for (int u = 0; u < nu; ++u)
                 if (a.counts && !((front >> u) & 1u)) a.counts[(size_t)(v0 + u) * (size_t)a.n + (size_t)g] = 0u;
@@ -447,7 +506,7 @@ cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s)
     if (a.n == 0 || a.nv == 0) return cudaSuccess;
     if (a.nv > kMaxBatchViews) return cudaErrorInvalidValue;
     const int blocks = (int)((a.n + 127) / 128);
-    const size_t smem = sizeof(gavis_camera) * (size_t)a.nv;
+    const size_t smem = (sizeof(gavis_camera) + sizeof(ScreenBound)) * (size_t)a.nv;
     if (smem > 48 * 1024) {
         // opt in to larger dynamic shared memory for big batches
         cudaFuncSetAttribute(k_project<0, 0, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
