@@ -402,7 +402,7 @@ def run_gavis(args):
     ctx.prof_enable(True, pairs=True)
     ctx.vf_build(gs, train, degree=L, params=prm_vf, out=vf)
     r_vf = ctx.prof_read()
-    vis_vf, pairs_vis = r_vf["visible"], r_vf["pairs"][1]
+    vis_vf, keys_vf, pairs_vis = r_vf["visible"], r_vf["keys"], r_vf["pairs"][1]
     ctx.prof_enable(True, pairs=True)
     ctx.score_views(gs, vf, cand, params=prm_sc, out=outs, sync_best=False)
     r_sc = ctx.prof_read()
@@ -536,7 +536,7 @@ def run_gavis(args):
         ms, nl = st[dom]
         achieved = pairs * fpp / (ms / 1e3) / 1e12
         tile = prm_sc.tile if dom == "composite_ua" else prm_vf.tile
-        prof_k = profile_for("k_" + dom, tile)
+        prof_k = profile_for("k_" + dom, tile, args.workload)
         roof = {"kernel": "k_" + dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
                 "traffic": prof_k.get("bytes_per_launch") if prof_k else None,
@@ -553,6 +553,23 @@ def run_gavis(args):
                              "achieved_pairs_per_s": pairs / (ms / 1e3),
                              "frac": pairs / (ms / 1e3) / peak_pairs,
                              "source": "warp instructions per pair from the ncu capture in profiles/"}
+    elif dom == "sort":
+        # the sort stage (histogram, scan and scatter launches of both binning
+        # levels): 16 B per item per 8-bit pass (key and value read once and
+        # written once; histogram reads not counted), 4 passes for stage A's
+        # 32-bit record keys, 2 for stage B's 16-bit tile keys, 1 for the tile
+        # order of the scoring pass (one 8-byte item per view tile)
+        ms, nl = st[dom]
+        tiles_sc = n_cand * (-(-W // prm_sc.tile)) * (-(-H // prm_sc.tile)) if prm_sc.tile <= 16 else 0
+        sort_bytes = ((vis_vf + vis_sc) * 4 * 16 + (keys_vf + keys_sc) * 2 * 16 + tiles_sc * 16) * args.steps
+        achieved = sort_bytes / (ms / 1e3) / 1e9
+        hbm_pk = pk.get("hbm_gbs", 6800.0)
+        roof = {"kernel": "sort", "bound": "hbm", "achieved": achieved, "peak": hbm_pk, "unit": "GB/s",
+                "frac": achieved / hbm_pk, "traffic": None,
+                "algorithmic_bytes_per_step": sort_bytes / args.steps,
+                "what": "the sort stage's device time (all its launches); 16 B per item per 8-bit pass, 4 passes "
+                        "per visible record, 2 per tile entry, 1 per scoring view tile",
+                "avg_launch_ms": ms / max(nl, 1), "launches": nl}
     else:
         ms, nl = st[dom]
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
@@ -730,10 +747,10 @@ def kernel_source_sha(path, kernel):
     return None
 
 
-def profile_for(kernel, tile):
+def profile_for(kernel, tile, workload):
     """The committed ncu figures of a kernel (DRAM bytes per launch, warp
     instructions per pair), when they were taken on the current source of
-    the kernel at the same tile size (else None)."""
+    the kernel, at the same tile size, for this workload (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -741,18 +758,12 @@ def profile_for(kernel, tile):
         with open(p) as f:
             d = json.load(f)
         e = d.get(f"{kernel}/tile{tile}")
-        if not e:
+        if not e or e.get("workload") != workload:
             return None
         src = os.path.join(ROOT, "paper_2605_30342_gb300", "csrc", e["source"])
         return e if kernel_source_sha(src, kernel) == e.get("kernel_sha") else None
     except Exception:
         return None
-
-
-def traffic_for(kernel, tile):
-    """DRAM bytes per launch from the committed ncu summary (see profile_for)."""
-    e = profile_for(kernel, tile)
-    return e["bytes_per_launch"] if e else None
 
 
 def run_serving(args):

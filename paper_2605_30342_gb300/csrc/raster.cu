@@ -196,12 +196,15 @@ __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, s
     const uint32_t room = cap_M > (size_t)base ? (uint32_t)min(cap_M - (size_t)base, (size_t)0xffffffffu) : 0u;
     for (uint32_t j0 = 0; j0 < total; j0 += 32) {
         const uint32_t j = j0 + (uint32_t)lane;
-        int k = 0;   // last lane whose entries start at or before j
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const uint32_t e = __shfl_sync(0xffffffffu, excl, k + step);
-            if (e <= j) k += step;
-        }
+        // the last lane whose entries start at or before j: the lanes that
+        // start before the window, plus those whose start lies in the window
+        // at or before j (a visible record has at least one tile, so the
+        // valid lanes' starts are distinct; the empty lanes past the last
+        // record start at `total`, which no j reaches)
+        const uint32_t before = (uint32_t)__popc(__ballot_sync(0xffffffffu, excl < j0));
+        const uint32_t starts =
+            __reduce_or_sync(0xffffffffu, (excl >= j0 && excl - j0 < 32u) ? 1u << (excl - j0) : 0u);
+        const int k = (int)(before + (uint32_t)__popc(starts & (0xffffffffu >> (31 - lane)))) - 1;
         const uint32_t ek = __shfl_sync(0xffffffffu, excl, k), wk = __shfl_sync(0xffffffffu, w, k);
         const uint32_t fk = __shfl_sync(0xffffffffu, kfirst, k), gk = __shfl_sync(0xffffffffu, g, k);
         const float rk = __shfl_sync(0xffffffffu, rw, k);

@@ -19,22 +19,26 @@ def bench():
     return mod
 
 
-def test_traffic_keyed_by_kernel_and_tile(bench):
+def test_traffic_keyed_by_kernel_tile_and_workload(bench):
     with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
         entries = json.load(f)
     assert entries, "no committed traffic figures"
     for key, e in entries.items():
         kernel, tile = key.split("/tile")
         sha = bench.kernel_source_sha(os.path.join(ROOT, "paper_2605_30342_gb300", "csrc", e["source"]), kernel)
-        got = bench.traffic_for(kernel, int(tile))
+        got = bench.profile_for(kernel, int(tile), e["workload"])
         # reported exactly when the source still matches the capture
-        assert got == (e["bytes_per_launch"] if sha == e["kernel_sha"] else None), key
+        assert (got["bytes_per_launch"] if got else None) == (e["bytes_per_launch"] if sha == e["kernel_sha"] else None), key
+        # and only for the workload it was captured on
+        for other in (1, 2, 3, 4):
+            if other != e["workload"]:
+                assert bench.profile_for(kernel, int(tile), other) is None, (key, other)
         # the full-launch figure is the capture scaled by the launch's units
         assert abs(e["bytes_per_launch"] - e["captured_bytes_per_launch"] * e["scale"]) <= 1e-4 * e["bytes_per_launch"]
     for tile in (8, 16, 32):   # a tile without a capture reports nothing
         if f"k_composite_vis/tile{tile}" not in entries:
-            assert bench.traffic_for("k_composite_vis", tile) is None
-    assert bench.traffic_for("k_no_such_kernel", 16) is None
+            assert bench.profile_for("k_composite_vis", tile, 3) is None
+    assert bench.profile_for("k_no_such_kernel", 16, 3) is None
 
 
 def test_kernel_sha_follows_the_definition(bench, tmp_path):
