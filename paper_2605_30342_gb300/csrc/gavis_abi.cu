@@ -566,13 +566,16 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     {
         Stage st(ctx, GAVIS_STAGE_EMIT, s);
         // the stage-A keys are spent: their buffer holds the rectangles in stage-A order
+        // the stage-B offsets per warp of 32 records (each warp scans its own records)
         uint2 *rect_sorted = reinterpret_cast<uint2 *>(KL.a_k0);
-        CK(launch_gather_rects(recs, RL.rect, (size_t)nrec, KL.a_cnt, rect_sorted, s));
-        CK(exclusive_scan_u32(KL.a_cnt, KL.a_off, (size_t)nrec, KL.tmp, nullptr, s));
-        CK(launch_emit_tiles(recs, KL.a_off, (size_t)nrec, RL.rect, n, G.TW, G.TH, KL.b_k0, KL.b_v0, s, nullptr,
-                             ~(size_t)0, nullptr, tb, rect_sorted));
+        uint32_t *warp_cnt = KL.a_cnt, *warp_off = KL.a_off;
+        const size_t nwarps = ((size_t)nrec + 31) / 32;
+        CK(launch_gather_rects(recs, RL.rect, (size_t)nrec, warp_cnt, rect_sorted, s));
+        CK(exclusive_scan_u32(warp_cnt, warp_off, nwarps, KL.tmp, nullptr, s));
+        CK(launch_emit_tiles(recs, nullptr, (size_t)nrec, RL.rect, n, G.TW, G.TH, KL.b_k0, KL.b_v0, s, nullptr,
+                             ~(size_t)0, nullptr, tb, rect_sorted, warp_off));
         if (tb >= 0) {   // tile entries before each view: a second read-back
-            CK(launch_entry_offsets(KL.a_off, SL.voff, nv, (uint32_t)M, SL.eoff, s));
+            CK(launch_entry_offsets(nullptr, SL.voff, nv, (uint32_t)M, SL.eoff, s, warp_off, rect_sorted));
             CK(cudaMemcpyAsync(h_eoff, SL.eoff, ((size_t)nv + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
         }

@@ -196,8 +196,10 @@ cudaError_t launch_segment_blocks(const uint32_t *off, int nv, const KeyParams *
 size_t radix_segment_blocks_max(size_t cap, int nv);
 // eoff[v] (v = 0..nv) as launch_entry_offsets, from device counts: records
 // past min(visible, cap_R) and entries past min(total, cap_M) are cut off.
+// warp_off / rect_sorted (optional): as launch_entry_offsets.
 cudaError_t launch_entry_offsets_dev(const uint32_t *off_sorted, const uint32_t *voff, int nv, const BatchInfo *info,
-                                     size_t cap_R, size_t cap_M, uint32_t *eoff, cudaStream_t s);
+                                     size_t cap_R, size_t cap_M, uint32_t *eoff, cudaStream_t s,
+                                     const uint32_t *warp_off = nullptr, const uint2 *rect_sorted = nullptr);
 // Two-level binning.  Stage A: one key per visible (view, Gaussian) record,
 // ((view << zb) | (depth bits - zmin)), value the record index, sorted.
 // Stage B: in that order, one entry per tile of the record's rectangle with
@@ -208,25 +210,33 @@ cudaError_t launch_emit_records(const uint32_t *counts, const uint32_t *pos, con
                                 int zb, uint32_t zmin, uint64_t *keyA, uint32_t *valA, cudaStream_t s,
                                 size_t cap_R = ~(size_t)0, uint32_t *overflow = nullptr);
 // eoff[v] (v = 0..nv) = stage-B tile entries of the views before v, from the
-// stage-B offsets of the records (stage-A order) and voff (device [nv + 1]).
+// stage-B offsets of the records (stage-A order) and voff (device [nv + 1]);
+// with warp_off (per-warp offsets, launch_gather_rects) the offsets come from
+// those and rect_sorted instead of off_sorted.
 cudaError_t launch_entry_offsets(const uint32_t *off_sorted, const uint32_t *voff, int nv, uint32_t M,
-                                 uint32_t *eoff, cudaStream_t s);
+                                 uint32_t *eoff, cudaStream_t s, const uint32_t *warp_off = nullptr,
+                                 const uint2 *rect_sorted = nullptr);
 // d_nrec / d_M (optional): actual counts in device memory for graph replays;
 // entries past cap_M are not written and set *overflow (when given).
 cudaError_t launch_gather_counts(const uint32_t *valA, const uint32_t *counts, size_t nrec, uint32_t *cnt_sorted,
                                  cudaStream_t s, const unsigned long long *d_nrec = nullptr);
-// rect_sorted[i] = rect[valA[i]] and cnt_sorted[i] = its tile count (one
-// gather of the rectangle, in stage-A order).
-cudaError_t launch_gather_rects(const uint32_t *valA, const uint2 *rect, size_t nrec, uint32_t *cnt_sorted,
+// rect_sorted[i] = rect[valA[i]] (one gather of the rectangle, in stage-A
+// order) and warp_cnt[w] = the tiles of records [32 w, 32 w + 32), for
+// ceil(nrec / 32) warps (0 past the live records); an exclusive scan of
+// warp_cnt gives the warps' first tile entries (the warp_off of
+// launch_emit_tiles).
+cudaError_t launch_gather_rects(const uint32_t *valA, const uint2 *rect, size_t nrec, uint32_t *warp_cnt,
                                 uint2 *rect_sorted, cudaStream_t s, const unsigned long long *d_nrec = nullptr);
 // tb: tile keys are v * TT + tile (tb < 0) or (v << tb) | tile (2^tb >= TT),
 // which lets a group of 2^g views be sorted on its low tb + g bits.
 // rect_sorted (optional): the rectangles in stage-A order (read in order
-// instead of gathered from rect).
+// instead of gathered from rect).  warp_off (optional): the first tile entry
+// of each warp's 32 records, used instead of off_sorted.
 cudaError_t launch_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect,
                               int64_t n, int TW, int TH, uint32_t *keyB, uint32_t *valB, cudaStream_t s,
                               const unsigned long long *d_nrec = nullptr, size_t cap_M = ~(size_t)0,
-                              uint32_t *overflow = nullptr, int tb = -1, const uint2 *rect_sorted = nullptr);
+                              uint32_t *overflow = nullptr, int tb = -1, const uint2 *rect_sorted = nullptr,
+                              const uint32_t *warp_off = nullptr);
 cudaError_t launch_ranges(const uint32_t *keys, size_t M, uint2 *ranges, cudaStream_t s,
                           const unsigned long long *d_M = nullptr, int tb = -1, uint32_t TT = 0);
 // canonical keys ((view*tiles + tile) << 32) | depth bits, for verification

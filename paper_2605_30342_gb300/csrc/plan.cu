@@ -251,17 +251,18 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
         bool alt_a = false, alt_b = false;
         PK(radix_sort_segments<uint32_t>(ak0, av0, ak1, av1, blk_a, nblk_a, 32, tmp, &alt_a, cs, true));
         const uint32_t *recs = alt_a ? av1 : av0;
+        // stage-B offsets per warp of 32 records (acnt, aoff hold the warps' counts and offsets)
         PK(launch_gather_rects(recs, rect, R, acnt, rect_sorted, cs, &info->b.visible));
-        PK(exclusive_scan_u32(acnt, aoff, R, tmp, nullptr, cs, false, &info->b.visible));
+        PK(exclusive_scan_u32(acnt, aoff, (R + 31) / 32, tmp, nullptr, cs));
         // stage B: tile keys (view << tb) | tile sorted on 16 bits per group
         // of 2^(16 - tb) views when the tile index fits tb <= 16 bits and the
         // batch's views do not (as the batched call), else view * TT + tile
         const int vb = bits_of((uint64_t)nv - 1), tbits = bits_of((uint64_t)TT - 1);
         const int tb = tbits + vb > 16 && tbits <= 16 && ((nv - 1) >> (16 - tbits)) < 64 ? tbits : -1;
-        PK(launch_emit_tiles(recs, aoff, R, rect, n, TW, TH, bk0, bv0, cs, &info->b.visible, M,
-                             &info->entries_over, tb, rect_sorted));
+        PK(launch_emit_tiles(recs, nullptr, R, rect, n, TW, TH, bk0, bv0, cs, &info->b.visible, M,
+                             &info->entries_over, tb, rect_sorted, aoff));
         if (tb >= 0) {
-            PK(launch_entry_offsets_dev(aoff, voff, nv, &info->b, R, M, eoff, cs));
+            PK(launch_entry_offsets_dev(nullptr, voff, nv, &info->b, R, M, eoff, cs, aoff, rect_sorted));
             PK(launch_segment_blocks(eoff, nv, nullptr, 1 << (16 - tb), M, blk_b, nblk_b, cs));
             PK(radix_sort_segments<uint32_t>(bk0, bv0, bk1, bv1, blk_b, nblk_b, 16, tmp, &alt_b, cs, true));
         } else {

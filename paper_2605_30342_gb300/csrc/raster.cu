@@ -121,11 +121,26 @@ __global__ void k_emit_records(const uint32_t *counts, const uint32_t *pos, cons
 
 // eoff[v] = tile entries of the views before v (v = 0..nv): the stage-B
 // offset of each view's first record (records are in view order)
-__global__ void k_entry_offsets(const uint32_t *off_sorted, const uint32_t *voff, int nv, uint32_t M, uint32_t *eoff)
+__device__ __forceinline__ uint32_t rect_tiles(uint2 rc)
+{
+    return ((rc.x >> 16) - (rc.x & 0xffffu) + 1u) * ((rc.y >> 16) - (rc.y & 0xffffu) + 1u);
+}
+
+// the first tile entry of record r: its warp's offset plus the tiles of the
+// warp's records before it
+__device__ __forceinline__ uint32_t record_entry_offset(const uint32_t *warp_off, const uint2 *rect_sorted, uint32_t r)
+{
+    uint32_t o = warp_off[r >> 5];
+    for (uint32_t q = r & ~31u; q < r; ++q) o += rect_tiles(rect_sorted[q]);
+    return o;
+}
+
+__global__ void k_entry_offsets(const uint32_t *off_sorted, const uint32_t *voff, int nv, uint32_t M, uint32_t *eoff,
+                                const uint32_t *warp_off, const uint2 *rect_sorted)
 {
     for (int v = threadIdx.x; v <= nv; v += blockDim.x) {
         const uint32_t r = voff[v];
-        eoff[v] = v < nv && r < voff[nv] ? off_sorted[r] : M;
+        eoff[v] = v < nv && r < voff[nv] ? (warp_off ? record_entry_offset(warp_off, rect_sorted, r) : off_sorted[r]) : M;
     }
 }
 
@@ -139,15 +154,24 @@ __global__ void k_gather_counts(const uint32_t *valA, const uint32_t *counts, si
 
 // the tile rectangle of each record in stage-A order (one gather), and its
 // tile count, which the rectangle gives
-__global__ void k_gather_rects(const uint32_t *valA, const uint2 *rect, size_t nrec, uint32_t *cnt_sorted,
+// warp_cnt[w] = tiles of the records [32 w, 32 w + 32) (0 past the live
+// records), for every warp of the capacity (blocks of whole warps)
+__global__ void k_gather_rects(const uint32_t *valA, const uint2 *rect, size_t nrec, uint32_t *warp_cnt,
                                uint2 *rect_sorted, const unsigned long long *d_nrec)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nrec || (d_nrec && i >= (size_t)*d_nrec)) return;
-    const uint2 rc = rect[valA[i]];
-    rect_sorted[i] = rc;
-    cnt_sorted[i] = ((rc.x >> 16) - (rc.x & 0xffffu) + 1u) * ((rc.y >> 16) - (rc.y & 0xffffu) + 1u);
+    size_t live = nrec;
+    if (d_nrec && (size_t)*d_nrec < live) live = (size_t)*d_nrec;
+    uint32_t cnt = 0u;
+    if (i < live) {
+        const uint2 rc = rect[valA[i]];
+        rect_sorted[i] = rc;
+        cnt = rect_tiles(rc);
+    }
+    const uint32_t ws = __reduce_add_sync(0xffffffffu, cnt);
+    if ((threadIdx.x & 31u) == 0u && i < nrec) warp_cnt[i >> 5] = ws;
 }
+
 
 // Tile keys: v * TT + tile (tb < 0), or (v << tb) | tile with 2^tb >= TT, so
 // that the keys of a group of 2^g views differ only in their low tb + g bits.
@@ -162,7 +186,8 @@ __device__ __forceinline__ uint32_t tile_index(uint32_t key, int tb, uint32_t TT
 // over the warp's prefix counts, so the stores are coalesced.
 __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect, int64_t n,
                              int TW, int TH, uint32_t *keyB, uint32_t *valB, const unsigned long long *d_nrec,
-                             size_t cap_M, uint32_t *overflow, int tb, const uint2 *rect_sorted)
+                             size_t cap_M, uint32_t *overflow, int tb, const uint2 *rect_sorted,
+                             const uint32_t *warp_off)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = (int)(threadIdx.x & 31u);
@@ -180,8 +205,7 @@ __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, s
         w = (rc.x >> 16) - x0 + 1u;
         cnt = w * ((rc.y >> 16) - y0 + 1u);
         kfirst = (tb < 0 ? v * (uint32_t)(TW * TH) : v << tb) + y0 * (uint32_t)TW + x0;
-        off = off_sorted[i];
-        if ((size_t)off + cnt > cap_M && overflow) *overflow = 1u;
+        off = warp_off ? warp_off[i >> 5] : off_sorted[i];
     }
     const float rw = 1.0f / (float)w;
     uint32_t inc = cnt;
@@ -193,6 +217,7 @@ __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, s
     const uint32_t excl = inc - cnt;
     const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
     const uint32_t base = __shfl_sync(0xffffffffu, off, 0);   // the valid lanes are a prefix of the warp
+    if (cnt && (size_t)base + excl + cnt > cap_M && overflow) *overflow = 1u;
     const uint32_t room = cap_M > (size_t)base ? (uint32_t)min(cap_M - (size_t)base, (size_t)0xffffffffu) : 0u;
     for (uint32_t j0 = 0; j0 < total; j0 += 32) {
         const uint32_t j = j0 + (uint32_t)lane;
@@ -826,10 +851,10 @@ cudaError_t launch_emit_records(const uint32_t *counts, const uint32_t *pos, con
 }
 
 cudaError_t launch_entry_offsets(const uint32_t *off_sorted, const uint32_t *voff, int nv, uint32_t M,
-                                 uint32_t *eoff, cudaStream_t s)
+                                 uint32_t *eoff, cudaStream_t s, const uint32_t *warp_off, const uint2 *rect_sorted)
 {
     if (nv <= 0) return cudaSuccess;
-    k_entry_offsets<<<1, 256, 0, s>>>(off_sorted, voff, nv, M, eoff); count_launch();
+    k_entry_offsets<<<1, 256, 0, s>>>(off_sorted, voff, nv, M, eoff, warp_off, rect_sorted); count_launch();
     return cudaGetLastError();
 }
 
@@ -841,22 +866,22 @@ cudaError_t launch_gather_counts(const uint32_t *valA, const uint32_t *counts, s
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_rects(const uint32_t *valA, const uint2 *rect, size_t nrec, uint32_t *cnt_sorted,
+cudaError_t launch_gather_rects(const uint32_t *valA, const uint2 *rect, size_t nrec, uint32_t *warp_cnt,
                                 uint2 *rect_sorted, cudaStream_t s, const unsigned long long *d_nrec)
 {
     if (nrec == 0) return cudaSuccess;
-    k_gather_rects<<<nblk(nrec, 256), 256, 0, s>>>(valA, rect, nrec, cnt_sorted, rect_sorted, d_nrec); count_launch();
+    k_gather_rects<<<nblk(nrec, 256), 256, 0, s>>>(valA, rect, nrec, warp_cnt, rect_sorted, d_nrec); count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect,
                               int64_t n, int TW, int TH, uint32_t *keyB, uint32_t *valB, cudaStream_t s,
                               const unsigned long long *d_nrec, size_t cap_M, uint32_t *overflow, int tb,
-                              const uint2 *rect_sorted)
+                              const uint2 *rect_sorted, const uint32_t *warp_off)
 {
     if (nrec == 0) return cudaSuccess;
     k_emit_tiles<<<nblk(nrec, 256), 256, 0, s>>>(valA, off_sorted, nrec, rect, n, TW, TH, keyB, valB, d_nrec, cap_M,
-                                                 overflow, tb, rect_sorted); count_launch();
+                                                 overflow, tb, rect_sorted, warp_off); count_launch();
     return cudaGetLastError();
 }
 
