@@ -199,8 +199,10 @@ __device__ __forceinline__ bool may_have_tiles(const gavis_camera &cam, const Sc
 }
 
 // VAR: per-Gaussian colour covariance from coefficient variances
+// Geometry-only launches fit six CTAs per SM (80 registers); the appearance
+// launches keep 64 coefficient registers per lane and fit four.
 template <int LC, int LV, bool UA, bool VAR>
-__global__ void __launch_bounds__(128, 4) k_project(ProjectArgs a)
+__global__ void __launch_bounds__(128, UA ? 4 : 6) k_project(ProjectArgs a)
 {
     extern __shared__ gavis_camera s_cams[];   // nv cameras, then their screen-bound factors
     ScreenBound *s_sb = reinterpret_cast<ScreenBound *>(s_cams + a.nv);
