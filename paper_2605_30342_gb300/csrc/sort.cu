@@ -95,15 +95,27 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_partials(unsigned long lo
     }
 }
 
+// self_prefix: partials hold the chunks' plain sums, and each block adds up
+// those of the chunks before it (no separate scan of the partials)
 template <bool FLAGS>
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *in, uint32_t *out, size_t n,
                                                              const unsigned long long *partials,
-                                                             const unsigned long long *d_n)
+                                                             const unsigned long long *d_n, bool self_prefix)
 {
     __shared__ uint32_t s_warp[32];
+    __shared__ unsigned long long s_sum[32];
+    __shared__ unsigned long long s_pre;
     if (d_n && *d_n < n) n = (size_t)*d_n;
     if ((size_t)blockIdx.x * kScanChunk >= n) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (self_prefix) {
+        unsigned long long acc = 0;
+        for (unsigned c = threadIdx.x; c < blockIdx.x; c += kScanThreads) acc += partials[c];
+        acc = block_sum_u64(acc, s_sum);
+        if (threadIdx.x == 0) s_pre = acc;
+        __syncthreads();
+    }
+    const unsigned long long chunk_pre = self_prefix ? s_pre : partials[blockIdx.x];
     const size_t base = (size_t)blockIdx.x * kScanChunk + (size_t)threadIdx.x * kScanItems;
     uint32_t x[kScanItems];
     uint32_t sum = 0;
@@ -132,7 +144,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *in,
         s_warp[lane] = w;   // inclusive over warps
     }
     __syncthreads();
-    uint32_t run = (uint32_t)partials[blockIdx.x] + (warp ? s_warp[warp - 1] : 0u) + inc - sum;
+    uint32_t run = (uint32_t)chunk_pre + (warp ? s_warp[warp - 1] : 0u) + inc - sum;
 #pragma unroll
     for (int r = 0; r < kScanItems; ++r) {
         size_t i = base + r;
@@ -558,12 +570,18 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, void
     } else {
         k_scan_reduce<false><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partials, d_n); count_launch();
     }
-    k_scan_partials<<<1, kScanThreads, 0, s>>>(partials, (int)nb, d_total); count_launch();
-    if (flags) {
-        k_scan_apply<true><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partials, d_n); count_launch();
-    } else {
-        k_scan_apply<false><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partials, d_n); count_launch();
+    // a requested total takes the separate scan of the partials; otherwise
+    // each apply block sums the partials before it
+    const bool self_prefix = d_total == nullptr;
+    if (!self_prefix) {
+        k_scan_partials<<<1, kScanThreads, 0, s>>>(partials, (int)nb, d_total); count_launch();
     }
+    if (flags) {
+        k_scan_apply<true><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partials, d_n, self_prefix);
+    } else {
+        k_scan_apply<false><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partials, d_n, self_prefix);
+    }
+    count_launch();
     return cudaGetLastError();
 }
 
