@@ -181,9 +181,11 @@ __device__ __forceinline__ uint32_t tile_index(uint32_t key, int tb, uint32_t TT
 }
 
 // stage B: the tiles of each record, in stage-A order.  A warp takes 32
-// consecutive records, whose entries are contiguous; its lanes write those
-// entries in order, lane j of a round finding its record by a binary search
-// over the warp's prefix counts, so the stores are coalesced.
+// consecutive records, whose entries are contiguous (from the warp's offset,
+// warp_off, or its first record's, off_sorted); its lanes write those
+// entries in order, lane j of a round finding its record from a ballot of the
+// records that start before the round and an OR of the window positions
+// where the others start, so the stores are coalesced.
 __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect, int64_t n,
                              int TW, int TH, uint32_t *keyB, uint32_t *valB, const unsigned long long *d_nrec,
                              size_t cap_M, uint32_t *overflow, int tb, const uint2 *rect_sorted,
