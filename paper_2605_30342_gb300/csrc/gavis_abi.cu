@@ -575,7 +575,7 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
         CK(launch_emit_tiles(recs, nullptr, (size_t)nrec, RL.rect, n, G.TW, G.TH, KL.b_k0, KL.b_v0, s, nullptr,
                              ~(size_t)0, nullptr, tb, rect_sorted, warp_off));
         if (tb >= 0) {   // tile entries before each view: a second read-back
-            CK(launch_entry_offsets(nullptr, SL.voff, nv, (uint32_t)M, SL.eoff, s, warp_off, rect_sorted));
+            CK(launch_entry_offsets(warp_off, rect_sorted, SL.voff, nv, (uint32_t)M, SL.eoff, s));
             CK(cudaMemcpyAsync(h_eoff, SL.eoff, ((size_t)nv + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
         }

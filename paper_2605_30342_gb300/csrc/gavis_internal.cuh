@@ -196,10 +196,9 @@ cudaError_t launch_segment_blocks(const uint32_t *off, int nv, const KeyParams *
 size_t radix_segment_blocks_max(size_t cap, int nv);
 // eoff[v] (v = 0..nv) as launch_entry_offsets, from device counts: records
 // past min(visible, cap_R) and entries past min(total, cap_M) are cut off.
-// warp_off / rect_sorted (optional): as launch_entry_offsets.
-cudaError_t launch_entry_offsets_dev(const uint32_t *off_sorted, const uint32_t *voff, int nv, const BatchInfo *info,
-                                     size_t cap_R, size_t cap_M, uint32_t *eoff, cudaStream_t s,
-                                     const uint32_t *warp_off = nullptr, const uint2 *rect_sorted = nullptr);
+cudaError_t launch_entry_offsets_dev(const uint32_t *warp_off, const uint2 *rect_sorted, const uint32_t *voff, int nv,
+                                     const BatchInfo *info, size_t cap_R, size_t cap_M, uint32_t *eoff,
+                                     cudaStream_t s);
 // Two-level binning.  Stage A: one key per visible (view, Gaussian) record,
 // ((view << zb) | (depth bits - zmin)), value the record index, sorted.
 // Stage B: in that order, one entry per tile of the record's rectangle with
@@ -209,13 +208,12 @@ cudaError_t launch_entry_offsets_dev(const uint32_t *off_sorted, const uint32_t 
 cudaError_t launch_emit_records(const uint32_t *counts, const uint32_t *pos, const GeoRec *geo, int nv, int64_t n,
                                 int zb, uint32_t zmin, uint64_t *keyA, uint32_t *valA, cudaStream_t s,
                                 size_t cap_R = ~(size_t)0, uint32_t *overflow = nullptr);
-// eoff[v] (v = 0..nv) = stage-B tile entries of the views before v, from the
-// stage-B offsets of the records (stage-A order) and voff (device [nv + 1]);
-// with warp_off (per-warp offsets, launch_gather_rects) the offsets come from
-// those and rect_sorted instead of off_sorted.
-cudaError_t launch_entry_offsets(const uint32_t *off_sorted, const uint32_t *voff, int nv, uint32_t M,
-                                 uint32_t *eoff, cudaStream_t s, const uint32_t *warp_off = nullptr,
-                                 const uint2 *rect_sorted = nullptr);
+// eoff[v] (v = 0..nv) = stage-B tile entries of the views before v: record
+// voff[v]'s first entry, from the per-warp offsets (warp_off, of
+// launch_gather_rects) and the rectangles of the warp's earlier records
+// (rect_sorted); voff is device [nv + 1].
+cudaError_t launch_entry_offsets(const uint32_t *warp_off, const uint2 *rect_sorted, const uint32_t *voff, int nv,
+                                 uint32_t M, uint32_t *eoff, cudaStream_t s);
 // d_nrec / d_M (optional): actual counts in device memory for graph replays;
 // entries past cap_M are not written and set *overflow (when given).
 cudaError_t launch_gather_counts(const uint32_t *valA, const uint32_t *counts, size_t nrec, uint32_t *cnt_sorted,

@@ -262,7 +262,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
         PK(launch_emit_tiles(recs, nullptr, R, rect, n, TW, TH, bk0, bv0, cs, &info->b.visible, M,
                              &info->entries_over, tb, rect_sorted, aoff));
         if (tb >= 0) {
-            PK(launch_entry_offsets_dev(nullptr, voff, nv, &info->b, R, M, eoff, cs, aoff, rect_sorted));
+            PK(launch_entry_offsets_dev(aoff, rect_sorted, voff, nv, &info->b, R, M, eoff, cs));
             PK(launch_segment_blocks(eoff, nv, nullptr, 1 << (16 - tb), M, blk_b, nblk_b, cs));
             PK(radix_sort_segments<uint32_t>(bk0, bv0, bk1, bv1, blk_b, nblk_b, 16, tmp, &alt_b, cs, true));
         } else {

@@ -135,12 +135,12 @@ __device__ __forceinline__ uint32_t record_entry_offset(const uint32_t *warp_off
     return o;
 }
 
-__global__ void k_entry_offsets(const uint32_t *off_sorted, const uint32_t *voff, int nv, uint32_t M, uint32_t *eoff,
-                                const uint32_t *warp_off, const uint2 *rect_sorted)
+__global__ void k_entry_offsets(const uint32_t *warp_off, const uint2 *rect_sorted, const uint32_t *voff, int nv,
+                                uint32_t M, uint32_t *eoff)
 {
     for (int v = threadIdx.x; v <= nv; v += blockDim.x) {
         const uint32_t r = voff[v];
-        eoff[v] = v < nv && r < voff[nv] ? (warp_off ? record_entry_offset(warp_off, rect_sorted, r) : off_sorted[r]) : M;
+        eoff[v] = v < nv && r < voff[nv] ? record_entry_offset(warp_off, rect_sorted, r) : M;
     }
 }
 
@@ -852,11 +852,11 @@ cudaError_t launch_emit_records(const uint32_t *counts, const uint32_t *pos, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_entry_offsets(const uint32_t *off_sorted, const uint32_t *voff, int nv, uint32_t M,
-                                 uint32_t *eoff, cudaStream_t s, const uint32_t *warp_off, const uint2 *rect_sorted)
+cudaError_t launch_entry_offsets(const uint32_t *warp_off, const uint2 *rect_sorted, const uint32_t *voff, int nv,
+                                 uint32_t M, uint32_t *eoff, cudaStream_t s)
 {
     if (nv <= 0) return cudaSuccess;
-    k_entry_offsets<<<1, 256, 0, s>>>(off_sorted, voff, nv, M, eoff, warp_off, rect_sorted); count_launch();
+    k_entry_offsets<<<1, 256, 0, s>>>(warp_off, rect_sorted, voff, nv, M, eoff); count_launch();
     return cudaGetLastError();
 }
 

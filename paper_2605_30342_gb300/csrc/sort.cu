@@ -316,11 +316,11 @@ __global__ void __launch_bounds__(1024) k_segment_blocks(const uint32_t *off, in
     }
 }
 
-// warp_off (optional): per-warp entry offsets; record r's offset is its
-// warp's plus the tiles of the warp's records before it (rect_sorted)
-__global__ void k_entry_offsets_dev(const uint32_t *off_sorted, const uint32_t *voff, int nv, const BatchInfo *info,
-                                    unsigned long long cap_R, unsigned long long cap_M, uint32_t *eoff,
-                                    const uint32_t *warp_off, const uint2 *rect_sorted)
+// record r's first tile entry: its warp's offset (warp_off) plus the tiles
+// of the warp's records before it (rect_sorted)
+__global__ void k_entry_offsets_dev(const uint32_t *warp_off, const uint2 *rect_sorted, const uint32_t *voff, int nv,
+                                    const BatchInfo *info, unsigned long long cap_R, unsigned long long cap_M,
+                                    uint32_t *eoff)
 {
     const unsigned long long nrec = info->visible < cap_R ? info->visible : cap_R;
     const unsigned long long M = info->total < cap_M ? info->total : cap_M;
@@ -328,16 +328,12 @@ __global__ void k_entry_offsets_dev(const uint32_t *off_sorted, const uint32_t *
         const uint32_t r = voff[v];
         unsigned long long e = M;
         if (v < nv && (unsigned long long)r < nrec) {
-            if (warp_off) {
-                uint32_t o = warp_off[r >> 5];
-                for (uint32_t q = r & ~31u; q < r; ++q) {
-                    const uint2 rc = rect_sorted[q];
-                    o += ((rc.x >> 16) - (rc.x & 0xffffu) + 1u) * ((rc.y >> 16) - (rc.y & 0xffffu) + 1u);
-                }
-                e = o;
-            } else {
-                e = off_sorted[r];
+            uint32_t o = warp_off[r >> 5];
+            for (uint32_t q = r & ~31u; q < r; ++q) {
+                const uint2 rc = rect_sorted[q];
+                o += ((rc.x >> 16) - (rc.x & 0xffffu) + 1u) * ((rc.y >> 16) - (rc.y & 0xffffu) + 1u);
             }
+            e = o;
         }
         eoff[v] = (uint32_t)(e < M ? e : M);
     }
@@ -638,12 +634,11 @@ cudaError_t launch_segment_blocks(const uint32_t *off, int nv, const KeyParams *
     return cudaGetLastError();
 }
 
-cudaError_t launch_entry_offsets_dev(const uint32_t *off_sorted, const uint32_t *voff, int nv, const BatchInfo *info,
-                                     size_t cap_R, size_t cap_M, uint32_t *eoff, cudaStream_t s,
-                                     const uint32_t *warp_off, const uint2 *rect_sorted)
+cudaError_t launch_entry_offsets_dev(const uint32_t *warp_off, const uint2 *rect_sorted, const uint32_t *voff, int nv,
+                                     const BatchInfo *info, size_t cap_R, size_t cap_M, uint32_t *eoff, cudaStream_t s)
 {
     if (nv <= 0) return cudaSuccess;
-    k_entry_offsets_dev<<<1, 256, 0, s>>>(off_sorted, voff, nv, info, cap_R, cap_M, eoff, warp_off, rect_sorted);
+    k_entry_offsets_dev<<<1, 256, 0, s>>>(warp_off, rect_sorted, voff, nv, info, cap_R, cap_M, eoff);
     count_launch();
     return cudaGetLastError();
 }
