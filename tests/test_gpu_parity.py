@@ -235,11 +235,12 @@ def test_calls_on_two_streams_are_ordered(ctx, gv):
 # --------------------------------------------------------------------------- VF CONST
 
 @pytest.mark.parametrize("name", list(CASES))
-def test_single_view_visibility_parity(ctx, gv, name):
+@pytest.mark.parametrize("tile", [16, 8, 32])
+def test_single_view_visibility_parity(ctx, gv, name, tile):
     c = case(name)
     sc, cams = c["scene"], c["train"][:3]
     gs = gpu_scene(gv, sc)
-    sumT, cnt = ctx.debug_visibility(gs, cams)
+    sumT, cnt = ctx.debug_visibility(gs, cams, gv.Params(tile=tile))
     sumT, cnt = sumT.cpu().numpy(), cnt.cpu().numpy()
     for v, cam in enumerate(cams):
         rs, rc, amb, _, b = oracle.visibility_view(cam, sc, want_bounds=True)
@@ -271,6 +272,22 @@ def test_vf_build_parity(ctx, gv, name, dtype):
     err = (np.abs(g - ref) - rad - rel * (np.abs(ref) + rad)) / P
     n_rad = int((rad.max(1) > 0).sum())
     assert err.max() <= TOL, (err.max(), f"{n_rad} of {sc.n} Gaussians have a nonzero radius")
+
+
+@pytest.mark.parametrize("name", ["tiny", "room_small"])
+@pytest.mark.parametrize("tile", [8, 32])
+def test_vf_build_parity_other_tiles(ctx, gv, name, tile):
+    """The field build at the tile edges other than the default (the
+    visibility pass runs 1 or 16 warps per tile there)."""
+    c = case(name)
+    sc, train = c["scene"], c["train"]
+    gs = gpu_scene(gv, sc)
+    L = c["vf_degree"]
+    vf = ctx.vf_build(gs, train, degree=L, dtype=torch.float32, params=gv.Params(tile=tile, vf_degree=L))
+    g = vf.coeffs.double().cpu().numpy()
+    ref, _, _, rad = oracle.vf_build(train, sc, L, want_rad=True)
+    err = (np.abs(g - ref) - rad) / len(train)
+    assert err.max() <= TOL, err.max()
 
 
 @pytest.mark.parametrize("L", [4, 5])
