@@ -6,7 +6,9 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import scenegen as sg
+from _util import GAP, TOL, compare_views, score_excess, sorted_gap
 
 pytestmark = pytest.mark.gpu
 
@@ -72,6 +74,32 @@ def test_alone_equals_mix(gv, scenes):
     again = srv.wait(rid)
     assert torch.equal(again["score"], alone[0]["score"])
     srv.close()
+
+
+def test_server_matches_oracle(gv):
+    """Through the server against the oracle directly: two requests at two
+    resolutions on one scene whose field is the oracle's VF CONST, submitted
+    together so that they share batches; each request's entropy maps and
+    scores agree with the oracle's VF QUERY + UA raster + entropy score."""
+    c = sg.config(1, n=900, n_train=3, n_cand=4, train_wh=(100, 75), cand_wh=(100, 75))
+    sc, L = c["scene"], c["vf_degree"]
+    g, _, _ = oracle.vf_build(c["train"], sc, L)
+    g32 = g.astype(np.float32)
+    gs = gv.Gaussians.from_numpy(sc)
+    vf = gv.VisibilityField(torch.as_tensor(g32).cuda(), L, len(c["train"]), 1.0)
+    reqs = [c["cand"], sg.fibonacci_cameras(3, 3.1, 64, 48)]
+    srv = gv.Server(0, n_workers=1, max_views_per_batch=16)
+    sid = srv.add_scene(gs, vf)
+    rids = [srv.submit(sid, cams, params=gv.Params(vf_degree=L), want_unc=True) for cams in reqs]
+    res = [srv.wait(r) for r in rids]
+    srv.close()
+    for cams, r in zip(reqs, res):
+        ref = oracle.score_views(sc, g32.astype(np.float64), L, len(c["train"]), cams)
+        err, n_band = compare_views(r["unc"].cpu().numpy(), None, ref)
+        assert err <= TOL, (err, n_band)
+        assert score_excess(r["score"].cpu().numpy(), ref).max() <= TOL
+        if sorted_gap(ref["score"]) > GAP:
+            assert r["best"] == ref["best"]
 
 
 def test_admission_respects_budget(gv, scenes):

@@ -14,8 +14,9 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import scenegen as sg
-from _util import TOL
+from _util import GAP, TOL, compare_views, score_excess, sorted_gap
 
 pytestmark = pytest.mark.gpu
 
@@ -67,6 +68,34 @@ def test_noalloc_matches_score_views_twice(gv, k, kw):
         assert (rgb - ref["rgb"][0]).abs().max().item() <= TOL
         assert abs(score.item() - ref["score"][0].item()) <= TOL
     ctx.close()
+
+
+def test_noalloc_matches_oracle(gv):
+    """Against the oracle directly: the field comes from the oracle's VF CONST
+    (rounded to f32), each view is scored by the allocation-free call, and
+    per-pixel entropy, RGB and the view score agree with the oracle's
+    VF QUERY + UA raster + entropy score within the parity tolerance."""
+    c = sg.config(1, n=900, n_train=3, n_cand=3, train_wh=(100, 75), cand_wh=(100, 75))
+    sc, cand, L = c["scene"], c["cand"], c["vf_degree"]
+    g, _, _ = oracle.vf_build(c["train"], sc, L)
+    g32 = g.astype(np.float32)
+    gs = gv.Gaussians.from_numpy(sc)
+    vf = gv.VisibilityField(torch.as_tensor(g32).cuda(), L, len(c["train"]), 1.0)
+    ref = oracle.score_views(sc, g32.astype(np.float64), L, len(c["train"]), cand)
+    prm = gv.Params(vf_degree=L)
+    unc_all, rgb_all, score_all = [], [], []
+    for cam in cand:
+        rc, msg, rgb, unc, score = call_noalloc(gv, gs, vf, cam, prm)
+        assert rc == 0, msg
+        unc_all.append(unc.cpu().numpy())
+        rgb_all.append(rgb.cpu().numpy())
+        score_all.append(score.item())
+    err, n_band = compare_views(np.stack(unc_all), np.stack(rgb_all), ref)
+    assert err <= TOL, (err, n_band)
+    score_all = np.asarray(score_all, dtype=np.float32)
+    assert score_excess(score_all, ref).max() <= TOL
+    if sorted_gap(ref["score"]) > GAP:
+        assert int(np.argmax(score_all)) == ref["best"]
 
 
 def test_noalloc_rejects_oversized_inputs(gv):
