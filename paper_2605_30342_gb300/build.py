@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libgavis.so")
-SOURCES = ["gavis_abi.cu", "project.cu", "sort.cu", "raster.cu", "noalloc.cu", "server.cu", "plan.cu"]
+SOURCES = ["gavis_abi.cu", "project.cu", "sort.cu", "raster.cu", "bin.cu", "noalloc.cu", "server.cu", "plan.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -315,33 +315,44 @@ RecLayout rec_layout(void *base, size_t nvn, bool ua, size_t nwords)
 struct KeyLayout {
     uint64_t *a_k0, *a_k1;
     uint32_t *a_v0, *a_v1, *a_cnt, *a_off;
-    uint32_t *b_k0, *b_k1, *b_v0, *b_v1;
+    uint32_t *b_k0, *b_k1, *b_v0, *b_v1;   // stage B by counting: b_v0 only
     RsBlock *blk_a, *blk_b;   // block tables of the segmented sorts
+    BinLayout bin;            // stage B by counting
     void *tmp;
     size_t bytes;
 };
 
-// nseg: the most segments (view groups) either sort splits into
-KeyLayout key_layout(void *base, size_t nrec, size_t M, size_t nseg)
+// nseg: the most segments (view groups) either sort splits into; bin_tt > 0:
+// stage B by counting over nv views of bin_tt tiles (no stage-B sort space)
+KeyLayout key_layout(void *base, size_t nrec, size_t M, size_t nseg, int nv = 0, int bin_tt = 0)
 {
     KeyLayout L;
+    memset(&L, 0, sizeof(L));
     char *p = reinterpret_cast<char *>(base);
     size_t off = 0;
     auto take = [&](size_t b) { char *q = p ? p + off : nullptr; off += align256(b); return q; };
+    const bool counting = bin_tt > 0;
     L.a_k0 = reinterpret_cast<uint64_t *>(take(nrec * 8));
     L.a_k1 = reinterpret_cast<uint64_t *>(take(nrec * 8));
     L.a_v0 = reinterpret_cast<uint32_t *>(take(nrec * 4));
     L.a_v1 = reinterpret_cast<uint32_t *>(take(nrec * 4));
     L.a_cnt = reinterpret_cast<uint32_t *>(take(nrec * 4));
     L.a_off = reinterpret_cast<uint32_t *>(take(nrec * 4));
-    L.b_k0 = reinterpret_cast<uint32_t *>(take(M * 4));
-    L.b_k1 = reinterpret_cast<uint32_t *>(take(M * 4));
     L.b_v0 = reinterpret_cast<uint32_t *>(take(M * 4));
-    L.b_v1 = reinterpret_cast<uint32_t *>(take(M * 4));
+    if (!counting) {
+        L.b_k0 = reinterpret_cast<uint32_t *>(take(M * 4));
+        L.b_k1 = reinterpret_cast<uint32_t *>(take(M * 4));
+        L.b_v1 = reinterpret_cast<uint32_t *>(take(M * 4));
+        L.blk_b = reinterpret_cast<RsBlock *>(take((M / kRadixTile + nseg + 1) * sizeof(RsBlock)));
+    }
     L.blk_a = reinterpret_cast<RsBlock *>(take((nrec / kRadixTile + nseg + 1) * sizeof(RsBlock)));
-    L.blk_b = reinterpret_cast<RsBlock *>(take((M / kRadixTile + nseg + 1) * sizeof(RsBlock)));
-    const size_t big = (nrec > M ? nrec : M) + (nseg + 1) * (size_t)kRadixTile;   // a partial block per segment at most
+    const size_t sorted = counting ? nrec : (nrec > M ? nrec : M);
+    const size_t big = sorted + (nseg + 1) * (size_t)kRadixTile;   // a partial block per segment at most
     L.tmp = take(radix_tmp_bytes(big) + scan_tmp_bytes(big) + 64);
+    if (counting) {
+        const BinLayout b0 = bin_layout(nullptr, nrec, nv, bin_tt);
+        L.bin = bin_layout(take(b0.bytes), nrec, nv, bin_tt);
+    }
     L.bytes = off;
     return L;
 }
@@ -507,9 +518,12 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     }
     const int nseg_b = tb < 0 ? 1 : (nv + (1 << gbb) - 1) >> gbb;
     const size_t nseg = (size_t)(nseg_a > nseg_b ? nseg_a : nseg_b);
-    KeyLayout KL = key_layout(nullptr, (size_t)nrec, (size_t)M, nseg);
+    // stage B by counting where a view's tile counters fit shared memory
+    const bool counting = bin_by_counting(G.TT);
+    const int bin_tt = counting ? G.TT : 0;
+    KeyLayout KL = key_layout(nullptr, (size_t)nrec, (size_t)M, nseg, nv, bin_tt);
     if ((rc = ensure(ctx, ctx->keys, KL.bytes, s)) != GAVIS_OK) return rc;
-    KL = key_layout(ctx->keys.p, (size_t)nrec, (size_t)M, nseg);
+    KL = key_layout(ctx->keys.p, (size_t)nrec, (size_t)M, nseg, nv, bin_tt);
     // block table of a segmented sort over the segments [seg[s], seg[s+1]),
     // staged through pinned memory (the previous table's copy has finished:
     // a stream synchronisation lies between any two uses)
@@ -559,52 +573,63 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
         CK(radix_sort_segments<uint32_t>(k0, KL.a_v0, k1, KL.a_v1, KL.blk_a, nblk, gb + zb, KL.tmp, &alt_a, s));
     }
     const uint32_t *recs = alt_a ? KL.a_v1 : KL.a_v0;
-    // stage B: tile entries in stage-A order, i.e. view by view.  When the
-    // tile index fits in tb <= 16 bits the keys are (view << tb) | tile and
-    // each group of 2^(16 - tb) views is sorted on 16 bits (two passes) over
-    // its contiguous entries; otherwise keys are view * TT + tile, one sort.
-    {
+    const uint32_t *keys = nullptr, *vals = KL.b_v0;
+    if (counting) {
+        // stage B by counting: the lists and their ranges straight from the
+        // records' rectangles in stage-A order
         Stage st(ctx, GAVIS_STAGE_EMIT, s);
-        // the stage-A keys are spent: their buffer holds the rectangles in stage-A order
-        // the stage-B offsets per warp of 32 records (each warp scans its own records)
-        uint2 *rect_sorted = reinterpret_cast<uint2 *>(KL.a_k0);
-        uint32_t *warp_cnt = KL.a_cnt, *warp_off = KL.a_off;
-        const size_t nwarps = ((size_t)nrec + 31) / 32;
-        CK(launch_gather_rects(recs, RL.rect, (size_t)nrec, warp_cnt, rect_sorted, s));
-        CK(exclusive_scan_u32(warp_cnt, warp_off, nwarps, KL.tmp, nullptr, s));
-        CK(launch_emit_tiles(recs, nullptr, (size_t)nrec, RL.rect, n, G.TW, G.TH, KL.b_k0, KL.b_v0, s, nullptr,
-                             ~(size_t)0, nullptr, tb, rect_sorted, warp_off));
-        if (tb >= 0) {   // tile entries before each view: a second read-back
-            CK(launch_entry_offsets(warp_off, rect_sorted, SL.voff, nv, (uint32_t)M, SL.eoff, s));
-            CK(cudaMemcpyAsync(h_eoff, SL.eoff, ((size_t)nv + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-        }
-    }
-    {
-        Stage st(ctx, GAVIS_STAGE_SORT, s);
-        if (tb < 0) {
-            CK(radix_sort_pairs<uint32_t>(KL.b_k0, KL.b_v0, KL.b_k1, KL.b_v1, (size_t)M, bits_of((uint64_t)nvt - 1),
-                                          KL.tmp, &alt_b, s));
-        } else {
-            const int gsz = 1 << gbb;
-            std::vector<uint64_t> seg((size_t)nseg_b + 1);
-            for (int g = 0; g <= nseg_b; ++g) {
-                seg[(size_t)g] = h_eoff[g * gsz < nv ? g * gsz : nv];
-                if (seg[(size_t)g] > M || (g > 0 && seg[(size_t)g] < seg[(size_t)g - 1]))
-                    return fail(ctx, GAVIS_ERR_CUDA, "internal: inconsistent per-view entry offsets");
+        uint2 *rect_sorted = reinterpret_cast<uint2 *>(KL.a_k0);   // the stage-A keys are spent
+        CK(launch_gather_rects(recs, RL.rect, (size_t)nrec, KL.a_cnt, rect_sorted, s));
+        CK(launch_bin_tiles(recs, rect_sorted, SL.voff, nv, n, G.TW, G.TT, (size_t)nrec, nullptr, KL.bin, SL.ranges,
+                            KL.b_v0, ~(size_t)0, nullptr, s));
+    } else {
+        // stage B: tile entries in stage-A order, i.e. view by view.  When the
+        // tile index fits in tb <= 16 bits the keys are (view << tb) | tile and
+        // each group of 2^(16 - tb) views is sorted on 16 bits (two passes) over
+        // its contiguous entries; otherwise keys are view * TT + tile, one sort.
+        {
+            Stage st(ctx, GAVIS_STAGE_EMIT, s);
+            // the stage-A keys are spent: their buffer holds the rectangles in stage-A order
+            // the stage-B offsets per warp of 32 records (each warp scans its own records)
+            uint2 *rect_sorted = reinterpret_cast<uint2 *>(KL.a_k0);
+            uint32_t *warp_cnt = KL.a_cnt, *warp_off = KL.a_off;
+            const size_t nwarps = ((size_t)nrec + 31) / 32;
+            CK(launch_gather_rects(recs, RL.rect, (size_t)nrec, warp_cnt, rect_sorted, s));
+            CK(exclusive_scan_u32(warp_cnt, warp_off, nwarps, KL.tmp, nullptr, s));
+            CK(launch_emit_tiles(recs, nullptr, (size_t)nrec, RL.rect, n, G.TW, G.TH, KL.b_k0, KL.b_v0, s, nullptr,
+                                 ~(size_t)0, nullptr, tb, rect_sorted, warp_off));
+            if (tb >= 0) {   // tile entries before each view: a second read-back
+                CK(launch_entry_offsets(warp_off, rect_sorted, SL.voff, nv, (uint32_t)M, SL.eoff, s));
+                CK(cudaMemcpyAsync(h_eoff, SL.eoff, ((size_t)nv + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
             }
-            size_t nblk = 0;
-            if ((rc = upload_blocks(seg, KL.blk_b, nblk)) != GAVIS_OK) return rc;
-            CK(radix_sort_segments<uint32_t>(KL.b_k0, KL.b_v0, KL.b_k1, KL.b_v1, KL.blk_b, nblk, 16, KL.tmp, &alt_b,
-                                             s));
         }
-    }
-    const uint32_t *keys = alt_b ? KL.b_k1 : KL.b_k0;
-    const uint32_t *vals = alt_b ? KL.b_v1 : KL.b_v0;
-    {
-        Stage st(ctx, GAVIS_STAGE_RANGES, s);
-        CK(cudaMemsetAsync(SL.ranges, 0, nvt * sizeof(uint2), s));
-        CK(launch_ranges(keys, (size_t)M, SL.ranges, s, nullptr, tb, (uint32_t)G.TT));
+        {
+            Stage st(ctx, GAVIS_STAGE_SORT, s);
+            if (tb < 0) {
+                CK(radix_sort_pairs<uint32_t>(KL.b_k0, KL.b_v0, KL.b_k1, KL.b_v1, (size_t)M, bits_of((uint64_t)nvt - 1),
+                                              KL.tmp, &alt_b, s));
+            } else {
+                const int gsz = 1 << gbb;
+                std::vector<uint64_t> seg((size_t)nseg_b + 1);
+                for (int g = 0; g <= nseg_b; ++g) {
+                    seg[(size_t)g] = h_eoff[g * gsz < nv ? g * gsz : nv];
+                    if (seg[(size_t)g] > M || (g > 0 && seg[(size_t)g] < seg[(size_t)g - 1]))
+                        return fail(ctx, GAVIS_ERR_CUDA, "internal: inconsistent per-view entry offsets");
+                }
+                size_t nblk = 0;
+                if ((rc = upload_blocks(seg, KL.blk_b, nblk)) != GAVIS_OK) return rc;
+                CK(radix_sort_segments<uint32_t>(KL.b_k0, KL.b_v0, KL.b_k1, KL.b_v1, KL.blk_b, nblk, 16, KL.tmp, &alt_b,
+                                                 s));
+            }
+        }
+        keys = alt_b ? KL.b_k1 : KL.b_k0;
+        vals = alt_b ? KL.b_v1 : KL.b_v0;
+        {
+            Stage st(ctx, GAVIS_STAGE_RANGES, s);
+            CK(cudaMemsetAsync(SL.ranges, 0, nvt * sizeof(uint2), s));
+            CK(launch_ranges(keys, (size_t)M, SL.ranges, s, nullptr, tb, (uint32_t)G.TT));
+        }
     }
     // The uncertainty pass takes tiles longest list first, so that its
     // persistent warps do not end on a few long lists; at tile 32 the natural
@@ -623,7 +648,10 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
         if (off < out.cap && out.keys) {
             const int64_t m = (int64_t)M < out.cap - off ? (int64_t)M : out.cap - off;
             // canonical keys; one batch, so the view index is the call's
-            CK(launch_keys_export(keys, vals, (size_t)m, RL.geo, n, G.TT, out.keys + off, s, tb));
+            if (counting)
+                CK(launch_keys_from_ranges(SL.ranges, vals, nv, G.TT, RL.geo, n, (size_t)m, out.keys + off, s));
+            else
+                CK(launch_keys_export(keys, vals, (size_t)m, RL.geo, n, G.TT, out.keys + off, s, tb));
             CK(cudaMemcpyAsync(out.vals + off, vals, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
         }
         if (out.ranges)

@@ -241,6 +241,42 @@ cudaError_t launch_ranges(const uint32_t *keys, size_t M, uint2 *ranges, cudaStr
 cudaError_t launch_keys_export(const uint32_t *keyB, const uint32_t *valB, size_t M, const GeoRec *geo, int64_t n,
                                int tiles_per_view, uint64_t *out, cudaStream_t s, int tb = -1);
 
+// ---------------------------------------------------------------- bin.cu
+// Stage B by counting (no sort of the tile entries): the lists of every
+// (view, tile) of a batch, records in stage-A order, from the rectangles of
+// the stage-A-ordered records.  Each view's records go in chunks of
+// kBinChunk to one warp, whose per-tile counters live in shared memory, so
+// views of up to kBinMaxTiles tiles take this path; larger ones the sort.
+constexpr int kBinChunk = 1024;
+constexpr int kBinMaxTiles = 2048;
+inline bool bin_by_counting(int TT) { return TT >= 1 && TT <= kBinMaxTiles; }
+struct BinLayout {
+    uint32_t *roff;        // [nv + 1] records before each view (clamped to the live records)
+    uint32_t *chunk_off;   // [nv + 1] chunks before each view
+    uint32_t *table;       // [chunks][TT] per-chunk tile counts, then their prefix over the view's chunks
+    uint32_t *tile_tot;    // [nv * TT] list lengths
+    uint32_t *tile_start;  // [nv * TT] list starts
+    void *scan_tmp;
+    size_t bytes;
+};
+// the most chunks cap_R records of nv views can make
+size_t bin_chunks_max(size_t cap_R, int nv);
+BinLayout bin_layout(void *base, size_t cap_R, int nv, int TT);
+// kernel attributes (shared memory above 48 KB); call before stream capture
+void bin_prepare();
+// recs: record indices v n + g in stage-A order, rect_sorted their
+// rectangles, voff[v] (v = 0..nv) the records before view v.  The live
+// records are min(cap_R, *d_nrec) (d_nrec optional).  Writes ranges[v TT +
+// t] and vals (the Gaussian index of every entry); entries at positions >=
+// cap_M are not written and set *overflow, and the ranges are cut off there.
+cudaError_t launch_bin_tiles(const uint32_t *recs, const uint2 *rect_sorted, const uint32_t *voff, int nv, int64_t n,
+                             int TW, int TT, size_t cap_R, const unsigned long long *d_nrec, const BinLayout &B,
+                             uint2 *ranges, uint32_t *vals, size_t cap_M, uint32_t *overflow, cudaStream_t s);
+// canonical keys ((view * TT + tile) << 32) | depth bits of the lists'
+// entries, at the entries' positions (those below cap)
+cudaError_t launch_keys_from_ranges(const uint2 *ranges, const uint32_t *vals, int nv, int TT, const GeoRec *geo,
+                                    int64_t n, size_t cap, uint64_t *out, cudaStream_t s);
+
 struct CompositeArgs {
     const uint2 *ranges;
     const uint32_t *vals;

@@ -142,14 +142,20 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     const size_t o_scan = take(scan_tmp_bytes(nwords) + 64);
     const size_t o_ak0 = take(R * 4), o_ak1 = take(R * 4), o_av0 = take(R * 4), o_av1 = take(R * 4);
     const size_t o_acnt = take(R * 4), o_aoff = take(R * 4), o_rs = take(R * 8);
-    const size_t o_bk0 = take(M * 4), o_bk1 = take(M * 4), o_bv0 = take(M * 4), o_bv1 = take(M * 4);
+    // stage B by counting (views of up to kBinMaxTiles tiles): one value
+    // array and the count tables; else keys and values of a sort
+    const bool counting = bin_by_counting(TT);
+    const size_t o_bv0 = take(M * 4);
+    const size_t o_bk0 = counting ? 0 : take(M * 4), o_bk1 = counting ? 0 : take(M * 4);
+    const size_t o_bv1 = counting ? 0 : take(M * 4);
+    const size_t o_bin = counting ? take(bin_layout(nullptr, R, B, TT).bytes) : 0;
     // segmented sorts: block tables for the largest batch, key parameters,
     // per-view record and entry offsets
-    const size_t nblk_a = radix_segment_blocks_max(R, B), nblk_b = radix_segment_blocks_max(M, B);
+    const size_t nblk_a = radix_segment_blocks_max(R, B), nblk_b = counting ? 0 : radix_segment_blocks_max(M, B);
     const size_t o_blka = take(nblk_a * sizeof(RsBlock)), o_blkb = take(nblk_b * sizeof(RsBlock));
     const size_t o_kp = take(sizeof(KeyParams));
     const size_t o_voff = take(((size_t)B + 1) * 4), o_eoff = take(((size_t)B + 1) * 4);
-    size_t big = R > M ? R : M;
+    size_t big = counting || R > M ? R : M;   // the largest sort
     if (nvt > big) big = nvt;   // the tile-order sort shares the temporary space
     const size_t seg_items = (nblk_a > nblk_b ? nblk_a : nblk_b) * (size_t)kRadixTile;
     const size_t o_tmp = take(radix_tmp_bytes(big > seg_items ? big : seg_items) + scan_tmp_bytes(big) + 64);
@@ -184,8 +190,11 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     uint32_t *av0 = reinterpret_cast<uint32_t *>(b + o_av0), *av1 = reinterpret_cast<uint32_t *>(b + o_av1);
     uint32_t *acnt = reinterpret_cast<uint32_t *>(b + o_acnt), *aoff = reinterpret_cast<uint32_t *>(b + o_aoff);
     uint2 *rect_sorted = reinterpret_cast<uint2 *>(b + o_rs);
-    uint32_t *bk0 = reinterpret_cast<uint32_t *>(b + o_bk0), *bk1 = reinterpret_cast<uint32_t *>(b + o_bk1);
-    uint32_t *bv0 = reinterpret_cast<uint32_t *>(b + o_bv0), *bv1 = reinterpret_cast<uint32_t *>(b + o_bv1);
+    uint32_t *bk0 = counting ? nullptr : reinterpret_cast<uint32_t *>(b + o_bk0);
+    uint32_t *bk1 = counting ? nullptr : reinterpret_cast<uint32_t *>(b + o_bk1);
+    uint32_t *bv0 = reinterpret_cast<uint32_t *>(b + o_bv0);
+    uint32_t *bv1 = counting ? nullptr : reinterpret_cast<uint32_t *>(b + o_bv1);
+    const BinLayout bins = counting ? bin_layout(b + o_bin, R, B, TT) : BinLayout{};
     void *tmp = b + o_tmp, *scan_tmp = b + o_scan;
     uint2 *ranges = reinterpret_cast<uint2 *>(b + o_rng);
     float *tile_sums = reinterpret_cast<float *>(b + o_ts);
@@ -223,6 +232,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
 
     // the chain of every batch, captured on a private stream
     radix_prepare();
+    bin_prepare();
     composite_prepare(p->tile);
     PK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     const long long k0 = g_launches.load();
@@ -251,28 +261,35 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
         bool alt_a = false, alt_b = false;
         PK(radix_sort_segments<uint32_t>(ak0, av0, ak1, av1, blk_a, nblk_a, 32, tmp, &alt_a, cs, true));
         const uint32_t *recs = alt_a ? av1 : av0;
-        // stage-B offsets per warp of 32 records (acnt, aoff hold the warps' counts and offsets)
-        PK(launch_gather_rects(recs, rect, R, acnt, rect_sorted, cs, &info->b.visible));
-        PK(exclusive_scan_u32(acnt, aoff, (R + 31) / 32, tmp, nullptr, cs));
-        // stage B: tile keys (view << tb) | tile sorted on 16 bits per group
-        // of 2^(16 - tb) views when the tile index fits tb <= 16 bits and the
-        // batch's views do not (as the batched call), else view * TT + tile
-        const int vb = bits_of((uint64_t)nv - 1), tbits = bits_of((uint64_t)TT - 1);
-        const int tb = tbits + vb > 16 && tbits <= 16 && ((nv - 1) >> (16 - tbits)) < 64 ? tbits : -1;
-        PK(launch_emit_tiles(recs, nullptr, R, rect, n, TW, TH, bk0, bv0, cs, &info->b.visible, M,
-                             &info->entries_over, tb, rect_sorted, aoff));
-        if (tb >= 0) {
-            PK(launch_entry_offsets_dev(aoff, rect_sorted, voff, nv, &info->b, R, M, eoff, cs));
-            PK(launch_segment_blocks(eoff, nv, nullptr, 1 << (16 - tb), M, blk_b, nblk_b, cs));
-            PK(radix_sort_segments<uint32_t>(bk0, bv0, bk1, bv1, blk_b, nblk_b, 16, tmp, &alt_b, cs, true));
+        if (counting) {   // stage B by counting, as the batched call
+            PK(launch_gather_rects(recs, rect, R, acnt, rect_sorted, cs, &info->b.visible));
+            PK(launch_bin_tiles(recs, rect_sorted, voff, nv, n, TW, TT, R, &info->b.visible, bins, ranges, bv0, M,
+                                &info->entries_over, cs));
+            ca.vals = bv0;
         } else {
-            PK(radix_sort_pairs<uint32_t>(bk0, bv0, bk1, bv1, M, bits_of((uint64_t)nvt_b - 1), tmp, &alt_b, cs,
-                                          &info->b.total));
+            // stage-B offsets per warp of 32 records (acnt, aoff hold the warps' counts and offsets)
+            PK(launch_gather_rects(recs, rect, R, acnt, rect_sorted, cs, &info->b.visible));
+            PK(exclusive_scan_u32(acnt, aoff, (R + 31) / 32, tmp, nullptr, cs));
+            // stage B: tile keys (view << tb) | tile sorted on 16 bits per group
+            // of 2^(16 - tb) views when the tile index fits tb <= 16 bits and the
+            // batch's views do not (as the batched call), else view * TT + tile
+            const int vb = bits_of((uint64_t)nv - 1), tbits = bits_of((uint64_t)TT - 1);
+            const int tb = tbits + vb > 16 && tbits <= 16 && ((nv - 1) >> (16 - tbits)) < 64 ? tbits : -1;
+            PK(launch_emit_tiles(recs, nullptr, R, rect, n, TW, TH, bk0, bv0, cs, &info->b.visible, M,
+                                 &info->entries_over, tb, rect_sorted, aoff));
+            if (tb >= 0) {
+                PK(launch_entry_offsets_dev(aoff, rect_sorted, voff, nv, &info->b, R, M, eoff, cs));
+                PK(launch_segment_blocks(eoff, nv, nullptr, 1 << (16 - tb), M, blk_b, nblk_b, cs));
+                PK(radix_sort_segments<uint32_t>(bk0, bv0, bk1, bv1, blk_b, nblk_b, 16, tmp, &alt_b, cs, true));
+            } else {
+                PK(radix_sort_pairs<uint32_t>(bk0, bv0, bk1, bv1, M, bits_of((uint64_t)nvt_b - 1), tmp, &alt_b, cs,
+                                              &info->b.total));
+            }
+            const uint32_t *keys = alt_b ? bk1 : bk0;
+            ca.vals = alt_b ? bv1 : bv0;
+            PK(cudaMemsetAsync(ranges, 0, nvt_b * sizeof(uint2), cs));
+            PK(launch_ranges(keys, M, ranges, cs, &info->b.total, tb, (uint32_t)TT));
         }
-        const uint32_t *keys = alt_b ? bk1 : bk0;
-        ca.vals = alt_b ? bv1 : bv0;
-        PK(cudaMemsetAsync(ranges, 0, nvt_b * sizeof(uint2), cs));
-        PK(launch_ranges(keys, M, ranges, cs, &info->b.total, tb, (uint32_t)TT));
         ca.order = nullptr;
         if (ordered) {   // the batched call's longest-list-first tile order
             PK(launch_order_keys(ranges, nvt_b, ok0, ov0, cs));

@@ -73,8 +73,9 @@ def test_bins_bit_exact(ctx, gv, name, tile):
 
 def test_bins_bit_exact_with_view_groups(ctx, gv):
     """600 views in one call: view bits + depth bits exceed 32 and view bits
-    + tile bits exceed 16, so both sorts run per group of views (3 groups
-    each); keys, values and ranges stay bit-exact, and scoring equals the
+    + tile bits exceed 16, so the depth sort runs per group of views (3
+    groups) and the tile lists are counted over all 600 views at once; keys,
+    values and ranges stay bit-exact, and scoring equals the
     one-view-per-batch path."""
     sc = sg.tiny_scene(2000, seed=3, sh_degree=1)
     cams = sg.fibonacci_cameras(600, 3.0, 128, 96, 60.0)
@@ -98,6 +99,27 @@ def test_bins_bit_exact_with_view_groups(ctx, gv):
     b = ctx.score_views(gs, vf, cams, params=gv.Params(tile=8, views_per_batch=1))
     for k in ("unc", "rgb", "score"):
         assert torch.equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("W,H,tile,nv", [(640, 480, 16, 3),     # 1200 tiles a view
+                                          (512, 256, 8, 3),      # 2048
+                                          (328, 400, 8, 2),      # 2050
+                                          (1280, 720, 16, 2)])   # 3600
+def test_bins_bit_exact_tile_counts(ctx, gv, W, H, tile, nv):
+    """The tile lists are built by counting when a view's tile counters fit
+    in shared memory and by the segmented 16-bit sort otherwise (more than
+    2048 tiles a view); both give the oracle's keys, values and ranges bit
+    for bit, on either side of the switch."""
+    sc = sg.tiny_scene(4000, seed=11, sh_degree=1)
+    cams = sg.fibonacci_cameras(nv, 2.6, W, H, 70.0)
+    gs = gpu_scene(gv, sc)
+    keys, vals, ranges = ctx.debug_bins(gs, cams, gv.Params(tile=tile))
+    rk, rv = oracle.bins(cams, sc, tile=tile)
+    TT = ((W + tile - 1) // tile) * ((H + tile - 1) // tile)
+    assert len(rk) > 0
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), rk)
+    assert np.array_equal(vals.cpu().numpy().view(np.uint32), rv)
+    assert np.array_equal(ranges.cpu().numpy().view(np.uint32), oracle.ranges(rk, nv * TT))
 
 
 def _edge_scene(cams, n_per, seed):

@@ -68,6 +68,21 @@ def test_plan_equals_score_views(ctx, gv, tile):
     plan.close()
 
 
+def test_plan_equals_score_views_sorted_tiles(ctx, gv):
+    """Views of more than 2048 tiles (here 96 x 88 at tile 8) take the sorted
+    tile lists in the captured chain too; replays equal gavis_score_views."""
+    c, gs, vf = setup(gv, ctx, n=20000, n_train=4, n_cand=3, train_wh=(160, 120), cand_wh=(768, 704))
+    cand = c["cand"]
+    p = gv.Params(tile=8, vf_degree=c["vf_degree"])
+    rec, cap = needed(gv, ctx, gs, vf, cand, p)
+    plan = ctx.plan(gs, vf, len(cand), 768, 704, cap, record_capacity=rec, params=p, want_rgb=True, want_unc=True)
+    plan.launch(cand)
+    torch.cuda.synchronize()
+    assert plan.overflowed() == (False, rec, cap)
+    assert_same(plan, ctx.score_views(gs, vf, cand, params=p))
+    plan.close()
+
+
 def test_plan_matches_oracle(ctx, gv):
     c = sg.config(1, n=900, n_train=3, n_cand=5, train_wh=(100, 75), cand_wh=(100, 75))
     sc, cand, L = c["scene"], c["cand"], c["vf_degree"]
