@@ -112,6 +112,11 @@ typedef struct {
     float logdet_Q0;             /* log |Q_0| of the prior colour covariance, Q_0 = I_3 -> 0 */
     int32_t tile;                /* tile edge in pixels: 8, 16 or 32 (16) */
     int32_t views_per_batch;     /* views per kernel chain: 0 = as many as the budget allows (at most 256), 1 = plain; at most 1024 are used */
+    int32_t tile_lists;          /* how each (view, tile) list of depth-ordered Gaussians is built: 0 = automatic (by
+                                    counting when the views have at most 2048 tiles and a batch at least 2^20 visible
+                                    (view, Gaussian) records, else by sorting the tile entries), 1 = by counting
+                                    whenever the views have at most 2048 tiles, 2 = by sorting; the lists, and so
+                                    every output, are the same bits either way */
 } gavis_params;
 
 typedef struct gavis_ctx gavis_ctx;
@@ -129,7 +134,7 @@ const char *gavis_last_error(const gavis_ctx *ctx);
 
 /* Fill *p with the paper's defaults (Alg. UQ inputs and the construction
  * hyperparameters): kappa 1, L 2, eps_T 1e-4, q_cut 9, beta 0.5, o0 0.15,
- * sigma_c2 0.01, logdet_Q0 0, tile 16, views_per_batch 0. */
+ * sigma_c2 0.01, logdet_Q0 0, tile 16, views_per_batch 0, tile_lists 0. */
 int gavis_params_default(gavis_params *p);
 
 /* a_l = 4 pi e^{-kappa} i_l(kappa), l = 0..L (the per-degree factor of

@@ -60,7 +60,7 @@ class gavis_vf(C.Structure):
 class gavis_params(C.Structure):
     _fields_ = [("kappa", C.c_float), ("vf_degree", C.c_int32), ("eps_T", C.c_float), ("q_cut", C.c_float),
                 ("beta", C.c_float), ("o0", C.c_float), ("sigma_c2", C.c_float), ("logdet_Q0", C.c_float),
-                ("tile", C.c_int32), ("views_per_batch", C.c_int32)]
+                ("tile", C.c_int32), ("views_per_batch", C.c_int32), ("tile_lists", C.c_int32)]
 
 
 class gavis_views_out(C.Structure):

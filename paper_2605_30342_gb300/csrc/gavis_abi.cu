@@ -194,6 +194,7 @@ int check_params(gavis_ctx *ctx, const gavis_params *p)
     if (!(p->sigma_c2 > 0.0f)) return fail(ctx, GAVIS_ERR_ARG, "sigma_c2 must be > 0");
     if (!(p->kappa >= 0.0f)) return fail(ctx, GAVIS_ERR_ARG, "kappa must be >= 0");
     if (p->views_per_batch < 0) return fail(ctx, GAVIS_ERR_ARG, "views_per_batch must be >= 0");
+    if (p->tile_lists < 0 || p->tile_lists > 2) return fail(ctx, GAVIS_ERR_ARG, "tile_lists must be 0, 1 or 2");
     return GAVIS_OK;
 }
 
@@ -518,8 +519,10 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     }
     const int nseg_b = tb < 0 ? 1 : (nv + (1 << gbb) - 1) >> gbb;
     const size_t nseg = (size_t)(nseg_a > nseg_b ? nseg_a : nseg_b);
-    // stage B by counting where a view's tile counters fit shared memory
-    const bool counting = bin_by_counting(G.TT);
+    // stage B by counting where a view's tile counters fit shared memory and
+    // (automatic choice) the batch is large enough to keep the GPU busy
+    const bool counting = bin_by_counting(G.TT) && p->tile_lists != 2 &&
+                          (p->tile_lists == 1 || nrec >= (unsigned long long)kBinMinRecords);
     const int bin_tt = counting ? G.TT : 0;
     KeyLayout KL = key_layout(nullptr, (size_t)nrec, (size_t)M, nseg, nv, bin_tt);
     if ((rc = ensure(ctx, ctx->keys, KL.bytes, s)) != GAVIS_OK) return rc;
@@ -887,6 +890,7 @@ int gavis_params_default(gavis_params *p)
     p->logdet_Q0 = 0.0f;
     p->tile = 16;
     p->views_per_batch = 0;
+    p->tile_lists = 0;
     return GAVIS_OK;
 }
 

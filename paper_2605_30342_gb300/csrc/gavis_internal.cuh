@@ -247,8 +247,12 @@ cudaError_t launch_keys_export(const uint32_t *keyB, const uint32_t *valB, size_
 // the stage-A-ordered records.  Each view's records go in chunks of
 // kBinChunk to one warp, whose per-tile counters live in shared memory, so
 // views of up to kBinMaxTiles tiles take this path; larger ones the sort.
+// A warp walks its chunk serially, so a batch needs many chunks to fill the
+// GPU: the automatic choice takes this path from kBinMinRecords visible
+// records a batch (a batch of a few thousand records a view is faster sorted).
 constexpr int kBinChunk = 1024;
 constexpr int kBinMaxTiles = 2048;
+constexpr int kBinMinRecords = 1 << 20;
 inline bool bin_by_counting(int TT) { return TT >= 1 && TT <= kBinMaxTiles; }
 struct BinLayout {
     uint32_t *roff;        // [nv + 1] records before each view (clamped to the live records)

@@ -102,6 +102,7 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     if (!gs || !vf || !p || !score || n_cams < 1 || n_cams > 16384 || W < 1 || H < 1 || W > 16384 || H > 16384 ||
         entry_capacity < 1 || record_capacity < 0 || gs->n < 1 || gs->n >= ((int64_t)1 << 31) || !gs->sh ||
         vf->n != gs->n || !(p->tile == 8 || p->tile == 16 || p->tile == 32) || p->views_per_batch < 0 ||
+        p->tile_lists < 0 || p->tile_lists > 2 ||
         ((uintptr_t)gs->rots & 15u)) {
         set_error(ctx, "gavis_plan_create: invalid argument (sizes, tile must be 8/16/32, rots 16-byte aligned)");
         return GAVIS_ERR_ARG;
@@ -144,7 +145,8 @@ int gavis_plan_create(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf 
     const size_t o_acnt = take(R * 4), o_aoff = take(R * 4), o_rs = take(R * 8);
     // stage B by counting (views of up to kBinMaxTiles tiles): one value
     // array and the count tables; else keys and values of a sort
-    const bool counting = bin_by_counting(TT);
+    const bool counting = bin_by_counting(TT) && p->tile_lists != 2 &&
+                          (p->tile_lists == 1 || R >= (size_t)kBinMinRecords);
     const size_t o_bv0 = take(M * 4);
     const size_t o_bk0 = counting ? 0 : take(M * 4), o_bk1 = counting ? 0 : take(M * 4);
     const size_t o_bv1 = counting ? 0 : take(M * 4);

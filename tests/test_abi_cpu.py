@@ -43,6 +43,7 @@ def test_params_default_are_the_paper_defaults(lib):
     assert (p.kappa, p.vf_degree, p.eps_T, p.q_cut, p.beta, p.o0) == (1.0, 2, pytest.approx(1e-4), 9.0, 0.5,
                                                                       pytest.approx(0.15))
     assert p.sigma_c2 == pytest.approx(0.01) and p.logdet_Q0 == 0.0 and p.tile == 16
+    assert p.views_per_batch == 0 and p.tile_lists == 0
 
 
 def test_host_vmf_coefficients_match_oracle(lib):

@@ -53,13 +53,14 @@ def case(name):
 
 # --------------------------------------------------------------------------- bins / keys
 
+@pytest.mark.parametrize("lists", [1, 2])   # tile lists by counting / by sorting
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("tile", [16, 8])
-def test_bins_bit_exact(ctx, gv, name, tile):
+def test_bins_bit_exact(ctx, gv, name, tile, lists):
     c = case(name)
     sc, cams = c["scene"], c["cand"]
     gs = gpu_scene(gv, sc)
-    keys, vals, ranges = ctx.debug_bins(gs, cams, gv.Params(tile=tile))
+    keys, vals, ranges = ctx.debug_bins(gs, cams, gv.Params(tile=tile, tile_lists=lists))
     rk, rv = oracle.bins(cams, sc, tile=tile)
     gk = keys.cpu().numpy().view(np.uint64)
     gvals = vals.cpu().numpy().view(np.uint32)
@@ -89,11 +90,12 @@ def test_bins_bit_exact_with_view_groups(ctx, gv):
     assert vbits + int(zb.max() - zb.min()).bit_length() > 32
     assert vbits + (TT - 1).bit_length() > 16
     gs = gpu_scene(gv, sc)
-    keys, vals, ranges = ctx.debug_bins(gs, cams, gv.Params(tile=8))
     rk, rv = oracle.bins(cams, sc, tile=8)
-    assert np.array_equal(keys.cpu().numpy().view(np.uint64), rk)
-    assert np.array_equal(vals.cpu().numpy().view(np.uint32), rv)
-    assert np.array_equal(ranges.cpu().numpy().view(np.uint32), oracle.ranges(rk, len(cams) * TT))
+    for lists in (1, 2):
+        keys, vals, ranges = ctx.debug_bins(gs, cams, gv.Params(tile=8, tile_lists=lists))
+        assert np.array_equal(keys.cpu().numpy().view(np.uint64), rk)
+        assert np.array_equal(vals.cpu().numpy().view(np.uint32), rv)
+        assert np.array_equal(ranges.cpu().numpy().view(np.uint32), oracle.ranges(rk, len(cams) * TT))
     vf = gv.VisibilityField(torch.zeros((sc.n, 9), device="cuda"), 2, 0, 1.0)
     a = ctx.score_views(gs, vf, cams, params=gv.Params(tile=8, views_per_batch=0))
     b = ctx.score_views(gs, vf, cams, params=gv.Params(tile=8, views_per_batch=1))
@@ -101,19 +103,21 @@ def test_bins_bit_exact_with_view_groups(ctx, gv):
         assert torch.equal(a[k], b[k]), k
 
 
+@pytest.mark.parametrize("lists", [0, 1, 2])
 @pytest.mark.parametrize("W,H,tile,nv", [(640, 480, 16, 3),     # 1200 tiles a view
                                           (512, 256, 8, 3),      # 2048
                                           (328, 400, 8, 2),      # 2050
                                           (1280, 720, 16, 2)])   # 3600
-def test_bins_bit_exact_tile_counts(ctx, gv, W, H, tile, nv):
+def test_bins_bit_exact_tile_counts(ctx, gv, W, H, tile, nv, lists):
     """The tile lists are built by counting when a view's tile counters fit
-    in shared memory and by the segmented 16-bit sort otherwise (more than
-    2048 tiles a view); both give the oracle's keys, values and ranges bit
-    for bit, on either side of the switch."""
+    in shared memory (and asked for, or the batch is large) and by the
+    segmented 16-bit sort otherwise (more than 2048 tiles a view, or
+    tile_lists = 2); every choice gives the oracle's keys, values and ranges
+    bit for bit, on either side of the tile-count switch."""
     sc = sg.tiny_scene(4000, seed=11, sh_degree=1)
     cams = sg.fibonacci_cameras(nv, 2.6, W, H, 70.0)
     gs = gpu_scene(gv, sc)
-    keys, vals, ranges = ctx.debug_bins(gs, cams, gv.Params(tile=tile))
+    keys, vals, ranges = ctx.debug_bins(gs, cams, gv.Params(tile=tile, tile_lists=lists))
     rk, rv = oracle.bins(cams, sc, tile=tile)
     TT = ((W + tile - 1) // tile) * ((H + tile - 1) // tile)
     assert len(rk) > 0
@@ -149,8 +153,9 @@ def _edge_scene(cams, n_per, seed):
                     sh=rng.normal(0, 0.3, (n, 1, 3)).astype(np.float32), sh_degree=0)
 
 
+@pytest.mark.parametrize("lists", [1, 2])
 @pytest.mark.parametrize("tile", [16, 8, 32])
-def test_bins_bit_exact_screen_edges(ctx, gv, tile):
+def test_bins_bit_exact_screen_edges(ctx, gv, tile, lists):
     """Footprints that just reach into, or just miss, the tile grid at every
     border, for cameras with orthonormal, uniformly scaled and sheared
     rotation matrices and wide and narrow fields of view: the bins stay
@@ -178,7 +183,7 @@ def test_bins_bit_exact_screen_edges(ctx, gv, tile):
         miss += int(np.sum(outside & (st != 1)))
     assert reach > 500 and miss > 500, (reach, miss)
     gs = gpu_scene(gv, sc)
-    keys, vals, ranges = ctx.debug_bins(gs, cams, gv.Params(tile=tile))
+    keys, vals, ranges = ctx.debug_bins(gs, cams, gv.Params(tile=tile, tile_lists=lists))
     rk, rv = oracle.bins(cams, sc, tile=tile)
     assert np.array_equal(keys.cpu().numpy().view(np.uint64), rk)
     assert np.array_equal(vals.cpu().numpy().view(np.uint32), rv)
@@ -417,6 +422,25 @@ def test_expected_depth_parity(ctx, gv, name, tile):
     assert np.abs(d).max() > 1.0   # the case exercises depths well above 1
 
 
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("tile", [16, 8, 32])
+def test_tile_list_builders_give_the_same_bits(ctx, gv, name, tile):
+    """The field and the scores from tile lists built by counting and by
+    sorting are the same bits (the lists are: test_bins_bit_exact pins both
+    to the oracle)."""
+    c = case(name)
+    gs = gpu_scene(gv, c["scene"])
+    L = c["vf_degree"]
+    out = {}
+    for lists in (1, 2):
+        p = gv.Params(tile=tile, vf_degree=L, tile_lists=lists)
+        vf = ctx.vf_build(gs, c["train"], degree=L, params=p)
+        out[lists] = (vf.coeffs, ctx.score_views(gs, vf, c["cand"], params=p))
+    assert torch.equal(out[1][0], out[2][0])
+    for k in ("score", "unc", "rgb"):
+        assert torch.equal(out[1][1][k], out[2][1][k]), k
+
+
 def test_score_batched_equals_plain(ctx, gv):
     c = case("room_small")
     g32 = oracle_gamma(c)
@@ -522,6 +546,9 @@ def test_invalid_arguments_raise(ctx, gv):
     assert e.value.code == gv.ERR_ARG
     with pytest.raises(gv.GavisError):
         ctx.score_views(gs, vf, c["cand"][:1], params=gv.Params(tile=12))
+    with pytest.raises(gv.GavisError) as e:
+        ctx.score_views(gs, vf, c["cand"][:1], params=gv.Params(tile_lists=3))
+    assert e.value.code == gv.ERR_ARG
 
 
 # --------------------------------------------------------------------------- density control

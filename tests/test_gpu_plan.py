@@ -52,11 +52,12 @@ def assert_same(plan, ref):
         assert torch.equal(plan.unc, ref["unc"])
 
 
+@pytest.mark.parametrize("lists", [1, 2])   # tile lists by counting / by sorting in the captured chain
 @pytest.mark.parametrize("tile", [16, 8, 32])
-def test_plan_equals_score_views(ctx, gv, tile):
+def test_plan_equals_score_views(ctx, gv, tile, lists):
     c, gs, vf = setup(gv, ctx, n=20000, n_train=4, n_cand=6, train_wh=(160, 120), cand_wh=(200, 136))
     cand = c["cand"]
-    p = gv.Params(tile=tile, vf_degree=c["vf_degree"])
+    p = gv.Params(tile=tile, vf_degree=c["vf_degree"], tile_lists=lists)
     rec, cap = needed(gv, ctx, gs, vf, cand, p)
     plan = ctx.plan(gs, vf, len(cand), cand[0].W, cand[0].H, cap, record_capacity=rec, params=p, want_rgb=True,
                     want_unc=True)
@@ -135,10 +136,11 @@ def test_plan_reads_scene_values_at_launch(ctx, gv):
     plan.close()
 
 
-def test_plan_flags_overflow(ctx, gv):
+@pytest.mark.parametrize("lists", [1, 2])
+def test_plan_flags_overflow(ctx, gv, lists):
     c, gs, vf = setup(gv, ctx, n=20000, n_train=4, n_cand=4, train_wh=(160, 120), cand_wh=(160, 120))
     cand = c["cand"]
-    p = gv.Params(tile=16, vf_degree=c["vf_degree"])
+    p = gv.Params(tile=16, vf_degree=c["vf_degree"], tile_lists=lists)
     rec, need = needed(gv, ctx, gs, vf, cand, p)
     few_entries = ctx.plan(gs, vf, len(cand), 160, 120, need // 3, params=p)
     few_entries.launch(cand)
