@@ -240,21 +240,50 @@ __global__ void __launch_bounds__(kBinWarps * 32) k_bin_count(const uint2 *rect_
 }
 
 // per (view, tile): the column of the view's chunks becomes its exclusive
-// prefix, in place; tile_tot = the column's sum.  A thread walks its column
-// kBinColBatch chunks at a time, all their loads in flight before the stores
-// (a store may alias a later load as far as the compiler knows).
-constexpr int kBinColBatch = 16;
-__global__ void k_bin_columns(uint32_t *table, const uint32_t *chunk_off, int TT, uint32_t *tile_tot)
+// prefix, in place; tile_tot = the column's sum.  A CTA takes 32 tiles of a
+// view (a lane each) and its kColWarps warps split the view's chunks into
+// consecutive segments: each warp sums its segment, the segment sums are
+// prefixed across the warps in shared memory, and each warp rewrites its
+// segment from its offset.  A thread keeps kBinColBatch loads in flight
+// before the stores (a store may alias a later load as far as the compiler
+// knows).
+constexpr int kColWarps = 8;
+constexpr int kBinColBatch = 8;
+__global__ void __launch_bounds__(kColWarps * 32) k_bin_columns(uint32_t *table, const uint32_t *chunk_off, int TT,
+                                                               uint32_t *tile_tot)
 {
-    const int t = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    __shared__ uint32_t s_part[kColWarps][32];
+    const int lane = (int)(threadIdx.x & 31u), warp = (int)(threadIdx.x >> 5);
+    const int t = (int)blockIdx.x * 32 + lane;
     const int v = (int)blockIdx.y;
-    if (t >= TT) return;
     const uint32_t c0 = chunk_off[v], c1 = chunk_off[v + 1];
+    const uint32_t per = (c1 - c0 + kColWarps - 1) / kColWarps;
+    const uint32_t s0 = min(c0 + (uint32_t)warp * per, c1), s1 = min(s0 + per, c1);
     const size_t st = (size_t)TT;
-    uint32_t *p = table + (size_t)c0 * st + (size_t)t;
-    uint32_t run = 0u;
-    for (uint32_t c = c0; c < c1; c += kBinColBatch, p += kBinColBatch * st) {
-        const uint32_t k = c1 - c < (uint32_t)kBinColBatch ? c1 - c : (uint32_t)kBinColBatch;
+    const bool live = t < TT;
+    uint32_t sum = 0u;
+    if (live) {
+        const uint32_t *p = table + (size_t)s0 * st + (size_t)t;
+        for (uint32_t c = s0; c < s1; c += kBinColBatch, p += kBinColBatch * st) {
+            const uint32_t k = s1 - c < (uint32_t)kBinColBatch ? s1 - c : (uint32_t)kBinColBatch;
+#pragma unroll
+            for (int i = 0; i < kBinColBatch; ++i) sum += (uint32_t)i < k ? p[i * st] : 0u;
+        }
+    }
+    s_part[warp][lane] = sum;
+    __syncthreads();
+    uint32_t run = 0u, tot = 0u;
+#pragma unroll
+    for (int w = 0; w < kColWarps; ++w) {
+        const uint32_t x = s_part[w][lane];
+        if (w < warp) run += x;
+        tot += x;
+    }
+    if (!live) return;
+    if (warp == 0) tile_tot[(size_t)v * st + (size_t)t] = tot;
+    uint32_t *p = table + (size_t)s0 * st + (size_t)t;
+    for (uint32_t c = s0; c < s1; c += kBinColBatch, p += kBinColBatch * st) {
+        const uint32_t k = s1 - c < (uint32_t)kBinColBatch ? s1 - c : (uint32_t)kBinColBatch;
         uint32_t x[kBinColBatch];
 #pragma unroll
         for (int i = 0; i < kBinColBatch; ++i) x[i] = (uint32_t)i < k ? p[i * st] : 0u;
@@ -264,7 +293,6 @@ __global__ void k_bin_columns(uint32_t *table, const uint32_t *chunk_off, int TT
             run += x[i];
         }
     }
-    tile_tot[(size_t)v * st + (size_t)t] = run;
 }
 
 // ranges of the lists, cut off at the entry capacity (entries past it are
@@ -398,7 +426,8 @@ cudaError_t launch_bin_tiles(const uint32_t *recs, const uint2 *rect_sorted, con
     k_bin_count<<<grid, kBinWarps * 32, count_smem(TW, TH), s>>>(rect_sorted, B.roff, B.chunk_off, nv, TW,
                                                                  TH, B.table);
     count_launch();
-    k_bin_columns<<<dim3(nblk((size_t)TT, 128), (unsigned)nv), 128, 0, s>>>(B.table, B.chunk_off, TT, B.tile_tot);
+    k_bin_columns<<<dim3(nblk((size_t)TT, 32), (unsigned)nv), kColWarps * 32, 0, s>>>(B.table, B.chunk_off, TT,
+                                                                                   B.tile_tot);
     count_launch();
     cudaError_t e = exclusive_scan_u32(B.tile_tot, B.tile_start, nvt, B.scan_tmp, nullptr, s);
     if (e != cudaSuccess) return e;
