@@ -403,10 +403,12 @@ def run_gavis(args):
     ctx.vf_build(gs, train, degree=L, params=prm_vf, out=vf)
     r_vf = ctx.prof_read()
     vis_vf, keys_vf, pairs_vis = r_vf["visible"], r_vf["keys"], r_vf["pairs"][1]
+    sorted_vf = r_vf["sorted_keys"]
     ctx.prof_enable(True, pairs=True)
     ctx.score_views(gs, vf, cand, params=prm_sc, out=outs, sync_best=False)
     r_sc = ctx.prof_read()
     vis_sc, keys_sc, pairs_ua = r_sc["visible"], r_sc["keys"], r_sc["pairs"][0]
+    sorted_sc = r_sc["sorted_keys"]
     ctx.prof_enable(False)
     b = torch.tensor([], dtype=cdt).element_size()
     K, Kc = (L + 1) ** 2, (sc.sh_degree + 1) ** 2
@@ -583,18 +585,40 @@ def run_gavis(args):
         # the sort stage (histogram, scan and scatter launches of both binning
         # levels): 16 B per item per 8-bit pass (key and value read once and
         # written once; histogram reads not counted), 4 passes for stage A's
-        # 32-bit record keys, 2 for stage B's 16-bit tile keys, 1 for the tile
-        # order of the scoring pass (one 8-byte item per view tile)
+        # 32-bit record keys, 2 for stage B's 16-bit tile keys where the tile
+        # lists were sorted (counted lists have no sort), 1 for the tile order
+        # of the scoring pass (one 8-byte item per view tile)
         ms, nl = st[dom]
         tiles_sc = n_cand * (-(-W // prm_sc.tile)) * (-(-H // prm_sc.tile)) if prm_sc.tile <= 16 else 0
-        sort_bytes = ((vis_vf + vis_sc) * 4 * 16 + (keys_vf + keys_sc) * 2 * 16 + tiles_sc * 16) * args.steps
+        sort_bytes = ((vis_vf + vis_sc) * 4 * 16 + (sorted_vf + sorted_sc) * 2 * 16 + tiles_sc * 16) * args.steps
         achieved = sort_bytes / (ms / 1e3) / 1e9
         hbm_pk = pk.get("hbm_gbs", 6800.0)
         roof = {"kernel": "sort", "bound": "hbm", "achieved": achieved, "peak": hbm_pk, "unit": "GB/s",
                 "frac": achieved / hbm_pk, "traffic": None,
                 "algorithmic_bytes_per_step": sort_bytes / args.steps,
                 "what": "the sort stage's device time (all its launches); 16 B per item per 8-bit pass, 4 passes "
-                        "per visible record, 2 per tile entry, 1 per scoring view tile",
+                        "per visible record, 2 per sorted tile entry, 1 per scoring view tile",
+                "avg_launch_ms": ms / max(nl, 1), "launches": nl}
+    elif dom == "project":
+        # the projection stage (the field build's geometry-only launches and
+        # the scoring launches): every Gaussian's record read once per group
+        # of 32 views (centre, scale, rotation, opacity; colour and field
+        # coefficients for scoring), one visibility bit per (view, Gaussian),
+        # and per visible record its 32 B geometry (+ 32 B appearance for
+        # scoring), 8 B rectangle and 4 B depth written
+        ms, nl = st[dom]
+        coeff = (Kc * 3 + K) * b
+        groups_vf, groups_sc = -(-len(train) // 32), -(-n_cand // 32)
+        proj_bytes = (groups_vf * sc.n * 44 + groups_sc * sc.n * (44 + coeff) + (len(train) + n_cand) * sc.n / 8
+                      + vis_vf * 44 + vis_sc * 76) * args.steps
+        achieved = proj_bytes / (ms / 1e3) / 1e9
+        hbm_pk = pk.get("hbm_gbs", 6800.0)
+        roof = {"kernel": "k_project", "bound": "hbm", "achieved": achieved, "peak": hbm_pk, "unit": "GB/s",
+                "frac": achieved / hbm_pk, "traffic": None,
+                "algorithmic_bytes_per_step": proj_bytes / args.steps,
+                "what": "the projection stage's device time (all its launches); Gaussian records read once per "
+                        "group of 32 views, a visibility bit per (view, Gaussian), 44 B (field build) or 76 B "
+                        "(scoring) written per visible record",
                 "avg_launch_ms": ms / max(nl, 1), "launches": nl}
     else:
         ms, nl = st[dom]

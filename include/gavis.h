@@ -435,8 +435,10 @@ int gavis_prof_enable(gavis_ctx *ctx, int on);
  * gavis_prof_enable, the total number of kernels this library launched in the
  * process (*total_launches, host) and the work counted (pairs[0] pairs
  * composited by the uncertainty pass, pairs[1] by the visibility pass,
- * pairs[2] tile keys sorted, pairs[3] visible (view, Gaussian) records;
- * host [4]).  Any output pointer may be NULL. */
+ * pairs[2] tile entries (one per record and tile of its rectangle),
+ * pairs[3] visible (view, Gaussian) records, pairs[4] the tile entries whose
+ * lists were built by sorting (the others were counted: gavis_params
+ * tile_lists); host [5]).  Any output pointer may be NULL. */
 int gavis_prof_read(gavis_ctx *ctx, double *ms, int64_t *launches, int64_t *total_launches, uint64_t *pairs);
 
 #ifdef __cplusplus

@@ -408,14 +408,16 @@ class Context:
         self._check(self._lib.gavis_prof_enable(self._h, (2 if pairs else 1) if on else 0))
 
     def prof_read(self):
-        """dict(stage -> (ms, launches)), total kernel launches, pairs (ua, vis)."""
+        """dict(stage -> (ms, launches)), total kernel launches, pairs (ua, vis), tile entries (keys), visible
+        records, and the tile entries whose lists were sorted (sorted_keys; the others were counted)."""
         ms = (C.c_double * len(STAGES))()
         la = (C.c_int64 * len(STAGES))()
         tot = C.c_int64(0)
-        pairs = (C.c_uint64 * 4)()
+        pairs = (C.c_uint64 * 5)()
         self._check(self._lib.gavis_prof_read(self._h, ms, la, C.byref(tot), pairs))
         return dict(stages={k: (ms[i], int(la[i])) for i, k in enumerate(STAGES)}, total_launches=int(tot.value),
-                    pairs=(int(pairs[0]), int(pairs[1])), keys=int(pairs[2]), visible=int(pairs[3]))
+                    pairs=(int(pairs[0]), int(pairs[1])), keys=int(pairs[2]), visible=int(pairs[3]),
+                    sorted_keys=int(pairs[4]))
 
     # -------------------------------------------------------------- verification hooks
     def debug_bins(self, gs: Gaussians, cams, params=None, cap=None, stream=None):

@@ -65,8 +65,9 @@ struct gavis_ctx {
     double prof_ms[GAVIS_STAGE_COUNT] = {};
     long long prof_launches[GAVIS_STAGE_COUNT] = {};
     unsigned long long *d_pairs = nullptr;   // device [2]
-    unsigned long long prof_keys = 0;        // tile keys sorted since gavis_prof_enable
+    unsigned long long prof_keys = 0;        // tile entries since gavis_prof_enable
     unsigned long long prof_visible = 0;     // visible (view, Gaussian) records since then
+    unsigned long long prof_sorted = 0;      // tile entries whose lists were built by sorting
     // end of the last call's GPU work, for ordering the next call after it
     cudaEvent_t tail = nullptr;
     cudaStream_t tail_stream = nullptr;
@@ -523,6 +524,7 @@ int run_batch(gavis_ctx *ctx, Mode mode, const gavis_gaussians *gs, const gavis_
     // (automatic choice) the batch is large enough to keep the GPU busy
     const bool counting = bin_by_counting(G.TT) && p->tile_lists != 2 &&
                           (p->tile_lists == 1 || nrec >= (unsigned long long)kBinMinRecords);
+    if (ctx->prof_on && !counting) ctx->prof_sorted += M;
     const int bin_tt = counting ? G.TT : 0;
     KeyLayout KL = key_layout(nullptr, (size_t)nrec, (size_t)M, nseg, nv, bin_tt);
     if ((rc = ensure(ctx, ctx->keys, KL.bytes, s)) != GAVIS_OK) return rc;
@@ -841,6 +843,7 @@ int gavis_prof_enable(gavis_ctx *ctx, int on)
     }
     ctx->prof_keys = 0;
     ctx->prof_visible = 0;
+    ctx->prof_sorted = 0;
     ctx->prof_on = on != 0;
     ctx->prof_pairs = on >= 2;
     return GAVIS_OK;
@@ -871,6 +874,7 @@ int gavis_prof_read(gavis_ctx *ctx, double *ms, int64_t *launches, int64_t *tota
         pairs[1] = h[1];
         pairs[2] = ctx->prof_keys;
         pairs[3] = ctx->prof_visible;
+        pairs[4] = ctx->prof_sorted;
     }
     return GAVIS_OK;
 }

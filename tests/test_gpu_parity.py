@@ -126,6 +126,28 @@ def test_bins_bit_exact_tile_counts(ctx, gv, W, H, tile, nv, lists):
     assert np.array_equal(ranges.cpu().numpy().view(np.uint32), oracle.ranges(rk, nv * TT))
 
 
+@pytest.mark.parametrize("W,H,tile,fov", [(16, 2048, 8, 3.0),     # 2 x 256 tiles
+                                          (4096, 16, 8, 90.0),    # 512 x 2
+                                          (2000, 8, 16, 80.0),    # 125 x 1
+                                          (24, 24, 16, 60.0)])    # 2 x 2, ragged
+def test_bins_bit_exact_extreme_aspect(ctx, gv, W, H, tile, fov):
+    """Tile grids one or two tiles wide or high: the counted lists' corner
+    differences sit one tile column or row apart (or at the grid's far edge),
+    and the lists still equal the oracle's; so do the sorted ones."""
+    sc = sg.tiny_scene(4000, seed=11, sh_degree=1)
+    cams = [sg.look_at_camera((0.1, 0.2, -3.0), (0, 0, 0), W, H, fov),
+            sg.look_at_camera((2.5, 0.3, 1.0), (0, 0, 0), W, H, fov)]
+    gs = gpu_scene(gv, sc)
+    rk, rv = oracle.bins(cams, sc, tile=tile)
+    TT = ((W + tile - 1) // tile) * ((H + tile - 1) // tile)
+    assert len(rk) > 0
+    for lists in (1, 2):
+        keys, vals, ranges = ctx.debug_bins(gs, cams, gv.Params(tile=tile, tile_lists=lists))
+        assert np.array_equal(keys.cpu().numpy().view(np.uint64), rk), lists
+        assert np.array_equal(vals.cpu().numpy().view(np.uint32), rv), lists
+        assert np.array_equal(ranges.cpu().numpy().view(np.uint32), oracle.ranges(rk, len(cams) * TT)), lists
+
+
 def _edge_scene(cams, n_per, seed):
     """Gaussians whose centres project near the image borders of each camera:
     up to 8 px inside to 40 px outside, at depths 0.25-8 and scales 1e-3-0.5,
@@ -439,6 +461,24 @@ def test_tile_list_builders_give_the_same_bits(ctx, gv, name, tile):
     assert torch.equal(out[1][0], out[2][0])
     for k in ("score", "unc", "rgb"):
         assert torch.equal(out[1][1][k], out[2][1][k]), k
+
+
+def test_prof_counts_sorted_tile_entries(ctx, gv):
+    """gavis_prof_read reports the tile entries whose lists were sorted: all
+    of them with tile_lists = 2, none with tile_lists = 1 (views of at most
+    2048 tiles), and the same total of entries and records either way."""
+    c = case("room_small")
+    gs = gpu_scene(gv, c["scene"])
+    L = c["vf_degree"]
+    vf = ctx.vf_build(gs, c["train"], degree=L)
+    got = {}
+    for lists in (1, 2):
+        ctx.prof_enable(True)
+        ctx.score_views(gs, vf, c["cand"], params=gv.Params(vf_degree=L, tile_lists=lists))
+        got[lists] = ctx.prof_read()
+        ctx.prof_enable(False)
+    assert got[1]["keys"] == got[2]["keys"] > 0 and got[1]["visible"] == got[2]["visible"] > 0
+    assert got[1]["sorted_keys"] == 0 and got[2]["sorted_keys"] == got[2]["keys"]
 
 
 def test_score_batched_equals_plain(ctx, gv):
