@@ -186,10 +186,10 @@ __global__ void k_bin_chunks(const uint32_t *voff, int nv, size_t nrec, const un
 // from the rectangles' corners: +1 at (x0, y0) and (x1 + 1, y1 + 1), -1 at
 // (x1 + 1, y0) and (x0, y1 + 1) in a per-warp difference array (modulo 2^32;
 // the prefix sums are the counts), then prefix sums along x (a lane per row)
-// and along y (a lane per column).  Rows are TW + 1 words apart (an odd
-// stride keeps the lanes of the row pass on different banks; column TW
-// takes the x1 + 1 = TW corners, which no tile reads), and corners on row
-// TH are left out (no tile below).
+// and along y (a lane per column).  Rows are TW + 1 words apart (column TW
+// takes the x1 + 1 = TW corners, which no tile reads; for an even TW the odd
+// stride also puts the lanes of the row pass on different banks), and
+// corners on row TH are left out (no tile below).
 __global__ void __launch_bounds__(kBinWarps * 32) k_bin_count(const uint2 *rect_sorted, const uint32_t *roff,
                                                               const uint32_t *chunk_off, int nv, int TW, int TH,
                                                               uint32_t *table)
