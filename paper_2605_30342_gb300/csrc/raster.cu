@@ -186,10 +186,40 @@ __device__ __forceinline__ uint32_t tile_index(uint32_t key, int tb, uint32_t TT
 // entries in order, lane j of a round finding its record from a ballot of the
 // records that start before the round and an OR of the window positions
 // where the others start, so the stores are coalesced.
+// q = floor(x / d) for 32-bit x and a divisor d fixed for the launch, by a
+// multiply-high and shifts (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", 1994: the unsigned case with a 33-bit
+// multiplier 2^32 + m).  The host derives m, s1, s2 from d.
+struct DivU32 {
+    uint32_t m, s1, s2;
+};
+DivU32 divu32(uint32_t d)
+{
+    uint32_t l = 0;
+    while (l < 32 && (1ull << l) < (unsigned long long)d) ++l;   // ceil(log2 d)
+    DivU32 r;
+    r.m = (uint32_t)((((1ull << l) - (unsigned long long)d) << 32) / (unsigned long long)d + 1ull);
+    r.s1 = l < 1 ? l : 1u;
+    r.s2 = l > 1 ? l - 1u : 0u;
+    return r;
+}
+__device__ __forceinline__ uint32_t div_u32(uint32_t x, DivU32 d)
+{
+    const uint32_t t = __umulhi(d.m, x);
+    return (t + ((x - t) >> d.s1)) >> d.s2;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect, int64_t n,
-                             int TW, int TH, uint32_t *keyB, uint32_t *valB, const unsigned long long *d_nrec,
-                             size_t cap_M, uint32_t *overflow, int tb, const uint2 *rect_sorted,
-                             const uint32_t *warp_off)
+                             DivU32 div_n, int TW, int TH, uint32_t *keyB, uint32_t *valB,
+                             const unsigned long long *d_nrec, size_t cap_M, uint32_t *overflow, int tb,
+                             const uint2 *rect_sorted, const uint32_t *warp_off)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = (int)(threadIdx.x & 31u);
@@ -200,7 +230,7 @@ __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, s
     uint32_t g = 0, kfirst = 0, w = 1, cnt = 0, off = 0;
     if (i < live) {
         const uint32_t r = valA[i];   // record indices are 32-bit: v = r / n in 32-bit arithmetic
-        const uint32_t v = r / (uint32_t)n;
+        const uint32_t v = div_u32(r, div_n);
         g = r - v * (uint32_t)n;
         const uint2 rc = rect_sorted ? rect_sorted[i] : rect[r];
         const uint32_t x0 = rc.x & 0xffffu, y0 = rc.y & 0xffffu;
@@ -209,7 +239,7 @@ __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, s
         kfirst = (tb < 0 ? v * (uint32_t)(TW * TH) : v << tb) + y0 * (uint32_t)TW + x0;
         off = warp_off ? warp_off[i >> 5] : off_sorted[i];
     }
-    const float rw = 1.0f / (float)w;
+    const float rw = rcp_approx((float)w);
     uint32_t inc = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -236,12 +266,13 @@ __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, s
         const uint32_t fk = __shfl_sync(0xffffffffu, kfirst, k), gk = __shfl_sync(0xffffffffu, g, k);
         const float rk = __shfl_sync(0xffffffffu, rw, k);
         if (j < total && j < room) {
-            // row and column of entry m of the rectangle: the float quotient
-            // is within one of m / wk for m < 2^22 (relative error < 2^-22),
-            // and one correction step each way makes it exact
+            // row and column of entry m of the rectangle: with the
+            // approximate reciprocal the float quotient has a relative error
+            // below 2^-21, so for m < 2^20 it is within one of m / wk, and one
+            // correction step each way makes it exact
             const uint32_t m = j - ek;
             uint32_t ty, tx;
-            if (m < (1u << 22)) {
+            if (m < (1u << 20)) {
                 ty = (uint32_t)((float)m * rk);
                 int d = (int)(m - ty * wk);
                 if (d < 0) { --ty; d += (int)wk; }
@@ -882,8 +913,9 @@ cudaError_t launch_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, 
                               const uint2 *rect_sorted, const uint32_t *warp_off)
 {
     if (nrec == 0) return cudaSuccess;
-    k_emit_tiles<<<nblk(nrec, 256), 256, 0, s>>>(valA, off_sorted, nrec, rect, n, TW, TH, keyB, valB, d_nrec, cap_M,
-                                                 overflow, tb, rect_sorted, warp_off); count_launch();
+    k_emit_tiles<<<nblk(nrec, 256), 256, 0, s>>>(valA, off_sorted, nrec, rect, n, divu32((uint32_t)n), TW, TH, keyB,
+                                                 valB, d_nrec, cap_M, overflow, tb, rect_sorted, warp_off);
+    count_launch();
     return cudaGetLastError();
 }
 
