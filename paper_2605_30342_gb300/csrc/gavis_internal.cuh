@@ -41,6 +41,29 @@ struct __align__(16) UaRec {
     float4 b;
 };
 
+// q = floor(x / d) for 32-bit x and a divisor d fixed for a launch, by a
+// multiply-high and shifts (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", 1994: the unsigned case with a 33-bit
+// multiplier 2^32 + m).  The host derives m, s1, s2 from d (d >= 1).
+struct DivU32 {
+    uint32_t m, s1, s2;
+};
+inline DivU32 divu32(uint32_t d)
+{
+    uint32_t l = 0;
+    while (l < 32 && (1ull << l) < (unsigned long long)d) ++l;   // ceil(log2 d)
+    DivU32 r;
+    r.m = (uint32_t)((((1ull << l) - (unsigned long long)d) << 32) / (unsigned long long)d + 1ull);
+    r.s1 = l < 1 ? l : 1u;
+    r.s2 = l > 1 ? l - 1u : 0u;
+    return r;
+}
+__device__ __forceinline__ uint32_t div_u32(uint32_t x, DivU32 d)
+{
+    const uint32_t t = __umulhi(d.m, x);
+    return (t + ((x - t) >> d.s1)) >> d.s2;
+}
+
 struct RasterConsts {
     float eps_T, q_cut, beta, o0;
     float k_c;   // 1/2 log|Q_c| + 3/2 log(2 pi e)
@@ -304,6 +327,8 @@ struct CompositeArgs {
     // the visibility pass adds per warp into *pairs
     uint32_t *pair_counts;
     unsigned long long *pairs;
+    // set by the uncertainty pass's launcher: division by the tiles of a view and by TW
+    DivU32 div_tiles, div_TW;
 };
 // 8 x 8 pixel blocks per tile: the uncertainty pass's work items
 __host__ __device__ constexpr int blocks_per_tile(int tile) { return (tile / 8) * (tile / 8); }

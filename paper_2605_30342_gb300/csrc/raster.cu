@@ -180,35 +180,7 @@ __device__ __forceinline__ uint32_t tile_index(uint32_t key, int tb, uint32_t TT
     return tb < 0 ? key : (key >> tb) * TT + (key & ((1u << tb) - 1u));
 }
 
-// stage B: the tiles of each record, in stage-A order.  A warp takes 32
-// consecutive records, whose entries are contiguous (from the warp's offset,
-// warp_off, or its first record's, off_sorted); its lanes write those
-// entries in order, lane j of a round finding its record from a ballot of the
-// records that start before the round and an OR of the window positions
-// where the others start, so the stores are coalesced.
-// q = floor(x / d) for 32-bit x and a divisor d fixed for the launch, by a
-// multiply-high and shifts (Granlund and Montgomery, "Division by invariant
-// integers using multiplication", 1994: the unsigned case with a 33-bit
-// multiplier 2^32 + m).  The host derives m, s1, s2 from d.
-struct DivU32 {
-    uint32_t m, s1, s2;
-};
-DivU32 divu32(uint32_t d)
-{
-    uint32_t l = 0;
-    while (l < 32 && (1ull << l) < (unsigned long long)d) ++l;   // ceil(log2 d)
-    DivU32 r;
-    r.m = (uint32_t)((((1ull << l) - (unsigned long long)d) << 32) / (unsigned long long)d + 1ull);
-    r.s1 = l < 1 ? l : 1u;
-    r.s2 = l > 1 ? l - 1u : 0u;
-    return r;
-}
-__device__ __forceinline__ uint32_t div_u32(uint32_t x, DivU32 d)
-{
-    const uint32_t t = __umulhi(d.m, x);
-    return (t + ((x - t) >> d.s1)) >> d.s2;
-}
-
+// approximate reciprocal (PTX rcp.approx)
 __device__ __forceinline__ float rcp_approx(float x)
 {
     float y;
@@ -216,6 +188,12 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
+// stage B: the tiles of each record, in stage-A order.  A warp takes 32
+// consecutive records, whose entries are contiguous (from the warp's offset,
+// warp_off, or its first record's, off_sorted); its lanes write those
+// entries in order, lane j of a round finding its record from a ballot of the
+// records that start before the round and an OR of the window positions
+// where the others start, so the stores are coalesced.
 __global__ void k_emit_tiles(const uint32_t *valA, const uint32_t *off_sorted, size_t nrec, const uint2 *rect, int64_t n,
                              DivU32 div_n, int TW, int TH, uint32_t *keyB, uint32_t *valB,
                              const unsigned long long *d_nrec, size_t cap_M, uint32_t *overflow, int tb,
@@ -412,10 +390,10 @@ __global__ void __launch_bounds__(kUaWarps * 32) k_composite_ua(CompositeArgs a)
         if (item >= items) break;
         const unsigned long long slot = item / BPT;
         const int blk = (int)(item - slot * BPT);
-        const unsigned long long bt = a.order ? (unsigned long long)a.order[slot] : slot;   // (view, tile)
-        const int vb = (int)(bt / (unsigned long long)tiles);
-        const int t = (int)(bt - (unsigned long long)vb * tiles);
-        const int tx = t % a.TW, ty = t / a.TW;
+        const uint32_t bt = a.order ? a.order[slot] : (uint32_t)slot;   // (view, tile); nv * tiles < 2^32
+        const int vb = (int)div_u32(bt, a.div_tiles);
+        const int t = (int)(bt - (uint32_t)vb * (uint32_t)tiles);
+        const int ty = (int)div_u32((uint32_t)t, a.div_TW), tx = t - ty * a.TW;
         const int wx = (blk % (TILE / 8)) * 8, wy = (blk / (TILE / 8)) * 8;
         const int i = tx * TILE + wx + (lane & 7);
         const int j0 = ty * TILE + wy + (lane >> 3);
@@ -533,8 +511,8 @@ __global__ void __launch_bounds__(kUaWarps * 32) k_composite_ua(CompositeArgs a)
         for (int o = 16; o > 0; o >>= 1) h += __shfl_down_sync(0xffffffffu, h, o);
         const uint32_t wp = PAIRS ? __reduce_add_sync(0xffffffffu, npairs) : 0u;
         if (lane == 0) {   // at the block's natural index: summed per view in (tile, block) order
-            a.tile_sums[bt * BPT + blk] = h;
-            if (PAIRS) a.pair_counts[bt * BPT + blk] = wp;
+            a.tile_sums[(size_t)bt * BPT + blk] = h;
+            if (PAIRS) a.pair_counts[(size_t)bt * BPT + blk] = wp;
         }
     }
 }
@@ -1011,12 +989,18 @@ void prepare_ua_tile()
     ua_resident_ctas<TILE, false, false, true>();
 }
 
-cudaError_t launch_composite_ua(const CompositeArgs &a, cudaStream_t s)
+cudaError_t launch_composite_ua(const CompositeArgs &a_in, cudaStream_t s)
 {
     const unsigned long long items =
-        (unsigned long long)a.nv * (unsigned long long)(a.TW * a.TH) * (unsigned long long)blocks_per_tile(a.tile);
+        (unsigned long long)a_in.nv * (unsigned long long)(a_in.TW * a_in.TH) *
+        (unsigned long long)blocks_per_tile(a_in.tile);
     if (items == 0) return cudaSuccess;
-    if (!a.work) return cudaErrorInvalidValue;
+    // (view, tile) indices are 32-bit in the kernel
+    if (!a_in.work || (unsigned long long)a_in.nv * (unsigned long long)(a_in.TW * a_in.TH) >= (1ull << 32))
+        return cudaErrorInvalidValue;
+    CompositeArgs a = a_in;
+    a.div_tiles = divu32((uint32_t)(a.TW * a.TH));
+    a.div_TW = divu32((uint32_t)a.TW);
     cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s);   // the work counter
     if (e != cudaSuccess) return e;
     switch (a.tile) {
