@@ -238,7 +238,8 @@ int gavis_augment(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf,
 /* Autotuner (no counterpart in the paper): times the chain on the sample
  * cameras with tile edges 8, 16 and 32 (one warm-up and two timed runs each,
  * CUDA events on `stream`) and writes the fastest into p->tile.  mode 0 tunes
- * gavis_score_views (vf required), mode 1 gavis_vf_build (vf ignored).
+ * gavis_score_views with colour, uncertainty and scores written (vf
+ * required), mode 1 gavis_vf_build (vf ignored).
  * Choices are cached per workload shape (mode, W x H, power-of-two buckets of
  * the Gaussian and camera counts, SH degrees) in the process, and appended to
  * the file named by the environment variable GAVIS_AUTOTUNE_CACHE when set

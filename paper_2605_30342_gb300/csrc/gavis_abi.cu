@@ -1270,15 +1270,19 @@ int gavis_autotune(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf
             return GAVIS_OK;
         }
     }
-    // scratch outputs of the trial runs
+    // scratch outputs of the trial runs: scoring trials write the uncertainty
+    // and the colour (the full output of the UQ rasterizer, whose colour path
+    // is part of the composite's cost)
     const size_t plane = (size_t)cams[0].W * cams[0].H;
     const int L = mode == 0 ? vf->degree : p->vf_degree;
     const size_t K = (size_t)(L + 1) * (L + 1);
-    const size_t bytes = mode == 0 ? align256((size_t)n_cams * 4) + (size_t)n_cams * plane * 4
+    const size_t bytes = mode == 0 ? align256((size_t)n_cams * 4) + align256((size_t)n_cams * plane * 4) +
+                                         (size_t)n_cams * plane * 12
                                    : (size_t)gs->n * K * 4;
     if ((rc = ensure(ctx, ctx->tune, bytes, s)) != GAVIS_OK) return rc;
     float *score = reinterpret_cast<float *>(ctx->tune.p);
     float *unc = reinterpret_cast<float *>(reinterpret_cast<char *>(ctx->tune.p) + align256((size_t)n_cams * 4));
+    float *rgb = reinterpret_cast<float *>(reinterpret_cast<char *>(unc) + align256((size_t)n_cams * plane * 4));
     gavis_vf tv;
     tv.n = gs->n; tv.coeffs = ctx->tune.p; tv.degree = L; tv.dtype = GAVIS_F32; tv.n_train_views = 0; tv.kappa = 0;
     cudaEvent_t e0 = take_event(ctx), e1 = take_event(ctx);
@@ -1291,7 +1295,7 @@ int gavis_autotune(gavis_ctx *ctx, const gavis_gaussians *gs, const gavis_vf *vf
         double ms_sum = 0.0;
         for (int rep = 0; rep < 3; ++rep) {   // the first run warms up the workspace
             CK(cudaEventRecord(e0, s));
-            rc = mode == 0 ? gavis_score_views(ctx, gs, vf, cams, n_cams, &q, nullptr, unc, score, nullptr, nullptr, stream)
+            rc = mode == 0 ? gavis_score_views(ctx, gs, vf, cams, n_cams, &q, rgb, unc, score, nullptr, nullptr, stream)
                            : gavis_vf_build(ctx, gs, cams, n_cams, &q, &tv, 0, stream);
             if (rc != GAVIS_OK) return rc;
             CK(cudaEventRecord(e1, s));
