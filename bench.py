@@ -551,79 +551,11 @@ def run_gavis(args):
     # ---------------- roofline of the dominant kernel ----------------
     st = prof["stages"]
     pk, pk_kind = peaks()
-    dom = max(st, key=lambda k: st[k][0])
-    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak = 2.0 * n_sm * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12   # TFLOP/s, FMA = 2 flops
-    roof = None
-    if dom in ("composite_ua", "composite_vis"):
-        # pairs of the timed steps: the instrumented step's count (the same
-        # work every step) times the steps
-        pairs = (pairs_ua if dom == "composite_ua" else pairs_vis) * args.steps
-        fpp = FLOPS_PER_PAIR_UA if dom == "composite_ua" else FLOPS_PER_PAIR_VIS
-        ms, nl = st[dom]
-        achieved = pairs * fpp / (ms / 1e3) / 1e12
-        tile = prm_sc.tile if dom == "composite_ua" else prm_vf.tile
-        prof_k = profile_for("k_" + dom, tile, args.workload)
-        roof = {"kernel": "k_" + dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak,
-                "traffic": prof_k.get("bytes_per_launch") if prof_k else None,
-                "peak_source": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
-                               f"(sm_max_mhz of {pk_kind} peaks file)",
-                "units_per_launch": pairs / max(nl, 1), "unit_name": "pixel-Gaussian pairs",
-                "flops_per_unit": fpp, "avg_launch_ms": ms / max(nl, 1), "launches": nl}
-        ipp = prof_k.get("warp_inst_per_pair") if prof_k else None
-        if ipp:
-            # the kernel is issue-bound: its ceiling is the SMs' warp-instruction
-            # issue rate divided by the instructions it issues per pair
-            peak_pairs = n_sm * ISSUE_PER_SM_CLK * sm_mhz * 1e6 / ipp
-            roof["issue"] = {"warp_inst_per_pair": ipp, "peak_pairs_per_s": peak_pairs,
-                             "achieved_pairs_per_s": pairs / (ms / 1e3),
-                             "frac": pairs / (ms / 1e3) / peak_pairs,
-                             "source": "warp instructions per pair from the ncu capture in profiles/"}
-    elif dom == "sort":
-        # the sort stage (histogram, scan and scatter launches of both binning
-        # levels): 16 B per item per 8-bit pass (key and value read once and
-        # written once; histogram reads not counted), 4 passes for stage A's
-        # 32-bit record keys, 2 for stage B's 16-bit tile keys where the tile
-        # lists were sorted (counted lists have no sort), 1 for the tile order
-        # of the scoring pass (one 8-byte item per view tile)
-        ms, nl = st[dom]
-        tiles_sc = n_cand * (-(-W // prm_sc.tile)) * (-(-H // prm_sc.tile)) if prm_sc.tile <= 16 else 0
-        sort_bytes = ((vis_vf + vis_sc) * 4 * 16 + (sorted_vf + sorted_sc) * 2 * 16 + tiles_sc * 16) * args.steps
-        achieved = sort_bytes / (ms / 1e3) / 1e9
-        hbm_pk = pk.get("hbm_gbs", 6800.0)
-        roof = {"kernel": "sort", "bound": "hbm", "achieved": achieved, "peak": hbm_pk, "unit": "GB/s",
-                "frac": achieved / hbm_pk, "traffic": None,
-                "algorithmic_bytes_per_step": sort_bytes / args.steps,
-                "what": "the sort stage's device time (all its launches); 16 B per item per 8-bit pass, 4 passes "
-                        "per visible record, 2 per sorted tile entry, 1 per scoring view tile",
-                "avg_launch_ms": ms / max(nl, 1), "launches": nl}
-    elif dom == "project":
-        # the projection stage (the field build's geometry-only launches and
-        # the scoring launches): every Gaussian's record read once per group
-        # of 32 views (centre, scale, rotation, opacity; colour and field
-        # coefficients for scoring), one visibility bit per (view, Gaussian),
-        # and per visible record its 32 B geometry (+ 32 B appearance for
-        # scoring), 8 B rectangle and 4 B depth written
-        ms, nl = st[dom]
-        coeff = (Kc * 3 + K) * b
-        groups_vf, groups_sc = -(-len(train) // 32), -(-n_cand // 32)
-        proj_bytes = (groups_vf * sc.n * 44 + groups_sc * sc.n * (44 + coeff) + (len(train) + n_cand) * sc.n / 8
-                      + vis_vf * 44 + vis_sc * 76) * args.steps
-        achieved = proj_bytes / (ms / 1e3) / 1e9
-        hbm_pk = pk.get("hbm_gbs", 6800.0)
-        roof = {"kernel": "k_project", "bound": "hbm", "achieved": achieved, "peak": hbm_pk, "unit": "GB/s",
-                "frac": achieved / hbm_pk, "traffic": None,
-                "algorithmic_bytes_per_step": proj_bytes / args.steps,
-                "what": "the projection stage's device time (all its launches); Gaussian records read once per "
-                        "group of 32 views, a visibility bit per (view, Gaussian), 44 B (field build) or 76 B "
-                        "(scoring) written per visible record",
-                "avg_launch_ms": ms / max(nl, 1), "launches": nl}
-    else:
-        ms, nl = st[dom]
-        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-                "frac": None, "traffic": None, "avg_launch_ms": ms / max(nl, 1), "launches": nl}
+    work = dict(steps=args.steps, workload=args.workload, pairs_ua=pairs_ua, pairs_vis=pairs_vis,
+                tile_sc=prm_sc.tile, tile_vf=prm_vf.tile, n_cand=n_cand, n_train=len(train), W=W, H=H,
+                vis_vf=vis_vf, vis_sc=vis_sc, sorted_vf=sorted_vf, sorted_sc=sorted_sc, n=sc.n, K=K, Kc=Kc, b=b)
+    roof = stage_roofline(st, work, pk, pk_kind, n_sm)
 
     # ---------------- storage precision against the float64 oracle ----------------
     prec = None
@@ -680,6 +612,88 @@ def run_gavis(args):
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def stage_roofline(st, w, pk, pk_kind, n_sm):
+    """Roofline of the step's dominant stage.  st: stage -> (device ms over
+    the timed steps, launches); w: the work counts of one step (pairs
+    composited, visible records, tile entries whose lists were sorted, view
+    and Gaussian counts, tiles, coefficient sizes) and the number of timed
+    steps; pk: measured peaks (hbm_gbs, sm_max_mhz).  The composites report
+    FP32 work per pair against the FP32 FMA peak (plus the issue roofline
+    when a capture of the current kernel gives its instructions per pair),
+    the sort and the projection algorithmic bytes against the HBM peak; any
+    other stage reports its time only."""
+    dom = max(st, key=lambda k: st[k][0])
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    fp32_peak = 2.0 * n_sm * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12   # TFLOP/s, FMA = 2 flops
+    hbm_pk = pk.get("hbm_gbs", 6800.0)
+    ms, nl = st[dom]
+    steps = w["steps"]
+    if dom in ("composite_ua", "composite_vis"):
+        # pairs of the timed steps: the instrumented step's count (the same
+        # work every step) times the steps
+        pairs = (w["pairs_ua"] if dom == "composite_ua" else w["pairs_vis"]) * steps
+        fpp = FLOPS_PER_PAIR_UA if dom == "composite_ua" else FLOPS_PER_PAIR_VIS
+        achieved = pairs * fpp / (ms / 1e3) / 1e12
+        tile = w["tile_sc"] if dom == "composite_ua" else w["tile_vf"]
+        prof_k = profile_for("k_" + dom, tile, w["workload"])
+        roof = {"kernel": "k_" + dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak,
+                "traffic": prof_k.get("bytes_per_launch") if prof_k else None,
+                "peak_source": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
+                               f"(sm_max_mhz of {pk_kind} peaks file)",
+                "units_per_launch": pairs / max(nl, 1), "unit_name": "pixel-Gaussian pairs",
+                "flops_per_unit": fpp, "avg_launch_ms": ms / max(nl, 1), "launches": nl}
+        ipp = prof_k.get("warp_inst_per_pair") if prof_k else None
+        if ipp:
+            # the kernel is issue-bound: its ceiling is the SMs' warp-instruction
+            # issue rate divided by the instructions it issues per pair
+            peak_pairs = n_sm * ISSUE_PER_SM_CLK * sm_mhz * 1e6 / ipp
+            roof["issue"] = {"warp_inst_per_pair": ipp, "peak_pairs_per_s": peak_pairs,
+                             "achieved_pairs_per_s": pairs / (ms / 1e3),
+                             "frac": pairs / (ms / 1e3) / peak_pairs,
+                             "source": "warp instructions per pair from the ncu capture in profiles/"}
+        return roof
+    if dom == "sort":
+        # the sort stage (histogram, scan and scatter launches of both binning
+        # levels): 16 B per item per 8-bit pass (key and value read once and
+        # written once; histogram reads not counted), 4 passes for stage A's
+        # 32-bit record keys, 2 for stage B's 16-bit tile keys where the tile
+        # lists were sorted (counted lists have no sort), 1 for the tile order
+        # of the scoring pass (one 8-byte item per view tile)
+        tiles_sc = w["n_cand"] * (-(-w["W"] // w["tile_sc"])) * (-(-w["H"] // w["tile_sc"])) \
+            if w["tile_sc"] <= 16 else 0
+        sort_bytes = ((w["vis_vf"] + w["vis_sc"]) * 4 * 16 + (w["sorted_vf"] + w["sorted_sc"]) * 2 * 16
+                      + tiles_sc * 16) * steps
+        achieved = sort_bytes / (ms / 1e3) / 1e9
+        return {"kernel": "sort", "bound": "hbm", "achieved": achieved, "peak": hbm_pk, "unit": "GB/s",
+                "frac": achieved / hbm_pk, "traffic": None,
+                "algorithmic_bytes_per_step": sort_bytes / steps,
+                "what": "the sort stage's device time (all its launches); 16 B per item per 8-bit pass, 4 passes "
+                        "per visible record, 2 per sorted tile entry, 1 per scoring view tile",
+                "avg_launch_ms": ms / max(nl, 1), "launches": nl}
+    if dom == "project":
+        # the projection stage (the field build's geometry-only launches and
+        # the scoring launches): every Gaussian's record read once per group
+        # of 32 views (centre, scale, rotation, opacity; colour and field
+        # coefficients for scoring), one visibility bit per (view, Gaussian),
+        # and per visible record its 32 B geometry (+ 32 B appearance for
+        # scoring), 8 B rectangle and 4 B depth written
+        coeff = (w["Kc"] * 3 + w["K"]) * w["b"]
+        groups_vf, groups_sc = -(-w["n_train"] // 32), -(-w["n_cand"] // 32)
+        proj_bytes = (groups_vf * w["n"] * 44 + groups_sc * w["n"] * (44 + coeff)
+                      + (w["n_train"] + w["n_cand"]) * w["n"] / 8 + w["vis_vf"] * 44 + w["vis_sc"] * 76) * steps
+        achieved = proj_bytes / (ms / 1e3) / 1e9
+        return {"kernel": "k_project", "bound": "hbm", "achieved": achieved, "peak": hbm_pk, "unit": "GB/s",
+                "frac": achieved / hbm_pk, "traffic": None,
+                "algorithmic_bytes_per_step": proj_bytes / steps,
+                "what": "the projection stage's device time (all its launches); Gaussian records read once per "
+                        "group of 32 views, a visibility bit per (view, Gaussian), 44 B (field build) or 76 B "
+                        "(scoring) written per visible record",
+                "avg_launch_ms": ms / max(nl, 1), "launches": nl}
+    return {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+            "frac": None, "traffic": None, "avg_launch_ms": ms / max(nl, 1), "launches": nl}
 
 
 def make_plan(gv, ctx, gs, vf, cand, recs, W, H, prm_sc, visible, keys):

@@ -55,3 +55,52 @@ def test_kernel_sha_follows_the_definition(bench, tmp_path):
     inside.write_text(src[:j + 1] + "\n    // changed\n" + src[j + 1:])
     assert bench.kernel_source_sha(str(inside), "k_composite_vis") != base
     assert bench.kernel_source_sha(RASTER, "k_no_such_kernel") is None
+
+
+def _work(**kw):
+    w = dict(steps=5, workload=3, pairs_ua=2.8e9, pairs_vis=6.29e9, tile_sc=16, tile_vf=16, n_cand=256, n_train=200,
+             W=640, H=480, vis_vf=37_450_361, vis_sc=59_298_525, sorted_vf=200_000_000, sorted_sc=0, n=1_000_000,
+             K=16, Kc=16, b=2)
+    w.update(kw)
+    return w
+
+
+def _stages(dom, ms=10.0):
+    st = {k: (1.0, 5) for k in ("project", "scan", "emit", "sort", "ranges", "composite_ua", "composite_vis",
+                                 "reduce", "vf_accum")}
+    st[dom] = (ms, 5)
+    return st
+
+
+PEAKS = {"hbm_gbs": 6691.1, "sm_max_mhz": 2070.0}
+
+
+def test_roofline_of_each_dominant_stage(bench):
+    """Every stage the step can be dominated by gets a roofline whose
+    fraction is its achieved rate over the peak, from the stated per-unit
+    counts; the sort counts stage-B passes only for the sorted tile entries."""
+    w = _work()
+    fp32 = 2.0 * 152 * bench.FP32_LANES_PER_SM * 2070.0 * 1e6 / 1e12
+    for dom, fpp, pairs in (("composite_vis", bench.FLOPS_PER_PAIR_VIS, w["pairs_vis"]),
+                            ("composite_ua", bench.FLOPS_PER_PAIR_UA, w["pairs_ua"])):
+        r = bench.stage_roofline(_stages(dom, 50.0), w, PEAKS, "measured", 152)
+        assert r["kernel"] == "k_" + dom and r["bound"] == "alu" and r["peak"] == pytest.approx(fp32)
+        assert r["achieved"] == pytest.approx(pairs * w["steps"] * fpp / 0.05 / 1e12)
+        assert r["frac"] == pytest.approx(r["achieved"] / fp32)
+    r = bench.stage_roofline(_stages("sort", 25.0), w, PEAKS, "measured", 152)
+    tiles_sc = 256 * 40 * 30
+    per_step = (w["vis_vf"] + w["vis_sc"]) * 64 + w["sorted_vf"] * 32 + tiles_sc * 16
+    assert r["kernel"] == "sort" and r["algorithmic_bytes_per_step"] == pytest.approx(per_step)
+    assert r["frac"] == pytest.approx(per_step * 5 / 0.025 / 1e9 / 6691.1)
+    # counted tile lists add no stage-B sort bytes
+    r2 = bench.stage_roofline(_stages("sort", 25.0), _work(sorted_vf=0), PEAKS, "measured", 152)
+    assert r2["algorithmic_bytes_per_step"] == pytest.approx(per_step - w["sorted_vf"] * 32)
+    r = bench.stage_roofline(_stages("project", 20.0), w, PEAKS, "measured", 152)
+    coeff = (16 * 3 + 16) * 2
+    per_step = (7 * 1e6 * 44 + 8 * 1e6 * (44 + coeff) + 456 * 1e6 / 8 + w["vis_vf"] * 44 + w["vis_sc"] * 76)
+    assert r["kernel"] == "k_project" and r["bound"] == "hbm"
+    assert r["algorithmic_bytes_per_step"] == pytest.approx(per_step)
+    assert r["frac"] == pytest.approx(per_step * 5 / 0.020 / 1e9 / 6691.1)
+    # a stage without a model reports its time and no fraction
+    r = bench.stage_roofline(_stages("emit", 30.0), w, PEAKS, "measured", 152)
+    assert r["kernel"] == "emit" and r["frac"] is None and r["avg_launch_ms"] == pytest.approx(6.0)
